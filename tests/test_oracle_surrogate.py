@@ -1,0 +1,135 @@
+"""Pins of the oracle's MLP (forward, backward, Adam) and surrogate post-processing."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from oracle import surrogate as sur
+from synth.states import PATM
+
+from helpers import random_states
+
+
+def test_bf16_rounding_known_values():
+    x = np.array([1.0, 1.00390625, 1.01171875, 1.0078125 + 2 ** -8 + 2 ** -20, -2.5, 3.14159265, 0.0,
+                  65504.0, 1e-40])
+    want = np.array([1.0, 1.0, 1.015625, 1.015625, -2.5, 3.140625, 0.0, 65536.0, 0.0])
+    got = mlp.bf16_round(x)
+    assert np.array_equal(got[:8], want[:8])
+    assert abs(got[8]) < 1e-38
+
+
+def test_gelu_closed_forms():
+    x = np.linspace(-6, 6, 101)
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    assert np.allclose(mlp.gelu(x) - mlp.gelu(-x), x, atol=1e-15, rtol=0)
+    assert mlp.gelu(np.array([40.0]))[0] == 40.0
+    assert mlp.gelu_grad(np.array([0.0]))[0] == 0.5
+    h = 1e-6
+    fd = (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_grad(x), fd, atol=1e-8)
+
+
+def _net(rng, dims):
+    Ws = [rng.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i]) for i in range(len(dims) - 1)]
+    bs = [0.1 * rng.standard_normal(dims[i + 1]) for i in range(len(dims) - 1)]
+    return Ws, bs
+
+
+def test_forward_and_backward_match_torch_autograd():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    dims = [11, 16, 16, 16, 9]
+    Ws, bs = _net(rng, dims)
+    x = rng.standard_normal((7, 11))
+    t = rng.standard_normal((7, 9))
+    out, cache = mlp.forward(Ws, bs, x, emulate_bf16=False)
+    dW, db = mlp.backward(Ws, bs, cache, out, t)
+    Wt = [torch.tensor(W, requires_grad=True) for W in Ws]
+    bt = [torch.tensor(b, requires_grad=True) for b in bs]
+    a = torch.tensor(x)
+    for l in range(len(Ws)):
+        a = a @ Wt[l].T + bt[l]
+        if l < len(Ws) - 1:
+            a = torch.nn.functional.gelu(a, approximate="none")
+    loss = ((a - torch.tensor(t)) ** 2).mean()
+    loss.backward()
+    assert np.allclose(out, a.detach().numpy(), rtol=1e-13, atol=1e-13)
+    for l in range(len(Ws)):
+        assert np.allclose(dW[l], Wt[l].grad.numpy(), rtol=1e-11, atol=1e-14)
+        assert np.allclose(db[l], bt[l].grad.numpy(), rtol=1e-11, atol=1e-14)
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    Ws, bs = _net(rng, [3, 5, 4, 2])
+    x = rng.standard_normal((6, 3))
+    t = rng.standard_normal((6, 2))
+    out, cache = mlp.forward(Ws, bs, x, emulate_bf16=False)
+    dW, db = mlp.backward(Ws, bs, cache, out, t)
+    h = 1e-6
+    for l in range(3):
+        for idx in [(0, 0), (1, 2), (Ws[l].shape[0] - 1, Ws[l].shape[1] - 1)]:
+            Wp = [W.copy() for W in Ws]; Wp[l][idx] += h
+            Wm = [W.copy() for W in Ws]; Wm[l][idx] -= h
+            lp = mlp.mse_loss(mlp.forward(Wp, bs, x, False)[0], t)
+            lm = mlp.mse_loss(mlp.forward(Wm, bs, x, False)[0], t)
+            assert abs(dW[l][idx] - (lp - lm) / (2 * h)) < 1e-7
+
+
+def test_adam_first_step_is_signed_lr():
+    p = [np.array([1.0, -2.0, 3.0])]
+    g = [np.array([0.5, -1e-3, 2.0])]
+    m = [np.zeros(3)]; v = [np.zeros(3)]
+    p1, _, _ = mlp.adam_step([p[0].copy()], g, m, v, 1, lr=1e-2, eps=0.0)
+    assert np.allclose(p1[0] - p[0], -1e-2 * np.sign(g[0]), rtol=1e-12)
+
+
+def test_boxcox_roundtrip_and_log_limit():
+    y = np.logspace(-30, 0, 61)
+    assert np.allclose(sur.boxcox_inv(sur.boxcox(y)), y, rtol=1e-9, atol=0)
+    assert np.allclose(sur.boxcox(y, lam=1e-9), np.log(y), rtol=1e-6)
+    assert sur.boxcox(np.array([-1e-3]))[0] == -1.0 / sur.LAMBDA
+    assert sur.boxcox_inv(np.array([-20.0]))[0] == 0.0
+
+
+def test_projection_conserves_and_is_weighted_least_squares(h2, om_h2):
+    T, p, Y = random_states(h2, 5, 3, "H2")
+    rng = np.random.default_rng(0)
+    A = sur.element_mass_matrix(h2)
+    assert np.allclose(A.sum(axis=0), 1.0, rtol=1e-14)
+    for i in range(T.size):
+        Y0 = Y[:, i]
+        Yp = Y0 * (1.0 + 0.02 * rng.standard_normal(Y0.size))
+        Ypp, ok = sur.project(h2, Y0, Yp)
+        assert ok
+        assert np.max(np.abs(A @ Ypp - A @ Y0)) < 1e-13
+        # KKT: D^{-1} (Y'' - Y') lies in the row space of A
+        D = Yp + 1e-12
+        r = (Ypp - Yp) / D
+        lam, *_ = np.linalg.lstsq(A.T, r, rcond=None)
+        assert np.max(np.abs(A.T @ lam - r)) < 1e-9 * max(1.0, np.max(np.abs(r)))
+        Yq, ok = sur.project(h2, Y0, Y0)
+        assert ok and np.max(np.abs(Yq - Y0)) < 1e-15
+
+
+def test_temperature_from_enthalpy(h2, om_h2):
+    T, p, Y = random_states(h2, 4, 8, "H2", Tlo=300.0, Thi=2500.0)
+    for i in range(T.size):
+        h0 = om_h2.enthalpy_mass(T[i], Y[:, i])
+        Tn, ok = sur.temperature_from_enthalpy(om_h2, h0, Y[:, i], 1000.0)
+        assert ok and abs(Tn - T[i]) < 1e-8 * T[i]
+
+
+def test_heat_release_matches_energy_equation(h2, om_h2):
+    """For a tiny step, -rho sum h_k dY_k/(W_k dt) equals rho cp dT/dt."""
+    T, p, Y = random_states(h2, 4, 9, "H2")
+    for i in range(T.size):
+        y0 = np.r_[T[i], Y[:, i]]
+        qs = []
+        for dt in (2e-14, 1e-14):      # Richardson: remove the O(dt) truncation of the quotient
+            y1, st, _, _ = om_h2.rodas4(p[i], y0, dt, 1e-12, 1e-22)
+            qs.append(sur.heat_release(om_h2, T[i], p[i], Y[:, i], y1[1:], dt))
+        q = 2.0 * qs[1] - qs[0]
+        f = om_h2.rhs(p[i], y0)
+        q_ref = om_h2.density(T[i], p[i], Y[:, i]) * om_h2.cp_mass(T[i], Y[:, i]) * f[0]
+        assert abs(q - q_ref) <= 1e-5 * abs(q_ref)
