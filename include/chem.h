@@ -1,0 +1,140 @@
+/*
+ * chem.h -- C ABI of the GB300 per-cell chemistry library (libchem.so).
+ *
+ * The hot path of the reactive-flow framework of the paper: advancing every cell's
+ * constant-pressure reactor over one CFD time step (§2: finite-rate chemistry, integrated on the
+ * CPU with CVODE in the paper; §3.1: the chemistry step of the GPU solver's time loop), an MLP
+ * surrogate of that step (§2, §3.1: DNN inference on the GPU), and a serving loop that batches
+ * chemistry requests from many flow solvers.
+ *
+ * Conventions (every entry point):
+ *   - Return CHEM_OK (0) on success, a negative CHEM_E* code on failure; chem_last_error()
+ *     returns a thread-local message describing the last failure.  No C++ exception crosses
+ *     this boundary.
+ *   - State arrays are DEVICE pointers owned by the caller, FP64, species-major SoA:
+ *       T[ncells], p[ncells] (dyn/cm^2), Y[k * ld + i] for species k and cell i, ld >= ncells.
+ *     Units are CHEMKIN cgs (K, dyn/cm^2, s).
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream) and runs asynchronously; pointers must stay valid until the stream reaches it.
+ *     Per-cell outcomes are written to the optional status array (CHEM_CELL_* codes).
+ *   - The library owns the device copies of mechanisms and models, and draws per-call
+ *     temporaries from the CUDA stream-ordered allocator (cudaMallocAsync / cudaFreeAsync on
+ *     `stream`), the allocation strategy of §3.2.
+ */
+#ifndef CHEM_H
+#define CHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CHEM_OK = 0,
+  CHEM_WCELLS = 1,      /* some cells finished with a non-OK status (synchronous calls only) */
+  CHEM_EINVAL = -1,     /* invalid argument */
+  CHEM_ENOMEM = -2,     /* device or host allocation failed */
+  CHEM_ECUDA = -3,      /* a CUDA runtime call failed */
+  CHEM_EBUSY = -4,      /* request can never be admitted (larger than the memory budget) */
+  CHEM_ETIMEOUT = -5,   /* a wait ran out of time */
+  CHEM_ENOTFOUND = -6   /* unknown handle or id */
+};
+
+/* per-cell status written by the integrator */
+enum {
+  CHEM_CELL_OK = 0,
+  CHEM_CELL_MAX_STEPS = 1,    /* step-attempt limit reached; last accepted state kept */
+  CHEM_CELL_H_UNDERFLOW = 2,  /* step size fell below 1e-12 dt; last accepted state kept */
+  CHEM_CELL_NONFINITE = 3,    /* non-finite input (or T <= 0, p <= 0); cell left unchanged */
+  CHEM_CELL_SINGULAR_LU = 4   /* exactly zero pivot in the iteration matrix */
+};
+
+typedef void* chem_stream_t;                 /* cudaStream_t */
+typedef struct chem_mech_s* chem_mech_t;
+typedef struct chem_model_s* chem_model_t;
+typedef struct chem_server_s* chem_server_t;
+
+/* ---------------------------------------------------------------------------------------
+ * Mechanisms (NASA-7 thermo, Arrhenius / third-body / Troe kinetics; §2 names Cantera as the
+ * source of these models).
+ * ------------------------------------------------------------------------------------- */
+
+/* Host-side description of a mechanism.  All arrays are host pointers, row-major, read during
+ * the call only.  Reactions list up to three species per side (-1 padded; a species appearing
+ * twice is listed twice).  rtype: 0 plain, 1 third-body, 2 Troe fall-off.  Ea and Ea0 in
+ * cal/mol, A in cgs units.  troe[j] = (A0, b0, Ea0, a, T3, T1, T2), has_t2[j] selects the T2
+ * term.  eff[j * ns + k] is the collision efficiency of species k in reaction j (types 1, 2). */
+typedef struct chem_mech_desc {
+  int32_t n_species, n_elements, n_reactions;
+  const double* elem_mass;   /* [ne]  g/mol */
+  const int32_t* comp;       /* [ns * ne] atoms of each element in each species */
+  const double* nasa_lo;     /* [ns * 7] coefficients for T < 1000 K */
+  const double* nasa_hi;     /* [ns * 7] coefficients for T >= 1000 K */
+  const int32_t* rtype;      /* [nr] */
+  const int32_t* reac;       /* [nr * 3] */
+  const int32_t* prod;       /* [nr * 3] */
+  const double* A;           /* [nr] */
+  const double* b;           /* [nr] */
+  const double* Ea;          /* [nr] */
+  const double* troe;        /* [nr * 7] */
+  const int32_t* has_t2;     /* [nr] */
+  const double* eff;         /* [nr * ns] */
+} chem_mech_desc;
+
+/* Parse a CHEMMECH text file (format written by synth.mechanism.Mechanism.to_text) and upload
+ * it to the current device.  *out receives a handle owned by the caller (chem_free_mechanism). */
+int chem_load_mechanism(const char* path, chem_mech_t* out);
+/* Same from an in-memory description. */
+int chem_load_mechanism_desc(const chem_mech_desc* desc, chem_mech_t* out);
+int chem_free_mechanism(chem_mech_t m);
+int chem_mechanism_info(chem_mech_t m, int* n_species, int* n_reactions, int* n_elements);
+
+/* ---------------------------------------------------------------------------------------
+ * FP64 integrator: each cell is an adiabatic constant-pressure reactor, dY_k/dt =
+ * W_k wdot_k / rho, dT/dt = -sum_k h_k wdot_k / (rho cp), advanced over [0, dt] with the
+ * L-stable Rosenbrock method Rodas4 (Hairer & Wanner §IV.7), an analytic Jacobian and a dense
+ * LU with partial pivoting per sub-step; adaptive sub-steps from h0 = dt with the weighted RMS
+ * error norm sc_i = atol + rtol max(|y_i|, |y_new_i|) over (T, Y).
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct chem_options {
+  int32_t max_steps;      /* step attempts per cell before CHEM_CELL_MAX_STEPS; 0 -> 100000 */
+  int32_t group_threads;  /* threads per cell: 0 auto (32 if ns+1 <= 16 else 128), 32, 64, 128, 256 */
+  int32_t groups_per_cta; /* 0 auto */
+  int32_t max_ctas;       /* 0 auto (SM count x resident CTAs per SM) */
+} chem_options;
+
+/* Advance ncells cells in place over dt.  ld = ncells.  Asynchronous on stream.
+ * CHEM_EINVAL if ncells < 0, dt <= 0, rtol <= 0, atol <= 0 or a required pointer is NULL;
+ * ncells == 0 is a no-op. */
+int chem_advance(chem_mech_t m, double* T, const double* p, double* Y, double dt,
+                 int64_t ncells, double rtol, double atol, chem_stream_t stream);
+
+/* Extended form.  idx (device, nullable): advance only cells idx[0..ncells) of arrays whose
+ * leading dimension is ld (indexed mode, used for surrogate fallback); otherwise cells
+ * [0, ncells).  status (int8), nsub (accepted sub-steps), nrej (rejected attempts): device
+ * arrays indexed like the cells they describe (by idx[c] in indexed mode), each nullable.
+ * opt nullable (defaults). */
+int chem_advance_ex(chem_mech_t m, double* T, const double* p, double* Y, int64_t ld,
+                    double dt, int64_t ncells, double rtol, double atol, const int32_t* idx,
+                    int8_t* status, int32_t* nsub, int32_t* nrej, const chem_options* opt,
+                    chem_stream_t stream);
+
+/* Right-hand side f[i * ld + c] (i = 0 is dT/dt, i = 1 + k is dY_k/dt) and, if J is non-NULL,
+ * the analytic Jacobian J[(i * N + j) * ld + c] = df_i/dy_j (N = ns + 1) of every cell, computed
+ * by the same device code the integrator uses.  Device pointers; asynchronous. */
+int chem_eval_rhs_jac(chem_mech_t m, const double* T, const double* p, const double* Y,
+                      int64_t ld, int64_t ncells, double* f, double* J, chem_stream_t stream);
+
+/* Measured FP64 FMA throughput of the current device (TFLOP/s, 2 flops per FMA) from a
+ * register-resident FMA chain kernel; synchronous. */
+int chem_fp64_fma_peak(double* tflops);
+
+const char* chem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEM_H */

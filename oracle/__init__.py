@@ -58,6 +58,7 @@ def lib():
         L.or_rodas4.argtypes = [P, d, P, d, d, d, i, P, P]
         L.or_rodas4.restype = i
         L.or_advance.argtypes = [P, i64, P, P, P, i64, d, d, d, P, P, i]
+        L.or_advance_dt.argtypes = [P, i64, P, P, P, i64, P, d, d, P, i]
         L.or_rk4.argtypes = [P, d, P, d, i64]
         L.or_rodas4_tableau.argtypes = [P, P, P, P, P]
         L.or_rodas4_linear.argtypes = [i, P, P, d, i, P]
@@ -150,6 +151,18 @@ class OracleMech:
         lib().or_advance(self.h, n, _p(T), _p(p), _p(Y), n, float(dt), float(rtol), float(atol),
                          _p(st), _p(nsub), int(nthreads))
         return T, Y, st, nsub
+
+    def advance_dt(self, T, p, Y, dt, rtol=1e-6, atol=1e-10, nthreads=0):
+        """Batch advance with a per-cell step length dt [n]."""
+        T = np.array(T, np.float64)
+        p = np.ascontiguousarray(p, np.float64)
+        Y = np.array(Y, np.float64, order="C")
+        dt = np.ascontiguousarray(dt, np.float64)
+        n = T.shape[0]
+        st = np.zeros(n, np.int8)
+        lib().or_advance_dt(self.h, n, _p(T), _p(p), _p(Y), n, _p(dt), float(rtol), float(atol),
+                            _p(st), int(nthreads))
+        return T, Y, st
 
     def rk4(self, p, y, dt, nsteps):
         y = np.array(y, np.float64)

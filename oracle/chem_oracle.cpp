@@ -655,6 +655,26 @@ void or_advance(const or_mech* m, int64_t n, double* T, const double* p, double*
   }
 }
 
+void or_advance_dt(const or_mech* m, int64_t n, double* T, const double* p, double* Y, int64_t ld,
+                   const double* dt, double rtol, double atol, int8_t* status, int nthreads) {
+  const int ns = m->ns, N = ns + 1;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> y(N);
+    y[0] = T[i];
+    for (int k = 0; k < ns; ++k) y[k + 1] = Y[(size_t)k * ld + i];
+    int st = or_rodas4(m, p[i], y.data(), dt[i], rtol, atol, 100000, nullptr, nullptr);
+    if (st != OR_NONFINITE) {
+      T[i] = y[0];
+      for (int k = 0; k < ns; ++k) Y[(size_t)k * ld + i] = y[k + 1];
+    }
+    if (status) status[i] = (int8_t)st;
+  }
+}
+
 void or_rk4(const or_mech* m, double p, double* y, double dt, int64_t nsteps) {
   const int N = m->ns + 1;
   std::vector<double> k1(N), k2(N), k3(N), k4(N), yt(N);

@@ -48,6 +48,9 @@ int or_rodas4(const or_mech* m, double p, double* y, double dt, double rtol, dou
 /* Batch over cells with OpenMP.  Y is species-major: Y[k*ld + i].  status/nsub may be NULL. */
 void or_advance(const or_mech* m, int64_t n, double* T, const double* p, double* Y, int64_t ld,
                 double dt, double rtol, double atol, int8_t* status, int32_t* nsub, int nthreads);
+/* Same with a per-cell step length dt[n] (status may be NULL). */
+void or_advance_dt(const or_mech* m, int64_t n, double* T, const double* p, double* Y, int64_t ld,
+                   const double* dt, double rtol, double atol, int8_t* status, int nthreads);
 /* Classical RK4 with nsteps equal steps over dt (brute-force reference). */
 void or_rk4(const or_mech* m, double p, double* y, double dt, int64_t nsteps);
 

@@ -1,0 +1,119 @@
+"""GB300-native per-cell chemistry: FP64 Rodas4 integrator, BF16 MLP surrogate, serving loop.
+
+Python entry points mirror the C ABI in include/chem.h one to one; they only marshal torch
+tensors (device memory and streams) into pointers.  All arithmetic runs in libchem.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (CELL_H_UNDERFLOW, CELL_MAX_STEPS, CELL_NONFINITE, CELL_OK,  # noqa: F401
+                   CELL_SINGULAR_LU, ChemError, check)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _require(t, dtype, name):
+    import torch
+    if t is None:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Mechanism:
+    """A mechanism uploaded to the current device (chem_load_mechanism[_desc])."""
+
+    def __init__(self, mech=None, path=None):
+        L = _lib.load()
+        h = ctypes.c_void_p()
+        if path is not None:
+            check(L.chem_load_mechanism(path.encode(), ctypes.byref(h)))
+        else:
+            self._keep = [np.ascontiguousarray(a, dtype=t) for a, t in (
+                (mech.elem_mass, np.float64), (mech.comp, np.int32), (mech.nasa_lo, np.float64),
+                (mech.nasa_hi, np.float64), (mech.rtype, np.int32), (mech.reac, np.int32),
+                (mech.prod, np.int32), (mech.A, np.float64), (mech.b, np.float64),
+                (mech.Ea, np.float64), (mech.troe, np.float64), (mech.has_t2, np.int32),
+                (mech.eff, np.float64))]
+            d = _lib.MechDesc(mech.ns, mech.ne, mech.nr,
+                              *[a.ctypes.data_as(ctypes.c_void_p) for a in self._keep])
+            check(L.chem_load_mechanism_desc(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        ns, nr, ne = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(L.chem_mechanism_info(h, ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(ne)))
+        self.ns, self.nr, self.ne = ns.value, nr.value, ne.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().chem_free_mechanism(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def options(max_steps=0, group_threads=0, groups_per_cta=0, max_ctas=0):
+    return _lib.Options(max_steps, group_threads, groups_per_cta, max_ctas)
+
+
+def advance(mech, T, p, Y, dt, rtol=1e-6, atol=1e-10, idx=None, status=None, nsub=None,
+            nrej=None, opts=None, stream=None, ncells=None):
+    """chem_advance_ex: advance cells in place.  Y is [ns, ld] (species-major)."""
+    import torch
+    _require(T, torch.float64, "T"); _require(p, torch.float64, "p"); _require(Y, torch.float64, "Y")
+    _require(idx, torch.int32, "idx"); _require(status, torch.int8, "status")
+    _require(nsub, torch.int32, "nsub"); _require(nrej, torch.int32, "nrej")
+    ld = Y.shape[1]
+    if ncells is None:
+        ncells = idx.numel() if idx is not None else T.numel()
+    return check(_lib.load().chem_advance_ex(
+        mech.handle, _ptr(T), _ptr(p), _ptr(Y), ld, float(dt), int(ncells), float(rtol),
+        float(atol), _ptr(idx), _ptr(status), _ptr(nsub), _ptr(nrej),
+        ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)))
+
+
+def advance_simple(mech, T, p, Y, dt, rtol=1e-6, atol=1e-10, stream=None):
+    """chem_advance: ld = ncells = T.numel()."""
+    import torch
+    _require(T, torch.float64, "T"); _require(p, torch.float64, "p"); _require(Y, torch.float64, "Y")
+    return check(_lib.load().chem_advance(mech.handle, _ptr(T), _ptr(p), _ptr(Y), float(dt),
+                                          T.numel(), float(rtol), float(atol), _stream_ptr(stream)))
+
+
+def eval_rhs_jac(mech, T, p, Y, with_jacobian=True, stream=None):
+    """chem_eval_rhs_jac: returns f [N, n] and J [N*N, n] (or None)."""
+    import torch
+    n = T.numel()
+    N = mech.ns + 1
+    f = torch.empty((N, n), dtype=torch.float64, device=T.device)
+    J = torch.empty((N * N, n), dtype=torch.float64, device=T.device) if with_jacobian else None
+    check(_lib.load().chem_eval_rhs_jac(mech.handle, _ptr(T), _ptr(p), _ptr(Y), Y.shape[1], n,
+                                        _ptr(f), _ptr(J), _stream_ptr(stream)))
+    return f, J
+
+
+def fp64_fma_peak():
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s."""
+    v = ctypes.c_double()
+    check(_lib.load().chem_fp64_fma_peak(ctypes.byref(v)))
+    return v.value

@@ -1,0 +1,89 @@
+"""ctypes binding of libchem.so: argument marshalling only.
+
+Every computation runs in the CUDA kernels behind the C ABI (include/chem.h).  There is no CPU
+fallback: importing this module fails loudly if the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+D = ctypes.c_double
+
+CHEM_OK = 0
+CHEM_WCELLS = 1
+CHEM_EINVAL = -1
+CHEM_ENOMEM = -2
+CHEM_ECUDA = -3
+CHEM_EBUSY = -4
+CHEM_ETIMEOUT = -5
+CHEM_ENOTFOUND = -6
+
+CELL_OK, CELL_MAX_STEPS, CELL_H_UNDERFLOW, CELL_NONFINITE, CELL_SINGULAR_LU = 0, 1, 2, 3, 4
+
+
+class ChemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libchem error {code}: {msg}")
+        self.code = code
+
+
+class MechDesc(ctypes.Structure):
+    _fields_ = [("n_species", I32), ("n_elements", I32), ("n_reactions", I32),
+                ("elem_mass", P), ("comp", P), ("nasa_lo", P), ("nasa_hi", P), ("rtype", P),
+                ("reac", P), ("prod", P), ("A", P), ("b", P), ("Ea", P), ("troe", P),
+                ("has_t2", P), ("eff", P)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("max_steps", I32), ("group_threads", I32), ("groups_per_cta", I32),
+                ("max_ctas", I32)]
+
+
+# name -> (restype, argtypes); the library must export every one of them
+SIGNATURES = {
+    "chem_load_mechanism": (ctypes.c_int, [ctypes.c_char_p, P]),
+    "chem_load_mechanism_desc": (ctypes.c_int, [P, P]),
+    "chem_free_mechanism": (ctypes.c_int, [P]),
+    "chem_mechanism_info": (ctypes.c_int, [P, P, P, P]),
+    "chem_advance": (ctypes.c_int, [P, P, P, P, D, I64, D, D, P]),
+    "chem_advance_ex": (ctypes.c_int, [P, P, P, P, I64, D, I64, D, D, P, P, P, P, P, P]),
+    "chem_eval_rhs_jac": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P]),
+    "chem_fp64_fma_peak": (ctypes.c_int, [P]),
+    "chem_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load (building first if needed) libchem.so.  Raises if that is impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libchem.so missing at {path}")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(rc):
+    if rc < 0:
+        msg = load().chem_last_error()
+        raise ChemError(rc, msg.decode() if msg else "")
+    return rc

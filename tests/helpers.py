@@ -20,9 +20,8 @@ def prereacted_mixing_states(om, mech, n, seed):
     st = mixing_states(mech, n, seed)
     T, p, Y = st["T"].copy(), st["p"], st["Y"].copy()
     idx = np.nonzero(st["react"])[0]
-    for i in idx:
-        y, s, _, _ = om.rodas4(p[i], np.r_[T[i], Y[:, i]], st["t_react"][i], 1e-8, 1e-14)
-        assert s == 0
-        T[i] = y[0]
-        Y[:, i] = y[1:]
+    T1, Y1, status = om.advance_dt(T[idx], p[idx], Y[:, idx], st["t_react"][idx], 1e-8, 1e-14)
+    assert np.all(status == 0)
+    T[idx] = T1
+    Y[:, idx] = Y1
     return T, p, Y
