@@ -166,6 +166,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """Integrator only, on a small case: the quasi-DNS H2 field or the LES CH4 field."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from synth.mechanism import ch4_mechanism, h2_mechanism
+    from synth.states import les_field, load_table
+    if args.case == "h2":
+        mech, f, dt = h2_mechanism(), make_field(0, args.cells), DT
+    else:
+        mech = ch4_mechanism()
+        f, dt = les_field(load_table("ch4_flamelet.npz"), n=args.cells, seed=12347), 1e-6
+    dm = cg.Mechanism(mech)
+    T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+    Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+    ms = []
+    for k in range(args.warmup + args.steps):
+        T = T0.clone(); Y = Y0.clone()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        cg.advance(dm, T, p, Y, dt, RTOL, ATOL)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms.append(a.elapsed_time(b))
+    print(json.dumps({"case": args.case, "cells": args.cells, "ms": ms,
+                      "cells_per_s": args.cells / (np.mean(ms) * 1e-3)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -174,7 +203,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["h2", "ch4"], default=None,
+                    help="time only the integrator on a small case (profiling)")
+    ap.add_argument("--cells", type=int, default=65536)
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
