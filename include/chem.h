@@ -122,6 +122,22 @@ int chem_advance_ex(chem_mech_t m, double* T, const double* p, double* Y, int64_
                     int8_t* status, int32_t* nsub, int32_t* nrej, const chem_options* opt,
                     chem_stream_t stream);
 
+/* Allocation-free form of chem_advance_ex (cells [0, ncells), default options).  It calls no
+ * device allocator: the only scratch a launch needs, the 8-byte counter of the kernel's work
+ * queue, lives in a 256-byte file-scope __device__ array inside the library (held by every GPU
+ * that loads the library until the process exits), so callers that may not allocate device
+ * memory -- a flow solver that already owns the device memory through its own pools, code under
+ * a hard allocation budget, a latency-critical loop that must not enter the allocator -- can
+ * still advance their cells.  The caller passes all inputs and outputs as for chem_advance_ex.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
+ * must therefore happen outside any stream capture.  All calls share the array and the counter
+ * is reset at the start of each call: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller (one stream, or events).  The scratch does not grow with ncells.
+ * The paper has no counterpart of this entry point. */
+int chem_advance_noalloc(chem_mech_t m, double* T, const double* p, double* Y, int64_t ld,
+                         double dt, int64_t ncells, double rtol, double atol, int8_t* status,
+                         int32_t* nsub, int32_t* nrej, chem_stream_t stream);
+
 /* Right-hand side f[i * ld + c] (i = 0 is dT/dt, i = 1 + k is dY_k/dt) and, if J is non-NULL,
  * the analytic Jacobian J[(i * N + j) * ld + c] = df_i/dy_j (N = ns + 1) of every cell, computed
  * by the same device code the integrator uses.  Device pointers; asynchronous. */

@@ -53,6 +53,7 @@ SIGNATURES = {
     "chem_mechanism_info": (ctypes.c_int, [P, P, P, P]),
     "chem_advance": (ctypes.c_int, [P, P, P, P, D, I64, D, D, P]),
     "chem_advance_ex": (ctypes.c_int, [P, P, P, P, I64, D, I64, D, D, P, P, P, P, P, P]),
+    "chem_advance_noalloc": (ctypes.c_int, [P, P, P, P, I64, D, I64, D, D, P, P, P, P]),
     "chem_eval_rhs_jac": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P]),
     "chem_fp64_fma_peak": (ctypes.c_int, [P]),
     "chem_last_error": (ctypes.c_char_p, []),

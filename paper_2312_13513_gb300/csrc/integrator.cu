@@ -850,9 +850,95 @@ __global__ void fma_peak_kernel(double* out, int iters, double a, double b) {
   if (s == 12345.678) out[0] = s;     // keeps the chains live
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the integrator launch.
+//
+// The work queue of the persistent kernel needs one zeroed 8-byte counter per launch; the
+// regular entry points draw it from the stream-ordered allocator.  Callers that may not
+// allocate device memory (a flow solver that has already claimed the device memory for its own
+// fields and pools, code running under a hard allocation budget, or a latency-critical loop that
+// must not touch the allocator) use chem_advance_noalloc instead, which takes the counter from
+// this file-scope array.  Every GPU that loads the library holds the array until the process
+// exits.  All calls share it, so calls that overlap on the GPU race on the counter.
+// ---------------------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = 256;
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocScratchBytes / 8];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.  In
+// host code the array's name is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress with the device current.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  CHEM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal %d out of range for the allocation-free entry point", dev);
+    return CHEM_EINVAL;
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    CHEM_CUDA_TRY(cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CHEM_OK;
+}
+}  // namespace
+
+int launch_advance_noalloc(chem_mech_s* m, double* T, const double* p, double* Y, int64_t ld,
+                           double dt, int64_t ncells, double rtol, double atol, int8_t* status,
+                           int32_t* nsub, int32_t* nrej, cudaStream_t stream) {
+  if (!m) { set_error("NULL mechanism"); return CHEM_EINVAL; }
+  if (ncells < 0 || !(dt > 0.0) || !(rtol > 0.0) || !(atol > 0.0) || !std::isfinite(dt)) {
+    set_error("invalid arguments (ncells=%lld dt=%g rtol=%g atol=%g)", (long long)ncells, dt, rtol, atol);
+    return CHEM_EINVAL;
+  }
+  if (!T || !p || !Y) { set_error("NULL state pointer"); return CHEM_EINVAL; }
+  if (ld < ncells) { set_error("ld (%lld) < ncells (%lld)", (long long)ld, (long long)ncells); return CHEM_EINVAL; }
+  // scratch needed by one launch: the work-queue counter, independent of ncells
+  const size_t need = sizeof(unsigned long long);
+  if (need > kNoAllocScratchBytes) {
+    set_error("allocation-free integrator needs %zu scratch bytes, only %zu available", need,
+              kNoAllocScratchBytes);
+    return CHEM_EINVAL;
+  }
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  if (ncells == 0) return CHEM_OK;
+  LaunchShape s;
+  rc = pick_shape(m, nullptr, &s);
+  if (rc) return rc;
+  unsigned long long* counter = (unsigned long long*)scratch;
+  CHEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream));
+  AdvanceParams P;
+  P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
+  P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells; P.dt = dt; P.rtol = rtol; P.atol = atol;
+  P.idx = nullptr; P.status = status; P.nsub = nsub; P.nrej = nrej;
+  P.max_steps = 100000;
+  P.counter = counter;
+  switch (s.G) {
+    case 32: return launch_adv_t<32>(s, P, nullptr, stream);
+    case 64: return launch_adv_t<64>(s, P, nullptr, stream);
+    case 128: return launch_adv_t<128>(s, P, nullptr, stream);
+    default: return launch_adv_t<256>(s, P, nullptr, stream);
+  }
+}
+
 }  // namespace chem
 
 using namespace chem;
+
+extern "C" int chem_advance_noalloc(chem_mech_t m, double* T, const double* p, double* Y,
+                                    int64_t ld, double dt, int64_t ncells, double rtol,
+                                    double atol, int8_t* status, int32_t* nsub, int32_t* nrej,
+                                    chem_stream_t stream) {
+  return launch_advance_noalloc(m, T, p, Y, ld, dt, ncells, rtol, atol, status, nsub, nrej,
+                                (cudaStream_t)stream);
+}
 
 extern "C" int chem_advance(chem_mech_t m, double* T, const double* p, double* Y, double dt,
                             int64_t ncells, double rtol, double atol, chem_stream_t stream) {
