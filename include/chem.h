@@ -101,7 +101,7 @@ int chem_mechanism_info(chem_mech_t m, int* n_species, int* n_reactions, int* n_
 
 typedef struct chem_options {
   int32_t max_steps;      /* step attempts per cell before CHEM_CELL_MAX_STEPS; 0 -> 100000 */
-  int32_t group_threads;  /* threads per cell: 0 auto (32 if ns+1 <= 16 else 128), 32, 64, 128, 256 */
+  int32_t group_threads;  /* threads per cell: 0 auto (4 if ns+1 <= 16 else 128); 4, 8, 16, 32, 64, 128, 256 */
   int32_t groups_per_cta; /* 0 auto */
   int32_t max_ctas;       /* 0 auto (SM count x resident CTAs per SM) */
 } chem_options;
@@ -143,6 +143,56 @@ int chem_advance_noalloc(chem_mech_t m, double* T, const double* p, double* Y, i
  * by the same device code the integrator uses.  Device pointers; asynchronous. */
 int chem_eval_rhs_jac(chem_mech_t m, const double* T, const double* p, const double* Y,
                       int64_t ld, int64_t ncells, double* f, double* J, chem_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
+ * BF16 MLP surrogate of the chemistry step (§2: the paper replaces CVODE by per-species DNNs
+ * run on the GPU; here one network maps the state to the step's composition change).
+ * Inputs x = [T, ln p, BC(Y_k)] with BC(y) = (y^0.1 - 1)/0.1, z-scored; outputs the z-scored
+ * increment of BC(Y_k) over the training step dt; hidden width 512, 4 GELU layers, BF16
+ * weights and activations, FP32 accumulation on tcgen05 tensor cores.
+ * ------------------------------------------------------------------------------------- */
+typedef struct chem_surrogate_desc {
+  int32_t n_species;         /* ns (<= 16); inputs nin = ns + 2 */
+  int32_t hidden;            /* must be 512 */
+  double dt;                 /* step the network was trained for (s) */
+  const float* W[5];         /* host, row-major [out x in]: [512 x nin], 3 x [512 x 512], [ns x 512] */
+  const float* b[5];         /* host: [512] x 4, [ns] */
+  const float* x_mean;       /* [nin] feature mean and standard deviation */
+  const float* x_std;
+  const float* y_mean;       /* [ns] output mean and standard deviation */
+  const float* y_std;
+  const float* box_lo;       /* [nin] training box of the raw features (trust region) */
+  const float* box_hi;
+} chem_surrogate_desc;
+
+/* Upload a surrogate (weights rounded to BF16) for use with mechanism m on the current device. */
+int chem_surrogate_create(const chem_surrogate_desc* desc, chem_mech_t m, chem_model_t* out);
+/* Same from a CHEMSUR1 binary file: magic, int32 ns, int32 hidden, double dt, then W[l], b[l]
+ * (l = 0..4), x_mean, x_std, y_mean, y_std, box_lo, box_hi as little-endian float32. */
+int chem_surrogate_load(const char* path, chem_mech_t m, chem_model_t* out);
+int chem_surrogate_free(chem_model_t model);
+
+/* Network pass only (features, MLP, inverse transform): ynet[k * ncells + c] = predicted Y_k
+ * (FP32) and out_of_box[c] = 1 where the features leave the training box.  Device pointers.
+ * Synchronises the stream to report a pipeline timeout (CHEM_ECUDA). */
+int chem_surrogate_forward(chem_model_t model, const double* T, const double* p, const double* Y,
+                           int64_t ld, int64_t ncells, float* ynet, uint8_t* out_of_box,
+                           chem_stream_t stream);
+
+/* Surrogate chemistry step in place: network, element-conservation projection, clipping,
+ * temperature from enthalpy conservation (Newton), acceptance tests; cells outside the training
+ * box or failing a test are advanced by the FP64 integrator instead (indexed, same call,
+ * asynchronous).  dt must equal the model's training step.  route_out[c] (nullable, int8):
+ * 0 = network, 1 = FP64 fallback. */
+int chem_surrogate_advance(chem_model_t model, chem_mech_t m, double* T, const double* p,
+                           double* Y, int64_t ld, double dt, int64_t ncells, double rtol,
+                           double atol, int8_t* route_out, chem_stream_t stream);
+
+/* BF16 tensor-core GEMM used by training: C[M x N] (FP32, row pitch ldc) = A[M x K] B[N x K]^T
+ * (+ bias[N], nullable); A, B device BF16 with K contiguous, row pitches lda/ldb (elements,
+ * 16-byte multiples).  *err (device int) is set to 1 if a pipeline wait times out. */
+int chem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+                   const float* bias, int M, int N, int K, int* err, chem_stream_t stream);
 
 /* Measured FP64 FMA throughput of the current device (TFLOP/s, 2 flops per FMA) from a
  * register-resident FMA chain kernel; synchronous. */

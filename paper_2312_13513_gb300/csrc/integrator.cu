@@ -6,7 +6,9 @@
 // dense LU with partial pivoting, six stages, embedded error estimate, adaptive sub-steps.
 //
 // Work decomposition ("group per cell"): a group of G threads owns one cell at a time.
-//   G = 32  (one warp per cell)  for small mechanisms (N = ns + 1 <= 16, H2-sized);
+//   G = 4   (eight cells per warp, sub-warp groups) for small mechanisms (N = ns + 1 <= 16,
+//           H2-sized): FP64 instructions issue warp-wide whatever the active mask, so a warp per
+//           10-unknown cell would leave most FP64 lanes idle;
 //   G = 128 (a CTA-sized group per cell, named barriers) for CH4-sized ones (N ~ 54).
 // Inside a group, threads split the species, the reactions, the Jacobian entries, the LU
 // trailing updates and the triangular solves; sums use warp shuffles.  The mechanism (NASA-7
@@ -102,11 +104,14 @@ inline WsLayout make_ws(int ns, int nr, int G) {
   int o = 0;
   auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };   // keep 16-byte alignment
   w.y = take(N); w.ynew = take(N); w.ys = take(N); w.fs = take(N); w.f0 = take(N);
-  w.u = take(6 * N); w.J = take(N * w.LD); w.M = take(N * w.LD); w.invd = take(N);
+  w.u = take(6 * N); w.M = take(N * w.LD); w.invd = take(N);
+  // groups of at least a warp keep J(y) across rejected attempts; sub-warp groups re-evaluate it
+  // every attempt (identical values) so that all groups of a warp stay in lockstep
+  w.J = G >= 32 ? take(N * w.LD) : w.M;
   w.C = take(ns); w.hRT = take(ns); w.gRT = take(ns); w.cpR = take(ns); w.dcpR = take(ns);
   w.wdot = take(ns); w.dwdT = take(ns); w.rk = take(ns); w.Hm = take(ns); w.lcol = take(N);
   w.q = take(nr); w.dqdT = take(nr); w.dq = take(7 * nr);
-  w.red = take(8 * (G / 32) + 8);
+  w.red = take(8 * (G >= 32 ? G / 32 : 1) + 8);
   w.stage = take(CHUNK * (N + 1));
   w.ctl = take(2);
   w.piv = take((N + 1) / 2);      // ints
@@ -140,8 +145,21 @@ __device__ __forceinline__ WsPtr bind_ws(double* b, const WsLayout& w) {
 template <int G>
 struct Grp {
   int tid, gid;
+  unsigned mask;      // lanes of this group within its warp (G <= 32)
+  __device__ __forceinline__ void init() {
+    tid = threadIdx.x % G;
+    gid = threadIdx.x / G;
+    if constexpr (G >= 32) {
+      mask = 0xffffffffu;
+    } else {
+      const unsigned lane = threadIdx.x & 31u;
+      mask = ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+  }
   __device__ __forceinline__ void sync() const {
-    if (G == 32) {
+    if (G < 32) {
+      __syncwarp(mask);
+    } else if (G == 32) {
       __syncwarp();
     } else {
       asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "n"(G) : "memory");
@@ -149,18 +167,21 @@ struct Grp {
   }
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <int G>
+__device__ __forceinline__ double sub_sum(double v, unsigned mask) {
+  constexpr int W = G < 32 ? G : 32;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
   return v;
 }
 
-// Sum of K values over the group; every thread receives bitwise-identical results.
+// Sum of K values over the group; every thread receives bitwise-identical results (a butterfly
+// adds the same two partial sums in every lane).
 template <int G, int K>
 __device__ __forceinline__ void gsum(const Grp<G>& g, double (&v)[K], double* red) {
 #pragma unroll
-  for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
-  if (G == 32) return;
+  for (int i = 0; i < K; ++i) v[i] = sub_sum<G>(v[i], g.mask);
+  if (G <= 32) return;
   constexpr int NW = G / 32;
   if ((g.tid & 31) == 0)
 #pragma unroll
@@ -178,13 +199,14 @@ __device__ __forceinline__ void gsum(const Grp<G>& g, double (&v)[K], double* re
 // argmax of |a| with ties resolved to the lowest index; identical result in every thread
 template <int G>
 __device__ __forceinline__ void gargmax(const Grp<G>& g, double& best, int& bi, double* red) {
+  constexpr int W = G < 32 ? G : 32;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double ob = __shfl_xor_sync(0xffffffffu, best, o);
-    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+  for (int o = W / 2; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(g.mask, best, o);
+    int oi = __shfl_xor_sync(g.mask, bi, o);
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
-  if (G == 32) return;
+  if (G <= 32) return;
   constexpr int NW = G / 32;
   if ((g.tid & 31) == 0) {
     red[g.tid >> 5] = best;
@@ -214,8 +236,9 @@ struct JacArgs {
 };
 
 template <int G>
-__device__ void eval_fj(const Grp<G>& g, const MechView& m, const WsPtr& w, const JacArgs& jp,
-                        int LD, const double* y, double p, double* f, bool jac) {
+__device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const WsPtr& w,
+                                     const JacArgs& jp, int LD, const double* y, double p,
+                                     double* f, double* Jout, bool jac) {
   const int ns = m.ns, nr = m.nr;
   const double T = y[0];
   const double lnT = log(T);
@@ -380,7 +403,7 @@ __device__ void eval_fj(const Grp<G>& g, const MechView& m, const WsPtr& w, cons
 
   // analytic Jacobian (A5): d(wdot)/dC by the precomputed assembly program ...
   const int N = m.N;
-  double* J = w.J;
+  double* J = Jout;
   for (int e = g.tid; e < ns * ns; e += G) J[(1 + e / ns) * LD + 1 + e % ns] = 0.0;
   g.sync();
   for (int e = g.tid; e < jp.nent; e += G) {
@@ -515,6 +538,7 @@ struct AdvanceParams {
   int32_t* nrej;
   int max_steps;
   unsigned long long* counter;
+  const unsigned int* ncells_dev;   // when set, the cell count is read from device memory
 };
 
 __device__ __forceinline__ void stage_mech(const unsigned char* src, unsigned char* dst, int bytes) {
@@ -523,139 +547,116 @@ __device__ __forceinline__ void stage_mech(const unsigned char* src, unsigned ch
   for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
+// one Rodas4 attempt from w.y with step h; J(y) and f(y) are (re)evaluated when need_j.
+// Returns false on an exactly singular iteration matrix; *en receives the error norm.
 template <int G>
-__device__ void integrate_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
-                               const AdvanceParams& P, int c, int64_t cell) {
+__device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& w,
+                               const AdvanceParams& P, double p, double h, bool need_j,
+                               double* en) {
   const int N = m.N, LD = P.ws.LD;
-  for (int i = g.tid; i < N; i += G) w.y[i] = w.stage[i * CHUNK + c];
-  const double p = w.stage[N * CHUNK + c];
-  g.sync();
-  double bad[1] = {0.0};
-  for (int i = g.tid; i < N; i += G) {
-    const double v = w.y[i];
-    if (!isfinite(v) || (i == 0 && !(v > 0.0))) bad[0] += 1.0;
+  if (need_j) eval_fj<G>(g, m, w, P.jp, LD, w.y, p, w.f0, w.J, true);
+  const double ig = 1.0 / (kGamma * h);
+  for (int e = g.tid; e < N * N; e += G) {
+    const int i = e / N, j = e % N;
+    w.M[i * LD + j] = (i == j ? ig : 0.0) - w.J[i * LD + j];
   }
-  if (g.tid == 0 && (!isfinite(p) || !(p > 0.0))) bad[0] += 1.0;
-  gsum<G, 1>(g, bad, w.red);
-  int status = CHEM_CELL_OK, nacc = 0, nrej = 0;
-  if (bad[0] != 0.0) {
-    status = CHEM_CELL_NONFINITE;
-  } else {
-    const double dt = P.dt;
-    double t = 0.0, h = dt, facmax = 6.0;
-    int attempts = 0;
-    bool have_j = false;
-    for (;;) {
-      if (attempts >= P.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
-      bool last = false;
-      if (h >= dt - t) { h = dt - t; last = true; }
-      if (h < 1e-12 * dt) { status = CHEM_CELL_H_UNDERFLOW; break; }
-      if (!have_j) {
-        eval_fj<G>(g, m, w, P.jp, LD, w.y, p, w.f0, true);
-        have_j = true;
-      }
-      ++attempts;
-      const double ig = 1.0 / (kGamma * h);
-      for (int e = g.tid; e < N * N; e += G) {
-        const int i = e / N, j = e % N;
-        w.M[i * LD + j] = (i == j ? ig : 0.0) - w.J[i * LD + j];
-      }
-      g.sync();
-      if (!lu_factor<G>(g, w.M, N, LD, w.piv, w.invd, w.lcol, w.red)) {
-        status = CHEM_CELL_SINGULAR_LU;
-        break;
-      }
-      const double invh = 1.0 / h;
-      for (int s = 0; s < 6; ++s) {
-        const double* src = w.f0;
-        if (s > 0) {
-          for (int i = g.tid; i < N; i += G) {
-            double v = w.y[i];
-            for (int j = 0; j < s; ++j) v += kRA[s][j] * w.u[j * N + i];
-            w.ys[i] = v;
-          }
-          g.sync();
-          eval_fj<G>(g, m, w, P.jp, LD, w.ys, p, w.fs, false);
-          src = w.fs;
-        }
-        double* us = w.u + s * N;
-        for (int i = g.tid; i < N; i += G) {
-          double v = src[i];
-          for (int j = 0; j < s; ++j) v += (kRC[s][j] * invh) * w.u[j * N + i];
-          us[i] = v;
-        }
-        g.sync();
-        lu_solve<G>(g, w.M, N, LD, w.piv, w.invd, us);
-      }
-      double acc[1] = {0.0};
+  g.sync();
+  if (!lu_factor<G>(g, w.M, N, LD, w.piv, w.invd, w.lcol, w.red)) return false;
+  const double invh = 1.0 / h;
+  for (int s = 0; s < 6; ++s) {
+    const double* src = w.f0;
+    if (s > 0) {
       for (int i = g.tid; i < N; i += G) {
         double v = w.y[i];
-#pragma unroll
-        for (int s = 0; s < 6; ++s) v += kRM[s] * w.u[s * N + i];
-        w.ynew[i] = v;
-        const double sc = P.atol + P.rtol * fmax(fabs(w.y[i]), fabs(v));
-        const double r = w.u[5 * N + i] / sc;
-        acc[0] += r * r;
+        for (int j = 0; j < s; ++j) v += kRA[s][j] * w.u[j * N + i];
+        w.ys[i] = v;
       }
-      gsum<G, 1>(g, acc, w.red);
-      const double en = sqrt(acc[0] / (double)N);
-      if (en <= 1.0) {
-        for (int i = g.tid; i < N; i += G) w.y[i] = w.ynew[i];
-        g.sync();
-        have_j = false;
-        ++nacc;
-        if (last) break;
-        t += h;
-        double fac = 0.9 * pow(en, -0.25);
-        if (fac < 0.2) fac = 0.2;
-        if (fac > facmax) fac = facmax;
-        h = h * fac;
-        facmax = 6.0;
-      } else {
-        ++nrej;
-        double fac = 0.2;
-        if (isfinite(en)) {
-          fac = 0.9 * pow(en, -0.25);
-          if (fac < 0.2) fac = 0.2;
-        }
-        h = h * fac;
-        facmax = 1.0;
-      }
+      g.sync();
+      eval_fj<G>(g, m, w, P.jp, LD, w.ys, p, w.fs, nullptr, false);
+      src = w.fs;
     }
-    for (int i = g.tid; i < N; i += G) w.stage[i * CHUNK + c] = w.y[i];
+    double* us = w.u + s * N;
+    for (int i = g.tid; i < N; i += G) {
+      double v = src[i];
+      for (int j = 0; j < s; ++j) v += (kRC[s][j] * invh) * w.u[j * N + i];
+      us[i] = v;
+    }
+    g.sync();
+    lu_solve<G>(g, w.M, N, LD, w.piv, w.invd, us);
   }
-  if (g.tid == 0) {
-    if (P.status) P.status[cell] = (int8_t)status;
-    if (P.nsub) P.nsub[cell] = nacc;
-    if (P.nrej) P.nrej[cell] = nrej;
+  double acc[1] = {0.0};
+  for (int i = g.tid; i < N; i += G) {
+    double v = w.y[i];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) v += kRM[s] * w.u[s * N + i];
+    w.ynew[i] = v;
+    const double sc = P.atol + P.rtol * fmax(fabs(w.y[i]), fabs(v));
+    const double r = w.u[5 * N + i] / sc;
+    acc[0] += r * r;
   }
-  g.sync();
+  gsum<G, 1>(g, acc, w.red);
+  *en = sqrt(acc[0] / (double)N);
+  return true;
 }
 
+// Chunk bookkeeping of one group: the current chunk of CHUNK consecutive queue entries staged
+// in shared memory and the position of the cell being integrated.
+struct ChunkPos {
+  long long base;
+  int nloc, c;
+  bool exhausted;
+  long long ncells;     // cells in the queue (from the launch or from device memory)
+};
+
 template <int G>
-__global__ void __launch_bounds__(256) advance_kernel(const AdvanceParams P) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  stage_mech(P.blob, smem, P.lay.bytes);
-  __syncthreads();
-  const MechView m = bind_mech(smem, P.lay);
-  Grp<G> g;
-  g.tid = threadIdx.x % G;
-  g.gid = threadIdx.x / G;
-  double* wbase = (double*)(smem + P.lay.bytes) + (size_t)g.gid * P.ws.total;
-  const WsPtr w = bind_ws(wbase, P.ws);
+__device__ __forceinline__ int64_t cell_of(const AdvanceParams& P, long long base, int c) {
+  return P.idx ? (int64_t)P.idx[base + c] : (int64_t)(base + c);
+}
+
+// Move to the next cell: store a finished chunk, claim and load the next one when needed.
+// Loads the cell's state into w.y and returns its pressure; false when the queue is empty.
+template <int G>
+__device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
+                          const AdvanceParams& P, ChunkPos& q, double* p) {
   const int N = m.N;
   for (;;) {
+    if (q.c + 1 < q.nloc) {
+      ++q.c;
+      for (int i = g.tid; i < N; i += G) w.y[i] = w.stage[i * CHUNK + q.c];
+      *p = w.stage[N * CHUNK + q.c];
+      g.sync();
+      return true;
+    }
+    if (q.nloc > 0) {
+      // coalesced store of the finished chunk (rows T, Y_1..Y_ns)
+      for (int e = g.tid; e < N * CHUNK; e += G) {
+        const int row = e / CHUNK, c = e % CHUNK;
+        if (c >= q.nloc) continue;
+        const int64_t cell = cell_of<G>(P, q.base, c);
+        const double v = w.stage[row * CHUNK + c];
+        if (row == 0) P.T[cell] = v;
+        else P.Y[(int64_t)(row - 1) * P.ld + cell] = v;
+      }
+      q.nloc = 0;
+      g.sync();
+    }
+    if (q.exhausted) return false;
     if (g.tid == 0) w.ctl[0] = atomicAdd(P.counter, (unsigned long long)CHUNK);
     g.sync();
     const long long base = (long long)w.ctl[0];
     g.sync();
-    if (base >= P.ncells) break;
-    const int nloc = (int)min((long long)CHUNK, P.ncells - base);
+    if (base >= q.ncells) {
+      q.exhausted = true;
+      return false;
+    }
+    q.base = base;
+    q.nloc = (int)min((long long)CHUNK, q.ncells - base);
+    q.c = -1;
     // coalesced load of the chunk: rows T, Y_1..Y_ns, p; each row CHUNK consecutive cells
     for (int e = g.tid; e < (N + 1) * CHUNK; e += G) {
       const int row = e / CHUNK, c = e % CHUNK;
-      if (c >= nloc) continue;
-      const int64_t cell = P.idx ? (int64_t)P.idx[base + c] : base + c;
+      if (c >= q.nloc) continue;
+      const int64_t cell = cell_of<G>(P, q.base, c);
       double v;
       if (row == 0) v = P.T[cell];
       else if (row <= m.ns) v = P.Y[(int64_t)(row - 1) * P.ld + cell];
@@ -663,19 +664,133 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceParams P) {
       w.stage[row * CHUNK + c] = v;
     }
     g.sync();
-    for (int c = 0; c < nloc; ++c) {
-      const int64_t cell = P.idx ? (int64_t)P.idx[base + c] : base + c;
-      integrate_cell<G>(g, m, w, P, c, cell);
+  }
+}
+
+// Persistent integrator.  Each loop iteration performs at most one Rodas4 attempt per group;
+// cell changes happen between iterations.  For sub-warp groups every group of a warp executes
+// the attempt body each iteration (an idle group works on a dummy state whose results are
+// discarded), so the warp's FP64 instructions stay converged across its groups.
+template <int G>
+__global__ void __launch_bounds__(512) advance_kernel(const AdvanceParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  stage_mech(P.blob, smem, P.lay.bytes);
+  __syncthreads();
+  const MechView m = bind_mech(smem, P.lay);
+  Grp<G> g;
+  g.init();
+  double* wbase = (double*)(smem + P.lay.bytes) + (size_t)g.gid * P.ws.total;
+  const WsPtr w = bind_ws(wbase, P.ws);
+  const int N = m.N;
+  // benign dummy state for groups without a cell
+  for (int i = g.tid; i < N; i += G) w.y[i] = i == 0 ? 1000.0 : 1.0 / m.ns;
+  g.sync();
+
+  const double dt = P.dt;
+  long long ncells = P.ncells;
+  if (P.ncells_dev) ncells = min((long long)*P.ncells_dev, (long long)P.ncells);
+  ChunkPos q{0, 0, 0, false, ncells};
+  bool active = false, have_j = false;
+  double p = 1.0e6, t = 0.0, h = dt, facmax = 6.0;
+  int attempts = 0, nacc = 0, nrej = 0;
+
+  for (;;) {
+    // ---- cell management (group-local) ----
+    while (!active) {
+      if (!next_cell<G>(g, m, w, P, q, &p)) break;
+      double bad[1] = {0.0};
+      for (int i = g.tid; i < N; i += G) {
+        const double v = w.y[i];
+        if (!isfinite(v) || (i == 0 && !(v > 0.0))) bad[0] += 1.0;
+      }
+      if (g.tid == 0 && (!isfinite(p) || !(p > 0.0))) bad[0] += 1.0;
+      gsum<G, 1>(g, bad, w.red);
+      if (bad[0] != 0.0) {
+        if (g.tid == 0) {
+          const int64_t cell = cell_of<G>(P, q.base, q.c);
+          if (P.status) P.status[cell] = (int8_t)CHEM_CELL_NONFINITE;
+          if (P.nsub) P.nsub[cell] = 0;
+          if (P.nrej) P.nrej[cell] = 0;
+        }
+        for (int i = g.tid; i < N; i += G) w.y[i] = i == 0 ? 1000.0 : 1.0 / m.ns;
+        g.sync();
+        continue;
+      }
+      active = true;
+      have_j = false;
+      t = 0.0; h = dt; facmax = 6.0;
+      attempts = 0; nacc = 0; nrej = 0;
     }
-    for (int e = g.tid; e < N * CHUNK; e += G) {
-      const int row = e / CHUNK, c = e % CHUNK;
-      if (c >= nloc) continue;
-      const int64_t cell = P.idx ? (int64_t)P.idx[base + c] : base + c;
-      const double v = w.stage[row * CHUNK + c];
-      if (row == 0) P.T[cell] = v;
-      else P.Y[(int64_t)(row - 1) * P.ld + cell] = v;
+    if (G >= 32) {
+      if (!active) break;
+    } else {
+      if (__all_sync(0xffffffffu, !active)) break;
     }
-    g.sync();
+
+    // ---- one attempt ----
+    int status = CHEM_CELL_OK;
+    bool stop = false, last = false;
+    if (active) {
+      if (attempts >= P.max_steps) {
+        stop = true; status = CHEM_CELL_MAX_STEPS;
+      } else {
+        if (h >= dt - t) { h = dt - t; last = true; }
+        if (h < 1e-12 * dt) { stop = true; status = CHEM_CELL_H_UNDERFLOW; }
+      }
+    }
+    const bool run = active && !stop;
+    bool finished = false;
+    if (run || G < 32) {
+      double en = 0.0;
+      const bool need_j = (G < 32) || !have_j;
+      const bool ok = rodas4_attempt<G>(g, m, w, P, p, run ? h : dt, need_j, &en);
+      if (run) {
+        have_j = true;
+        if (!ok) {
+          stop = true; status = CHEM_CELL_SINGULAR_LU;
+        } else {
+          ++attempts;
+          if (en <= 1.0) {
+            for (int i = g.tid; i < N; i += G) w.y[i] = w.ynew[i];
+            g.sync();
+            have_j = false;
+            ++nacc;
+            if (last) {
+              finished = true;
+            } else {
+              t += h;
+              double fac = 0.9 * pow(en, -0.25);
+              if (fac < 0.2) fac = 0.2;
+              if (fac > facmax) fac = facmax;
+              h = h * fac;
+              facmax = 6.0;
+            }
+          } else {
+            ++nrej;
+            double fac = 0.2;
+            if (isfinite(en)) {
+              fac = 0.9 * pow(en, -0.25);
+              if (fac < 0.2) fac = 0.2;
+            }
+            h = h * fac;
+            facmax = 1.0;
+          }
+        }
+      }
+    }
+    if (active && (stop || finished)) {
+      // the last accepted state goes back into the chunk staging area
+      for (int i = g.tid; i < N; i += G) w.stage[i * CHUNK + q.c] = w.y[i];
+      if (g.tid == 0) {
+        const int64_t cell = cell_of<G>(P, q.base, q.c);
+        if (P.status) P.status[cell] = (int8_t)status;
+        if (P.nsub) P.nsub[cell] = nacc;
+        if (P.nrej) P.nrej[cell] = nrej;
+      }
+      g.sync();
+      active = false;
+    }
+    if (G < 32) __syncwarp();
   }
 }
 
@@ -693,14 +808,13 @@ struct EvalParams {
 };
 
 template <int G>
-__global__ void __launch_bounds__(256) eval_kernel(const EvalParams P) {
+__global__ void __launch_bounds__(512) eval_kernel(const EvalParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   stage_mech(P.blob, smem, P.lay.bytes);
   __syncthreads();
   const MechView m = bind_mech(smem, P.lay);
   Grp<G> g;
-  g.tid = threadIdx.x % G;
-  g.gid = threadIdx.x / G;
+  g.init();
   const int gpb = blockDim.x / G;
   double* wbase = (double*)(smem + P.lay.bytes) + (size_t)g.gid * P.ws.total;
   const WsPtr w = bind_ws(wbase, P.ws);
@@ -708,7 +822,7 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalParams P) {
   for (int64_t c = (int64_t)blockIdx.x * gpb + g.gid; c < P.ncells; c += (int64_t)gridDim.x * gpb) {
     for (int i = g.tid; i < N; i += G) w.y[i] = i == 0 ? P.T[c] : P.Y[(int64_t)(i - 1) * P.ld + c];
     g.sync();
-    eval_fj<G>(g, m, w, P.jp, LD, w.y, P.p[c], w.f0, P.J != nullptr);
+    eval_fj<G>(g, m, w, P.jp, LD, w.y, P.p[c], w.f0, w.J, P.J != nullptr);
     for (int i = g.tid; i < N; i += G) P.f[(int64_t)i * P.ld + c] = w.f0[i];
     if (P.J)
       for (int e = g.tid; e < N * N; e += G)
@@ -728,11 +842,13 @@ struct LaunchShape {
   WsLayout ws;
 };
 
+constexpr int kMaxThreads = 512;
+
 int pick_shape(const chem_mech_s* m, const chem_options* opt, LaunchShape* s) {
   const int N = m->ns + 1;
-  int G = (opt && opt->group_threads) ? opt->group_threads : (N <= 16 ? 32 : 128);
-  if (G != 32 && G != 64 && G != 128 && G != 256) {
-    set_error("group_threads must be 32, 64, 128 or 256 (got %d)", G);
+  int G = (opt && opt->group_threads) ? opt->group_threads : (N <= 16 ? 4 : 128);
+  if (G != 4 && G != 8 && G != 16 && G != 32 && G != 64 && G != 128 && G != 256) {
+    set_error("group_threads must be 4, 8, 16, 32, 64, 128 or 256 (got %d)", G);
     return CHEM_EINVAL;
   }
   s->G = G;
@@ -743,15 +859,17 @@ int pick_shape(const chem_mech_s* m, const chem_options* opt, LaunchShape* s) {
   CHEM_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t per_group = (size_t)s->ws.total * 8;
   const size_t fixed = (size_t)m->lay.bytes;
-  int groups = (opt && opt->groups_per_cta) ? opt->groups_per_cta : 256 / G;
-  groups = std::min(groups, 256 / G);
-  while (groups > 1 && fixed + per_group * groups > (size_t)smem_max) --groups;
+  const int unit = G < 32 ? 32 / G : 1;          // groups per warp: whole warps only
+  int groups = (opt && opt->groups_per_cta) ? opt->groups_per_cta : kMaxThreads / G;
+  groups = std::min(groups, kMaxThreads / G);
+  if (G > 32) groups = std::min(groups, 15);     // named barriers 1..15
+  while (groups > unit && fixed + per_group * groups > (size_t)smem_max) groups -= unit;
+  groups = std::max(unit, (groups / unit) * unit);
   if (fixed + per_group * groups > (size_t)smem_max) {
     set_error("mechanism too large for shared memory (%zu bytes needed, %d available)",
-              fixed + per_group, smem_max);
+              fixed + per_group * groups, smem_max);
     return CHEM_EINVAL;
   }
-  if (G > 32 && groups > 15) groups = 15;      // named barriers 1..15
   s->groups = groups;
   s->threads = G * groups;
   s->smem = fixed + per_group * groups;
@@ -768,7 +886,7 @@ int launch_adv_t(const LaunchShape& s, const AdvanceParams& P, const chem_option
   CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CHEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<G>, s.threads, s.smem));
   if (per_sm < 1) { set_error("kernel does not fit on an SM"); return CHEM_EINVAL; }
-  int64_t chunks = (P.ncells + CHUNK - 1) / CHUNK;
+  int64_t chunks = (P.ncells + CHUNK - 1) / CHUNK;     // an upper bound when ncells_dev is set
   int64_t grid = (int64_t)sms * per_sm;
   if (opt && opt->max_ctas > 0) grid = std::min<int64_t>(grid, opt->max_ctas);
   grid = std::min<int64_t>(grid, (chunks + s.groups - 1) / s.groups);
@@ -787,6 +905,19 @@ int launch_eval_t(const LaunchShape& s, const EvalParams& P, cudaStream_t stream
   eval_kernel<G><<<(unsigned)grid, s.threads, s.smem, stream>>>(P);
   CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
+}
+
+int dispatch_adv(const LaunchShape& s, const AdvanceParams& P, const chem_options* opt,
+                 cudaStream_t stream) {
+  switch (s.G) {
+    case 4: return launch_adv_t<4>(s, P, opt, stream);
+    case 8: return launch_adv_t<8>(s, P, opt, stream);
+    case 16: return launch_adv_t<16>(s, P, opt, stream);
+    case 32: return launch_adv_t<32>(s, P, opt, stream);
+    case 64: return launch_adv_t<64>(s, P, opt, stream);
+    case 128: return launch_adv_t<128>(s, P, opt, stream);
+    default: return launch_adv_t<256>(s, P, opt, stream);
+  }
 }
 
 JacArgs jac_args(const chem_mech_s* m) {
@@ -826,12 +957,35 @@ int launch_advance(chem_mech_s* m, double* T, const double* p, double* Y, int64_
   P.idx = idx; P.status = status; P.nsub = nsub; P.nrej = nrej;
   P.max_steps = (opt && opt->max_steps > 0) ? opt->max_steps : 100000;
   P.counter = counter;
-  switch (s.G) {
-    case 32: rc = launch_adv_t<32>(s, P, opt, stream); break;
-    case 64: rc = launch_adv_t<64>(s, P, opt, stream); break;
-    case 128: rc = launch_adv_t<128>(s, P, opt, stream); break;
-    default: rc = launch_adv_t<256>(s, P, opt, stream); break;
-  }
+  P.ncells_dev = nullptr;
+  rc = dispatch_adv(s, P, opt, stream);
+  cudaError_t fe = cudaFreeAsync(counter, stream);
+  if (rc) return rc;
+  CHEM_CUDA_TRY(fe);
+  return CHEM_OK;
+}
+
+// Indexed integrator launch whose cell count (<= capacity) is read from device memory by the
+// kernel: the surrogate's fallback pass runs without a host round trip.
+int launch_advance_counted(chem_mech_s* m, double* T, const double* p, double* Y, int64_t ld,
+                           double dt, int64_t capacity, const unsigned int* count_dev, double rtol,
+                           double atol, const int32_t* idx, cudaStream_t stream) {
+  if (!m || !count_dev || !idx) { set_error("NULL argument"); return CHEM_EINVAL; }
+  if (capacity <= 0) return CHEM_OK;
+  LaunchShape s;
+  int rc = pick_shape(m, nullptr, &s);
+  if (rc) return rc;
+  unsigned long long* counter = nullptr;
+  CHEM_CUDA_TRY(cudaMallocAsync((void**)&counter, sizeof(unsigned long long), stream));
+  CHEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream));
+  AdvanceParams P;
+  P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
+  P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = capacity; P.dt = dt; P.rtol = rtol; P.atol = atol;
+  P.idx = idx; P.status = nullptr; P.nsub = nullptr; P.nrej = nullptr;
+  P.max_steps = 100000;
+  P.counter = counter;
+  P.ncells_dev = count_dev;
+  rc = dispatch_adv(s, P, nullptr, stream);
   cudaError_t fe = cudaFreeAsync(counter, stream);
   if (rc) return rc;
   CHEM_CUDA_TRY(fe);
@@ -920,12 +1074,8 @@ int launch_advance_noalloc(chem_mech_s* m, double* T, const double* p, double* Y
   P.idx = nullptr; P.status = status; P.nsub = nsub; P.nrej = nrej;
   P.max_steps = 100000;
   P.counter = counter;
-  switch (s.G) {
-    case 32: return launch_adv_t<32>(s, P, nullptr, stream);
-    case 64: return launch_adv_t<64>(s, P, nullptr, stream);
-    case 128: return launch_adv_t<128>(s, P, nullptr, stream);
-    default: return launch_adv_t<256>(s, P, nullptr, stream);
-  }
+  P.ncells_dev = nullptr;
+  return dispatch_adv(s, P, nullptr, stream);
 }
 
 }  // namespace chem
@@ -969,6 +1119,9 @@ extern "C" int chem_eval_rhs_jac(chem_mech_t m, const double* T, const double* p
   P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells; P.f = f; P.J = J;
   cudaStream_t st = (cudaStream_t)stream;
   switch (s.G) {
+    case 4: return launch_eval_t<4>(s, P, st);
+    case 8: return launch_eval_t<8>(s, P, st);
+    case 16: return launch_eval_t<16>(s, P, st);
     case 32: return launch_eval_t<32>(s, P, st);
     case 64: return launch_eval_t<64>(s, P, st);
     case 128: return launch_eval_t<128>(s, P, st);

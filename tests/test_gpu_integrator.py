@@ -94,7 +94,15 @@ def test_parity_ch4_les_subset(om_ch4, ch4, dm_ch4):
     assert out <= 3
 
 
-@pytest.mark.parametrize("G", [64, 256])
+@pytest.mark.parametrize("G", [4, 16, 32])
+def test_parity_h2_other_group_sizes(om_h2, h2, dm_h2, G):
+    T, p, Y = prereacted_mixing_states(om_h2, h2, 301, 17)
+    Tg, Yg, st, _, _ = _run(dm_h2, T, p, Y, 1e-6, opts=cg.options(group_threads=G))
+    assert np.all(st == 0)
+    assert_parity(om_h2, T, p, Y, Tg, Yg, 1e-6, 1e-6, 1e-10)
+
+
+@pytest.mark.parametrize("G", [32, 64, 256])
 def test_parity_ch4_other_group_sizes(om_ch4, ch4, dm_ch4, G):
     f = les_field(load_table("ch4_flamelet.npz"), n=67, seed=778)
     T, p, Y = f["T"], f["p"], f["Y"]
