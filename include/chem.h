@@ -173,11 +173,12 @@ int chem_surrogate_load(const char* path, chem_mech_t m, chem_model_t* out);
 int chem_surrogate_free(chem_model_t model);
 
 /* Network pass only (features, MLP, inverse transform): ynet[k * ncells + c] = predicted Y_k
- * (FP32) and out_of_box[c] = 1 where the features leave the training box.  Device pointers.
- * Synchronises the stream to report a pipeline timeout (CHEM_ECUDA). */
+ * (FP32), zout[k * ncells + c] (nullable) = raw network output, and out_of_box[c] = 1 where the
+ * features leave the training box.  Device pointers.  Synchronises the stream to report a
+ * pipeline timeout (CHEM_ECUDA). */
 int chem_surrogate_forward(chem_model_t model, const double* T, const double* p, const double* Y,
-                           int64_t ld, int64_t ncells, float* ynet, uint8_t* out_of_box,
-                           chem_stream_t stream);
+                           int64_t ld, int64_t ncells, float* ynet, float* zout,
+                           uint8_t* out_of_box, chem_stream_t stream);
 
 /* Surrogate chemistry step in place: network, element-conservation projection, clipping,
  * temperature from enthalpy conservation (Newton), acceptance tests; cells outside the training
@@ -190,7 +191,8 @@ int chem_surrogate_advance(chem_model_t model, chem_mech_t m, double* T, const d
 
 /* BF16 tensor-core GEMM used by training: C[M x N] (FP32, row pitch ldc) = A[M x K] B[N x K]^T
  * (+ bias[N], nullable); A, B device BF16 with K contiguous, row pitches lda/ldb (elements,
- * 16-byte multiples).  *err (device int) is set to 1 if a pipeline wait times out. */
+ * 16-byte multiples), M >= 128 and N >= 128 (ragged edges are zero-filled by TMA).  *err
+ * (device int) is set to 1 if a pipeline wait times out. */
 int chem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                    const float* bias, int M, int N, int K, int* err, chem_stream_t stream);
 

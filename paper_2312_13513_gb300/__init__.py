@@ -117,3 +117,96 @@ def fp64_fma_peak():
     v = ctypes.c_double()
     check(_lib.load().chem_fp64_fma_peak(ctypes.byref(v)))
     return v.value
+
+
+# ---------------------------------------------------------------------------------------------
+# surrogate
+# ---------------------------------------------------------------------------------------------
+SUR_FIELDS = ("W", "b", "x_mean", "x_std", "y_mean", "y_std", "box_lo", "box_hi")
+
+
+class Surrogate:
+    """A BF16 MLP surrogate bound to a mechanism (chem_surrogate_create / _load).
+
+    params: dict with W (5 FP32 arrays [out, in]), b (5 arrays), x_mean, x_std, y_mean, y_std,
+    box_lo, box_hi, dt.
+    """
+
+    def __init__(self, mech, params=None, path=None):
+        L = _lib.load()
+        h = ctypes.c_void_p()
+        if path is not None:
+            check(L.chem_surrogate_load(path.encode(), mech.handle, ctypes.byref(h)))
+        else:
+            keep = []
+
+            def arr(a):
+                a = np.ascontiguousarray(a, dtype=np.float32)
+                keep.append(a)
+                return a.ctypes.data_as(ctypes.c_void_p)
+
+            d = _lib.SurrogateDesc()
+            d.n_species = mech.ns
+            d.hidden = int(np.asarray(params["W"][0]).shape[0])
+            d.dt = float(params["dt"])
+            for l in range(5):
+                d.W[l] = arr(params["W"][l])
+                d.b[l] = arr(params["b"][l])
+            d.x_mean = arr(params["x_mean"]); d.x_std = arr(params["x_std"])
+            d.y_mean = arr(params["y_mean"]); d.y_std = arr(params["y_std"])
+            d.box_lo = arr(params["box_lo"]); d.box_hi = arr(params["box_hi"])
+            check(L.chem_surrogate_create(ctypes.byref(d), mech.handle, ctypes.byref(h)))
+        self.handle = h
+        self.mech = mech
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().chem_surrogate_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def surrogate_forward(model, T, p, Y, with_z=False, stream=None):
+    """chem_surrogate_forward: returns (ynet [ns, n] FP32, z [ns, n] or None, out_of_box [n])."""
+    import torch
+    n = T.numel()
+    ns = model.mech.ns
+    ynet = torch.empty((ns, n), dtype=torch.float32, device=T.device)
+    z = torch.empty((ns, n), dtype=torch.float32, device=T.device) if with_z else None
+    box = torch.empty(n, dtype=torch.uint8, device=T.device)
+    check(_lib.load().chem_surrogate_forward(model.handle, _ptr(T), _ptr(p), _ptr(Y), Y.shape[1], n,
+                                             _ptr(ynet), _ptr(z), _ptr(box), _stream_ptr(stream)))
+    return ynet, z, box
+
+
+def surrogate_advance(model, T, p, Y, dt, rtol=1e-6, atol=1e-10, route=None, stream=None):
+    """chem_surrogate_advance: network step with FP64 fallback, in place."""
+    import torch
+    _require(T, torch.float64, "T"); _require(p, torch.float64, "p"); _require(Y, torch.float64, "Y")
+    _require(route, torch.int8, "route")
+    return check(_lib.load().chem_surrogate_advance(
+        model.handle, model.mech.handle, _ptr(T), _ptr(p), _ptr(Y), Y.shape[1], float(dt), T.numel(),
+        float(rtol), float(atol), _ptr(route), _stream_ptr(stream)))
+
+
+def gemm_bf16(A, B, bias=None, err=None, stream=None):
+    """chem_gemm_bf16: C = A @ B.T (+ bias) with A [M, K], B [N, K] BF16 (K contiguous), FP32 C."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    own_err = err is None
+    if own_err:
+        err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    check(_lib.load().chem_gemm_bf16(_ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), C.stride(0),
+                                     _ptr(bias), M, N, K, _ptr(err), _stream_ptr(stream)))
+    if own_err:
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        if int(err.item()) != 0:
+            raise ChemError(-3, "gemm pipeline wait timed out")
+    return C

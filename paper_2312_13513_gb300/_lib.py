@@ -45,6 +45,12 @@ class Options(ctypes.Structure):
                 ("max_ctas", I32)]
 
 
+class SurrogateDesc(ctypes.Structure):
+    _fields_ = [("n_species", I32), ("hidden", I32), ("dt", D), ("W", P * 5), ("b", P * 5),
+                ("x_mean", P), ("x_std", P), ("y_mean", P), ("y_std", P), ("box_lo", P),
+                ("box_hi", P)]
+
+
 # name -> (restype, argtypes); the library must export every one of them
 SIGNATURES = {
     "chem_load_mechanism": (ctypes.c_int, [ctypes.c_char_p, P]),
@@ -56,6 +62,13 @@ SIGNATURES = {
     "chem_advance_noalloc": (ctypes.c_int, [P, P, P, P, I64, D, I64, D, D, P, P, P, P]),
     "chem_eval_rhs_jac": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P]),
     "chem_fp64_fma_peak": (ctypes.c_int, [P]),
+    "chem_surrogate_create": (ctypes.c_int, [P, P, P]),
+    "chem_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, P, P]),
+    "chem_surrogate_free": (ctypes.c_int, [P]),
+    "chem_surrogate_forward": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P, P]),
+    "chem_surrogate_advance": (ctypes.c_int, [P, P, P, P, P, I64, D, I64, D, D, P, P]),
+    "chem_gemm_bf16": (ctypes.c_int, [P, I64, P, I64, P, I64, P, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, P, P]),
     "chem_last_error": (ctypes.c_char_p, []),
 }
 

@@ -1,0 +1,202 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05) for sm_103a:
+//   C[M x N] (FP32) = A[M x K] * B[N x K]^T (+ bias[N]),  A and B BF16 with K contiguous.
+//
+// Used by the surrogate's training (forward and backward products of §2's MLP, trained with
+// Adam); inference uses the fused kernel in surrogate.cu built from the same primitives.
+// One CTA computes a 128 x 128 tile: warp 0 (one lane) streams 128 x 64 tiles of A and B with TMA
+// (128-byte swizzle) through a 4-stage mbarrier ring, warp 1 (one lane) issues
+// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16) into a TMEM accumulator, and the
+// four warps read their 32 TMEM lanes back with tcgen05.ld for the epilogue.  Every wait is
+// bounded: a timeout sets a device error flag and the kernel drains and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "chem_internal.h"
+#include "sm100.h"
+
+namespace chem {
+
+using namespace sm100;
+
+// ---------------------------------------------------------------------------------------
+// tensor maps (driver entry point fetched through the runtime; no link-time libcuda)
+// ---------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+// 2D BF16 row-major matrix [rows x cols] (cols contiguous, row pitch ld elements); box
+// box_cols x box_rows with 128-byte swizzle (box_cols * 2 must be 128).
+int make_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                   int box_rows, int box_cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) { set_error("cuTensorMapEncodeTiled unavailable"); return CHEM_ECUDA; }
+  if (((uintptr_t)base & 15) || (ld * 2) % 16) {
+    set_error("TMA operand must be 16-byte aligned with a 16-byte multiple row pitch");
+    return CHEM_EINVAL;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return CHEM_ECUDA; }
+  return CHEM_OK;
+}
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int TILE_A = BM * BK * 2;              // 16 KB
+constexpr int TILE_B = BN * BK * 2;              // 16 KB
+constexpr int GEMM_SMEM = STAGES * (TILE_A + TILE_B) + 1024 + 256;
+
+struct GemmArgs {
+  float* C;
+  const float* bias;
+  int M, N, K;
+  int64_t ldc;
+  int* err;
+};
+
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const GemmArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + STAGES * TILE_A;
+  uint64_t* full = (uint64_t*)(sB + STAGES * TILE_B);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_done = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(acc_done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int nk = (a.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(acc_done, 1);
+    fence_barrier_init();
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&empty[s], ph ^ 1, a.err)) break;
+      mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
+      tma_load_2d(sA + s * TILE_A, &tmA, &full[s], kb * BK, m0);
+      tma_load_2d(sB + s * TILE_B, &tmB, &full[s], kb * BK, n0);
+      ++issued;
+    }
+    // drain: wait for the loads still in flight before the CTA may exit
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+      mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, a.err);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, a.err)) break;
+      tc_fence_after();
+      const uint32_t abase = smem_addr(sA + s * TILE_A), bbase = smem_addr(sB + s * TILE_B);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        mma_bf16(tmem, sdesc_k128(abase + kk * 32), sdesc_k128(bbase + kk * 32), idesc,
+                 (kb > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(acc_done);
+  }
+  __syncwarp();
+  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31; tcgen05.ld is warp-collective, so
+  // the warp agrees on the wait's outcome first
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_done, 0, a.err));
+  tc_fence_after();
+  const int row = m0 + warp * 32 + lane;
+  if (ok) {
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
+      tmem_ld_wait();
+      if (row < a.M) {
+        float* out = a.C + (int64_t)row * a.ldc + n0 + c0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < a.N) out[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[col] : 0.0f);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+}  // namespace
+
+int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+              const float* bias, int M, int N, int K, int* err, cudaStream_t stream) {
+  if (M < BM || N < BN || K <= 0 || !A || !B || !C || !err) {
+    set_error("gemm_bf16: bad arguments (M=%d N=%d K=%d; M and N must be >= 128)", M, N, K);
+    return CHEM_EINVAL;
+  }
+  CUtensorMap ta, tb;
+  int rc = make_tmap_bf16(&ta, A, M, K, lda, BM, BK);
+  if (rc) return rc;
+  rc = make_tmap_bf16(&tb, B, N, K, ldb, BN, BK);
+  if (rc) return rc;
+  static bool attr_set = false;
+  if (!attr_set) {
+    CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
+    attr_set = true;
+  }
+  GemmArgs g{C, bias, M, N, K, ldc, err};
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  gemm_bf16_kernel<<<grid, 128, GEMM_SMEM, stream>>>(ta, tb, g);
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+}  // namespace chem
+
+using namespace chem;
+
+extern "C" int chem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
+                              int64_t ldc, const float* bias, int M, int N, int K, int* err,
+                              chem_stream_t stream) {
+  return gemm_bf16(A, lda, B, ldb, C, ldc, bias, M, N, K, err, (cudaStream_t)stream);
+}

@@ -1,0 +1,661 @@
+// BF16 MLP surrogate of the chemistry step (the paper's DNN chemistry, §2 / §3.1) on sm_103a.
+//
+// Network: x = z-scored [T, ln p, BC(Y_1..Y_ns)] (BC = Box-Cox, lambda = 0.1) -> 512 -> 512 ->
+// 512 -> 512 -> ns, GELU (exact erf form) after each hidden layer, BF16 weights and activations,
+// FP32 accumulation.  Outputs are z-scored increments of BC(Y) over the training step dt.
+//
+// surrogate_forward_kernel (persistent, one CTA per SM, 6 warps):
+//   warps 0-3  per 128-cell tile: build the input tile (FP64 state -> features -> BF16, written
+//              straight into shared memory in the 128-byte swizzled K-major layout the MMA reads),
+//              then after every layer read the FP32 accumulator from TMEM (tcgen05.ld), add the
+//              bias, apply GELU, round to BF16 and write the next layer's input tile in place;
+//              after the last layer apply the inverse transform (de-normalise, add to BC(Y0),
+//              invert Box-Cox) and write Y' (FP32).  The trust-region test (training box) is
+//              done on the features.
+//   warp 4     one lane streams weight tiles (256 x 64 BF16, 32 KB) with TMA into a 3-stage ring.
+//   warp 5     one lane issues tcgen05.mma (M = 128, N = 256 or 16, K = 16) into 512 TMEM columns.
+// surrogate_post_kernel (FP64, one thread per cell): element-conservation projection, clip,
+//   temperature from enthalpy by Newton (the paper's Thermo class, §3.1), acceptance tests, and
+//   compaction of rejected cells into a fallback list that the FP64 integrator then advances
+//   (indexed mode, count read from device memory).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <vector>
+
+#include "chem_internal.h"
+#include "sm100.h"
+
+namespace chem {
+
+using namespace sm100;
+
+int make_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                   int box_rows, int box_cols);
+
+constexpr int TM = 128;            // cells per tile
+constexpr int HID = 512;           // hidden width
+constexpr int KIN = 64;            // padded input width (one 128-byte K chunk)
+constexpr int NOUT = 16;           // padded output width
+constexpr int MAXNS = 16;          // outputs supported
+constexpr int WSTAGES = 3;
+constexpr int WSTAGE_BYTES = 256 * 64 * 2;
+constexpr int ACT_CHUNK = TM * 128;                  // 16 KB: 128 rows x 64 bf16
+constexpr int ACT_BYTES = 8 * ACT_CHUNK;             // 128 KB
+constexpr int FWD_SMEM = ACT_BYTES + WSTAGES * WSTAGE_BYTES + 1024 + 256;
+constexpr float BC_LAMBDA = 0.1f;
+
+struct SurParams {
+  const float* bias[5];
+  const float *xmu, *xsd, *ymu, *ysd, *lo, *hi;
+  int ns, nin;
+  const double* T;
+  const double* p;
+  const double* Y;
+  int64_t ld, ncells;
+  float* ynet;          // [ns][ncells]
+  float* zout;          // [ns][ncells] raw network output (nullable)
+  uint8_t* outbox;      // [ncells] 1 = features outside the training box
+  int* err;
+};
+
+__device__ __forceinline__ float gelu_f(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// the per-tile chunk schedule shared by the producer and the MMA issuer
+// layer 0: 2 chunks (rows 0-255, 256-511 of W1, K = 64); layers 1-3: 8 K-chunks x 2 halves;
+// layer 4: 8 K-chunks of W5 (16 rows)
+constexpr int CHUNKS_PER_TILE = 2 + 3 * 16 + 8;
+
+__global__ void __launch_bounds__(192, 1)
+    surrogate_forward_kernel(const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
+                             const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4,
+                             const __grid_constant__ CUtensorMap tW5, const SurParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* act = smem;
+  unsigned char* wst = smem + ACT_BYTES;
+  uint64_t* full = (uint64_t*)(wst + WSTAGES * WSTAGE_BYTES);
+  uint64_t* empty = full + WSTAGES;
+  uint64_t* acc_done = empty + WSTAGES;
+  uint64_t* act_ready = acc_done + 1;
+  uint32_t* tmem_slot = (uint32_t*)(act_ready + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long ntiles = (P.ncells + TM - 1) / TM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < WSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(acc_done, 1);
+    mbar_init(act_ready, 128);
+    fence_barrier_init();
+  }
+  if (warp == 4) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      prefetch_tmap(&tW1); prefetch_tmap(&tW2); prefetch_tmap(&tW3); prefetch_tmap(&tW4); prefetch_tmap(&tW5);
+      long long it = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int c = 0; c < CHUNKS_PER_TILE; ++c, ++it) {
+          const int s = (int)(it % WSTAGES);
+          if (!mbar_wait(&empty[s], (uint32_t)((it / WSTAGES) & 1) ^ 1u, P.err)) { ok = false; break; }
+          unsigned char* dst = wst + s * WSTAGE_BYTES;
+          if (c < 2) {
+            mbar_arrive_expect_tx(&full[s], WSTAGE_BYTES);
+            tma_load_2d(dst, &tW1, &full[s], 0, c * 256);
+          } else if (c < 2 + 48) {
+            const int l = (c - 2) / 16, r = (c - 2) % 16, kc = r / 2, nh = r % 2;
+            const CUtensorMap* tm = l == 0 ? &tW2 : (l == 1 ? &tW3 : &tW4);
+            mbar_arrive_expect_tx(&full[s], WSTAGE_BYTES);
+            tma_load_2d(dst, tm, &full[s], kc * 64, nh * 256);
+          } else {
+            const int kc = c - 50;
+            mbar_arrive_expect_tx(&full[s], NOUT * 128);
+            tma_load_2d(dst, &tW5, &full[s], kc * 64, 0);
+          }
+        }
+      }
+      // drain loads still in flight
+      const long long first = it > WSTAGES ? it - WSTAGES : 0;
+      for (long long k = first; k < it; ++k) mbar_wait(&full[k % WSTAGES], (uint32_t)((k / WSTAGES) & 1), P.err);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr uint32_t id256 = idesc_bf16_f32(128, 256);
+      constexpr uint32_t id16 = idesc_bf16_f32(128, NOUT);
+      long long it = 0, nready = 0;
+      bool ok = true;
+      const uint32_t abase = smem_addr(act);
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int c = 0;
+        for (int l = 0; l < 5 && ok; ++l) {
+          if (!mbar_wait(act_ready, (uint32_t)(nready & 1), P.err)) { ok = false; break; }
+          ++nready;
+          tc_fence_after();
+          const int nchunks = l == 0 ? 2 : (l < 4 ? 16 : 8);
+          for (int i = 0; i < nchunks; ++i, ++c, ++it) {
+            const int s = (int)(it % WSTAGES);
+            if (!mbar_wait(&full[s], (uint32_t)((it / WSTAGES) & 1), P.err)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t bbase = smem_addr(wst + s * WSTAGE_BYTES);
+            int kc, nh;
+            if (l == 0) { kc = 0; nh = i; }
+            else if (l < 4) { kc = i / 2; nh = i % 2; }
+            else { kc = i; nh = 0; }
+            const uint32_t d = tmem + (l < 4 ? nh * 256 : 0);
+            const uint32_t idesc = l < 4 ? id256 : id16;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_bf16(d, sdesc_k128(abase + kc * ACT_CHUNK + kk * 32), sdesc_k128(bbase + kk * 32), idesc,
+                       (kc > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+          }
+          if (ok) mma_commit(acc_done);
+        }
+      }
+    }
+  } else {
+    // ---------------- feature / epilogue warps 0-3: row r = TMEM lane r ----------------
+    const int r = warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    unsigned char* arow = act + r * 128;        // row r inside each 16 KB chunk
+    long long nacc = 0;
+    bool ok = true;
+    float bc0[MAXNS];
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const long long cell = tile * TM + r;
+      const bool valid = cell < P.ncells;
+      // ---- input features ----
+      float x[KIN];
+#pragma unroll
+      for (int i = 0; i < KIN; ++i) x[i] = 0.0f;
+      if (valid) {
+        bool outside = false;
+        float f[2 + MAXNS];
+        f[0] = (float)P.T[cell];
+        f[1] = (float)log(P.p[cell]);
+        for (int k = 0; k < P.ns; ++k) {
+          const double yk = P.Y[(int64_t)k * P.ld + cell];
+          const float yf = fmaxf((float)yk, 0.0f);
+          bc0[k] = (powf(yf, BC_LAMBDA) - 1.0f) / BC_LAMBDA;
+          f[2 + k] = bc0[k];
+        }
+        for (int i = 0; i < P.nin; ++i) {
+          if (!(f[i] >= P.lo[i] && f[i] <= P.hi[i])) outside = true;
+          x[i] = (f[i] - P.xmu[i]) / P.xsd[i];
+        }
+        P.outbox[cell] = outside ? 1 : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        uint4 v;
+        v.x = pack_bf16(x[8 * u + 0], x[8 * u + 1]);
+        v.y = pack_bf16(x[8 * u + 2], x[8 * u + 3]);
+        v.z = pack_bf16(x[8 * u + 4], x[8 * u + 5]);
+        v.w = pack_bf16(x[8 * u + 6], x[8 * u + 7]);
+        *reinterpret_cast<uint4*>(arow + ((u ^ (r & 7)) << 4)) = v;
+      }
+      fence_async_smem();
+      mbar_arrive(act_ready);
+      // ---- hidden layers ----
+      for (int l = 0; l < 4; ++l) {
+        // tcgen05.ld is warp-collective: the warp agrees on the wait's outcome
+        if (!__all_sync(0xffffffffu, mbar_wait(acc_done, (uint32_t)(nacc & 1), P.err))) { ok = false; break; }
+        ++nacc;
+        tc_fence_after();
+        const float* bias = P.bias[l];
+        for (int cc = 0; cc < HID / 32; ++cc) {
+          uint32_t a[32];
+          tmem_ld32(trow + cc * 32, a);
+          tmem_ld_wait();
+          unsigned char* chunk = arow + (cc >> 1) * ACT_CHUNK;
+          const int u0 = (cc & 1) * 4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = gelu_f(__uint_as_float(a[8 * q + e]) + __ldg(bias + cc * 32 + 8 * q + e));
+            uint4 pk;
+            pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
+            pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
+            *reinterpret_cast<uint4*>(chunk + (((u0 + q) ^ (r & 7)) << 4)) = pk;
+          }
+        }
+        tc_fence_before();
+        fence_async_smem();
+        mbar_arrive(act_ready);
+      }
+      if (!ok) break;
+      // ---- output layer and inverse transform ----
+      if (!__all_sync(0xffffffffu, mbar_wait(acc_done, (uint32_t)(nacc & 1), P.err))) { ok = false; break; }
+      ++nacc;
+      tc_fence_after();
+      uint32_t o[16];
+      tmem_ld16(trow, o);
+      tmem_ld_wait();
+      tc_fence_before();
+      if (valid) {
+        for (int k = 0; k < P.ns; ++k) {
+          const float z = __uint_as_float(o[k]) + __ldg(P.bias[4] + k);
+          if (P.zout) P.zout[(int64_t)k * P.ncells + cell] = z;
+          const float d = z * P.ysd[k] + P.ymu[k];
+          const float b1 = bc0[k] + d;
+          P.ynet[(int64_t)k * P.ncells + cell] = powf(fmaxf(1.0f + BC_LAMBDA * b1, 0.0f), 1.0f / BC_LAMBDA);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 4) tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 post-processing
+// ---------------------------------------------------------------------------------------
+constexpr int NEMAX = 8;
+
+struct PostParams {
+  const unsigned char* blob;   // mechanism blob (global memory)
+  MechLayout lay;
+  const double* Aem;           // [ne][ns] element mass fractions a_ek M_e / W_k
+  int ne;
+  double* T;
+  const double* p;
+  double* Y;
+  int64_t ld, ncells;
+  const float* ynet;
+  const uint8_t* outbox;
+  int8_t* route;
+  int32_t* fb_idx;
+  unsigned int* fb_count;
+};
+
+__device__ __forceinline__ void h_cp_mass(const unsigned char* blob, const MechLayout& L, double T,
+                                          const double* Y, int ld, int64_t cell, const double* Yloc,
+                                          double* h, double* cp) {
+  const int ns = L.ns;
+  const int rg = T < TMID ? 0 : 1;
+  const double* hc = (const double*)(blob + L.o_hc);
+  const double* cc = (const double*)(blob + L.o_cpc);
+  const double* invW = (const double*)(blob + L.o_invW);
+  const double invT = 1.0 / T;
+  double hs = 0.0, cs = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    const double* a = hc + (rg * ns + k) * 6;
+    const double* c = cc + (rg * ns + k) * 5;
+    const double hRT = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4]))) + a[5] * invT;
+    const double cpR = c[0] + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4])));
+    const double yk = Yloc ? Yloc[k] : Y[(int64_t)k * ld + cell];
+    hs += yk * hRT * __ldg(invW + k);
+    cs += yk * cpR * __ldg(invW + k);
+  }
+  *h = RU * T * hs;
+  *cp = RU * cs;
+}
+
+__global__ void surrogate_post_kernel(const PostParams P) {
+  const int ns = P.lay.ns;
+  for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < P.ncells;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    bool pass = P.outbox[cell] == 0;
+    double Y0[MAXNS], Y1[MAXNS];
+    double T0 = P.T[cell];
+    for (int k = 0; k < ns; ++k) {
+      Y0[k] = P.Y[(int64_t)k * P.ld + cell];
+      Y1[k] = (double)P.ynet[(int64_t)k * P.ncells + cell];
+      if (!isfinite(Y1[k])) pass = false;
+    }
+    double Tn = T0;
+    if (pass) {
+      // element-conservation projection: Y'' = Y' - D A^T (A D A^T)^-1 (A Y' - b)
+      const int ne = P.ne;
+      double b[NEMAX], rr[NEMAX], G[NEMAX][NEMAX], lam[NEMAX];
+      for (int e = 0; e < ne; ++e) {
+        double sb = 0.0, sr = 0.0;
+        for (int k = 0; k < ns; ++k) {
+          const double a = P.Aem[e * ns + k];
+          sb += a * Y0[k];
+          sr += a * Y1[k];
+        }
+        b[e] = sb;
+        rr[e] = sr - sb;
+      }
+      for (int e = 0; e < ne; ++e)
+        for (int f = 0; f <= e; ++f) {
+          double s = 0.0;
+          for (int k = 0; k < ns; ++k) s += P.Aem[e * ns + k] * (Y1[k] + 1e-12) * P.Aem[f * ns + k];
+          G[e][f] = s;
+          G[f][e] = s;
+        }
+      // Gaussian elimination with partial pivoting on the small SPD system
+      for (int e = 0; e < ne; ++e) lam[e] = rr[e];
+      for (int k = 0; k < ne; ++k) {
+        int pr = k;
+        for (int i = k + 1; i < ne; ++i)
+          if (fabs(G[i][k]) > fabs(G[pr][k])) pr = i;
+        if (G[pr][k] == 0.0) { pass = false; break; }
+        if (pr != k) {
+          for (int j = 0; j < ne; ++j) { const double t = G[k][j]; G[k][j] = G[pr][j]; G[pr][j] = t; }
+          const double t = lam[k]; lam[k] = lam[pr]; lam[pr] = t;
+        }
+        for (int i = k + 1; i < ne; ++i) {
+          const double l = G[i][k] / G[k][k];
+          for (int j = k; j < ne; ++j) G[i][j] -= l * G[k][j];
+          lam[i] -= l * lam[k];
+        }
+      }
+      if (pass) {
+        for (int i = ne - 1; i >= 0; --i) {
+          double s = lam[i];
+          for (int j = i + 1; j < ne; ++j) s -= G[i][j] * lam[j];
+          lam[i] = s / G[i][i];
+        }
+        double s0 = 0.0, s1 = 0.0;
+        for (int k = 0; k < ns; ++k) {
+          double c = 0.0;
+          for (int e = 0; e < ne; ++e) c += P.Aem[e * ns + k] * lam[e];
+          Y1[k] = fmax(Y1[k] - (Y1[k] + 1e-12) * c, 0.0);
+          s0 += Y0[k];
+          s1 += Y1[k];
+        }
+        double res = 0.0;
+        for (int e = 0; e < ne; ++e) {
+          double s = 0.0;
+          for (int k = 0; k < ns; ++k) s += P.Aem[e * ns + k] * Y1[k];
+          res = fmax(res, fabs(s - b[e]));
+        }
+        if (!(res <= 1e-9) || !(fabs(s1 - s0) <= 1e-9)) pass = false;
+      }
+      if (pass) {
+        // temperature from enthalpy conservation: h(T, Y'') = h(T0, Y0)
+        double h0, cp0;
+        h_cp_mass(P.blob, P.lay, T0, P.Y, (int)0, cell, Y0, &h0, &cp0);
+        bool conv = false;
+        for (int it = 0; it < 50; ++it) {
+          double hh, cp;
+          h_cp_mass(P.blob, P.lay, Tn, P.Y, 0, cell, Y1, &hh, &cp);
+          const double dT = (hh - h0) / cp;
+          Tn -= dT;
+          if (!(Tn >= 200.0 && Tn <= 6000.0)) break;
+          if (fabs(dT) < 1e-9 * Tn) { conv = true; break; }
+        }
+        if (!conv) pass = false;
+      }
+    }
+    if (pass) {
+      P.T[cell] = Tn;
+      for (int k = 0; k < ns; ++k) P.Y[(int64_t)k * P.ld + cell] = Y1[k];
+    } else {
+      const unsigned slot = atomicAdd(P.fb_count, 1u);
+      P.fb_idx[slot] = (int32_t)cell;
+    }
+    if (P.route) P.route[cell] = pass ? 0 : 1;
+  }
+}
+
+}  // namespace chem
+
+// ---------------------------------------------------------------------------------------
+// model object and entry points
+// ---------------------------------------------------------------------------------------
+struct chem_model_s {
+  int ns = 0, nin = 0, ne = 0;
+  double dt = 0.0;
+  int device = 0;
+  void* d_w = nullptr;       // all BF16 weights
+  void* d_f = nullptr;       // FP32 biases and statistics
+  double* d_A = nullptr;     // element mass-fraction matrix
+  const float* bias[5] = {};
+  const float *xmu = nullptr, *xsd = nullptr, *ymu = nullptr, *ysd = nullptr, *lo = nullptr, *hi = nullptr;
+  CUtensorMap tw[5];
+};
+
+namespace chem {
+
+static uint16_t f2bf(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  const uint32_t bias = ((u >> 16) & 1u) + 0x7fffu;
+  return (uint16_t)((u + bias) >> 16);
+}
+
+int surrogate_forward(chem_model_s* md, const double* T, const double* p, const double* Y, int64_t ld,
+                      int64_t ncells, float* ynet, float* zout, uint8_t* outbox, int* err,
+                      cudaStream_t stream) {
+  static bool attr = false;
+  if (!attr) {
+    CHEM_CUDA_TRY(cudaFuncSetAttribute(surrogate_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       FWD_SMEM));
+    attr = true;
+  }
+  SurParams P;
+  for (int l = 0; l < 5; ++l) P.bias[l] = md->bias[l];
+  P.xmu = md->xmu; P.xsd = md->xsd; P.ymu = md->ymu; P.ysd = md->ysd; P.lo = md->lo; P.hi = md->hi;
+  P.ns = md->ns; P.nin = md->nin; P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells;
+  P.ynet = ynet; P.zout = zout; P.outbox = outbox; P.err = err;
+  int dev = 0, sms = 0;
+  CHEM_CUDA_TRY(cudaGetDevice(&dev));
+  CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long ntiles = (ncells + TM - 1) / TM;
+  const int grid = (int)std::min<long long>(ntiles, sms);
+  surrogate_forward_kernel<<<grid, 192, FWD_SMEM, stream>>>(md->tw[0], md->tw[1], md->tw[2], md->tw[3],
+                                                            md->tw[4], P);
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+int launch_advance_counted(chem_mech_s* m, double* T, const double* p, double* Y, int64_t ld,
+                           double dt, int64_t capacity, const unsigned int* count_dev, double rtol,
+                           double atol, const int32_t* idx, cudaStream_t stream);
+
+}  // namespace chem
+
+using namespace chem;
+
+extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t mech, chem_model_t* out) {
+  if (!d || !mech || !out) { set_error("NULL argument"); return CHEM_EINVAL; }
+  *out = nullptr;
+  const int ns = d->n_species, nin = ns + 2;
+  if (ns != mech->ns || ns < 1 || ns > MAXNS || d->hidden != HID || nin > KIN || mech->ne > NEMAX) {
+    set_error("surrogate shape unsupported (ns=%d, mechanism ns=%d, hidden=%d, ne=%d)", ns, mech->ns,
+              d->hidden, mech->ne);
+    return CHEM_EINVAL;
+  }
+  if (!(d->dt > 0.0)) { set_error("surrogate dt must be positive"); return CHEM_EINVAL; }
+  for (int l = 0; l < 5; ++l)
+    if (!d->W[l] || !d->b[l]) { set_error("NULL weight or bias"); return CHEM_EINVAL; }
+  if (!d->x_mean || !d->x_std || !d->y_mean || !d->y_std || !d->box_lo || !d->box_hi) {
+    set_error("NULL normalisation statistics");
+    return CHEM_EINVAL;
+  }
+  chem_model_s* md = new chem_model_s();
+  md->ns = ns; md->nin = nin; md->ne = mech->ne; md->dt = d->dt;
+  // BF16 weights, zero padded: W1 [512 x 64], W2..W4 [512 x 512], W5 [16 x 512]
+  const size_t n1 = (size_t)HID * KIN, nh = (size_t)HID * HID, n5 = (size_t)NOUT * HID;
+  std::vector<uint16_t> wb(n1 + 3 * nh + n5, 0);
+  for (int o = 0; o < HID; ++o)
+    for (int i = 0; i < nin; ++i) wb[(size_t)o * KIN + i] = f2bf(d->W[0][(size_t)o * nin + i]);
+  for (int l = 1; l < 4; ++l)
+    for (size_t e = 0; e < nh; ++e) wb[n1 + (l - 1) * nh + e] = f2bf(d->W[l][e]);
+  for (int o = 0; o < ns; ++o)
+    for (int i = 0; i < HID; ++i) wb[n1 + 3 * nh + (size_t)o * HID + i] = f2bf(d->W[4][(size_t)o * HID + i]);
+  // FP32: 4 hidden biases, padded output bias, statistics
+  std::vector<float> fb(4 * HID + NOUT + 6 * KIN, 0.0f);
+  for (int l = 0; l < 4; ++l) memcpy(&fb[l * HID], d->b[l], HID * sizeof(float));
+  memcpy(&fb[4 * HID], d->b[4], ns * sizeof(float));
+  float* st = &fb[4 * HID + NOUT];
+  for (int i = 0; i < nin; ++i) {
+    st[i] = d->x_mean[i];
+    st[KIN + i] = d->x_std[i] > 0.0f ? d->x_std[i] : 1.0f;
+    st[4 * KIN + i] = d->box_lo[i];
+    st[5 * KIN + i] = d->box_hi[i];
+  }
+  for (int k = 0; k < ns; ++k) {
+    st[2 * KIN + k] = d->y_mean[k];
+    st[3 * KIN + k] = d->y_std[k];
+  }
+  std::vector<double> A((size_t)mech->ne * ns);
+  for (int e = 0; e < mech->ne; ++e)
+    for (int k = 0; k < ns; ++k)
+      A[(size_t)e * ns + k] = mech->comp[(size_t)k * mech->ne + e] * mech->elem_mass[e] / mech->W[k];
+  auto fail = [&](int rc) { chem_surrogate_free(md); return rc; };
+  if (cudaGetDevice(&md->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaGetDevice"));
+  cudaError_t e1 = cudaMalloc(&md->d_w, wb.size() * 2);
+  cudaError_t e2 = cudaMalloc(&md->d_f, fb.size() * 4);
+  cudaError_t e3 = cudaMalloc((void**)&md->d_A, A.size() * 8);
+  if (e1 || e2 || e3) return fail(cuda_fail(e1 ? e1 : (e2 ? e2 : e3), "cudaMalloc(surrogate)"));
+  if (cudaMemcpy(md->d_w, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(md->d_f, fb.data(), fb.size() * 4, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(md->d_A, A.data(), A.size() * 8, cudaMemcpyHostToDevice))
+    return fail(cuda_fail(cudaGetLastError(), "cudaMemcpy(surrogate)"));
+  const uint16_t* w = (const uint16_t*)md->d_w;
+  const float* f = (const float*)md->d_f;
+  for (int l = 0; l < 4; ++l) md->bias[l] = f + l * HID;
+  md->bias[4] = f + 4 * HID;
+  const float* sd = f + 4 * HID + NOUT;
+  md->xmu = sd; md->xsd = sd + KIN; md->ymu = sd + 2 * KIN; md->ysd = sd + 3 * KIN;
+  md->lo = sd + 4 * KIN; md->hi = sd + 5 * KIN;
+  int rc = make_tmap_bf16(&md->tw[0], w, HID, KIN, KIN, 256, 64);
+  for (int l = 1; l < 4 && !rc; ++l) rc = make_tmap_bf16(&md->tw[l], w + n1 + (l - 1) * nh, HID, HID, HID, 256, 64);
+  if (!rc) rc = make_tmap_bf16(&md->tw[4], w + n1 + 3 * nh, NOUT, HID, HID, NOUT, 64);
+  if (rc) return fail(rc);
+  *out = md;
+  return CHEM_OK;
+}
+
+extern "C" int chem_surrogate_load(const char* path, chem_mech_t mech, chem_model_t* out) {
+  if (!path || !mech || !out) { set_error("NULL argument"); return CHEM_EINVAL; }
+  std::ifstream f(path, std::ios::binary);
+  if (!f) { set_error("cannot open %s", path); return CHEM_ENOTFOUND; }
+  char magic[8];
+  int32_t ns = 0, hid = 0;
+  double dt = 0.0;
+  f.read(magic, 8);
+  f.read((char*)&ns, 4);
+  f.read((char*)&hid, 4);
+  f.read((char*)&dt, 8);
+  if (!f || memcmp(magic, "CHEMSUR1", 8) != 0 || ns < 1 || ns > MAXNS || hid != HID) {
+    set_error("%s: not a surrogate model file", path);
+    return CHEM_EINVAL;
+  }
+  const int nin = ns + 2;
+  const size_t sizes[5] = {(size_t)HID * nin, (size_t)HID * HID, (size_t)HID * HID, (size_t)HID * HID,
+                           (size_t)ns * HID};
+  const size_t bsz[5] = {HID, HID, HID, HID, (size_t)ns};
+  std::vector<float> W[5], b[5], xm(nin), xs(nin), ym(ns), ys(ns), lo(nin), hi(nin);
+  for (int l = 0; l < 5; ++l) {
+    W[l].resize(sizes[l]);
+    b[l].resize(bsz[l]);
+    f.read((char*)W[l].data(), sizes[l] * 4);
+    f.read((char*)b[l].data(), bsz[l] * 4);
+  }
+  f.read((char*)xm.data(), nin * 4); f.read((char*)xs.data(), nin * 4);
+  f.read((char*)ym.data(), ns * 4); f.read((char*)ys.data(), ns * 4);
+  f.read((char*)lo.data(), nin * 4); f.read((char*)hi.data(), nin * 4);
+  if (!f) { set_error("%s: truncated surrogate model file", path); return CHEM_EINVAL; }
+  chem_surrogate_desc d{};
+  d.n_species = ns; d.hidden = hid; d.dt = dt;
+  for (int l = 0; l < 5; ++l) { d.W[l] = W[l].data(); d.b[l] = b[l].data(); }
+  d.x_mean = xm.data(); d.x_std = xs.data(); d.y_mean = ym.data(); d.y_std = ys.data();
+  d.box_lo = lo.data(); d.box_hi = hi.data();
+  return chem_surrogate_create(&d, mech, out);
+}
+
+extern "C" int chem_surrogate_free(chem_model_t md) {
+  if (!md) { set_error("NULL model"); return CHEM_EINVAL; }
+  if (md->d_w) cudaFree(md->d_w);
+  if (md->d_f) cudaFree(md->d_f);
+  if (md->d_A) cudaFree(md->d_A);
+  delete md;
+  return CHEM_OK;
+}
+
+extern "C" int chem_surrogate_forward(chem_model_t md, const double* T, const double* p, const double* Y,
+                                      int64_t ld, int64_t ncells, float* ynet, float* zout,
+                                      uint8_t* out_of_box, chem_stream_t stream) {
+  if (!md) { set_error("NULL model"); return CHEM_EINVAL; }
+  if (ncells < 0 || ld < ncells) { set_error("bad ncells / ld"); return CHEM_EINVAL; }
+  if (ncells == 0) return CHEM_OK;
+  if (!T || !p || !Y || !ynet || !out_of_box) { set_error("NULL pointer"); return CHEM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  CHEM_CUDA_TRY(cudaMallocAsync((void**)&err, sizeof(int), st));
+  CHEM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  int rc = surrogate_forward(md, T, p, Y, ld, ncells, ynet, zout, out_of_box, err, st);
+  int herr = 0;
+  if (!rc) {
+    // the timeout flag is checked once the stream reaches this point
+    CHEM_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CHEM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  cudaFreeAsync(err, st);
+  if (rc) return rc;
+  if (herr) { set_error("surrogate forward kernel: a pipeline wait timed out"); return CHEM_ECUDA; }
+  return CHEM_OK;
+}
+
+extern "C" int chem_surrogate_advance(chem_model_t md, chem_mech_t mech, double* T, const double* p,
+                                      double* Y, int64_t ld, double dt, int64_t ncells, double rtol,
+                                      double atol, int8_t* route_out, chem_stream_t stream) {
+  if (!md || !mech) { set_error("NULL model or mechanism"); return CHEM_EINVAL; }
+  if (md->ns != mech->ns) { set_error("model and mechanism disagree on the species count"); return CHEM_EINVAL; }
+  if (ncells < 0 || ld < ncells || !(rtol > 0.0) || !(atol > 0.0)) { set_error("bad arguments"); return CHEM_EINVAL; }
+  if (!(fabs(dt - md->dt) <= 1e-12 * md->dt)) {
+    set_error("dt %g differs from the surrogate's training step %g", dt, md->dt);
+    return CHEM_EINVAL;
+  }
+  if (ncells == 0) return CHEM_OK;
+  if (!T || !p || !Y) { set_error("NULL state pointer"); return CHEM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  // per-call temporaries from the stream-ordered allocator: net output, box flags, fallback list
+  const size_t b_ynet = (size_t)ncells * md->ns * 4, b_box = ((size_t)ncells + 15) & ~(size_t)15;
+  const size_t b_idx = (size_t)ncells * 4;
+  unsigned char* ws = nullptr;
+  CHEM_CUDA_TRY(cudaMallocAsync((void**)&ws, b_ynet + b_box + b_idx + 64, st));
+  float* ynet = (float*)ws;
+  uint8_t* box = ws + b_ynet;
+  int32_t* fb_idx = (int32_t*)(ws + b_ynet + b_box);
+  unsigned int* fb_count = (unsigned int*)(ws + b_ynet + b_box + b_idx);
+  int* err = (int*)(fb_count + 4);
+  CHEM_CUDA_TRY(cudaMemsetAsync(fb_count, 0, 64, st));
+  int rc = surrogate_forward(md, T, p, Y, ld, ncells, ynet, nullptr, box, err, st);
+  if (!rc) {
+    PostParams Q;
+    Q.blob = (const unsigned char*)mech->d_blob; Q.lay = mech->lay; Q.Aem = md->d_A; Q.ne = md->ne;
+    Q.T = T; Q.p = p; Q.Y = Y; Q.ld = ld; Q.ncells = ncells; Q.ynet = ynet; Q.outbox = box;
+    Q.route = route_out; Q.fb_idx = fb_idx; Q.fb_count = fb_count;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long blocks = std::min<long long>((ncells + 255) / 256, (long long)sms * 16);
+    surrogate_post_kernel<<<(unsigned)blocks, 256, 0, st>>>(Q);
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) rc = cuda_fail(le, "surrogate_post_kernel");
+  }
+  if (!rc)
+    rc = launch_advance_counted(mech, T, p, Y, ld, dt, ncells, fb_count, rtol, atol, fb_idx, st);
+  cudaError_t fe = cudaFreeAsync(ws, st);
+  if (rc) return rc;
+  CHEM_CUDA_TRY(fe);
+  return CHEM_OK;
+}
