@@ -196,6 +196,42 @@ int chem_surrogate_advance(chem_model_t model, chem_mech_t m, double* T, const d
 int chem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                    const float* bias, int M, int N, int K, int* err, chem_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Surrogate training on the GPU (§2: GELU networks trained with Adam).  A trainer holds FP32
+ * master weights, Adam moments and BF16 copies of a n_in -> 512 x 4 -> n_out GELU network;
+ * every product runs on the tcgen05 GEMM.  Layout: X is BF16 [batch x 128] (features zero
+ * padded to 128 columns), targets FP32 [batch x n_out], all device pointers.
+ * ------------------------------------------------------------------------------------- */
+typedef struct chem_trainer_s* chem_trainer_t;
+
+/* W_init / b_init: host arrays [5] of row-major [out x in] weights and [out] biases, or NULL for
+ * a seeded Gaussian initialisation (std 1/sqrt(fan_in), zero biases).  batch: multiple of 128. */
+int chem_mlp_trainer_create(int n_in, int n_out, int batch, const float* const* W_init,
+                            const float* const* b_init, uint64_t seed, chem_trainer_t* out);
+int chem_mlp_trainer_free(chem_trainer_t t);
+/* forward pass of one batch, keeping the activations; out (nullable) receives [batch x n_out] */
+int chem_mlp_forward(chem_trainer_t t, const void* X, float* out, chem_stream_t stream);
+/* mean-squared-error gradients of the last forward pass; loss (device double, nullable) */
+int chem_mlp_backward(chem_trainer_t t, const float* target, double* loss, chem_stream_t stream);
+/* one Adam update (bias-corrected) of all parameters with the last gradients */
+int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float beta2, float eps,
+                       chem_stream_t stream);
+/* host copy of the parameters (which = 0) or of the last gradients (which = 1); W[l], b[l] are
+ * host arrays of the unpadded shapes (any may be NULL); synchronises the device */
+int chem_mlp_trainer_get(chem_trainer_t t, int which, float* const* W, float* const* b);
+
+/* Training data: raw features x [n x (ns + 2)] = [T, ln p, BC(Y0)] and targets
+ * t [n x ns] = BC(Y1) - BC(Y0) from states before (T0, p, Y0) and after (Y1) a step. */
+int chem_train_features(const double* T0, const double* p, const double* Y0, const double* Y1,
+                        int64_t ld, int64_t n, int ns, float* x_raw, float* t_raw,
+                        chem_stream_t stream);
+/* stats[4 x c] (device doubles): column sums, sums of squares, minima, maxima of A [n x c] */
+int chem_column_stats(const float* A, int64_t n, int c, double* stats, chem_stream_t stream);
+/* X = bf16((x - mean) / sd) zero padded to ldx columns; Tn = (t - tmean) / tsd (t nullable) */
+int chem_train_normalize(const float* x, int64_t n, int c, const float* mean, const float* sd,
+                         void* X, int ldx, const float* t, int ct, const float* tmean,
+                         const float* tsd, float* Tn, chem_stream_t stream);
+
 /* Measured FP64 FMA throughput of the current device (TFLOP/s, 2 flops per FMA) from a
  * register-resident FMA chain kernel; synchronous. */
 int chem_fp64_fma_peak(double* tflops);

@@ -67,6 +67,18 @@ SIGNATURES = {
     "chem_surrogate_free": (ctypes.c_int, [P]),
     "chem_surrogate_forward": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P, P]),
     "chem_surrogate_advance": (ctypes.c_int, [P, P, P, P, P, I64, D, I64, D, D, P, P]),
+    "chem_mlp_trainer_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
+                                               ctypes.c_uint64, P]),
+    "chem_mlp_trainer_free": (ctypes.c_int, [P]),
+    "chem_mlp_forward": (ctypes.c_int, [P, P, P, P]),
+    "chem_mlp_backward": (ctypes.c_int, [P, P, P, P]),
+    "chem_mlp_adam_step": (ctypes.c_int, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                          ctypes.c_float, P]),
+    "chem_mlp_trainer_get": (ctypes.c_int, [P, ctypes.c_int, P, P]),
+    "chem_train_features": (ctypes.c_int, [P, P, P, P, I64, I64, ctypes.c_int, P, P, P]),
+    "chem_column_stats": (ctypes.c_int, [P, I64, ctypes.c_int, P, P]),
+    "chem_train_normalize": (ctypes.c_int, [P, I64, ctypes.c_int, P, P, P, ctypes.c_int, P,
+                                            ctypes.c_int, P, P, P, P]),
     "chem_gemm_bf16": (ctypes.c_int, [P, I64, P, I64, P, I64, P, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, P, P]),
     "chem_last_error": (ctypes.c_char_p, []),

@@ -1,0 +1,432 @@
+// Training of the BF16 MLP surrogate on the GPU (§2: the paper's networks use GELU and are
+// trained with Adam).  Every product runs on the tcgen05 GEMM (gemm.cu); the rest are small
+// elementwise / reduction kernels here.
+//
+// Layer l maps in_pad[l] -> out_pad[l] features; training pads the input to 128 columns and the
+// output layer to 128 rows so that every GEMM dimension is at least one 128-wide tile (padding is
+// zero and stays zero: its gradients vanish).  Per step, with batch B:
+//   forward   Z_l = A_l W_l^T + b_l (FP32), A_{l+1} = bf16(GELU(Z_l))
+//   loss      L = mean over B x n_out of (Z_4 - target)^2,  dZ_4 = 2 (Z_4 - target) / (B n_out)
+//   backward  dW_l = dZ_l^T A_l,  db_l = sum_b dZ_l,  dA_{l-1} = dZ_l W_l,
+//             dZ_{l-1} = dA_{l-1} * GELU'(Z_{l-1})
+//   Adam      FP32 master weights with bias correction (Kingma & Ba), then BF16 copies of W and
+//             W^T for the next step's products.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "chem_internal.h"
+
+namespace chem {
+int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+              const float* bias, int M, int N, int K, int* err, cudaStream_t stream);
+}
+
+using namespace chem;
+
+namespace {
+
+constexpr int HID = 512;
+constexpr int PADIO = 128;
+constexpr int NL = 5;
+
+__device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float v) {
+  return 0.5f * (1.0f + erff(v * 0.70710678118654752f)) + v * 0.3989422804014327f * expf(-0.5f * v * v);
+}
+
+__global__ void k_gelu_fwd(const float* Z, __nv_bfloat16* A, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    A[i] = __float2bfloat16_rn(gelu(Z[i]));
+}
+
+__global__ void k_gelu_bwd(const float* dA, const float* Z, float* dZf, __nv_bfloat16* dZb, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float g = dA[i] * gelu_grad(Z[i]);
+    dZf[i] = g;
+    dZb[i] = __float2bfloat16_rn(g);
+  }
+}
+
+// out, dZ: [B x ld] (ld = 128); target: [B x nout]
+__global__ void k_mse_grad(const float* out, const float* target, float* dZf, __nv_bfloat16* dZb, double* loss,
+                           int B, int nout, int ld) {
+  double part = 0.0;
+  const float scale = 2.0f / ((float)B * (float)nout);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)B * ld;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / ld), c = (int)(i % ld);
+    float g = 0.0f;
+    if (c < nout) {
+      const float d = out[i] - target[(int64_t)b * nout + c];
+      part += (double)d * d;
+      g = scale * d;
+    }
+    dZf[i] = g;
+    dZb[i] = __float2bfloat16_rn(g);
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, part / ((double)B * nout));
+}
+
+// out[c * R + r] = in[r * C + c] (BF16), 32 x 32 tiles through shared memory
+__global__ void k_transpose(const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < C) t[i][threadIdx.x] = in[(int64_t)r * C + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < R && c < C) out[(int64_t)c * R + r] = t[threadIdx.x][i];
+  }
+}
+
+// column sums of a [R x C] FP32 matrix
+__global__ void k_colsum(const float* A, float* s, int R, int C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double acc = 0.0;
+  for (int r = 0; r < R; ++r) acc += A[(int64_t)r * C + c];
+  s[c] = (float)acc;
+}
+
+// Adam on a [rows x cols] parameter block (cols = 1 for biases); writes BF16 W and W^T if given
+__global__ void k_adam(float* W, const float* G, float* m, float* v, __nv_bfloat16* Wb, __nv_bfloat16* Wt,
+                       int rows, int cols, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float g = G[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * g;
+    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float w = W[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    W[i] = w;
+    if (Wb) {
+      const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+      Wb[i] = wb;
+      const int r = (int)(i / cols), c = (int)(i % cols);
+      Wt[(int64_t)c * rows + r] = wb;
+    }
+  }
+}
+
+__global__ void k_to_bf16(const float* W, __nv_bfloat16* Wb, __nv_bfloat16* Wt, int rows, int cols) {
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const __nv_bfloat16 wb = __float2bfloat16_rn(W[i]);
+    Wb[i] = wb;
+    const int r = (int)(i / cols), c = (int)(i % cols);
+    Wt[(int64_t)c * rows + r] = wb;
+  }
+}
+
+// ---- training data: raw features and targets, statistics, normalisation ----------------
+__global__ void k_train_features(const double* T0, const double* p, const double* Y0, const double* Y1,
+                                 int64_t ld, int64_t n, int ns, float* x, float* t) {
+  const int nin = ns + 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i * nin + 0] = (float)T0[i];
+    x[i * nin + 1] = (float)log(p[i]);
+    for (int k = 0; k < ns; ++k) {
+      const float y0 = fmaxf((float)Y0[(int64_t)k * ld + i], 0.0f);
+      const float y1 = fmaxf((float)Y1[(int64_t)k * ld + i], 0.0f);
+      const float b0 = (powf(y0, 0.1f) - 1.0f) / 0.1f;
+      const float b1 = (powf(y1, 0.1f) - 1.0f) / 0.1f;
+      x[i * nin + 2 + k] = b0;
+      t[i * ns + k] = b1 - b0;
+    }
+  }
+}
+
+// per-column sum, sum of squares, min and max of a [n x c] FP32 matrix (c <= 64)
+__global__ void k_col_stats(const float* A, int64_t n, int c, double* acc /*[4][c]*/) {
+  __shared__ double s1[64], s2[64], mn[64], mx[64];
+  for (int j = threadIdx.x; j < c; j += blockDim.x) { s1[j] = 0; s2[j] = 0; mn[j] = 1e300; mx[j] = -1e300; }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * c; i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % c);
+    const double v = A[i];
+    atomicAdd(&s1[j], v);
+    atomicAdd(&s2[j], v * v);
+    // min / max through CAS on the bit patterns of doubles
+    unsigned long long* pm = (unsigned long long*)&mn[j];
+    unsigned long long old = *pm, assumed;
+    while (v < __longlong_as_double(old)) {
+      assumed = old;
+      old = atomicCAS(pm, assumed, __double_as_longlong(v));
+      if (old == assumed) break;
+    }
+    unsigned long long* px = (unsigned long long*)&mx[j];
+    old = *px;
+    while (v > __longlong_as_double(old)) {
+      assumed = old;
+      old = atomicCAS(px, assumed, __double_as_longlong(v));
+      if (old == assumed) break;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < c; j += blockDim.x) {
+    atomicAdd(&acc[j], s1[j]);
+    atomicAdd(&acc[c + j], s2[j]);
+    unsigned long long* pm = (unsigned long long*)&acc[2 * c + j];
+    unsigned long long old = *pm, assumed;
+    while (mn[j] < __longlong_as_double(old)) {
+      assumed = old;
+      old = atomicCAS(pm, assumed, __double_as_longlong(mn[j]));
+      if (old == assumed) break;
+    }
+    unsigned long long* px = (unsigned long long*)&acc[3 * c + j];
+    old = *px;
+    while (mx[j] > __longlong_as_double(old)) {
+      assumed = old;
+      old = atomicCAS(px, assumed, __double_as_longlong(mx[j]));
+      if (old == assumed) break;
+    }
+  }
+}
+
+__global__ void k_init_stats(double* acc, int c) {
+  const int j = threadIdx.x;
+  if (j < c) { acc[j] = 0; acc[c + j] = 0; acc[2 * c + j] = 1e300; acc[3 * c + j] = -1e300; }
+}
+
+// X[i, 0:c] = bf16((x - mean) / std), zero up to ldx;  T[i, :] = (t - tmean) / tstd
+__global__ void k_normalize(const float* x, int64_t n, int c, const float* mean, const float* sd,
+                            __nv_bfloat16* X, int ldx, const float* t, int ct, const float* tmean,
+                            const float* tsd, float* Tn) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int j = 0; j < ldx; ++j)
+      X[i * ldx + j] = __float2bfloat16_rn(j < c ? (x[i * c + j] - mean[j]) / sd[j] : 0.0f);
+    if (t)
+      for (int j = 0; j < ct; ++j) Tn[i * ct + j] = (t[i * ct + j] - tmean[j]) / tsd[j];
+  }
+}
+
+inline unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 4096); }
+
+}  // namespace
+
+struct chem_trainer_s {
+  int nin, nout, B;
+  int in_pad[NL], out_pad[NL];
+  float *W[NL], *b[NL], *mW[NL], *vW[NL], *mb[NL], *vb[NL], *dW[NL], *db[NL];
+  __nv_bfloat16 *Wb[NL], *Wt[NL];
+  float* Z[NL];                    // pre-activations [B x out_pad]
+  __nv_bfloat16* A[NL];            // A[0] = caller's input, A[l] = bf16(GELU(Z[l-1]))
+  float *dA, *dZf;
+  __nv_bfloat16 *dZb, *dZt, *At;
+  int* err;
+  double* loss;
+  int step;
+  std::vector<void*> allocs;
+};
+
+static int tr_alloc(chem_trainer_s* t, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(trainer)");
+  t->allocs.push_back(*p);
+  CHEM_CUDA_TRY(cudaMemset(*p, 0, bytes));
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_trainer_free(chem_trainer_t t) {
+  if (!t) { set_error("NULL trainer"); return CHEM_EINVAL; }
+  for (void* p : t->allocs) cudaFree(p);
+  delete t;
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_trainer_create(int n_in, int n_out, int batch, const float* const* W_init,
+                                       const float* const* b_init, uint64_t seed, chem_trainer_t* out) {
+  if (!out || n_in < 1 || n_in > PADIO || n_out < 1 || n_out > PADIO || batch < 128 || batch % 128) {
+    set_error("trainer: n_in/n_out in [1, 128], batch a positive multiple of 128 required");
+    return CHEM_EINVAL;
+  }
+  *out = nullptr;
+  chem_trainer_s* t = new chem_trainer_s();
+  t->nin = n_in; t->nout = n_out; t->B = batch; t->step = 0;
+  const int ins[NL] = {PADIO, HID, HID, HID, HID}, outs[NL] = {HID, HID, HID, HID, PADIO};
+  const int real_in[NL] = {n_in, HID, HID, HID, HID}, real_out[NL] = {HID, HID, HID, HID, n_out};
+  int rc = CHEM_OK;
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<float> nd(0.0f, 1.0f);
+  for (int l = 0; l < NL && !rc; ++l) {
+    t->in_pad[l] = ins[l];
+    t->out_pad[l] = outs[l];
+    const size_t nw = (size_t)ins[l] * outs[l];
+    void* p;
+    if ((rc = tr_alloc(t, &p, nw * 4))) break; t->W[l] = (float*)p;
+    if ((rc = tr_alloc(t, &p, outs[l] * 4))) break; t->b[l] = (float*)p;
+    if ((rc = tr_alloc(t, &p, nw * 4))) break; t->mW[l] = (float*)p;
+    if ((rc = tr_alloc(t, &p, nw * 4))) break; t->vW[l] = (float*)p;
+    if ((rc = tr_alloc(t, &p, outs[l] * 4))) break; t->mb[l] = (float*)p;
+    if ((rc = tr_alloc(t, &p, outs[l] * 4))) break; t->vb[l] = (float*)p;
+    if ((rc = tr_alloc(t, &p, nw * 4))) break; t->dW[l] = (float*)p;
+    if ((rc = tr_alloc(t, &p, outs[l] * 4))) break; t->db[l] = (float*)p;
+    if ((rc = tr_alloc(t, &p, nw * 2))) break; t->Wb[l] = (__nv_bfloat16*)p;
+    if ((rc = tr_alloc(t, &p, nw * 2))) break; t->Wt[l] = (__nv_bfloat16*)p;
+    if ((rc = tr_alloc(t, &p, (size_t)batch * outs[l] * 4))) break; t->Z[l] = (float*)p;
+    if (l > 0) {
+      if ((rc = tr_alloc(t, &p, (size_t)batch * ins[l] * 2))) break;
+      t->A[l] = (__nv_bfloat16*)p;
+    }
+    // initial weights: caller's, else scaled Gaussian (1/sqrt(fan_in)); padding stays zero
+    std::vector<float> hw(nw, 0.0f), hb(outs[l], 0.0f);
+    const float sc = 1.0f / sqrtf((float)real_in[l]);
+    for (int o = 0; o < real_out[l]; ++o) {
+      for (int i = 0; i < real_in[l]; ++i)
+        hw[(size_t)o * ins[l] + i] = W_init && W_init[l] ? W_init[l][(size_t)o * real_in[l] + i] : sc * nd(rng);
+      hb[o] = b_init && b_init[l] ? b_init[l][o] : 0.0f;
+    }
+    if (cudaMemcpy(t->W[l], hw.data(), nw * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->b[l], hb.data(), outs[l] * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "cudaMemcpy(trainer)");
+      break;
+    }
+    k_to_bf16<<<grid_for(nw), 256>>>(t->W[l], t->Wb[l], t->Wt[l], outs[l], ins[l]);
+  }
+  void* p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 4), t->dA = (float*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 4), t->dZf = (float*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 2), t->dZb = (__nv_bfloat16*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 2), t->dZt = (__nv_bfloat16*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 2), t->At = (__nv_bfloat16*)p;
+  if (!rc) rc = tr_alloc(t, &p, 16), t->err = (int*)p;
+  if (!rc) rc = tr_alloc(t, &p, 16), t->loss = (double*)p;
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "trainer init");
+  if (rc) { chem_mlp_trainer_free(t); return rc; }
+  *out = t;
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_forward(chem_trainer_t t, const void* X, float* out, chem_stream_t stream) {
+  if (!t || !X) { set_error("NULL argument"); return CHEM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  t->A[0] = (__nv_bfloat16*)X;
+  const int B = t->B;
+  for (int l = 0; l < NL; ++l) {
+    int rc = gemm_bf16(t->A[l], t->in_pad[l], t->Wb[l], t->in_pad[l], t->Z[l], t->out_pad[l], t->b[l], B,
+                       t->out_pad[l], t->in_pad[l], t->err, st);
+    if (rc) return rc;
+    if (l < NL - 1) {
+      const int64_t n = (int64_t)B * t->out_pad[l];
+      k_gelu_fwd<<<grid_for(n), 256, 0, st>>>(t->Z[l], t->A[l + 1], n);
+    }
+  }
+  if (out) {
+    CHEM_CUDA_TRY(cudaMemcpy2DAsync(out, t->nout * 4, t->Z[NL - 1], PADIO * 4, t->nout * 4, B,
+                                    cudaMemcpyDeviceToDevice, st));
+  }
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* loss_out,
+                                 chem_stream_t stream) {
+  if (!t || !target) { set_error("NULL argument"); return CHEM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = t->B;
+  CHEM_CUDA_TRY(cudaMemsetAsync(t->loss, 0, sizeof(double), st));
+  k_mse_grad<<<grid_for((int64_t)B * PADIO), 256, 0, st>>>(t->Z[NL - 1], target, t->dZf, t->dZb, t->loss, B,
+                                                          t->nout, PADIO);
+  dim3 tb(32, 8);
+  for (int l = NL - 1; l >= 0; --l) {
+    const int nout = t->out_pad[l], nin = t->in_pad[l];
+    // dZ^T and A^T (batch contiguous) for the weight gradient
+    k_transpose<<<dim3((nout + 31) / 32, (B + 31) / 32), tb, 0, st>>>(t->dZb, t->dZt, B, nout);
+    k_transpose<<<dim3((nin + 31) / 32, (B + 31) / 32), tb, 0, st>>>(t->A[l], t->At, B, nin);
+    int rc = gemm_bf16(t->dZt, B, t->At, B, t->dW[l], nin, nullptr, nout, nin, B, t->err, st);
+    if (rc) return rc;
+    k_colsum<<<(nout + 127) / 128, 128, 0, st>>>(t->dZf, t->db[l], B, nout);
+    if (l > 0) {
+      rc = gemm_bf16(t->dZb, nout, t->Wt[l], nout, t->dA, nin, nullptr, B, nin, nout, t->err, st);
+      if (rc) return rc;
+      const int64_t n = (int64_t)B * nin;
+      k_gelu_bwd<<<grid_for(n), 256, 0, st>>>(t->dA, t->Z[l - 1], t->dZf, t->dZb, n);
+    }
+  }
+  if (loss_out) CHEM_CUDA_TRY(cudaMemcpyAsync(loss_out, t->loss, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float beta2, float eps,
+                                  chem_stream_t stream) {
+  if (!t || !(lr > 0.0f)) { set_error("bad Adam arguments"); return CHEM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  t->step += 1;
+  const float c1 = 1.0f - powf(beta1, (float)t->step), c2 = 1.0f - powf(beta2, (float)t->step);
+  for (int l = 0; l < NL; ++l) {
+    const int r = t->out_pad[l], c = t->in_pad[l];
+    k_adam<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[l], t->dW[l], t->mW[l], t->vW[l], t->Wb[l], t->Wt[l], r,
+                                                      c, lr, beta1, beta2, eps, c1, c2);
+    k_adam<<<grid_for(r), 256, 0, st>>>(t->b[l], t->db[l], t->mb[l], t->vb[l], nullptr, nullptr, r, 1, lr, beta1,
+                                        beta2, eps, c1, c2);
+  }
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+// copy parameters (which = 0) or gradients (which = 1) of the real (unpadded) layers to host
+extern "C" int chem_mlp_trainer_get(chem_trainer_t t, int which, float* const* W, float* const* b) {
+  if (!t || !W || !b) { set_error("NULL argument"); return CHEM_EINVAL; }
+  CHEM_CUDA_TRY(cudaDeviceSynchronize());
+  const int real_in[NL] = {t->nin, HID, HID, HID, HID}, real_out[NL] = {HID, HID, HID, HID, t->nout};
+  for (int l = 0; l < NL; ++l) {
+    const float* sw = which ? t->dW[l] : t->W[l];
+    const float* sb = which ? t->db[l] : t->b[l];
+    if (W[l])
+      CHEM_CUDA_TRY(cudaMemcpy2D(W[l], real_in[l] * 4, sw, t->in_pad[l] * 4, real_in[l] * 4, real_out[l],
+                                 cudaMemcpyDeviceToHost));
+    if (b[l]) CHEM_CUDA_TRY(cudaMemcpy(b[l], sb, real_out[l] * 4, cudaMemcpyDeviceToHost));
+  }
+  int herr = 0;
+  CHEM_CUDA_TRY(cudaMemcpy(&herr, t->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) { set_error("a GEMM pipeline wait timed out during training"); return CHEM_ECUDA; }
+  return CHEM_OK;
+}
+
+extern "C" int chem_train_features(const double* T0, const double* p, const double* Y0, const double* Y1,
+                                   int64_t ld, int64_t n, int ns, float* x_raw, float* t_raw,
+                                   chem_stream_t stream) {
+  if (!T0 || !p || !Y0 || !Y1 || !x_raw || !t_raw || n < 0 || ld < n || ns < 1 || ns > 62) {
+    set_error("bad arguments");
+    return CHEM_EINVAL;
+  }
+  if (n == 0) return CHEM_OK;
+  k_train_features<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(T0, p, Y0, Y1, ld, n, ns, x_raw, t_raw);
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+extern "C" int chem_column_stats(const float* A, int64_t n, int c, double* stats, chem_stream_t stream) {
+  if (!A || !stats || n < 1 || c < 1 || c > 64) { set_error("bad arguments"); return CHEM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  k_init_stats<<<1, 64, 0, st>>>(stats, c);
+  k_col_stats<<<grid_for(n * c), 256, 0, st>>>(A, n, c, stats);
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+extern "C" int chem_train_normalize(const float* x, int64_t n, int c, const float* mean, const float* sd,
+                                    void* X, int ldx, const float* t, int ct, const float* tmean,
+                                    const float* tsd, float* Tn, chem_stream_t stream) {
+  if (!x || !mean || !sd || !X || n < 0 || c < 1 || ldx < c || (t && (!tmean || !tsd || !Tn))) {
+    set_error("bad arguments");
+    return CHEM_EINVAL;
+  }
+  if (n == 0) return CHEM_OK;
+  k_normalize<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(x, n, c, mean, sd, (__nv_bfloat16*)X, ldx, t, ct,
+                                                             tmean, tsd, Tn);
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}

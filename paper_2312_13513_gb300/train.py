@@ -1,0 +1,225 @@
+"""Train the BF16 MLP surrogate of the chemistry step on the GPU.
+
+Data: states sampled from the quasi-DNS state distribution (synth.states.flamelet_samples),
+advanced over dt by the FP64 GPU integrator (chem_advance); features and targets
+(chem_train_features), statistics (chem_column_stats) and normalisation (chem_train_normalize)
+run in libchem kernels; the network is trained by chem_mlp_forward / chem_mlp_backward /
+chem_mlp_adam_step (tcgen05 GEMMs).  torch only holds device buffers, shuffles indices and
+gathers batches.
+
+    python -m paper_2312_13513_gb300.train --out model.chemsur --states 4194304 --epochs 40
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import os
+import struct
+import time
+
+import numpy as np
+
+from . import Mechanism, _lib, _ptr, _stream_ptr, advance, check
+
+PAD = 128
+
+
+class Trainer:
+    """chem_mlp_trainer_*: n_in -> 512 x 4 -> n_out GELU network with Adam."""
+
+    def __init__(self, n_in, n_out, batch, W=None, b=None, seed=0):
+        L = _lib.load()
+        self.n_in, self.n_out, self.batch = n_in, n_out, batch
+        h = ctypes.c_void_p()
+        if W is not None:
+            self._w = [np.ascontiguousarray(w, np.float32) for w in W]
+            self._b = [np.ascontiguousarray(x, np.float32) for x in b]
+            Wp = (ctypes.c_void_p * 5)(*[w.ctypes.data for w in self._w])
+            bp = (ctypes.c_void_p * 5)(*[x.ctypes.data for x in self._b])
+            check(L.chem_mlp_trainer_create(n_in, n_out, batch, Wp, bp, seed, ctypes.byref(h)))
+        else:
+            check(L.chem_mlp_trainer_create(n_in, n_out, batch, None, None, seed, ctypes.byref(h)))
+        self.handle = h
+
+    def forward(self, X, out=None, stream=None):
+        check(_lib.load().chem_mlp_forward(self.handle, _ptr(X), _ptr(out), _stream_ptr(stream)))
+
+    def backward(self, target, loss=None, stream=None):
+        check(_lib.load().chem_mlp_backward(self.handle, _ptr(target), _ptr(loss), _stream_ptr(stream)))
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        check(_lib.load().chem_mlp_adam_step(self.handle, ctypes.c_float(lr), ctypes.c_float(beta1),
+                                             ctypes.c_float(beta2), ctypes.c_float(eps),
+                                             _stream_ptr(stream)))
+
+    def get(self, which=0):
+        dims = [self.n_in, 512, 512, 512, 512, self.n_out]
+        W = [np.zeros((dims[i + 1], dims[i]), np.float32) for i in range(5)]
+        b = [np.zeros(dims[i + 1], np.float32) for i in range(5)]
+        Wp = (ctypes.c_void_p * 5)(*[w.ctypes.data for w in W])
+        bp = (ctypes.c_void_p * 5)(*[x.ctypes.data for x in b])
+        check(_lib.load().chem_mlp_trainer_get(self.handle, which, Wp, bp))
+        return W, b
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().chem_mlp_trainer_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def column_stats(A):
+    """mean, std, min, max per column of a [n x c] FP32 device tensor (chem_column_stats)."""
+    import torch
+    n, c = A.shape
+    st = torch.zeros(4 * c, dtype=torch.float64, device=A.device)
+    check(_lib.load().chem_column_stats(_ptr(A), n, c, _ptr(st), _stream_ptr(None)))
+    s = st.cpu().numpy().reshape(4, c)
+    mean = s[0] / n
+    var = np.maximum(s[1] / n - mean * mean, 0.0)
+    return mean, np.sqrt(var), s[2], s[3]
+
+
+def make_dataset(mech, dm, n, dt, seed, rtol=1e-6, atol=1e-10, stats=None):
+    """States (flamelet samples) advanced by the GPU integrator -> normalised X, target."""
+    import torch
+    from synth.states import flamelet_samples, load_table
+    f = flamelet_samples(load_table("h2_flamelet.npz"), n, seed)
+    dev = torch.device("cuda")
+    T0 = torch.tensor(f["T"], device=dev)
+    p = torch.tensor(f["p"], device=dev)
+    Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device=dev)
+    T1, Y1 = T0.clone(), Y0.clone()
+    advance(dm, T1, p, Y1, dt, rtol, atol)
+    ns = mech.ns
+    nin = ns + 2
+    x = torch.empty((n, nin), dtype=torch.float32, device=dev)
+    t = torch.empty((n, ns), dtype=torch.float32, device=dev)
+    check(_lib.load().chem_train_features(_ptr(T0), _ptr(p), _ptr(Y0), _ptr(Y1), n, n, ns, _ptr(x),
+                                          _ptr(t), _stream_ptr(None)))
+    if stats is None:
+        xm, xs, xlo, xhi = column_stats(x)
+        tm, ts, _, _ = column_stats(t)
+        # a constant feature (ln p at fixed pressure) has a rounding-noise deviation: scale 1
+        xs = np.where(xs > 1e-6 * np.maximum(1.0, np.abs(xm)), xs, 1.0)
+        ts = np.where(ts > 1e-12, ts, 1.0)
+        stats = {"x_mean": xm, "x_std": xs, "y_mean": tm, "y_std": ts, "box_lo": xlo, "box_hi": xhi}
+    X = torch.empty((n, PAD), dtype=torch.bfloat16, device=dev)
+    Tn = torch.empty((n, ns), dtype=torch.float32, device=dev)
+    f32 = lambda a: torch.tensor(np.asarray(a, np.float32), device=dev)
+    sx, sxs, sy, sys_ = f32(stats["x_mean"]), f32(stats["x_std"]), f32(stats["y_mean"]), f32(stats["y_std"])
+    check(_lib.load().chem_train_normalize(_ptr(x), n, nin, _ptr(sx), _ptr(sxs), _ptr(X), PAD, _ptr(t), ns,
+                                           _ptr(sy), _ptr(sys_), _ptr(Tn), _stream_ptr(None)))
+    torch.cuda.synchronize()
+    return {"X": X, "T": Tn, "stats": stats, "state0": (T0, p, Y0), "state1": (T1, Y1)}
+
+
+def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=1e-3, lr_final=3e-5, dt=5e-7, seed=7,
+          log=print, time_budget_s=None):
+    import torch
+    dm = Mechanism(mech)
+    t0 = time.time()
+    data = make_dataset(mech, dm, n_states, dt, seed)
+    log(f"dataset: {n_states} states in {time.time() - t0:.1f} s")
+    ns = mech.ns
+    tr = Trainer(ns + 2, ns, batch, seed=seed)
+    X, Tt = data["X"], data["T"]
+    n = X.shape[0]
+    steps_per_epoch = n // batch
+    total = epochs * steps_per_epoch
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    history = []
+    step = 0
+    t1 = time.time()
+    for ep in range(epochs):
+        perm = torch.randperm(n, device="cuda")
+        acc = 0.0
+        for i in range(steps_per_epoch):
+            idx = perm[i * batch:(i + 1) * batch]
+            xb = X.index_select(0, idx)
+            yb = Tt.index_select(0, idx)
+            # cosine learning-rate decay from lr to lr_final
+            frac = step / max(1, total - 1)
+            lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * frac))
+            tr.forward(xb)
+            tr.backward(yb, loss)
+            tr.adam(lr_t)
+            step += 1
+            if i % 64 == 0:
+                acc = float(loss.item())
+        history.append(acc)
+        log(f"epoch {ep + 1}/{epochs}: loss {acc:.4e}  ({time.time() - t1:.1f} s)")
+        if time_budget_s is not None and time.time() - t1 > time_budget_s:
+            log("time budget reached")
+            break
+    W, b = tr.get(0)
+    params = dict(data["stats"])
+    params.update({"W": W, "b": b, "dt": dt, "history": history})
+    return params
+
+
+def save_model(params, path):
+    """CHEMSUR1 file: magic, int32 ns, int32 hidden, float64 dt, then float32 arrays."""
+    W, b = params["W"], params["b"]
+    ns = W[4].shape[0]
+    with open(path, "wb") as f:
+        f.write(b"CHEMSUR1")
+        f.write(struct.pack("<iid", ns, W[0].shape[0], float(params["dt"])))
+        for l in range(5):
+            f.write(np.ascontiguousarray(W[l], np.float32).tobytes())
+            f.write(np.ascontiguousarray(b[l], np.float32).tobytes())
+        for k in ("x_mean", "x_std", "y_mean", "y_std", "box_lo", "box_hi"):
+            f.write(np.ascontiguousarray(params[k], np.float32).tobytes())
+
+
+def load_model_params(path):
+    with open(path, "rb") as f:
+        raw = f.read()
+    assert raw[:8] == b"CHEMSUR1"
+    ns, hid, dt = struct.unpack("<iid", raw[8:24])
+    nin = ns + 2
+    off = 24
+
+    def take(count, shape):
+        nonlocal off
+        a = np.frombuffer(raw, np.float32, count, off).reshape(shape).copy()
+        off += 4 * count
+        return a
+
+    dims = [nin, hid, hid, hid, hid, ns]
+    W, b = [], []
+    for l in range(5):
+        W.append(take(dims[l + 1] * dims[l], (dims[l + 1], dims[l])))
+        b.append(take(dims[l + 1], (dims[l + 1],)))
+    out = {"W": W, "b": b, "dt": dt}
+    for k, c in (("x_mean", nin), ("x_std", nin), ("y_mean", ns), ("y_std", ns), ("box_lo", nin),
+                 ("box_hi", nin)):
+        out[k] = take(c, (c,))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--states", type=int, default=1 << 22)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--budget", type=float, default=None, help="training time budget (s)")
+    args = ap.parse_args()
+    from synth.mechanism import h2_mechanism
+    params = train(h2_mechanism(), args.states, args.epochs, args.batch, args.lr, seed=args.seed,
+                   time_budget_s=args.budget)
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    save_model(params, args.out)
+    print("saved", args.out)
+
+
+if __name__ == "__main__":
+    main()

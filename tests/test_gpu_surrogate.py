@@ -35,6 +35,13 @@ def _random_params(ns, seed, dt=5e-7):
     return {"W": W, "b": b, "dt": dt}
 
 
+def _std(x):
+    """Feature scale; a constant feature (ln p at fixed pressure) gets scale 1, because its
+    standard deviation is rounding noise."""
+    sd = x.std(axis=0)
+    return np.where(sd > 1e-6 * np.maximum(1.0, np.abs(x.mean(axis=0))), sd, 1.0)
+
+
 def _oracle_z(params, T, p, Y):
     x = osur.features(T, p, Y)
     xz = (x - params["x_mean"]) / params["x_std"]
@@ -50,7 +57,7 @@ def test_forward_matches_oracle_mlp(h2):
     x = osur.features(T, p, Y)
     prm = _random_params(h2.ns, 3)
     prm["x_mean"] = x.mean(axis=0)
-    prm["x_std"] = np.where(x.std(axis=0) > 0, x.std(axis=0), 1.0)
+    prm["x_std"] = _std(x)
     prm["y_mean"] = 0.01 * np.arange(h2.ns)
     prm["y_std"] = 0.05 + 0.01 * np.arange(h2.ns)
     prm["box_lo"] = x.min(axis=0) - 1.0
@@ -77,7 +84,7 @@ def _identity_params(mech, x):
     prm["W"][4] = np.zeros_like(prm["W"][4])
     prm["b"][4] = np.zeros(mech.ns)
     prm["x_mean"] = x.mean(axis=0)
-    prm["x_std"] = np.where(x.std(axis=0) > 0, x.std(axis=0), 1.0)
+    prm["x_std"] = _std(x)
     prm["y_mean"] = np.zeros(mech.ns)
     prm["y_std"] = np.ones(mech.ns)
     prm["box_lo"] = x.min(axis=0) - 1.0
@@ -134,3 +141,87 @@ def test_surrogate_rejects_wrong_dt(h2):
     model = cg.Surrogate(dm, prm)
     with pytest.raises(cg.ChemError):
         cg.surrogate_advance(model, *to_dev(T, p, Y), 1e-6)
+
+
+# ---------------------------------------------------------------------------------------------
+# training kernels
+# ---------------------------------------------------------------------------------------------
+def _small_problem(seed, B=256, nin=11, nout=9):
+    rng = np.random.default_rng(seed)
+    dims = [nin, 512, 512, 512, 512, nout]
+    W = [omlp.bf16_round(rng.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i])) for i in range(5)]
+    b = [np.float32(0.1 * rng.standard_normal(dims[i + 1])).astype(np.float64) for i in range(5)]
+    X = omlp.bf16_round(rng.standard_normal((B, nin)))
+    T = rng.standard_normal((B, nout))
+    return W, b, X, T
+
+
+def test_trainer_forward_backward_match_oracle():
+    from paper_2312_13513_gb300.train import PAD, Trainer
+    W, b, X, T = _small_problem(1)
+    B, nin = X.shape
+    nout = T.shape[1]
+    tr = Trainer(nin, nout, B, W=W, b=b)
+    Xd = torch.zeros((B, PAD), dtype=torch.bfloat16, device="cuda")
+    Xd[:, :nin] = torch.tensor(X, dtype=torch.float32).to(torch.bfloat16)
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    out = torch.empty((B, nout), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tr.forward(Xd, out)
+    tr.backward(Td, loss)
+    dW, db = tr.get(1)
+    o_out, cache = omlp.forward(W, b, X, emulate_bf16=True)
+    assert np.max(np.abs(out.cpu().numpy() - o_out)) <= 1e-2 * max(1.0, np.max(np.abs(o_out)))
+    assert abs(loss.item() - omlp.mse_loss(o_out, T)) <= 1e-3 * omlp.mse_loss(o_out, T)
+    gW, gb = omlp.backward(W, b, cache, o_out, T)
+    for l in range(5):
+        rel = np.linalg.norm(dW[l] - gW[l]) / np.linalg.norm(gW[l])
+        relb = np.linalg.norm(db[l] - gb[l]) / np.linalg.norm(gb[l])
+        assert rel < 2e-2 and relb < 2e-2, (l, rel, relb)
+
+
+def test_adam_step_matches_oracle():
+    from paper_2312_13513_gb300.train import PAD, Trainer
+    W, b, X, T = _small_problem(2)
+    B, nin = X.shape
+    tr = Trainer(nin, T.shape[1], B, W=W, b=b)
+    Xd = torch.zeros((B, PAD), dtype=torch.bfloat16, device="cuda")
+    Xd[:, :nin] = torch.tensor(X, dtype=torch.float32).to(torch.bfloat16)
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    tr.forward(Xd)
+    tr.backward(Td)
+    dW, db = tr.get(1)
+    tr.adam(1e-3)
+    W1, b1 = tr.get(0)
+    params = [np.asarray(w, np.float64) for w in W] + [np.asarray(x, np.float64) for x in b]
+    grads = [np.asarray(g, np.float64) for g in dW] + [np.asarray(g, np.float64) for g in db]
+    m = [np.zeros_like(x) for x in params]
+    v = [np.zeros_like(x) for x in params]
+    ref, _, _ = omlp.adam_step(params, grads, m, v, 1, lr=1e-3)
+    got = [np.asarray(w, np.float64) for w in W1] + [np.asarray(x, np.float64) for x in b1]
+    for r, g in zip(ref, got):
+        assert np.max(np.abs(r - g)) <= 2e-6
+
+
+def test_training_reduces_loss():
+    """Fit the outputs of a fixed random teacher network: loss must fall by 10x."""
+    from paper_2312_13513_gb300.train import PAD, Trainer
+    Wt, bt, _, _ = _small_problem(3, nout=9)
+    rng = np.random.default_rng(4)
+    n, B = 8192, 512
+    X = omlp.bf16_round(rng.standard_normal((n, 11)))
+    Y, _ = omlp.forward(Wt, bt, X, emulate_bf16=False)
+    Xd = torch.zeros((n, PAD), dtype=torch.bfloat16, device="cuda")
+    Xd[:, :11] = torch.tensor(X, dtype=torch.float32).to(torch.bfloat16)
+    Yd = torch.tensor(Y, dtype=torch.float32, device="cuda")
+    tr = Trainer(11, 9, B, seed=5)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    first = None
+    for step in range(300):
+        i = (step * B) % n
+        tr.forward(Xd[i:i + B])
+        tr.backward(Yd[i:i + B], loss)
+        if first is None:
+            first = loss.item()
+        tr.adam(1e-3)
+    assert loss.item() < 0.1 * first, (first, loss.item())
