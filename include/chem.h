@@ -122,6 +122,27 @@ int chem_advance_ex(chem_mech_t m, double* T, const double* p, double* Y, int64_
                     int8_t* status, int32_t* nsub, int32_t* nrej, const chem_options* opt,
                     chem_stream_t stream);
 
+/* One set of cells for chem_advance_batch: device state arrays (as for chem_advance_ex), its
+ * own step and tolerances, optional index list and outputs. */
+typedef struct chem_segment {
+  double* T;
+  const double* p;
+  double* Y;
+  int64_t ld, ncells;
+  const int32_t* idx;        /* nullable: cells idx[0..ncells) */
+  int8_t* status;            /* nullable outputs, as for chem_advance_ex */
+  int32_t* nsub;
+  int32_t* nrej;
+  double dt, rtol, atol;
+} chem_segment;
+
+/* Advance several independent segments (different solvers' states, steps and tolerances) in one
+ * persistent launch: their 8-cell chunks share one work queue, so small requests fill the GPU
+ * together (iteration-level batching, used by the serving loop).  segs is a host array read
+ * during the call; the call returns once the descriptors are on the device (it synchronises
+ * the stream). */
+int chem_advance_batch(chem_mech_t m, const chem_segment* segs, int nseg, chem_stream_t stream);
+
 /* Allocation-free form of chem_advance_ex (cells [0, ncells), default options).  It calls no
  * device allocator: the only scratch a launch needs, the 8-byte counter of the kernel's work
  * queue, lives in a 256-byte file-scope __device__ array inside the library (held by every GPU
@@ -189,6 +210,13 @@ int chem_surrogate_advance(chem_model_t model, chem_mech_t m, double* T, const d
                            double* Y, int64_t ld, double dt, int64_t ncells, double rtol,
                            double atol, int8_t* route_out, chem_stream_t stream);
 
+/* Heat-release rate of a step (the accuracy measure of the surrogate):
+ * q[c] = -rho0 sum_k h_k(T0) (Y1_k - Y0_k) / (W_k dt) with h_k molar (formation included),
+ * rho0 from (T0, p, Y0).  erg / (cm^3 s).  Device pointers, asynchronous. */
+int chem_heat_release(chem_mech_t m, const double* T0, const double* p, const double* Y0,
+                      const double* Y1, int64_t ld, int64_t ncells, double dt, double* q,
+                      chem_stream_t stream);
+
 /* BF16 tensor-core GEMM used by training: C[M x N] (FP32, row pitch ldc) = A[M x K] B[N x K]^T
  * (+ bias[N], nullable); A, B device BF16 with K contiguous, row pitches lda/ldb (elements,
  * 16-byte multiples), M >= 128 and N >= 128 (ragged edges are zero-filled by TMA).  *err
@@ -231,6 +259,41 @@ int chem_column_stats(const float* A, int64_t n, int c, double* stats, chem_stre
 int chem_train_normalize(const float* x, int64_t n, int c, const float* mean, const float* sd,
                          void* X, int ldx, const float* t, int ct, const float* tmean,
                          const float* tsd, float* Tn, chem_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: chemistry sub-steps from many concurrent flow solvers on one GPU.  Solvers register
+ * their resident device states once and submit one request per sub-step; a server thread admits
+ * requests under a device-memory budget (resident states + per-request workspace), batches the
+ * admitted FP64 requests of a mechanism into one persistent launch and overlaps launches on a
+ * small stream pool (continuous batching).  Latency = submission to completion.
+ * ------------------------------------------------------------------------------------- */
+enum { CHEM_ROUTE_FP64 = 0, CHEM_ROUTE_SURROGATE = 1 };
+enum { CHEM_REQ_QUEUED = 0, CHEM_REQ_RUNNING = 1, CHEM_REQ_DONE = 2, CHEM_REQ_FAILED = 3 };
+
+typedef struct chem_serve_options {
+  int32_t n_streams;         /* concurrent launches (0 -> 4) */
+  double idle_poll_us;       /* polling interval while launches are in flight (0 -> 20 us) */
+} chem_serve_options;
+
+int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_options* opt, chem_server_t* out);
+/* Register a solver's resident state (device arrays owned by the caller, valid until the server
+ * is destroyed); model (nullable) enables the surrogate route.  CHEM_EBUSY if the state alone
+ * exceeds what is left of the budget. */
+int chem_serve_register_state(chem_server_t s, chem_mech_t m, chem_model_t model, double* T,
+                              double* p, double* Y, int64_t ld, int64_t ncells, int* state_id);
+/* Queue one sub-step of a registered state.  CHEM_EBUSY if the request could never be admitted
+ * (its workspace exceeds the budget left by the resident states). */
+int chem_serve_submit(chem_server_t s, int state_id, int route, double dt, double rtol,
+                      double atol, uint64_t* req_id);
+/* Non-blocking: *state = CHEM_REQ_*, *latency_s (nullable) = seconds from submission to
+ * completion once done, else -1. */
+int chem_serve_poll(chem_server_t s, uint64_t req_id, int* state, double* latency_s);
+/* Block until the request is done or timeout_s passes (CHEM_ETIMEOUT); never hangs. */
+int chem_serve_wait(chem_server_t s, uint64_t req_id, double timeout_s);
+/* out[6]: completed, failed, launches, requests launched, max concurrent launches, bytes in use */
+int chem_serve_stats(chem_server_t s, int64_t* out);
+/* Stops the server after its launches finish; queued requests fail. */
+int chem_serve_destroy(chem_server_t s);
 
 /* Measured FP64 FMA throughput of the current device (TFLOP/s, 2 flops per FMA) from a
  * register-resident FMA chain kernel; synchronous. */

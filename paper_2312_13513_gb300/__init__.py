@@ -210,3 +210,13 @@ def gemm_bf16(A, B, bias=None, err=None, stream=None):
         if int(err.item()) != 0:
             raise ChemError(-3, "gemm pipeline wait timed out")
     return C
+
+
+def heat_release(mech, T0, p, Y0, Y1, dt, stream=None):
+    """chem_heat_release: q [n] (erg/cm^3/s) of a step from (T0, p, Y0) to Y1."""
+    import torch
+    n = T0.numel()
+    q = torch.empty(n, dtype=torch.float64, device=T0.device)
+    check(_lib.load().chem_heat_release(mech.handle, _ptr(T0), _ptr(p), _ptr(Y0), _ptr(Y1), Y0.shape[1], n,
+                                        float(dt), _ptr(q), _stream_ptr(stream)))
+    return q

@@ -45,6 +45,15 @@ class Options(ctypes.Structure):
                 ("max_ctas", I32)]
 
 
+class Segment(ctypes.Structure):
+    _fields_ = [("T", P), ("p", P), ("Y", P), ("ld", I64), ("ncells", I64), ("idx", P),
+                ("status", P), ("nsub", P), ("nrej", P), ("dt", D), ("rtol", D), ("atol", D)]
+
+
+class ServeOptions(ctypes.Structure):
+    _fields_ = [("n_streams", I32), ("idle_poll_us", D)]
+
+
 class SurrogateDesc(ctypes.Structure):
     _fields_ = [("n_species", I32), ("hidden", I32), ("dt", D), ("W", P * 5), ("b", P * 5),
                 ("x_mean", P), ("x_std", P), ("y_mean", P), ("y_std", P), ("box_lo", P),
@@ -79,6 +88,15 @@ SIGNATURES = {
     "chem_column_stats": (ctypes.c_int, [P, I64, ctypes.c_int, P, P]),
     "chem_train_normalize": (ctypes.c_int, [P, I64, ctypes.c_int, P, P, P, ctypes.c_int, P,
                                             ctypes.c_int, P, P, P, P]),
+    "chem_heat_release": (ctypes.c_int, [P, P, P, P, P, I64, I64, D, P, P]),
+    "chem_advance_batch": (ctypes.c_int, [P, P, ctypes.c_int, P]),
+    "chem_serve_create": (ctypes.c_int, [ctypes.c_size_t, P, P]),
+    "chem_serve_register_state": (ctypes.c_int, [P, P, P, P, P, P, I64, I64, P]),
+    "chem_serve_submit": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, D, D, D, P]),
+    "chem_serve_poll": (ctypes.c_int, [P, ctypes.c_uint64, P, P]),
+    "chem_serve_wait": (ctypes.c_int, [P, ctypes.c_uint64, D]),
+    "chem_serve_stats": (ctypes.c_int, [P, P]),
+    "chem_serve_destroy": (ctypes.c_int, [P]),
     "chem_gemm_bf16": (ctypes.c_int, [P, I64, P, I64, P, I64, P, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, P, P]),
     "chem_last_error": (ctypes.c_char_p, []),

@@ -76,6 +76,7 @@ struct chem_mech_s {
 
 namespace chem {
 // integrator launch (used by the public entry points, the surrogate fallback and the server)
+int launch_advance_batch(chem_mech_s* m, const chem_segment* segs, int nseg, cudaStream_t stream);
 int launch_advance(chem_mech_s* m, double* T, const double* p, double* Y, int64_t ld, double dt,
                    int64_t ncells, double rtol, double atol, const int32_t* idx, int8_t* status,
                    int32_t* nsub, int32_t* nrej, const chem_options* opt, cudaStream_t stream,

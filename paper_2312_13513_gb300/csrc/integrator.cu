@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "chem_internal.h"
 
@@ -246,7 +247,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
   const int rg = (T < TMID) ? 0 : 1;
 
   // species thermo (A2): NASA-7 cp/R, h/RT, g/RT sharing T powers and ln T
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int k = g.tid; k < ns; k += G) {
     const double* hc = m.hc + (rg * ns + k) * 6;
     const double* sc = m.sc + (rg * ns + k) * 6;
@@ -257,6 +258,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
     w.hRT[k] = h;
     w.gRT[k] = h - s;
     w.cpR[k] = cp;
+    acc[3] += h - s;
     const double yw = y[1 + k] * m.invW[k];
     acc[0] += yw;
     acc[1] += yw * cp;
@@ -267,18 +269,31 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
       acc[2] += yw * d;
     }
   }
-  gsum<G, 3>(g, acc, w.red);
+  gsum<G, 4>(g, acc, w.red);
   const double S = acc[0];                 // sum Y/W
   const double cp = RU * acc[1];           // mixture cp (mass)
   const double dcpdT = RU * acc[2];
+  const double gshift = acc[3] / ns;       // mean g/RT: keeps exp(g/RT - gshift) in range
   const double rho = p / (RU * T * S);
   const double invrho = 1.0 / rho;
-  for (int k = g.tid; k < ns; k += G) w.C[k] = rho * y[1 + k] * m.invW[k];
+  // per-species exp(g/RT - gshift) and its inverse: 1/Kc of every reaction becomes a product
+  // (w.rk / w.Hm are free until the Jacobian section)
+  double* eg = w.rk;
+  double* ieg = w.Hm;
+  for (int k = g.tid; k < ns; k += G) {
+    w.C[k] = rho * y[1 + k] * m.invW[k];
+    const double e = exp(w.gRT[k] - gshift);
+    eg[k] = e;
+    ieg[k] = 1.0 / e;
+  }
   g.sync();
 
   // rates of progress (A3)
   const double Ctot = rho * S;
   const double lnPR = log(PATM / RU) - lnT;     // ln(p_atm / (R T))
+  // 1/Kc = exp(dG - dnu lnPR) = prod_products eg * prod_reactants ieg * ep1^dnu
+  const double ep1 = exp(gshift - lnPR);
+  const double iep1 = 1.0 / ep1;
   for (int j = g.tid; j < nr; j += G) {
     const short4 ri = m.rinfo[j];
     const short4 re = m.reac[j];
@@ -351,7 +366,16 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
         }
       }
     }
-    const double invKc = exp(dG - (double)ri.y * lnPR);   // 1 / Kc
+    double invKc = 1.0;                                   // 1 / Kc
+    if (re.x >= 0) invKc *= ieg[re.x];
+    if (re.y >= 0) invKc *= ieg[re.y];
+    if (re.z >= 0) invKc *= ieg[re.z];
+    if (pr.x >= 0) invKc *= eg[pr.x];
+    if (pr.y >= 0) invKc *= eg[pr.y];
+    if (pr.z >= 0) invKc *= eg[pr.z];
+    for (int d = ri.y; d > 0; --d) invKc *= ep1;
+    for (int d = ri.y; d < 0; ++d) invKc *= iep1;
+    if (!(invKc > 0.0 && invKc < 1.0e300)) invKc = exp(dG - (double)ri.y * lnPR);   // range fallback
     const double kr = kf * invKc;
     const double fwd = kf * Pf, rev = kr * Pr;
     const double mult = (ri.x == 1) ? Mc : 1.0;
@@ -522,23 +546,35 @@ __device__ void lu_solve(const Grp<G>& g, const double* M, int N, int LD, const 
 // ---------------------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------------------
+// One independent set of cells advanced by a launch: its own state arrays, step and
+// tolerances, optional index list and outputs.  A launch walks the chunks of all its segments
+// through one work queue (iteration-level batching of several requests).
+struct Segment {
+  double* T;
+  const double* p;
+  double* Y;
+  int64_t ld, ncells;
+  const int32_t* idx;
+  int8_t* status;
+  int32_t* nsub;
+  int32_t* nrej;
+  double dt, rtol, atol;
+  long long chunk_begin;           // first queue entry of this segment
+};
+
+constexpr int kMaxSegs = 32;       // segments per launch (kernel-parameter space)
+
 struct AdvanceParams {
   MechLayout lay;
   WsLayout ws;
   JacArgs jp;
   const unsigned char* blob;
-  double* T;
-  const double* p;
-  double* Y;
-  int64_t ld, ncells;
-  double dt, rtol, atol;
-  const int32_t* idx;
-  int8_t* status;
-  int32_t* nsub;
-  int32_t* nrej;
+  Segment segs[kMaxSegs];
+  int nseg;
+  long long total_chunks;
   int max_steps;
   unsigned long long* counter;
-  const unsigned int* ncells_dev;   // when set, the cell count is read from device memory
+  const unsigned int* ncells_dev;  // single segment: cell count read from device memory
 };
 
 __device__ __forceinline__ void stage_mech(const unsigned char* src, unsigned char* dst, int bytes) {
@@ -552,7 +588,7 @@ __device__ __forceinline__ void stage_mech(const unsigned char* src, unsigned ch
 template <int G>
 __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& w,
                                const AdvanceParams& P, double p, double h, bool need_j,
-                               double* en) {
+                               double rtol, double atol, double* en) {
   const int N = m.N, LD = P.ws.LD;
   if (need_j) eval_fj<G>(g, m, w, P.jp, LD, w.y, p, w.f0, w.J, true);
   const double ig = 1.0 / (kGamma * h);
@@ -590,7 +626,7 @@ __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& 
 #pragma unroll
     for (int s = 0; s < 6; ++s) v += kRM[s] * w.u[s * N + i];
     w.ynew[i] = v;
-    const double sc = P.atol + P.rtol * fmax(fabs(w.y[i]), fabs(v));
+    const double sc = atol + rtol * fmax(fabs(w.y[i]), fabs(v));
     const double r = w.u[5 * N + i] / sc;
     acc[0] += r * r;
   }
@@ -599,18 +635,24 @@ __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& 
   return true;
 }
 
-// Chunk bookkeeping of one group: the current chunk of CHUNK consecutive queue entries staged
-// in shared memory and the position of the cell being integrated.
+// Chunk bookkeeping of one group: the current chunk of up to CHUNK consecutive cells of one
+// segment, staged in shared memory, and the position of the cell being integrated.
 struct ChunkPos {
+  const Segment* seg;
   long long base;
   int nloc, c;
   bool exhausted;
-  long long ncells;     // cells in the queue (from the launch or from device memory)
+  long long total;      // queue entries (chunks) of the launch
 };
 
-template <int G>
-__device__ __forceinline__ int64_t cell_of(const AdvanceParams& P, long long base, int c) {
-  return P.idx ? (int64_t)P.idx[base + c] : (int64_t)(base + c);
+__device__ __forceinline__ int64_t cell_of(const Segment* S, long long base, int c) {
+  return S->idx ? (int64_t)S->idx[base + c] : (int64_t)(base + c);
+}
+
+__device__ __forceinline__ const Segment* segment_of(const AdvanceParams& P, long long chunk) {
+  int s = 0;
+  while (s + 1 < P.nseg && P.segs[s + 1].chunk_begin <= chunk) ++s;
+  return &P.segs[s];
 }
 
 // Move to the next cell: store a finished chunk, claim and load the next one when needed.
@@ -629,38 +671,43 @@ __device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
     }
     if (q.nloc > 0) {
       // coalesced store of the finished chunk (rows T, Y_1..Y_ns)
+      const Segment* S = q.seg;
       for (int e = g.tid; e < N * CHUNK; e += G) {
         const int row = e / CHUNK, c = e % CHUNK;
         if (c >= q.nloc) continue;
-        const int64_t cell = cell_of<G>(P, q.base, c);
+        const int64_t cell = cell_of(S, q.base, c);
         const double v = w.stage[row * CHUNK + c];
-        if (row == 0) P.T[cell] = v;
-        else P.Y[(int64_t)(row - 1) * P.ld + cell] = v;
+        if (row == 0) S->T[cell] = v;
+        else S->Y[(int64_t)(row - 1) * S->ld + cell] = v;
       }
       q.nloc = 0;
       g.sync();
     }
     if (q.exhausted) return false;
-    if (g.tid == 0) w.ctl[0] = atomicAdd(P.counter, (unsigned long long)CHUNK);
+    if (g.tid == 0) w.ctl[0] = atomicAdd(P.counter, 1ull);
     g.sync();
-    const long long base = (long long)w.ctl[0];
+    const long long chunk = (long long)w.ctl[0];
     g.sync();
-    if (base >= q.ncells) {
+    if (chunk >= q.total) {
       q.exhausted = true;
       return false;
     }
-    q.base = base;
-    q.nloc = (int)min((long long)CHUNK, q.ncells - base);
+    const Segment* S = segment_of(P, chunk);
+    const long long ncs = P.ncells_dev ? min((long long)*P.ncells_dev, (long long)S->ncells)
+                                       : (long long)S->ncells;
+    q.seg = S;
+    q.base = (chunk - S->chunk_begin) * CHUNK;
+    q.nloc = (int)min((long long)CHUNK, ncs - q.base);
     q.c = -1;
     // coalesced load of the chunk: rows T, Y_1..Y_ns, p; each row CHUNK consecutive cells
     for (int e = g.tid; e < (N + 1) * CHUNK; e += G) {
       const int row = e / CHUNK, c = e % CHUNK;
       if (c >= q.nloc) continue;
-      const int64_t cell = cell_of<G>(P, q.base, c);
+      const int64_t cell = cell_of(S, q.base, c);
       double v;
-      if (row == 0) v = P.T[cell];
-      else if (row <= m.ns) v = P.Y[(int64_t)(row - 1) * P.ld + cell];
-      else v = P.p[cell];
+      if (row == 0) v = S->T[cell];
+      else if (row <= m.ns) v = S->Y[(int64_t)(row - 1) * S->ld + cell];
+      else v = S->p[cell];
       w.stage[row * CHUNK + c] = v;
     }
     g.sync();
@@ -672,7 +719,7 @@ __device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
 // the attempt body each iteration (an idle group works on a dummy state whose results are
 // discarded), so the warp's FP64 instructions stay converged across its groups.
 template <int G>
-__global__ void __launch_bounds__(512) advance_kernel(const AdvanceParams P) {
+__global__ void __launch_bounds__(512) advance_kernel(const __grid_constant__ AdvanceParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   stage_mech(P.blob, smem, P.lay.bytes);
   __syncthreads();
@@ -686,11 +733,12 @@ __global__ void __launch_bounds__(512) advance_kernel(const AdvanceParams P) {
   for (int i = g.tid; i < N; i += G) w.y[i] = i == 0 ? 1000.0 : 1.0 / m.ns;
   g.sync();
 
-  const double dt = P.dt;
-  long long ncells = P.ncells;
-  if (P.ncells_dev) ncells = min((long long)*P.ncells_dev, (long long)P.ncells);
-  ChunkPos q{0, 0, 0, false, ncells};
+  long long total = P.total_chunks;
+  if (P.ncells_dev)
+    total = (min((long long)*P.ncells_dev, (long long)P.segs[0].ncells) + CHUNK - 1) / CHUNK;
+  ChunkPos q{&P.segs[0], 0, 0, 0, false, total};
   bool active = false, have_j = false;
+  double dt = 1.0, rtol = 1e-6, atol = 1e-10;
   double p = 1.0e6, t = 0.0, h = dt, facmax = 6.0;
   int attempts = 0, nacc = 0, nrej = 0;
 
@@ -707,10 +755,11 @@ __global__ void __launch_bounds__(512) advance_kernel(const AdvanceParams P) {
       gsum<G, 1>(g, bad, w.red);
       if (bad[0] != 0.0) {
         if (g.tid == 0) {
-          const int64_t cell = cell_of<G>(P, q.base, q.c);
-          if (P.status) P.status[cell] = (int8_t)CHEM_CELL_NONFINITE;
-          if (P.nsub) P.nsub[cell] = 0;
-          if (P.nrej) P.nrej[cell] = 0;
+          const Segment* S = q.seg;
+          const int64_t cell = cell_of(S, q.base, q.c);
+          if (S->status) S->status[cell] = (int8_t)CHEM_CELL_NONFINITE;
+          if (S->nsub) S->nsub[cell] = 0;
+          if (S->nrej) S->nrej[cell] = 0;
         }
         for (int i = g.tid; i < N; i += G) w.y[i] = i == 0 ? 1000.0 : 1.0 / m.ns;
         g.sync();
@@ -718,6 +767,7 @@ __global__ void __launch_bounds__(512) advance_kernel(const AdvanceParams P) {
       }
       active = true;
       have_j = false;
+      dt = q.seg->dt; rtol = q.seg->rtol; atol = q.seg->atol;
       t = 0.0; h = dt; facmax = 6.0;
       attempts = 0; nacc = 0; nrej = 0;
     }
@@ -743,7 +793,7 @@ __global__ void __launch_bounds__(512) advance_kernel(const AdvanceParams P) {
     if (run || G < 32) {
       double en = 0.0;
       const bool need_j = (G < 32) || !have_j;
-      const bool ok = rodas4_attempt<G>(g, m, w, P, p, run ? h : dt, need_j, &en);
+      const bool ok = rodas4_attempt<G>(g, m, w, P, p, run ? h : dt, need_j, rtol, atol, &en);
       if (run) {
         have_j = true;
         if (!ok) {
@@ -782,10 +832,11 @@ __global__ void __launch_bounds__(512) advance_kernel(const AdvanceParams P) {
       // the last accepted state goes back into the chunk staging area
       for (int i = g.tid; i < N; i += G) w.stage[i * CHUNK + q.c] = w.y[i];
       if (g.tid == 0) {
-        const int64_t cell = cell_of<G>(P, q.base, q.c);
-        if (P.status) P.status[cell] = (int8_t)status;
-        if (P.nsub) P.nsub[cell] = nacc;
-        if (P.nrej) P.nrej[cell] = nrej;
+        const Segment* S = q.seg;
+        const int64_t cell = cell_of(S, q.base, q.c);
+        if (S->status) S->status[cell] = (int8_t)status;
+        if (S->nsub) S->nsub[cell] = nacc;
+        if (S->nrej) S->nrej[cell] = nrej;
       }
       g.sync();
       active = false;
@@ -886,7 +937,7 @@ int launch_adv_t(const LaunchShape& s, const AdvanceParams& P, const chem_option
   CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CHEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<G>, s.threads, s.smem));
   if (per_sm < 1) { set_error("kernel does not fit on an SM"); return CHEM_EINVAL; }
-  int64_t chunks = (P.ncells + CHUNK - 1) / CHUNK;     // an upper bound when ncells_dev is set
+  int64_t chunks = P.total_chunks;     // an upper bound when the count is read on the device
   int64_t grid = (int64_t)sms * per_sm;
   if (opt && opt->max_ctas > 0) grid = std::min<int64_t>(grid, opt->max_ctas);
   grid = std::min<int64_t>(grid, (chunks + s.groups - 1) / s.groups);
@@ -953,8 +1004,9 @@ int launch_advance(chem_mech_s* m, double* T, const double* p, double* Y, int64_
   CHEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream));
   AdvanceParams P;
   P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
-  P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells; P.dt = dt; P.rtol = rtol; P.atol = atol;
-  P.idx = idx; P.status = status; P.nsub = nsub; P.nrej = nrej;
+  P.segs[0] = Segment{T, p, Y, ld, ncells, idx, status, nsub, nrej, dt, rtol, atol, 0};
+  P.nseg = 1;
+  P.total_chunks = (ncells + CHUNK - 1) / CHUNK;
   P.max_steps = (opt && opt->max_steps > 0) ? opt->max_steps : 100000;
   P.counter = counter;
   P.ncells_dev = nullptr;
@@ -980,8 +1032,9 @@ int launch_advance_counted(chem_mech_s* m, double* T, const double* p, double* Y
   CHEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream));
   AdvanceParams P;
   P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
-  P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = capacity; P.dt = dt; P.rtol = rtol; P.atol = atol;
-  P.idx = idx; P.status = nullptr; P.nsub = nullptr; P.nrej = nullptr;
+  P.segs[0] = Segment{T, p, Y, ld, capacity, idx, nullptr, nullptr, nullptr, dt, rtol, atol, 0};
+  P.nseg = 1;
+  P.total_chunks = (capacity + CHUNK - 1) / CHUNK;
   P.max_steps = 100000;
   P.counter = counter;
   P.ncells_dev = count_dev;
@@ -989,6 +1042,49 @@ int launch_advance_counted(chem_mech_s* m, double* T, const double* p, double* Y
   cudaError_t fe = cudaFreeAsync(counter, stream);
   if (rc) return rc;
   CHEM_CUDA_TRY(fe);
+  return CHEM_OK;
+}
+
+// Batched launch: the chunks of all segments go through one work queue of one persistent
+// launch (segment descriptors travel in the kernel parameters, kMaxSegs per launch; a larger
+// batch becomes consecutive launches on the stream).
+int launch_advance_batch(chem_mech_s* m, const chem_segment* segs, int nseg, cudaStream_t stream) {
+  if (!m || !segs || nseg < 1) { set_error("bad batch arguments"); return CHEM_EINVAL; }
+  for (int i = 0; i < nseg; ++i) {
+    const chem_segment& a = segs[i];
+    if (a.ncells < 0 || !(a.dt > 0.0) || !(a.rtol > 0.0) || !(a.atol > 0.0) || !std::isfinite(a.dt) ||
+        (a.ncells > 0 && (!a.T || !a.p || !a.Y)) || (!a.idx && a.ld < a.ncells)) {
+      set_error("segment %d: invalid arguments", i);
+      return CHEM_EINVAL;
+    }
+  }
+  LaunchShape s;
+  int rc = pick_shape(m, nullptr, &s);
+  if (rc) return rc;
+  for (int first = 0; first < nseg; first += kMaxSegs) {
+    const int cnt = std::min(kMaxSegs, nseg - first);
+    AdvanceParams P;
+    P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
+    long long total = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const chem_segment& a = segs[first + i];
+      P.segs[i] = Segment{a.T, a.p, a.Y, a.ld, a.ncells, a.idx, a.status, a.nsub, a.nrej, a.dt, a.rtol, a.atol, total};
+      total += (a.ncells + CHUNK - 1) / CHUNK;
+    }
+    if (total == 0) continue;
+    P.nseg = cnt;
+    P.total_chunks = total;
+    P.max_steps = 100000;
+    P.ncells_dev = nullptr;
+    unsigned long long* counter = nullptr;
+    CHEM_CUDA_TRY(cudaMallocAsync((void**)&counter, sizeof(unsigned long long), stream));
+    CHEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream));
+    P.counter = counter;
+    rc = dispatch_adv(s, P, nullptr, stream);
+    cudaError_t fe = cudaFreeAsync(counter, stream);
+    if (rc) return rc;
+    CHEM_CUDA_TRY(fe);
+  }
   return CHEM_OK;
 }
 
@@ -1070,8 +1166,9 @@ int launch_advance_noalloc(chem_mech_s* m, double* T, const double* p, double* Y
   CHEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream));
   AdvanceParams P;
   P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
-  P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells; P.dt = dt; P.rtol = rtol; P.atol = atol;
-  P.idx = nullptr; P.status = status; P.nsub = nsub; P.nrej = nrej;
+  P.segs[0] = Segment{T, p, Y, ld, ncells, nullptr, status, nsub, nrej, dt, rtol, atol, 0};
+  P.nseg = 1;
+  P.total_chunks = (ncells + CHUNK - 1) / CHUNK;
   P.max_steps = 100000;
   P.counter = counter;
   P.ncells_dev = nullptr;
@@ -1102,6 +1199,11 @@ extern "C" int chem_advance_ex(chem_mech_t m, double* T, const double* p, double
                                const chem_options* opt, chem_stream_t stream) {
   return launch_advance(m, T, p, Y, ld, dt, ncells, rtol, atol, idx, status, nsub, nrej, opt,
                         (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int chem_advance_batch(chem_mech_t m, const chem_segment* segs, int nseg,
+                                  chem_stream_t stream) {
+  return launch_advance_batch(m, segs, nseg, (cudaStream_t)stream);
 }
 
 extern "C" int chem_eval_rhs_jac(chem_mech_t m, const double* T, const double* p, const double* Y,

@@ -1,0 +1,361 @@
+// Serving loop: chemistry sub-steps requested by many concurrent flow solvers.
+//
+// In the paper one solver owns the GPU and its time loop calls the chemistry step once per CFD
+// step (§3.1, Fig. 1); here many solvers share one GPU.  Each solver registers its state arrays
+// once (they stay resident on the device) and then submits one request per sub-step.  A server
+// thread
+//   * admits queued requests in arrival order, skipping ahead to requests that fit, while the
+//     resident states plus the workspace of the requests in flight stay within the device-memory
+//     budget, and at most one request per state is in flight;
+//   * batches the admitted FP64 requests of each mechanism into one persistent integrator launch
+//     (chem_advance_batch: their cells share one work queue), surrogate requests into their own
+//     launches, each launch on the next free stream of a small pool so that launches overlap on
+//     the device;
+//   * retires launches when their CUDA event completes, records the latency from submission to
+//     completion and frees their budget, so requests arriving meanwhile are admitted as slots and
+//     memory free up (continuous batching).
+// chem_serve_poll never blocks; chem_serve_wait blocks at most the given timeout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "chem_internal.h"
+
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+enum { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2, Q_FAILED = 3 };
+
+struct StateRec {
+  chem_mech_t mech;
+  chem_model_t model;
+  double* T;
+  double* p;
+  double* Y;
+  int64_t ld, ncells;
+  size_t resident;
+  bool busy = false;
+};
+
+struct Req {
+  uint64_t id;
+  int state;
+  int route;
+  double dt, rtol, atol;
+  int status = Q_QUEUED;
+  size_t bytes = 0;
+  Clock::time_point t_submit, t_done;
+  std::string error;
+};
+
+struct Launch {
+  cudaEvent_t ev;
+  int stream;
+  std::vector<uint64_t> reqs;
+  size_t bytes;
+};
+
+}  // namespace
+
+extern "C" int chem_surrogate_advance(chem_model_t md, chem_mech_t mech, double* T, const double* p,
+                                      double* Y, int64_t ld, double dt, int64_t ncells, double rtol,
+                                      double atol, int8_t* route_out, chem_stream_t stream);
+
+struct chem_server_s {
+  size_t budget = 0, resident = 0, inflight = 0;
+  int device = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<bool> stream_busy;
+  std::map<int, StateRec> states;
+  int next_state = 1;
+  std::map<uint64_t, Req> reqs;
+  std::deque<uint64_t> pending;
+  uint64_t next_req = 1;
+  std::vector<Launch> launches;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread th;
+  bool stop = false;
+  int64_t n_launches = 0, n_batched = 0, n_done = 0, n_failed = 0, max_concurrent = 0;
+  double idle_poll_us = 20.0;
+};
+
+namespace {
+
+size_t request_bytes(const StateRec& s, int route) {
+  if (route == CHEM_ROUTE_SURROGATE)    // network output, box flags, fallback list
+    return (size_t)s.ncells * ((size_t)s.mech->ns * 4 + 1 + 4) + 4096;
+  return 4096;                           // work-queue counter
+}
+
+void server_loop(chem_server_s* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    // ---- retire finished launches ----
+    bool progressed = false;
+    for (size_t i = 0; i < S->launches.size();) {
+      Launch& L = S->launches[i];
+      cudaError_t q = cudaEventQuery(L.ev);
+      if (q == cudaErrorNotReady) { ++i; continue; }
+      const Clock::time_point now = Clock::now();
+      for (uint64_t id : L.reqs) {
+        Req& r = S->reqs[id];
+        r.status = q == cudaSuccess ? Q_DONE : Q_FAILED;
+        if (q != cudaSuccess) r.error = cudaGetErrorString(q);
+        r.t_done = now;
+        S->states[r.state].busy = false;
+        if (r.status == Q_DONE) ++S->n_done; else ++S->n_failed;
+      }
+      S->inflight -= L.bytes;
+      S->stream_busy[L.stream] = false;
+      cudaEventDestroy(L.ev);
+      S->launches.erase(S->launches.begin() + i);
+      progressed = true;
+    }
+    if (progressed) S->cv_done.notify_all();
+    if (S->stop && S->launches.empty()) break;
+
+    // ---- admit and launch ----
+    int free_stream = -1;
+    for (size_t k = 0; k < S->streams.size(); ++k)
+      if (!S->stream_busy[k]) { free_stream = (int)k; break; }
+    if (!S->stop && free_stream >= 0 && !S->pending.empty()) {
+      // FP64 requests grouped by mechanism (one batched launch each) and surrogate requests
+      std::map<chem_mech_t, std::vector<uint64_t>> fp64;
+      std::vector<uint64_t> sur;
+      size_t avail = S->budget - S->resident - S->inflight;
+      std::deque<uint64_t> keep;
+      for (uint64_t id : S->pending) {
+        Req& r = S->reqs[id];
+        StateRec& st = S->states[r.state];
+        const bool take = !st.busy && r.bytes <= avail &&
+                          (r.route == CHEM_ROUTE_FP64 || sur.size() < S->streams.size());
+        if (take) {
+          avail -= r.bytes;
+          st.busy = true;
+          if (r.route == CHEM_ROUTE_FP64) fp64[st.mech].push_back(id);
+          else sur.push_back(id);
+        } else {
+          keep.push_back(id);
+        }
+      }
+      S->pending.swap(keep);
+      // build launches; each needs a free stream, the rest go back to the queue front
+      std::vector<std::vector<uint64_t>> groups;
+      for (auto& kv : fp64) groups.push_back(kv.second);
+      for (uint64_t id : sur) groups.push_back({id});
+      std::vector<uint64_t> back;
+      for (auto& grp : groups) {
+        int sidx = -1;
+        for (size_t k = 0; k < S->streams.size(); ++k)
+          if (!S->stream_busy[k]) { sidx = (int)k; break; }
+        if (sidx < 0) {
+          for (uint64_t id : grp) { S->states[S->reqs[id].state].busy = false; back.push_back(id); }
+          continue;
+        }
+        size_t bytes = 0;
+        for (uint64_t id : grp) bytes += S->reqs[id].bytes;
+        cudaStream_t strm = S->streams[sidx];
+        int rc = CHEM_OK;
+        const Req& r0 = S->reqs[grp[0]];
+        if (r0.route == CHEM_ROUTE_FP64) {
+          std::vector<chem_segment> segs;
+          for (uint64_t id : grp) {
+            const Req& r = S->reqs[id];
+            const StateRec& st = S->states[r.state];
+            chem_segment g{};
+            g.T = st.T; g.p = st.p; g.Y = st.Y; g.ld = st.ld; g.ncells = st.ncells;
+            g.dt = r.dt; g.rtol = r.rtol; g.atol = r.atol;
+            segs.push_back(g);
+          }
+          rc = chem::launch_advance_batch(S->states[r0.state].mech, segs.data(), (int)segs.size(), strm);
+        } else {
+          const StateRec& st = S->states[r0.state];
+          rc = chem_surrogate_advance(st.model, st.mech, st.T, st.p, st.Y, st.ld, r0.dt, st.ncells, r0.rtol,
+                                      r0.atol, nullptr, strm);
+        }
+        const Clock::time_point now = Clock::now();
+        if (rc != CHEM_OK) {
+          const char* msg = chem_last_error();
+          for (uint64_t id : grp) {
+            Req& r = S->reqs[id];
+            r.status = Q_FAILED;
+            r.error = msg ? msg : "launch failed";
+            r.t_done = now;
+            S->states[r.state].busy = false;
+            ++S->n_failed;
+          }
+          S->cv_done.notify_all();
+          continue;
+        }
+        Launch L;
+        L.stream = sidx;
+        L.reqs = grp;
+        L.bytes = bytes;
+        cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
+        cudaEventRecord(L.ev, strm);
+        for (uint64_t id : grp) S->reqs[id].status = Q_RUNNING;
+        S->inflight += bytes;
+        S->stream_busy[sidx] = true;
+        S->launches.push_back(L);
+        ++S->n_launches;
+        S->n_batched += (int64_t)grp.size();
+        S->max_concurrent = std::max<int64_t>(S->max_concurrent, (int64_t)S->launches.size());
+      }
+      for (auto it = back.rbegin(); it != back.rend(); ++it) S->pending.push_front(*it);
+      if (!groups.empty()) continue;    // look again right away
+    }
+    // ---- wait ----
+    if (S->launches.empty()) {
+      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+    } else {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds((int)S->idle_poll_us));
+      lk.lock();
+    }
+  }
+}
+
+}  // namespace
+
+using namespace chem;
+
+extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_options* opt, chem_server_t* out) {
+  if (!out || hbm_budget_bytes == 0) { set_error("bad arguments"); return CHEM_EINVAL; }
+  *out = nullptr;
+  chem_server_s* S = new chem_server_s();
+  S->budget = hbm_budget_bytes;
+  const int ns = (opt && opt->n_streams > 0) ? opt->n_streams : 4;
+  if (opt && opt->idle_poll_us > 0) S->idle_poll_us = opt->idle_poll_us;
+  if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; return cuda_fail(cudaGetLastError(), "cudaGetDevice"); }
+  for (int i = 0; i < ns; ++i) {
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+      delete S;
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+    S->streams.push_back(st);
+    S->stream_busy.push_back(false);
+  }
+  S->th = std::thread(server_loop, S);
+  *out = S;
+  return CHEM_OK;
+}
+
+extern "C" int chem_serve_register_state(chem_server_t S, chem_mech_t m, chem_model_t model, double* T, double* p,
+                                         double* Y, int64_t ld, int64_t ncells, int* state_id) {
+  if (!S || !m || !T || !p || !Y || !state_id || ncells <= 0 || ld < ncells) {
+    set_error("bad arguments");
+    return CHEM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  StateRec st;
+  st.mech = m; st.model = model; st.T = T; st.p = p; st.Y = Y; st.ld = ld; st.ncells = ncells;
+  st.resident = (size_t)ncells * (m->ns + 2) * sizeof(double);
+  if (S->resident + st.resident > S->budget) {
+    set_error("state of %zu bytes does not fit the budget", st.resident);
+    return CHEM_EBUSY;
+  }
+  S->resident += st.resident;
+  const int id = S->next_state++;
+  S->states[id] = st;
+  *state_id = id;
+  return CHEM_OK;
+}
+
+extern "C" int chem_serve_submit(chem_server_t S, int state_id, int route, double dt, double rtol, double atol,
+                                 uint64_t* req_id) {
+  if (!S || !req_id || !(dt > 0.0) || !(rtol > 0.0) || !(atol > 0.0) ||
+      (route != CHEM_ROUTE_FP64 && route != CHEM_ROUTE_SURROGATE)) {
+    set_error("bad arguments");
+    return CHEM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->states.find(state_id);
+  if (it == S->states.end()) { set_error("unknown state %d", state_id); return CHEM_ENOTFOUND; }
+  if (route == CHEM_ROUTE_SURROGATE && !it->second.model) {
+    set_error("state %d has no surrogate model", state_id);
+    return CHEM_EINVAL;
+  }
+  Req r;
+  r.id = S->next_req++;
+  r.state = state_id; r.route = route; r.dt = dt; r.rtol = rtol; r.atol = atol;
+  r.bytes = request_bytes(it->second, route);
+  if (r.bytes > S->budget - S->resident) {
+    set_error("request needs %zu bytes beyond the resident states; budget left %zu", r.bytes,
+              S->budget - S->resident);
+    return CHEM_EBUSY;
+  }
+  r.t_submit = Clock::now();
+  S->reqs[r.id] = r;
+  S->pending.push_back(r.id);
+  *req_id = r.id;
+  S->cv_work.notify_one();
+  return CHEM_OK;
+}
+
+extern "C" int chem_serve_poll(chem_server_t S, uint64_t req_id, int* state, double* latency_s) {
+  if (!S || !state) { set_error("bad arguments"); return CHEM_EINVAL; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(req_id);
+  if (it == S->reqs.end()) { set_error("unknown request"); return CHEM_ENOTFOUND; }
+  *state = it->second.status;
+  if (latency_s)
+    *latency_s = it->second.status >= Q_DONE
+                     ? std::chrono::duration<double>(it->second.t_done - it->second.t_submit).count()
+                     : -1.0;
+  if (it->second.status == Q_FAILED) set_error("%s", it->second.error.c_str());
+  return CHEM_OK;
+}
+
+extern "C" int chem_serve_wait(chem_server_t S, uint64_t req_id, double timeout_s) {
+  if (!S || timeout_s < 0) { set_error("bad arguments"); return CHEM_EINVAL; }
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(req_id);
+  if (it == S->reqs.end()) { set_error("unknown request"); return CHEM_ENOTFOUND; }
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+  const bool ok = S->cv_done.wait_until(lk, deadline, [&] { return S->reqs[req_id].status >= Q_DONE; });
+  if (!ok) { set_error("request %llu not finished within %g s", (unsigned long long)req_id, timeout_s); return CHEM_ETIMEOUT; }
+  if (S->reqs[req_id].status == Q_FAILED) { set_error("%s", S->reqs[req_id].error.c_str()); return CHEM_ECUDA; }
+  return CHEM_OK;
+}
+
+extern "C" int chem_serve_stats(chem_server_t S, int64_t* out /*[6]*/) {
+  if (!S || !out) { set_error("bad arguments"); return CHEM_EINVAL; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  out[0] = S->n_done; out[1] = S->n_failed; out[2] = S->n_launches; out[3] = S->n_batched;
+  out[4] = S->max_concurrent; out[5] = (int64_t)(S->resident + S->inflight);
+  return CHEM_OK;
+}
+
+extern "C" int chem_serve_destroy(chem_server_t S) {
+  if (!S) { set_error("NULL server"); return CHEM_EINVAL; }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    // queued requests that never started are dropped as failed
+    for (uint64_t id : S->pending) {
+      Req& r = S->reqs[id];
+      r.status = Q_FAILED;
+      r.error = "server destroyed";
+    }
+    S->pending.clear();
+  }
+  S->cv_work.notify_all();
+  if (S->th.joinable()) S->th.join();
+  for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+  delete S;
+  return CHEM_OK;
+}

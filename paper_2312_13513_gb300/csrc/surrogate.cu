@@ -412,7 +412,48 @@ __global__ void surrogate_post_kernel(const PostParams P) {
   }
 }
 
+// heat-release rate of a step: q = -rho0 sum_k h_k(T0) (Y1_k - Y0_k) / (W_k dt), h_k molar
+__global__ void heat_release_kernel(const unsigned char* blob, MechLayout L, const double* T0, const double* p,
+                                    const double* Y0, const double* Y1, int64_t ld, int64_t n, double dt,
+                                    double* q) {
+  const int ns = L.ns;
+  const double* hc = (const double*)(blob + L.o_hc);
+  const double* invW = (const double*)(blob + L.o_invW);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const double T = T0[c], invT = 1.0 / T;
+    const int rg = T < TMID ? 0 : 1;
+    double S = 0.0, acc = 0.0;
+    for (int k = 0; k < ns; ++k) {
+      const double* a = hc + (rg * ns + k) * 6;
+      const double hRT = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4]))) + a[5] * invT;
+      const double y0 = Y0[(int64_t)k * ld + c];
+      S += y0 * __ldg(invW + k);
+      acc += hRT * (Y1[(int64_t)k * ld + c] - y0) * __ldg(invW + k);
+    }
+    const double rho = p[c] / (RU * T * S);
+    q[c] = -rho * RU * T * acc / dt;
+  }
+}
+
 }  // namespace chem
+
+extern "C" int chem_heat_release(chem_mech_t m, const double* T0, const double* p, const double* Y0,
+                                 const double* Y1, int64_t ld, int64_t ncells, double dt, double* q,
+                                 chem_stream_t stream) {
+  using namespace chem;
+  if (!m || !T0 || !p || !Y0 || !Y1 || !q || ncells < 0 || ld < ncells || !(dt > 0.0)) {
+    set_error("bad arguments");
+    return CHEM_EINVAL;
+  }
+  if (ncells == 0) return CHEM_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>((ncells + 255) / 256, 8192);
+  heat_release_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>((const unsigned char*)m->d_blob, m->lay, T0, p,
+                                                                  Y0, Y1, ld, ncells, dt, q);
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+namespace chem {}
 
 // ---------------------------------------------------------------------------------------
 // model object and entry points

@@ -6,7 +6,8 @@ stratified burner LES of §4.2) are not available; these generators stand in for
 * ``mixing_states``: H2/air mixture fraction Z ~ U[0, 1], T ~ U[900, 2200] K, p = 1 atm, with a
   seeded half of the cells flagged for partial reaction over t ~ logU[1e-7, 1e-3] s (the
   caller advances those cells with a reactor of its choice).
-* ``quasi_dns_field``: a 128^3 grid (x fastest) carrying a train of planar premixed fronts,
+* ``quasi_dns_field``: a 128^3 grid (x fastest; 128 x 128 x nz for more than 2^21 cells)
+  carrying a train of planar premixed fronts,
   c(x) = (1 + tanh(s(x)/delta))/2 with two fronts per 32-cell period and delta = 2 cells,
   mapped through a tabulated flamelet (T(c), Y(c)), then multiplied by seeded Gaussian random
   fields (correlation length 8 cells): T by (1 + 0.05 g), each Y_k by (1 + 0.10 g_k), and Y
@@ -83,11 +84,11 @@ def _interp_profile(c_grid, vals, c):
 def quasi_dns_field(table, n=1 << 20, seed=12346, grid=128, period=32, delta=2.0, corr_len=8.0):
     """Quasi-DNS-shaped H2 field: the first n cells (x fastest) of a grid^3 box."""
     rng = np.random.default_rng(seed)
-    shape = (grid, grid, grid)          # indexed [z, y, x]
+    nz = -(-n // (grid * grid))
+    shape = (max(grid, nz), grid, grid)  # indexed [z, y, x]; taller than grid^3 beyond 2^21 cells
     x = np.arange(grid)
     s = period / 4.0 - np.abs((x % period) - period / 2.0)
     c_x = 0.5 * (1.0 + np.tanh(s / delta))
-    nz = -(-n // (grid * grid))
     c = np.broadcast_to(c_x[None, None, :], (nz, grid, grid)).reshape(-1)[:n]
     T = np.interp(c, table["c"], table["T"])
     Y = _interp_profile(table["c"], table["Y"], c)

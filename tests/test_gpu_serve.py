@@ -1,0 +1,159 @@
+"""Serving loop and batched advances on the GPU."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2312_13513_gb300 as cg  # noqa: E402
+from paper_2312_13513_gb300 import serve  # noqa: E402
+from oracle import surrogate as osur  # noqa: E402
+from synth.states import les_field, load_table, quasi_dns_field  # noqa: E402
+
+from gpu_common import to_dev  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _h2_state(n, seed):
+    f = quasi_dns_field(load_table("h2_flamelet.npz"), n=n, seed=seed)
+    return f["T"], f["p"], f["Y"]
+
+
+def _identity_model(dm, mech, T, p, Y, dt=5e-7):
+    x = osur.features(T, p, Y)
+    rng = np.random.default_rng(0)
+    nin = mech.ns + 2
+    dims = [nin, 512, 512, 512, 512, mech.ns]
+    W = [rng.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i]) for i in range(5)]
+    b = [np.zeros(dims[i + 1]) for i in range(5)]
+    W[4] = np.zeros_like(W[4])
+    sd = x.std(axis=0)
+    prm = {"W": W, "b": b, "dt": dt, "x_mean": x.mean(axis=0),
+           "x_std": np.where(sd > 1e-6 * np.maximum(1, np.abs(x.mean(axis=0))), sd, 1.0),
+           "y_mean": np.zeros(mech.ns), "y_std": np.ones(mech.ns),
+           "box_lo": x.min(axis=0) - 1.0, "box_hi": x.max(axis=0) + 1.0}
+    return cg.Surrogate(dm, prm)
+
+
+def test_batch_equals_individual_launches(h2):
+    dm = cg.Mechanism(h2)
+    segs, ref = [], []
+    for i, (n, dt, rtol) in enumerate(((3000, 5e-7, 1e-6), (1234, 1e-6, 1e-7), (77, 2e-7, 1e-6))):
+        T, p, Y = _h2_state(n, 100 + i)
+        a = to_dev(T, p, Y)
+        b = to_dev(T, p, Y)
+        cg.advance(dm, b[0], b[1], b[2], dt, rtol)
+        segs.append({"T": a[0], "p": a[1], "Y": a[2], "dt": dt, "rtol": rtol})
+        ref.append(b)
+    serve.advance_batch(dm, segs)
+    torch.cuda.synchronize()
+    for s, r in zip(segs, ref):
+        assert torch.equal(s["T"], r[0]) and torch.equal(s["Y"], r[2])
+
+
+def _fresh(states):
+    return [tuple(x.clone() for x in s) for s in states]
+
+
+def test_same_result_alone_and_in_the_mix(h2, ch4):
+    dm_h2, dm_ch4 = cg.Mechanism(h2), cg.Mechanism(ch4)
+    base = [_h2_state(n, 200 + i) for i, n in enumerate((20000, 5000, 50000, 12000))]
+    f = les_field(load_table("ch4_flamelet.npz"), n=3000, seed=9)
+    base_ch4 = (f["T"], f["p"], f["Y"])
+    model = _identity_model(dm_h2, h2, *base[0])
+    dev = [to_dev(*s) for s in base] + [to_dev(*base_ch4)]
+    mechs = [dm_h2] * 4 + [dm_ch4]
+    routes = [serve.ROUTE_SURROGATE, serve.ROUTE_FP64, serve.ROUTE_FP64, serve.ROUTE_SURROGATE, serve.ROUTE_FP64]
+
+    def run(which):
+        states = _fresh(dev)
+        srv = serve.Server(8 << 30, n_streams=4)
+        ids = [srv.register(mechs[i], *states[i], model=model if i < 4 else None) for i in range(5)]
+        reqs = [srv.submit(ids[i], routes[i], 5e-7) for i in which]
+        for r in reqs:
+            srv.wait(r, 120.0)
+        st = srv.stats()
+        srv.close()
+        return states, st
+
+    alone = {}
+    for i in range(5):
+        states, _ = run([i])
+        alone[i] = states[i]
+    mixed, st = run(range(5))
+    assert st["completed"] == 5 and st["failed"] == 0
+    assert st["max_concurrent"] >= 2          # launches overlapped on the device
+    for i in range(5):
+        assert torch.equal(mixed[i][0], alone[i][0]) and torch.equal(mixed[i][2], alone[i][2]), i
+
+
+def test_small_budget_forces_queueing(h2):
+    dm = cg.Mechanism(h2)
+    states = [to_dev(*_h2_state(20000, 300 + i)) for i in range(4)]
+    model = _identity_model(dm, h2, *[s.cpu().numpy() for s in states[0]])
+    resident = sum(s[0].numel() * (h2.ns + 2) * 8 for s in states)
+    one_request = 20000 * (h2.ns * 4 + 5) + 4096
+    srv = serve.Server(resident + one_request + 1000, n_streams=4)
+    ids = [srv.register(dm, *s, model=model) for s in states]
+    reqs = [srv.submit(i, serve.ROUTE_SURROGATE, 5e-7) for i in ids]
+    for r in reqs:
+        srv.wait(r, 60.0)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 4 and st["max_concurrent"] == 1
+
+
+def test_never_admissible_request_is_rejected(h2):
+    dm = cg.Mechanism(h2)
+    s = to_dev(*_h2_state(20000, 400))
+    model = _identity_model(dm, h2, *[x.cpu().numpy() for x in s])
+    resident = 20000 * (h2.ns + 2) * 8
+    srv = serve.Server(resident + 10000, n_streams=2)
+    sid = srv.register(dm, *s, model=model)
+    with pytest.raises(cg.ChemError) as e:
+        srv.submit(sid, serve.ROUTE_SURROGATE, 5e-7)
+    assert e.value.code == -4
+    rid = srv.submit(sid, serve.ROUTE_FP64, 5e-7)       # the FP64 route fits
+    srv.wait(rid, 60.0)
+    srv.close()
+
+
+def test_wait_times_out_and_poll_does_not_block(h2):
+    dm = cg.Mechanism(h2)
+    s = to_dev(*_h2_state(1 << 20, 500))
+    srv = serve.Server(8 << 30)
+    sid = srv.register(dm, *s)
+    rid = srv.submit(sid, serve.ROUTE_FP64, 5e-7)
+    t0 = time.time()
+    state, lat = srv.poll(rid)
+    assert time.time() - t0 < 0.05 and state in (serve.QUEUED, serve.RUNNING)
+    with pytest.raises(cg.ChemError) as e:
+        srv.wait(rid, 1e-4)
+    assert e.value.code == -5
+    srv.wait(rid, 120.0)
+    state, lat = srv.poll(rid)
+    assert state == serve.DONE and lat > 0.0
+    srv.close()
+
+
+def test_failed_request_does_not_poison_others(h2):
+    dm = cg.Mechanism(h2)
+    a = to_dev(*_h2_state(5000, 600))
+    b = to_dev(*_h2_state(5000, 601))
+    model = _identity_model(dm, h2, *[x.cpu().numpy() for x in a], dt=1e-6)   # trained for 1e-6
+    srv = serve.Server(8 << 30)
+    sa = srv.register(dm, *a, model=model)
+    sb = srv.register(dm, *b)
+    bad = srv.submit(sa, serve.ROUTE_SURROGATE, 5e-7)     # wrong dt: fails at launch
+    good = srv.submit(sb, serve.ROUTE_FP64, 5e-7)
+    srv.wait(good, 60.0)
+    with pytest.raises(cg.ChemError):
+        srv.wait(bad, 60.0)
+    assert srv.poll(bad)[0] == serve.FAILED and srv.poll(good)[0] == serve.DONE
+    again = srv.submit(sa, serve.ROUTE_FP64, 5e-7)
+    srv.wait(again, 60.0)
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 1 and st["completed"] == 2
