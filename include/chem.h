@@ -237,7 +237,8 @@ typedef struct chem_trainer_s* chem_trainer_t;
 int chem_mlp_trainer_create(int n_in, int n_out, int batch, const float* const* W_init,
                             const float* const* b_init, uint64_t seed, chem_trainer_t* out);
 int chem_mlp_trainer_free(chem_trainer_t t);
-/* forward pass of one batch, keeping the activations; out (nullable) receives [batch x n_out] */
+/* forward pass of one batch, keeping the activations; out (nullable) receives [batch x n_out].
+ * X is read again by chem_mlp_backward: it must stay valid until that call's work is done. */
 int chem_mlp_forward(chem_trainer_t t, const void* X, float* out, chem_stream_t stream);
 /* mean-squared-error gradients of the last forward pass; loss (device double, nullable) */
 int chem_mlp_backward(chem_trainer_t t, const float* target, double* loss, chem_stream_t stream);

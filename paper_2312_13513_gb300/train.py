@@ -42,6 +42,8 @@ class Trainer:
         self.handle = h
 
     def forward(self, X, out=None, stream=None):
+        # the backward pass reads X again (weight gradient of the first layer): keep it alive
+        self._x = X
         check(_lib.load().chem_mlp_forward(self.handle, _ptr(X), _ptr(out), _stream_ptr(stream)))
 
     def backward(self, target, loss=None, stream=None):
