@@ -177,22 +177,175 @@ def run_case(args):
     else:
         mech = ch4_mechanism()
         f, dt = les_field(load_table("ch4_flamelet.npz"), n=args.cells, seed=12347), 1e-6
+    from paper_2312_13513_gb300 import flops as fl
     dm = cg.Mechanism(mech)
     T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
     Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+    nsub = torch.zeros(args.cells, dtype=torch.int32, device="cuda"); nrej = torch.zeros_like(nsub)
+    opts = cg.options(group_threads=args.group) if args.group else None
     ms = []
     for k in range(args.warmup + args.steps):
         T = T0.clone(); Y = Y0.clone()
         a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
-        cg.advance(dm, T, p, Y, dt, RTOL, ATOL)
+        cg.advance(dm, T, p, Y, dt, RTOL, ATOL, nsub=nsub, nrej=nrej, opts=opts)
         b.record()
         torch.cuda.synchronize()
         if k >= args.warmup:
             ms.append(a.elapsed_time(b))
-    print(json.dumps({"case": args.case, "cells": args.cells, "ms": ms,
-                      "cells_per_s": args.cells / (np.mean(ms) * 1e-3)}), flush=True)
+    acc = int(nsub.sum()); att = acc + int(nrej.sum())
+    _, _, folded = fl.launch_flops(mech, acc, att)
+    t = float(np.mean(ms)) * 1e-3
+    print(json.dumps({"case": args.case, "cells": args.cells, "group": args.group, "ms": ms,
+                      "cells_per_s": args.cells / t, "attempts_per_cell": att / args.cells,
+                      "fp64_tflops": folded / t / 1e12,
+                      "fp64_frac": folded / t / 1e12 / cg.fp64_fma_peak()}), flush=True)
+
+
+MODEL_PATH = os.path.join(ROOT, "paper_2312_13513_gb300", "models", "h2_quasi_dns.chemsur")
+
+
+def _time_ms(fn, stream, reps=1):
+    import torch
+    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+    out = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        a.record(stream); fn(); b.record(stream)
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
+def extra_ch4(fp64_peak, steps=2):
+    """Config 2: CH4/air-shaped mechanism (53 species, 325 reactions), 262144 LES cells."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from paper_2312_13513_gb300 import flops as fl
+    from synth.mechanism import ch4_mechanism
+    from synth.states import les_field, load_table
+    mech = ch4_mechanism()
+    dm = cg.Mechanism(mech)
+    f = les_field(load_table("ch4_flamelet.npz"), n=262144, seed=12347)
+    T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+    Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+    n = T0.numel()
+    ns_ = torch.zeros(n, dtype=torch.int32, device="cuda"); nr_ = torch.zeros_like(ns_)
+    T, Y = T0.clone(), Y0.clone()
+    stream = torch.cuda.current_stream()
+
+    def run():
+        T.copy_(T0); Y.copy_(Y0)
+        cg.advance(dm, T, p, Y, 1e-6, RTOL, ATOL, nsub=ns_, nrej=nr_, stream=stream)
+
+    run()
+    ms = _time_ms(run, stream, steps)
+    acc = int(ns_.sum()); att = acc + int(nr_.sum())
+    flo, tr, folded = fl.launch_flops(mech, acc, att)
+    t = min(ms) * 1e-3
+    return {"workload": "FP64 Rodas4, 262144 LES-shaped CH4/air cells (53 species, 325 reactions), "
+                        "dt=1e-6 s, 128-thread group per cell",
+            "ms": min(ms), "cell_updates_per_s": n / t,
+            "fp64_tflops": folded / t / 1e12, "fp64_frac": folded / t / 1e12 / fp64_peak,
+            "attempts_mean": att / n}
+
+
+def extra_surrogate(peaks, steps=3):
+    """Config 3: BF16 MLP surrogate vs the FP64 integrator on 2^22 quasi-DNS H2 cells."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from paper_2312_13513_gb300 import train as trn
+    from synth.mechanism import h2_mechanism
+    mech = h2_mechanism()
+    dm = cg.Mechanism(mech)
+    trained_here = False
+    if not os.path.exists(MODEL_PATH):
+        params = trn.train(mech, n_states=1 << 22, epochs=40, log=lambda *a: None, time_budget_s=90)
+        os.makedirs(os.path.dirname(MODEL_PATH), exist_ok=True)
+        trn.save_model(params, MODEL_PATH)
+        trained_here = True
+    model = cg.Surrogate(dm, path=MODEL_PATH)
+    f = make_field(0, 1 << 22)
+    n = f["T"].size
+    T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+    Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+    stream = torch.cuda.current_stream()
+    Tr, Yr = T0.clone(), Y0.clone()
+
+    def fp64():
+        Tr.copy_(T0); Yr.copy_(Y0)
+        cg.advance(dm, Tr, p, Yr, DT, RTOL, ATOL, stream=stream)
+
+    ms_fp64 = min(_time_ms(fp64, stream, 1))
+    Ts, Ys = T0.clone(), Y0.clone()
+    route = torch.empty(n, dtype=torch.int8, device="cuda")
+
+    def sur():
+        Ts.copy_(T0); Ys.copy_(Y0)
+        cg.surrogate_advance(model, Ts, p, Ys, DT, RTOL, ATOL, route=route, stream=stream)
+
+    sur()
+    ms_sur = min(_time_ms(sur, stream, steps))
+    ms_fwd = min(_time_ms(lambda: cg.surrogate_forward(model, T0, p, Y0, stream=stream), stream, steps))
+    qr = cg.heat_release(dm, T0, p, Y0, Yr, DT)
+    qs = cg.heat_release(dm, T0, p, Y0, Ys, DT)
+    err = float(((qs - qr).abs().sum() / qr.abs().sum()).item())
+    flop = 2.0 * (11 * 512 + 3 * 512 * 512 + 512 * 9) * n
+    tf = flop / (ms_fwd * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    return {"workload": "BF16 MLP 11-512x4-9 (tcgen05) with projection, Newton T and FP64 fallback, "
+                        "2^22 quasi-DNS H2 cells, dt=5e-7 s",
+            "surrogate_ms": ms_sur, "surrogate_cell_updates_per_s": n / (ms_sur * 1e-3),
+            "fp64_ms": ms_fp64, "fp64_cell_updates_per_s": n / (ms_fp64 * 1e-3),
+            "speedup_vs_fp64": ms_fp64 / ms_sur, "hrr_l1_rel_error_vs_fp64": err,
+            "fallback_fraction": float((route == 1).float().mean().item()),
+            "forward_kernel_ms": ms_fwd, "tensor_tflops": tf,
+            "tensor_frac_of_sustained": tf / peak, "model_trained_in_this_run": trained_here}
+
+
+def extra_serving(duration_s=10.0, seed=12349):
+    """Config 4: 64 closed-loop solvers (Exp(2 ms) think time), 70 % H2 / 30 % CH4, routes 50/50
+    (CH4 solvers use the FP64 route: no CH4 surrogate), 1e4-2e6 cells log-uniform."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from paper_2312_13513_gb300 import serve
+    from synth.mechanism import ch4_mechanism, h2_mechanism
+    from synth.states import les_field, load_table
+    rng = np.random.default_rng(seed)
+    h2, ch4 = h2_mechanism(), ch4_mechanism()
+    dm_h2, dm_ch4 = cg.Mechanism(h2), cg.Mechanism(ch4)
+    model = cg.Surrogate(dm_h2, path=MODEL_PATH) if os.path.exists(MODEL_PATH) else None
+    fh = make_field(7, 1 << 21)
+    fc = les_field(load_table("ch4_flamelet.npz"), n=1 << 21, seed=seed)
+    srv = serve.Server(150 << 30, n_streams=4)
+    solvers = []
+    for i in range(64):
+        n = int(np.exp(rng.uniform(np.log(1e4), np.log(2e6))))
+        is_h2 = rng.uniform() < 0.7
+        sur = rng.uniform() < 0.5
+        f = fh if is_h2 else fc
+        off = int(rng.integers(0, f["T"].size - n + 1))
+        T = torch.tensor(f["T"][off:off + n], device="cuda")
+        p = torch.tensor(f["p"][off:off + n], device="cuda")
+        Y = torch.tensor(np.ascontiguousarray(f["Y"][:, off:off + n]), device="cuda")
+        route = serve.ROUTE_SURROGATE if (is_h2 and sur and model is not None) else serve.ROUTE_FP64
+        sid = srv.register(dm_h2 if is_h2 else dm_ch4, T, p, Y, model=model if is_h2 else None)
+        solvers.append({"state_id": sid, "route": route, "dt": DT if is_h2 else 1e-6, "cells": n,
+                        "mech": "h2" if is_h2 else "ch4"})
+    res = serve.run_closed_loop(srv, solvers, duration_s=duration_s, mean_gap_s=2e-3, seed=seed)
+    st = srv.stats()
+    srv.close()
+    lat = np.array(res["latencies"]) * 1e3
+    return {"workload": "64 closed-loop solvers, Exp(2 ms) gaps, 1e4-2e6 cells log-uniform, "
+                        "70/30 H2/CH4, routes 50/50 (H2 only), 150 GB budget, 10 s",
+            "requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "cell_updates_per_s": res["cells"] / res["wall_s"], "wall_s": res["wall_s"],
+            "launches": st["launches"], "requests_per_launch": st["requests_launched"] / max(1, st["launches"]),
+            "max_concurrent_launches": st["max_concurrent"], "failed": st["failed"],
+            "cells_h2": int(sum(s["cells"] for s in solvers if s["mech"] == "h2")),
+            "cells_ch4": int(sum(s["cells"] for s in solvers if s["mech"] == "ch4"))}
 
 
 def main():
@@ -206,6 +359,7 @@ def main():
     ap.add_argument("--case", choices=["h2", "ch4"], default=None,
                     help="time only the integrator on a small case (profiling)")
     ap.add_argument("--cells", type=int, default=65536)
+    ap.add_argument("--group", type=int, default=0, help="threads per cell (profiling mode; 0 = auto)")
     args = ap.parse_args()
     if args.case:
         run_case(args)
@@ -345,6 +499,16 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(field, mech)
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = {}
+        for name, fn in (("ch4_les", lambda: extra_ch4(fp64_peak)),
+                         ("surrogate", lambda: extra_surrogate(_peaks())),
+                         ("serving", extra_serving)):
+            try:
+                extras[name] = fn()
+            except Exception as e:      # an extra measurement never hides the headline line
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
+        line["extras"] = extras
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

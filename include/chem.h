@@ -180,13 +180,17 @@ typedef struct chem_surrogate_desc {
   const float* b[5];         /* host: [512] x 4, [ns] */
   const float* x_mean;       /* [nin] feature mean and standard deviation */
   const float* x_std;
-  const float* y_mean;       /* [ns] output mean and standard deviation */
+  const float* y_mean;       /* [ns] output mean and standard deviation; y_std = 0 marks a species
+                                the step leaves unchanged (an inert one): its increment is 0 */
   const float* y_std;
   const float* box_lo;       /* [nin] training box of the raw features (trust region) */
   const float* box_hi;
 } chem_surrogate_desc;
 
-/* Upload a surrogate (weights rounded to BF16) for use with mechanism m on the current device. */
+/* Upload a surrogate for use with mechanism m on the current device.  Hidden and output weights
+ * are rounded to BF16; the first layer is compensated: its weights and input features are each
+ * split into a BF16 pair (hi + lo) and the product keeps the hi*hi, hi*lo and lo*hi terms, about
+ * 16 significant bits, because the rates depend exponentially on the temperature feature. */
 int chem_surrogate_create(const chem_surrogate_desc* desc, chem_mech_t m, chem_model_t* out);
 /* Same from a CHEMSUR1 binary file: magic, int32 ns, int32 hidden, double dt, then W[l], b[l]
  * (l = 0..4), x_mean, x_std, y_mean, y_std, box_lo, box_hi as little-endian float32. */
@@ -227,8 +231,10 @@ int chem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float
 /* ---------------------------------------------------------------------------------------
  * Surrogate training on the GPU (§2: GELU networks trained with Adam).  A trainer holds FP32
  * master weights, Adam moments and BF16 copies of a n_in -> 512 x 4 -> n_out GELU network;
- * every product runs on the tcgen05 GEMM.  Layout: X is BF16 [batch x 128] (features zero
- * padded to 128 columns), targets FP32 [batch x n_out], all device pointers.
+ * every product runs on the tcgen05 GEMM.  Layout: X is BF16 [batch x 128], each row the
+ * compensated split of the n_in features [x_hi | x_lo | x_hi | 0] (chem_train_normalize writes
+ * it; n_in <= 42); the first layer's BF16 weights are [W_hi | W_hi | W_lo | 0] and its master
+ * gradient is dZ^T (x_hi + x_lo).  Targets FP32 [batch x n_out], all device pointers.
  * ------------------------------------------------------------------------------------- */
 typedef struct chem_trainer_s* chem_trainer_t;
 
@@ -250,13 +256,15 @@ int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float beta2, flo
 int chem_mlp_trainer_get(chem_trainer_t t, int which, float* const* W, float* const* b);
 
 /* Training data: raw features x [n x (ns + 2)] = [T, ln p, BC(Y0)] and targets
- * t [n x ns] = BC(Y1) - BC(Y0) from states before (T0, p, Y0) and after (Y1) a step. */
+ * t [n x ns] = BC(Y1) - BC(Y0) (difference formed in FP64) from states before (T0, p, Y0) and
+ * after (Y1) a step. */
 int chem_train_features(const double* T0, const double* p, const double* Y0, const double* Y1,
                         int64_t ld, int64_t n, int ns, float* x_raw, float* t_raw,
                         chem_stream_t stream);
 /* stats[4 x c] (device doubles): column sums, sums of squares, minima, maxima of A [n x c] */
 int chem_column_stats(const float* A, int64_t n, int c, double* stats, chem_stream_t stream);
-/* X = bf16((x - mean) / sd) zero padded to ldx columns; Tn = (t - tmean) / tsd (t nullable) */
+/* v = (x - mean) / sd;  X row = [bf16(v) | bf16(v - bf16(v)) | bf16(v) | 0] (c columns each, zero
+ * padded to ldx >= 3 c); Tn = (t - tmean) / tsd (t nullable) */
 int chem_train_normalize(const float* x, int64_t n, int c, const float* mean, const float* sd,
                          void* X, int ldx, const float* t, int ct, const float* tmean,
                          const float* tsd, float* Tn, chem_stream_t stream);

@@ -6,8 +6,11 @@ the paper's per-species networks); here the layers are x -> 512 -> 512 -> 512 ->
 
 Conventions: W[l] has shape [n_out, n_in]; y = x @ W.T + b.  GELU is the exact form
 x * Phi(x) = 0.5 x (1 + erf(x / sqrt 2)).  BF16 emulation rounds a value first to FP32 and then
-to BF16 with round-to-nearest-even, at the points where the GPU path holds BF16 data: the input
-features, the weights, and each hidden activation after GELU.
+to BF16 with round-to-nearest-even, at the points where the GPU path holds BF16 data: the
+weights of layers 2-5 and each hidden activation after GELU.  The first layer is compensated:
+the input x and the weights W each become a pair of BF16 numbers, hi = bf16(v) and
+lo = bf16(v - hi), and the layer computes x_hi W_hi^T + x_lo W_hi^T + x_hi W_lo^T (the lo*lo
+product is left out).
 """
 from __future__ import annotations
 
@@ -37,13 +40,38 @@ def gelu_grad(x):
     return 0.5 * (1.0 + erf(x / np.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)
 
 
+def split_bf16(v):
+    """(hi, lo): hi = bf16(v), lo = bf16(v - hi).  hi + lo carries about 16 significant bits."""
+    v = np.asarray(v, np.float64)
+    hi = bf16_round(v)
+    return hi, bf16_round(v - hi)
+
+
+def first_layer(W, x):
+    """Compensated BF16 product x W^T of the first layer (no bias)."""
+    xh, xl = split_bf16(x)
+    wh, wl = split_bf16(W)
+    return xh @ wh.T + xl @ wh.T + xh @ wl.T
+
+
 def forward(Ws, bs, x, emulate_bf16=True):
     """Returns (output [M, n_out], cache).  cache holds the layer inputs a[l] and pre-activations z[l]."""
     rnd = bf16_round if emulate_bf16 else (lambda v: np.asarray(v, np.float64))
-    a = rnd(x)
+    if emulate_bf16:
+        xh, xl = split_bf16(x)
+        a = xh + xl                # the input the first layer's weight gradient sees
+    else:
+        a = np.asarray(x, np.float64)
     acts, pres = [a], []
     L = len(Ws)
     for l in range(L):
+        if l == 0 and emulate_bf16:
+            z = first_layer(Ws[0], x) + np.asarray(bs[0], np.float64)
+            pres.append(z)
+            a = rnd(gelu(z)) if L > 1 else z
+            if L > 1:
+                acts.append(a)
+            continue
         W = rnd(Ws[l])
         z = a @ W.T + np.asarray(bs[l], np.float64)
         pres.append(z)

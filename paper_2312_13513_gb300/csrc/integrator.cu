@@ -197,28 +197,37 @@ __device__ __forceinline__ void gsum(const Grp<G>& g, double (&v)[K], double* re
   g.sync();
 }
 
-// argmax of |a| with ties resolved to the lowest index; identical result in every thread
+// Pivot key of a matrix entry: the bit pattern of |a| read as an unsigned integer.  For
+// non-negative doubles the integer order is the numeric order, so the pivot search runs on the
+// integer pipes instead of FP64 compares (the FP64 pipe is the scarce one).  NaN maps to 0.
+__device__ __forceinline__ unsigned long long pivot_key(double a) {
+  const unsigned long long k = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+  return k > 0x7ff0000000000000ull ? 0ull : k;
+}
+
+// argmax of the keys with ties resolved to the lowest index; identical result in every thread
 template <int G>
-__device__ __forceinline__ void gargmax(const Grp<G>& g, double& best, int& bi, double* red) {
+__device__ __forceinline__ void gargmax(const Grp<G>& g, unsigned long long& best, int& bi, double* red) {
   constexpr int W = G < 32 ? G : 32;
 #pragma unroll
   for (int o = W / 2; o > 0; o >>= 1) {
-    double ob = __shfl_xor_sync(g.mask, best, o);
-    int oi = __shfl_xor_sync(g.mask, bi, o);
+    const unsigned long long ob = __shfl_xor_sync(g.mask, best, o);
+    const int oi = __shfl_xor_sync(g.mask, bi, o);
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
   if (G <= 32) return;
   constexpr int NW = G / 32;
+  unsigned long long* rk = (unsigned long long*)red;
   if ((g.tid & 31) == 0) {
-    red[g.tid >> 5] = best;
+    rk[g.tid >> 5] = best;
     ((int*)(red + NW))[g.tid >> 5] = bi;
   }
   g.sync();
-  best = red[0];
+  best = rk[0];
   bi = ((int*)(red + NW))[0];
   for (int w = 1; w < NW; ++w) {
-    double ob = red[w];
-    int oi = ((int*)(red + NW))[w];
+    const unsigned long long ob = rk[w];
+    const int oi = ((int*)(red + NW))[w];
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
   g.sync();
@@ -478,14 +487,15 @@ template <int G>
 __device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* piv, double* invd,
                           double* lcol, double* red) {
   for (int k = 0; k < N; ++k) {
-    double best = -1.0;
+    unsigned long long best = 0ull;
     int bi = k;
+    bool any = false;
     for (int i = k + g.tid; i < N; i += G) {
-      const double v = fabs(M[i * LD + k]);
-      if (v > best) { best = v; bi = i; }
+      const unsigned long long v = pivot_key(M[i * LD + k]);
+      if (!any || v > best) { best = v; bi = i; any = true; }
     }
     gargmax<G>(g, best, bi, red);
-    if (best == 0.0) return false;
+    if (best == 0ull) return false;
     const double pv = M[bi * LD + k];
     const double ip = 1.0 / pv;
     // phase A: swap rows k and bi (columns != k); multipliers from column k

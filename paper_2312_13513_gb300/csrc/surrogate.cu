@@ -3,6 +3,11 @@
 // Network: x = z-scored [T, ln p, BC(Y_1..Y_ns)] (BC = Box-Cox, lambda = 0.1) -> 512 -> 512 ->
 // 512 -> 512 -> ns, GELU (exact erf form) after each hidden layer, BF16 weights and activations,
 // FP32 accumulation.  Outputs are z-scored increments of BC(Y) over the training step dt.
+// The first layer is compensated: its input and weights are each split into a BF16 pair,
+// x = x_hi + x_lo and W = W_hi + W_lo, and one K = 64 product over the input row
+// [x_hi | x_lo | x_hi] with the weight row [W_hi | W_hi | W_lo] sums W_hi x_hi + W_hi x_lo +
+// W_lo x_hi (the W_lo x_lo term is below FP32 accumulation noise).  Reaction rates depend
+// exponentially on T, and a plain BF16 T feature (8-bit mantissa) is off by several kelvin.
 //
 // surrogate_forward_kernel (persistent, one CTA per SM, 6 warps):
 //   warps 0-3  per 128-cell tile: build the input tile (FP64 state -> features -> BF16, written
@@ -44,6 +49,7 @@ constexpr int HID = 512;           // hidden width
 constexpr int KIN = 64;            // padded input width (one 128-byte K chunk)
 constexpr int NOUT = 16;           // padded output width
 constexpr int MAXNS = 16;          // outputs supported
+static_assert(3 * (MAXNS + 2) <= KIN, "the compensated first layer needs 3 n_in <= KIN");
 constexpr int WSTAGES = 3;
 constexpr int WSTAGE_BYTES = 256 * 64 * 2;
 constexpr int ACT_CHUNK = TM * 128;                  // 16 KB: 128 rows x 64 bf16
@@ -200,7 +206,11 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int i = 0; i < P.nin; ++i) {
           if (!(f[i] >= P.lo[i] && f[i] <= P.hi[i])) outside = true;
-          x[i] = (f[i] - P.xmu[i]) / P.xsd[i];
+          const float v = (f[i] - P.xmu[i]) / P.xsd[i];
+          const float vh = __bfloat162float(__float2bfloat16_rn(v));
+          x[i] = vh;                      // [x_hi | x_lo | x_hi]
+          x[P.nin + i] = v - vh;
+          x[2 * P.nin + i] = vh;
         }
         P.outbox[cell] = outside ? 1 : 0;
       }
@@ -531,11 +541,21 @@ extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t m
   }
   chem_model_s* md = new chem_model_s();
   md->ns = ns; md->nin = nin; md->ne = mech->ne; md->dt = d->dt;
-  // BF16 weights, zero padded: W1 [512 x 64], W2..W4 [512 x 512], W5 [16 x 512]
+  // BF16 weights, zero padded: W1 [512 x 64] as [W_hi | W_hi | W_lo], W2..W4 [512 x 512],
+  // W5 [16 x 512]
   const size_t n1 = (size_t)HID * KIN, nh = (size_t)HID * HID, n5 = (size_t)NOUT * HID;
   std::vector<uint16_t> wb(n1 + 3 * nh + n5, 0);
   for (int o = 0; o < HID; ++o)
-    for (int i = 0; i < nin; ++i) wb[(size_t)o * KIN + i] = f2bf(d->W[0][(size_t)o * nin + i]);
+    for (int i = 0; i < nin; ++i) {
+      const float w = d->W[0][(size_t)o * nin + i];
+      const uint16_t hi = f2bf(w);
+      const uint32_t hbits = (uint32_t)hi << 16;
+      float wh;
+      memcpy(&wh, &hbits, 4);
+      wb[(size_t)o * KIN + i] = hi;
+      wb[(size_t)o * KIN + nin + i] = hi;
+      wb[(size_t)o * KIN + 2 * nin + i] = f2bf(w - wh);
+    }
   for (int l = 1; l < 4; ++l)
     for (size_t e = 0; e < nh; ++e) wb[n1 + (l - 1) * nh + e] = f2bf(d->W[l][e]);
   for (int o = 0; o < ns; ++o)

@@ -11,6 +11,11 @@
 //             dZ_{l-1} = dA_{l-1} * GELU'(Z_{l-1})
 //   Adam      FP32 master weights with bias correction (Kingma & Ba), then BF16 copies of W and
 //             W^T for the next step's products.
+// The first layer is compensated as in the inference kernel: an input row holds
+// [x_hi | x_lo | x_hi | 0] (n_in columns each) and the BF16 copy of W_1 holds
+// [W_hi | W_hi | W_lo | 0], so one product yields W_hi x_hi + W_hi x_lo + W_lo x_hi.  Its weight
+// gradient with respect to the FP32 master W_1 is dZ^T (x_hi + x_lo): the sum of the first two
+// column blocks of the product's gradient.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -119,6 +124,31 @@ __global__ void k_adam(float* W, const float* G, float* m, float* v, __nv_bfloat
   }
 }
 
+// compensated BF16 copy of the first layer: Wb row = [W_hi | W_hi | W_lo | 0] from master W[:, :nin]
+__global__ void k_split_bf16(const float* W, __nv_bfloat16* Wb, int rows, int ld, int nin) {
+  const int64_t n = (int64_t)rows * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / ld), c = (int)(i % ld);
+    float v = 0.0f;
+    if (c < 3 * nin) {
+      const float w = W[(int64_t)r * ld + c % nin];
+      const float wh = __bfloat162float(__float2bfloat16_rn(w));
+      v = c < 2 * nin ? wh : w - wh;
+    }
+    Wb[i] = __float2bfloat16_rn(v);
+  }
+}
+
+// fold the first layer's block gradient into the master's columns: dW[:, c] += dW[:, nin + c]
+// for c < nin, zero elsewhere (one thread per row: the row is read before it is written)
+__global__ void k_fold_split_grad(float* dW, int rows, int ld, int nin) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  float* row = dW + (int64_t)r * ld;
+  for (int c = 0; c < nin; ++c) row[c] += row[nin + c];
+  for (int c = nin; c < ld; ++c) row[c] = 0.0f;
+}
+
 __global__ void k_to_bf16(const float* W, __nv_bfloat16* Wb, __nv_bfloat16* Wt, int rows, int cols) {
   const int64_t n = (int64_t)rows * cols;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -137,12 +167,14 @@ __global__ void k_train_features(const double* T0, const double* p, const double
     x[i * nin + 0] = (float)T0[i];
     x[i * nin + 1] = (float)log(p[i]);
     for (int k = 0; k < ns; ++k) {
-      const float y0 = fmaxf((float)Y0[(int64_t)k * ld + i], 0.0f);
-      const float y1 = fmaxf((float)Y1[(int64_t)k * ld + i], 0.0f);
-      const float b0 = (powf(y0, 0.1f) - 1.0f) / 0.1f;
-      const float b1 = (powf(y1, 0.1f) - 1.0f) / 0.1f;
-      x[i * nin + 2 + k] = b0;
-      t[i * ns + k] = b1 - b0;
+      // the increment is formed in FP64: an FP32 difference of two Box-Cox values near -1/lambda
+      // is rounding noise for a species whose mass fraction barely moves over dt
+      const double y0 = fmax(Y0[(int64_t)k * ld + i], 0.0);
+      const double y1 = fmax(Y1[(int64_t)k * ld + i], 0.0);
+      const double b0 = (pow(y0, 0.1) - 1.0) / 0.1;
+      const double b1 = (pow(y1, 0.1) - 1.0) / 0.1;
+      x[i * nin + 2 + k] = (float)b0;
+      t[i * ns + k] = (float)(b1 - b0);
     }
   }
 }
@@ -199,13 +231,22 @@ __global__ void k_init_stats(double* acc, int c) {
   if (j < c) { acc[j] = 0; acc[c + j] = 0; acc[2 * c + j] = 1e300; acc[3 * c + j] = -1e300; }
 }
 
-// X[i, 0:c] = bf16((x - mean) / std), zero up to ldx;  T[i, :] = (t - tmean) / tstd
+// v = (x - mean) / std;  X[i, :] = [bf16(v_hi) | bf16(v - v_hi) | bf16(v_hi) | 0] (c columns each,
+// zero up to ldx);  T[i, :] = (t - tmean) / tstd
 __global__ void k_normalize(const float* x, int64_t n, int c, const float* mean, const float* sd,
                             __nv_bfloat16* X, int ldx, const float* t, int ct, const float* tmean,
                             const float* tsd, float* Tn) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    for (int j = 0; j < ldx; ++j)
-      X[i * ldx + j] = __float2bfloat16_rn(j < c ? (x[i * c + j] - mean[j]) / sd[j] : 0.0f);
+    for (int j = 0; j < ldx; ++j) {
+      float o = 0.0f;
+      if (j < 3 * c) {
+        const int jj = j % c;
+        const float v = (x[i * c + jj] - mean[jj]) / sd[jj];
+        const float vh = __bfloat162float(__float2bfloat16_rn(v));
+        o = (j >= c && j < 2 * c) ? v - vh : vh;
+      }
+      X[i * ldx + j] = __float2bfloat16_rn(o);
+    }
     if (t)
       for (int j = 0; j < ct; ++j) Tn[i * ct + j] = (t[i * ct + j] - tmean[j]) / tsd[j];
   }
@@ -247,8 +288,8 @@ extern "C" int chem_mlp_trainer_free(chem_trainer_t t) {
 
 extern "C" int chem_mlp_trainer_create(int n_in, int n_out, int batch, const float* const* W_init,
                                        const float* const* b_init, uint64_t seed, chem_trainer_t* out) {
-  if (!out || n_in < 1 || n_in > PADIO || n_out < 1 || n_out > PADIO || batch < 128 || batch % 128) {
-    set_error("trainer: n_in/n_out in [1, 128], batch a positive multiple of 128 required");
+  if (!out || n_in < 1 || 3 * n_in > PADIO || n_out < 1 || n_out > PADIO || batch < 128 || batch % 128) {
+    set_error("trainer: n_in in [1, 42], n_out in [1, 128], batch a positive multiple of 128 required");
     return CHEM_EINVAL;
   }
   *out = nullptr;
@@ -292,7 +333,8 @@ extern "C" int chem_mlp_trainer_create(int n_in, int n_out, int batch, const flo
       rc = cuda_fail(cudaGetLastError(), "cudaMemcpy(trainer)");
       break;
     }
-    k_to_bf16<<<grid_for(nw), 256>>>(t->W[l], t->Wb[l], t->Wt[l], outs[l], ins[l]);
+    if (l == 0) k_split_bf16<<<grid_for(nw), 256>>>(t->W[0], t->Wb[0], outs[0], ins[0], n_in);
+    else k_to_bf16<<<grid_for(nw), 256>>>(t->W[l], t->Wb[l], t->Wt[l], outs[l], ins[l]);
   }
   void* p;
   if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 4), t->dA = (float*)p;
@@ -346,6 +388,7 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
     k_transpose<<<dim3((nin + 31) / 32, (B + 31) / 32), tb, 0, st>>>(t->A[l], t->At, B, nin);
     int rc = gemm_bf16(t->dZt, B, t->At, B, t->dW[l], nin, nullptr, nout, nin, B, t->err, st);
     if (rc) return rc;
+    if (l == 0) k_fold_split_grad<<<(nout + 127) / 128, 128, 0, st>>>(t->dW[0], nout, nin, t->nin);
     k_colsum<<<(nout + 127) / 128, 128, 0, st>>>(t->dZf, t->db[l], B, nout);
     if (l > 0) {
       rc = gemm_bf16(t->dZb, nout, t->Wt[l], nout, t->dA, nin, nullptr, B, nin, nout, t->err, st);
@@ -367,8 +410,10 @@ extern "C" int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float
   const float c1 = 1.0f - powf(beta1, (float)t->step), c2 = 1.0f - powf(beta2, (float)t->step);
   for (int l = 0; l < NL; ++l) {
     const int r = t->out_pad[l], c = t->in_pad[l];
-    k_adam<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[l], t->dW[l], t->mW[l], t->vW[l], t->Wb[l], t->Wt[l], r,
-                                                      c, lr, beta1, beta2, eps, c1, c2);
+    k_adam<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[l], t->dW[l], t->mW[l], t->vW[l],
+                                                      l == 0 ? nullptr : t->Wb[l], t->Wt[l], r, c, lr, beta1,
+                                                      beta2, eps, c1, c2);
+    if (l == 0) k_split_bf16<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[0], t->Wb[0], r, c, t->nin);
     k_adam<<<grid_for(r), 256, 0, st>>>(t->b[l], t->db[l], t->mb[l], t->vb[l], nullptr, nullptr, r, 1, lr, beta1,
                                         beta2, eps, c1, c2);
   }
@@ -420,7 +465,7 @@ extern "C" int chem_column_stats(const float* A, int64_t n, int c, double* stats
 extern "C" int chem_train_normalize(const float* x, int64_t n, int c, const float* mean, const float* sd,
                                     void* X, int ldx, const float* t, int ct, const float* tmean,
                                     const float* tsd, float* Tn, chem_stream_t stream) {
-  if (!x || !mean || !sd || !X || n < 0 || c < 1 || ldx < c || (t && (!tmean || !tsd || !Tn))) {
+  if (!x || !mean || !sd || !X || n < 0 || c < 1 || ldx < 3 * c || (t && (!tmean || !tsd || !Tn))) {
     set_error("bad arguments");
     return CHEM_EINVAL;
   }

@@ -87,11 +87,15 @@ def column_stats(A):
     return mean, np.sqrt(var), s[2], s[3]
 
 
-def make_dataset(mech, dm, n, dt, seed, rtol=1e-6, atol=1e-10, stats=None):
-    """States (flamelet samples) advanced by the GPU integrator -> normalised X, target."""
+def make_dataset(mech, dm, n, dt, seed, rtol=1e-6, atol=1e-10, stats=None, front_fraction=0.5):
+    """States (flamelet samples) advanced by the GPU integrator -> normalised X, target.
+
+    X rows are the compensated split [x_hi | x_lo | x_hi | 0] of the z-scored features.  A species
+    whose increment is zero in every sample (an inert one) gets y_std = 0 in the stats: the
+    model then leaves it unchanged, and its training target is the constant 0."""
     import torch
     from synth.states import flamelet_samples, load_table
-    f = flamelet_samples(load_table("h2_flamelet.npz"), n, seed)
+    f = flamelet_samples(load_table("h2_flamelet.npz"), n, seed, front_fraction=front_fraction)
     dev = torch.device("cuda")
     T0 = torch.tensor(f["T"], device=dev)
     p = torch.tensor(f["p"], device=dev)
@@ -106,27 +110,31 @@ def make_dataset(mech, dm, n, dt, seed, rtol=1e-6, atol=1e-10, stats=None):
                                           _ptr(t), _stream_ptr(None)))
     if stats is None:
         xm, xs, xlo, xhi = column_stats(x)
-        tm, ts, _, _ = column_stats(t)
+        tm, ts, tlo, thi = column_stats(t)
         # a constant feature (ln p at fixed pressure) has a rounding-noise deviation: scale 1
         xs = np.where(xs > 1e-6 * np.maximum(1.0, np.abs(xm)), xs, 1.0)
-        ts = np.where(ts > 1e-12, ts, 1.0)
-        stats = {"x_mean": xm, "x_std": xs, "y_mean": tm, "y_std": ts, "box_lo": xlo, "box_hi": xhi}
+        inert = (tlo == 0.0) & (thi == 0.0)
+        ts = np.where(inert, 0.0, np.where(ts > 1e-12, ts, 1.0))
+        stats = {"x_mean": xm, "x_std": xs, "y_mean": np.where(inert, 0.0, tm), "y_std": ts,
+                 "box_lo": xlo, "box_hi": xhi}
     X = torch.empty((n, PAD), dtype=torch.bfloat16, device=dev)
     Tn = torch.empty((n, ns), dtype=torch.float32, device=dev)
     f32 = lambda a: torch.tensor(np.asarray(a, np.float32), device=dev)
-    sx, sxs, sy, sys_ = f32(stats["x_mean"]), f32(stats["x_std"]), f32(stats["y_mean"]), f32(stats["y_std"])
+    # an inert species' target is 0: normalise it with scale 1
+    sx, sxs, sy = f32(stats["x_mean"]), f32(stats["x_std"]), f32(stats["y_mean"])
+    sys_ = f32(np.where(np.asarray(stats["y_std"]) > 0.0, stats["y_std"], 1.0))
     check(_lib.load().chem_train_normalize(_ptr(x), n, nin, _ptr(sx), _ptr(sxs), _ptr(X), PAD, _ptr(t), ns,
                                            _ptr(sy), _ptr(sys_), _ptr(Tn), _stream_ptr(None)))
     torch.cuda.synchronize()
     return {"X": X, "T": Tn, "stats": stats, "state0": (T0, p, Y0), "state1": (T1, Y1)}
 
 
-def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=1e-3, lr_final=3e-5, dt=5e-7, seed=7,
-          log=print, time_budget_s=None):
+def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5, dt=5e-7, seed=7,
+          log=print, time_budget_s=None, front_fraction=0.5):
     import torch
     dm = Mechanism(mech)
     t0 = time.time()
-    data = make_dataset(mech, dm, n_states, dt, seed)
+    data = make_dataset(mech, dm, n_states, dt, seed, front_fraction=front_fraction)
     log(f"dataset: {n_states} states in {time.time() - t0:.1f} s")
     ns = mech.ns
     tr = Trainer(ns + 2, ns, batch, seed=seed)
@@ -211,16 +219,31 @@ def main():
     ap.add_argument("--states", type=int, default=1 << 22)
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=4096)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=3e-4)
+    ap.add_argument("--lr-final", type=float, default=1e-5)
+    ap.add_argument("--front-fraction", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--budget", type=float, default=None, help="training time budget (s)")
+    ap.add_argument("--log", default=None, help="also write the training log to this file")
     args = ap.parse_args()
     from synth.mechanism import h2_mechanism
-    params = train(h2_mechanism(), args.states, args.epochs, args.batch, args.lr, seed=args.seed,
-                   time_budget_s=args.budget)
+    lines = []
+
+    def log(msg):
+        print(msg, flush=True)
+        lines.append(msg)
+
+    log(f"train: states {args.states} epochs {args.epochs} batch {args.batch} lr {args.lr} -> "
+        f"{args.lr_final} (cosine) front_fraction {args.front_fraction} seed {args.seed}")
+    params = train(h2_mechanism(), args.states, args.epochs, args.batch, args.lr, args.lr_final,
+                   seed=args.seed, log=log, time_budget_s=args.budget,
+                   front_fraction=args.front_fraction)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     save_model(params, args.out)
-    print("saved", args.out)
+    log(f"saved {args.out}")
+    if args.log:
+        with open(args.log, "w") as f:
+            f.write("\n".join(lines) + "\n")
 
 
 if __name__ == "__main__":

@@ -101,11 +101,18 @@ def quasi_dns_field(table, n=1 << 20, seed=12346, grid=128, period=32, delta=2.0
     return {"T": T, "p": np.full(n, PATM), "Y": Y, "c": c}
 
 
-def flamelet_samples(table, n, seed):
-    """Independent samples of the quasi-DNS state distribution (no spatial structure):
-    c ~ U[0, 1] with the same T and Y perturbation amplitudes.  Used for training data."""
+def flamelet_samples(table, n, seed, front_fraction=0.0, delta=2.0, half_width=8.0):
+    """Independent samples of the quasi-DNS state distribution (no spatial structure) with the
+    same T and Y perturbation amplitudes.  Used for training data.  Progress variable: c ~ U[0, 1]
+    for a share 1 - front_fraction of the samples; the rest sample c across a resolved front,
+    c = (1 + tanh(s / delta)) / 2 with s ~ U[-half_width, half_width] cells, the density of c in
+    the quasi-DNS field (concentrated near the unburnt and burnt ends)."""
     rng = np.random.default_rng(seed)
     c = rng.uniform(0.0, 1.0, n)
+    nf = int(round(front_fraction * n))
+    if nf > 0:
+        s = rng.uniform(-half_width, half_width, nf)
+        c[rng.permutation(n)[:nf]] = 0.5 * (1.0 + np.tanh(s / delta))
     T = np.interp(c, table["c"], table["T"]) * (1.0 + 0.05 * rng.standard_normal(n))
     Y = _interp_profile(table["c"], table["Y"], c)
     Y = np.maximum(Y * (1.0 + 0.10 * rng.standard_normal(Y.shape)), 0.0)

@@ -1,4 +1,6 @@
 """GPU parity of the BF16 surrogate path (tcgen05 GEMM, fused forward, projection, fallback)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -7,6 +9,8 @@ torch = pytest.importorskip("torch")
 import paper_2312_13513_gb300 as cg  # noqa: E402
 from oracle import mlp as omlp  # noqa: E402
 from oracle import surrogate as osur  # noqa: E402
+
+from synth.states import load_table, quasi_dns_field  # noqa: E402
 
 from gpu_common import to_dev  # noqa: E402
 from helpers import random_states  # noqa: E402
@@ -45,9 +49,10 @@ def _std(x):
 def _oracle_z(params, T, p, Y):
     x = osur.features(T, p, Y)
     xz = (x - params["x_mean"]) / params["x_std"]
-    Wr = [omlp.bf16_round(w) for w in params["W"]]
+    # the device receives FP32 weights: the oracle rounds (layers 2-5) or splits (layer 1) those
+    W32 = [np.asarray(w, np.float32).astype(np.float64) for w in params["W"]]
     br = [np.asarray(bb, np.float32).astype(np.float64) for bb in params["b"]]
-    out, _ = omlp.forward(Wr, br, xz, emulate_bf16=True)
+    out, _ = omlp.forward(W32, br, xz, emulate_bf16=True)
     return out.T      # [ns, n]
 
 
@@ -72,6 +77,12 @@ def test_forward_matches_oracle_mlp(h2):
     dz = np.abs(z - zr)
     tol = 1e-2 * np.maximum(1.0, np.abs(zr))
     assert np.all(dz <= tol), (dz.max(), np.unravel_index(np.argmax(dz - tol), dz.shape))
+    # the compensated first layer: a plain BF16 one would sit much farther from the oracle
+    xz = (osur.features(T, p, Y) - prm["x_mean"]) / prm["x_std"]
+    W32 = [np.asarray(w, np.float32).astype(np.float64) for w in prm["W"]]
+    b32 = [np.asarray(bb, np.float32).astype(np.float64) for bb in prm["b"]]
+    zp, _ = omlp.forward([omlp.bf16_round(W32[0])] + W32[1:], b32, omlp.bf16_round(xz), emulate_bf16=True)
+    assert np.sqrt(np.mean(dz ** 2)) < 0.5 * np.sqrt(np.mean((zp.T - zr) ** 2))
     assert np.array_equal(box.cpu().numpy().astype(bool), T > 2000.0)
     # inverse transform: Y' = BC^-1(BC(Y0) + z sd + mu)
     yr = osur.boxcox_inv(osur.boxcox(Y) + zr * prm["y_std"][:, None] + prm["y_mean"][:, None])
@@ -180,6 +191,67 @@ def test_trainer_forward_backward_match_oracle():
         assert rel < 2e-2 and relb < 2e-2, (l, rel, relb)
 
 
+def _split_rows(x, pad):
+    """[x_hi | x_lo | x_hi | 0] BF16 rows (the trainer's compensated input layout)."""
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    xh = xt.to(torch.bfloat16)
+    xl = (xt - xh.float()).to(torch.bfloat16)
+    n, c = x.shape
+    X = torch.zeros((n, pad), dtype=torch.bfloat16, device="cuda")
+    X[:, :c], X[:, c:2 * c], X[:, 2 * c:3 * c] = xh, xl, xh
+    return X
+
+
+def test_normalize_writes_compensated_rows():
+    from paper_2312_13513_gb300 import _lib
+    from paper_2312_13513_gb300.train import PAD
+    rng = np.random.default_rng(21)
+    n, c = 1000, 11
+    x = (rng.standard_normal((n, c)) * 300.0 + 1000.0).astype(np.float32)
+    mean = np.float32(rng.standard_normal(c) * 10.0 + 1000.0)
+    sd = np.float32(np.abs(rng.standard_normal(c)) * 100.0 + 1.0)
+    xd = torch.tensor(x, device="cuda")
+    md, sdd = torch.tensor(mean, device="cuda"), torch.tensor(sd, device="cuda")
+    X = torch.full((n, PAD), 7.0, dtype=torch.bfloat16, device="cuda")
+    cg.check(_lib.load().chem_train_normalize(cg._ptr(xd), n, c, cg._ptr(md), cg._ptr(sdd), cg._ptr(X), PAD,
+                                              None, 0, None, None, None, None))
+    torch.cuda.synchronize()
+    v = (xd - md) / sdd
+    want = _split_rows(v.cpu().numpy(), PAD)
+    assert torch.equal(X, want)
+
+
+def test_trainer_compensated_first_layer_matches_oracle():
+    """Unrounded FP32 weights and inputs: the trainer's first layer is the compensated product."""
+    from paper_2312_13513_gb300.train import PAD, Trainer
+    rng = np.random.default_rng(23)
+    B, nin, nout = 256, 11, 9
+    dims = [nin, 512, 512, 512, 512, nout]
+    W = [np.float32(rng.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i])).astype(np.float64)
+         for i in range(5)]
+    b = [np.float32(0.1 * rng.standard_normal(dims[i + 1])).astype(np.float64) for i in range(5)]
+    X = np.float32(rng.standard_normal((B, nin)) * 2.0).astype(np.float64)
+    T = rng.standard_normal((B, nout))
+    tr = Trainer(nin, nout, B, W=W, b=b)
+    Xd = _split_rows(X, PAD)
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    out = torch.empty((B, nout), dtype=torch.float32, device="cuda")
+    tr.forward(Xd, out)
+    tr.backward(Td)
+    dW, _ = tr.get(1)
+    o_out, cache = omlp.forward(W, b, X, emulate_bf16=True)
+    got = out.cpu().numpy()
+    assert np.max(np.abs(got - o_out)) <= 1e-2 * max(1.0, np.max(np.abs(o_out)))
+    # a plain BF16 first layer would sit much farther from the compensated oracle
+    o_plain, _ = omlp.forward([omlp.bf16_round(W[0])] + W[1:], b, omlp.bf16_round(X), emulate_bf16=True)
+    e_gpu = np.sqrt(np.mean((got - o_out) ** 2))
+    e_plain = np.sqrt(np.mean((o_plain - o_out) ** 2))
+    assert e_gpu < 0.5 * e_plain, (e_gpu, e_plain)
+    gW, _ = omlp.backward(W, b, cache, o_out, T)
+    rel = np.linalg.norm(dW[0] - gW[0]) / np.linalg.norm(gW[0])
+    assert rel < 2e-2, rel
+
+
 def test_adam_step_matches_oracle():
     from paper_2312_13513_gb300.train import PAD, Trainer
     W, b, X, T = _small_problem(2)
@@ -225,3 +297,42 @@ def test_training_reduces_loss():
             first = loss.item()
         tr.adam(1e-3)
     assert loss.item() < 0.1 * first, (first, loss.item())
+
+
+# ---------------------------------------------------------------------------------------------
+# the trained model shipped with the package
+# ---------------------------------------------------------------------------------------------
+MODEL = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2312_13513_gb300",
+                     "models", "h2_quasi_dns.chemsur")
+
+
+@pytest.mark.skipif(not os.path.exists(MODEL), reason="no trained model in the package")
+def test_trained_surrogate_heat_release_error_vs_oracle(h2, om_h2):
+    """The shipped H2 model on a sample of a quasi-DNS-shaped field it was not trained on: field
+    L1 heat-release error of the surrogate step against the FP64 oracle <= 1 %, every cell
+    conserves the elements and its enthalpy."""
+    f = quasi_dns_field(load_table("h2_flamelet.npz"), n=1 << 21, seed=4242)
+    rng = np.random.default_rng(5)
+    s = np.sort(rng.choice(f["T"].size, 20000, replace=False))
+    T0, p, Y0 = f["T"][s], f["p"][s], f["Y"][:, s]
+    dm = cg.Mechanism(h2)
+    model = cg.Surrogate(dm, path=MODEL)
+    Td, pd, Yd = to_dev(T0, p, Y0)
+    route = torch.empty(T0.size, dtype=torch.int8, device="cuda")
+    cg.surrogate_advance(model, Td, pd, Yd, 5e-7, route=route)
+    torch.cuda.synchronize()
+    Ys = Yd.cpu().numpy()
+    T1, Y1 = om_h2.advance(T0, p, Y0, 5e-7, 1e-6, 1e-10)[:2]
+    q_ref = np.array([osur.heat_release(om_h2, T0[i], p[i], Y0[:, i], Y1[:, i], 5e-7) for i in range(T0.size)])
+    q_sur = np.array([osur.heat_release(om_h2, T0[i], p[i], Y0[:, i], Ys[:, i], 5e-7) for i in range(T0.size)])
+    err = osur.hrr_error(q_sur, q_ref)
+    assert err <= 0.01, err
+    A = osur.element_mass_matrix(h2)
+    assert np.max(np.abs(A @ Ys - A @ Y0)) <= 1e-9
+    # network-route cells: temperature from enthalpy conservation (Newton to 1e-9)
+    net = np.where(route.cpu().numpy() == 0)[0][::50]
+    assert net.size > 0
+    h0 = np.array([om_h2.enthalpy_mass(T0[i], Y0[:, i]) for i in net])
+    Tn = Td.cpu().numpy()
+    h1 = np.array([om_h2.enthalpy_mass(Tn[i], Ys[:, i]) for i in net])
+    assert np.max(np.abs(h1 - h0) / np.abs(h0).max()) <= 1e-8

@@ -29,6 +29,25 @@ def test_gelu_closed_forms():
     assert np.allclose(mlp.gelu_grad(x), fd, atol=1e-8)
 
 
+def test_compensated_first_layer_error_bound():
+    """hi + lo represents v to 2^-16 relative (two 8-bit significands); the dropped lo*lo term and
+    the rounding of lo bound the product error by 3 * 2^-17 * sum |x_j| |W_ij|, against about
+    2^-9 for a plain BF16 product.  BF16-representable operands give the exact product."""
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((400, 11)) * np.exp(rng.uniform(-3, 3, (400, 11)))
+    W = rng.standard_normal((64, 11))
+    exact = x @ W.T
+    scale = np.abs(x) @ np.abs(W).T
+    err = np.abs(mlp.first_layer(W, x) - exact)
+    assert np.all(err <= 3 * 2.0 ** -17 * scale)
+    plain = np.abs(mlp.bf16_round(x) @ mlp.bf16_round(W).T - exact)
+    assert np.median(plain / scale) > 30 * np.median(err / scale)
+    xb, Wb = mlp.bf16_round(x), mlp.bf16_round(W)
+    assert np.array_equal(mlp.first_layer(Wb, xb), xb @ Wb.T)
+    hi, lo = mlp.split_bf16(x)
+    assert np.all(np.abs(hi + lo - x) <= 2.0 ** -16 * np.abs(x))
+
+
 def _net(rng, dims):
     Ws = [rng.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i]) for i in range(len(dims) - 1)]
     bs = [0.1 * rng.standard_normal(dims[i + 1]) for i in range(len(dims) - 1)]
