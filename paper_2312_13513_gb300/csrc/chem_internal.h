@@ -34,18 +34,24 @@ struct MechLayout {
   int o_hc;                             // [2][ns][6]  h/RT:  a1, a2/2, a3/3, a4/4, a5/5, a6
   int o_sc;                             // [2][ns][6]  s/R:   a1 (x lnT), a2, a3/2, a4/3, a5/4, a7
   int o_cpc;                            // [2][ns][5]  cp/R:  a1..a5
-  int o_dcpc;                           // [2][ns][4]  d(cp/R)/dT: a2, 2 a3, 3 a4, 4 a5
   int o_lnA, o_beta, o_Ta;              // [nr]
   int o_troe;                           // [ntroe][8]: lnA0, b0, Ta0, a, 1/T3, 1/T1, T2, has_T2
   int o_effv;                           // [neff] efficiency - 1 (sparse, per third-body set)
-  int o_wnu;                            // [nprod] signed stoichiometric coefficient (double)
+  int o_const;                          // [kConsts] doubles, see kC_*
   int o_reac, o_prod;                   // [nr][4] int16 species (-1 pad), 4th entry unused
   int o_rinfo;                          // [nr][4] int16: type, dnu, third-body set, troe index
   int o_effidx;                         // [neff] int16 species
-  int o_wrx;                            // [nprod] int16 reaction
+  int o_wpk;                            // [nprod] int32 production term: reaction << 4 | (nu + 8)
   int o_effoff;                         // [ntb + 1] int32
   int o_woff;                           // [ns + 1] int32
 };
+
+// constants block of the blob: the stoichiometric-coefficient table indexed by the 4-bit code of
+// a production term (value = code - 8), ln(p_atm / R) and 1 / ns
+constexpr int kC_NU = 0;
+constexpr int kC_LNPR0 = 16;
+constexpr int kC_INVNS = 17;
+constexpr int kConsts = 18;
 
 // Jacobian-assembly program of d(wdot)/dC (global memory, read-only): entry e covers row
 // ent_row[e], column ent_col[e]; its value is sum over terms t in [ent_off[e], ent_off[e+1]) of

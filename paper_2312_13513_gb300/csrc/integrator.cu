@@ -58,10 +58,10 @@ constexpr double kGamma = 0.25;
 // ---------------------------------------------------------------------------------------
 struct MechView {
   int ns, nr, N;
-  const double *W, *invW, *hc, *sc, *cpc, *dcpc, *lnA, *beta, *Ta, *troe, *effv, *wnu;
+  const double *W, *invW, *hc, *sc, *cpc, *lnA, *beta, *Ta, *troe, *effv, *cst;
   const short4 *reac, *prod, *rinfo;
-  const int16_t *effidx, *wrx;
-  const int *effoff, *woff;
+  const int16_t* effidx;
+  const int *wpk, *effoff, *woff;
 };
 
 __device__ __forceinline__ MechView bind_mech(const unsigned char* s, const MechLayout& L) {
@@ -72,29 +72,37 @@ __device__ __forceinline__ MechView bind_mech(const unsigned char* s, const Mech
   m.hc = (const double*)(s + L.o_hc);
   m.sc = (const double*)(s + L.o_sc);
   m.cpc = (const double*)(s + L.o_cpc);
-  m.dcpc = (const double*)(s + L.o_dcpc);
   m.lnA = (const double*)(s + L.o_lnA);
   m.beta = (const double*)(s + L.o_beta);
   m.Ta = (const double*)(s + L.o_Ta);
   m.troe = (const double*)(s + L.o_troe);
   m.effv = (const double*)(s + L.o_effv);
-  m.wnu = (const double*)(s + L.o_wnu);
+  m.cst = (const double*)(s + L.o_const);
   m.reac = (const short4*)(s + L.o_reac);
   m.prod = (const short4*)(s + L.o_prod);
   m.rinfo = (const short4*)(s + L.o_rinfo);
   m.effidx = (const int16_t*)(s + L.o_effidx);
-  m.wrx = (const int16_t*)(s + L.o_wrx);
+  m.wpk = (const int*)(s + L.o_wpk);
   m.effoff = (const int*)(s + L.o_effoff);
   m.woff = (const int*)(s + L.o_woff);
   return m;
 }
 
-// per-group workspace layout (doubles unless noted); offsets in doubles
+// Per-cell scalars that a multi-warp group evaluates on its first warp only and shares through
+// the workspace (slot indices into w.sc).
+enum : int {
+  S_LNT, S_INVT, S_RHO, S_INVRHO, S_GSHIFT, S_EP1, S_IEP1, S_S, S_CP, S_DCP, S_Q, S_IRCP,
+  S_RS, S_QOR2R, S_RHS, S_CPS, S_J00, S_IG, S_INVH, S_EN, S_FAC, S_NSC
+};
+
+// per-group workspace layout (doubles unless noted); offsets in doubles.  The Jacobian is
+// assembled (negated) straight into the iteration-matrix buffer M and re-evaluated at every
+// attempt, so a group holds one N x N matrix.
 struct WsLayout {
-  int LD;                  // leading dimension of the N x N matrices (odd: no bank conflicts)
-  int y, ynew, ys, fs, f0, u, J, M, invd;
-  int C, hRT, gRT, cpR, dcpR, wdot, dwdT, rk, Hm, lcol;
-  int q, dqdT, dq, red, stage, ctl, piv;
+  int LD;                  // leading dimension of the N x N matrix (odd: no bank conflicts)
+  int y, ynew, ys, fs, f0, u, M, invd, tmp;
+  int C, hRT, gRT, cpR, dcpR, wdot, dwdT, rk, Hm;
+  int q, dqdT, dq, red, sc, stage, ctl, perm;
   int total;               // doubles
 };
 
@@ -105,38 +113,37 @@ inline WsLayout make_ws(int ns, int nr, int G) {
   int o = 0;
   auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };   // keep 16-byte alignment
   w.y = take(N); w.ynew = take(N); w.ys = take(N); w.fs = take(N); w.f0 = take(N);
-  w.u = take(6 * N); w.M = take(N * w.LD); w.invd = take(N);
-  // groups of at least a warp keep J(y) across rejected attempts; sub-warp groups re-evaluate it
-  // every attempt (identical values) so that all groups of a warp stay in lockstep
-  w.J = G >= 32 ? take(N * w.LD) : w.M;
+  w.u = take(6 * N); w.M = take(N * w.LD); w.invd = take(N); w.tmp = take(N);
   w.C = take(ns); w.hRT = take(ns); w.gRT = take(ns); w.cpR = take(ns); w.dcpR = take(ns);
-  w.wdot = take(ns); w.dwdT = take(ns); w.rk = take(ns); w.Hm = take(ns); w.lcol = take(N);
+  w.wdot = take(ns); w.dwdT = take(ns); w.rk = take(ns); w.Hm = take(ns);
   w.q = take(nr); w.dqdT = take(nr); w.dq = take(7 * nr);
   w.red = take(8 * (G >= 32 ? G / 32 : 1) + 8);
+  w.sc = take(S_NSC);
   w.stage = take(CHUNK * (N + 1));
   w.ctl = take(2);
-  w.piv = take((N + 1) / 2);      // ints
+  w.perm = take((N + 1) / 2);      // ints
   w.total = o;
   return w;
 }
 
 struct WsPtr {
-  double *y, *ynew, *ys, *fs, *f0, *u, *J, *M, *invd;
-  double *C, *hRT, *gRT, *cpR, *dcpR, *wdot, *dwdT, *rk, *Hm, *lcol;
-  double *q, *dqdT, *dq, *red, *stage;
+  double *y, *ynew, *ys, *fs, *f0, *u, *M, *invd, *tmp;
+  double *C, *hRT, *gRT, *cpR, *dcpR, *wdot, *dwdT, *rk, *Hm;
+  double *q, *dqdT, *dq, *red, *sc, *stage;
   unsigned long long* ctl;
-  int* piv;
+  int* perm;
 };
 
 __device__ __forceinline__ WsPtr bind_ws(double* b, const WsLayout& w) {
   WsPtr p;
   p.y = b + w.y; p.ynew = b + w.ynew; p.ys = b + w.ys; p.fs = b + w.fs; p.f0 = b + w.f0;
-  p.u = b + w.u; p.J = b + w.J; p.M = b + w.M; p.invd = b + w.invd;
+  p.u = b + w.u; p.M = b + w.M; p.invd = b + w.invd; p.tmp = b + w.tmp;
   p.C = b + w.C; p.hRT = b + w.hRT; p.gRT = b + w.gRT; p.cpR = b + w.cpR; p.dcpR = b + w.dcpR;
-  p.wdot = b + w.wdot; p.dwdT = b + w.dwdT; p.rk = b + w.rk; p.Hm = b + w.Hm; p.lcol = b + w.lcol;
-  p.q = b + w.q; p.dqdT = b + w.dqdT; p.dq = b + w.dq; p.red = b + w.red; p.stage = b + w.stage;
+  p.wdot = b + w.wdot; p.dwdT = b + w.dwdT; p.rk = b + w.rk; p.Hm = b + w.Hm;
+  p.q = b + w.q; p.dqdT = b + w.dqdT; p.dq = b + w.dq; p.red = b + w.red; p.sc = b + w.sc;
+  p.stage = b + w.stage;
   p.ctl = (unsigned long long*)(b + w.ctl);
-  p.piv = (int*)(b + w.piv);
+  p.perm = (int*)(b + w.perm);
   return p;
 }
 
@@ -197,6 +204,36 @@ __device__ __forceinline__ void gsum(const Grp<G>& g, double (&v)[K], double* re
   g.sync();
 }
 
+// First warp of a multi-warp group (every thread of a group of at most one warp).  Per-cell
+// scalar work runs there only: FP64 instructions are issued per warp whatever the number of
+// active lanes, so each extra warp that repeats a logarithm or a division costs as much as a warp
+// doing useful work.
+template <int G>
+__device__ __forceinline__ bool is_lead(const Grp<G>& g) { return G <= 32 || g.tid < 32; }
+
+// Sum of K values over the group, delivered to the lead threads only (all threads for G <= 32).
+// Ends with the group synchronised once (G > 32); the caller publishes derived scalars through
+// w.sc and synchronises again.
+template <int G, int K>
+__device__ __forceinline__ void gsum_lead(const Grp<G>& g, double (&v)[K], double* red) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[i] = sub_sum<G>(v[i], g.mask);
+  if (G <= 32) return;
+  constexpr int NW = G / 32;
+  if ((g.tid & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < K; ++i) red[i * NW + (g.tid >> 5)] = v[i];
+  g.sync();
+  if (g.tid < 32) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      double s = red[i * NW];
+      for (int w = 1; w < NW; ++w) s += red[i * NW + w];
+      v[i] = s;
+    }
+  }
+}
+
 // Pivot key of a matrix entry: the bit pattern of |a| read as an unsigned integer.  For
 // non-negative doubles the integer order is the numeric order, so the pivot search runs on the
 // integer pipes instead of FP64 compares (the FP64 pipe is the scarce one).  NaN maps to 0.
@@ -205,32 +242,20 @@ __device__ __forceinline__ unsigned long long pivot_key(double a) {
   return k > 0x7ff0000000000000ull ? 0ull : k;
 }
 
-// argmax of the keys with ties resolved to the lowest index; identical result in every thread
+__device__ __forceinline__ void argmax_merge(unsigned long long& best, int& bi, unsigned long long ob, int oi) {
+  if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+}
+
+// argmax (largest key, ties to the lowest index) across the lanes of a group within its warp
 template <int G>
-__device__ __forceinline__ void gargmax(const Grp<G>& g, unsigned long long& best, int& bi, double* red) {
+__device__ __forceinline__ void warp_argmax(const Grp<G>& g, unsigned long long& best, int& bi) {
   constexpr int W = G < 32 ? G : 32;
 #pragma unroll
   for (int o = W / 2; o > 0; o >>= 1) {
     const unsigned long long ob = __shfl_xor_sync(g.mask, best, o);
     const int oi = __shfl_xor_sync(g.mask, bi, o);
-    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    argmax_merge(best, bi, ob, oi);
   }
-  if (G <= 32) return;
-  constexpr int NW = G / 32;
-  unsigned long long* rk = (unsigned long long*)red;
-  if ((g.tid & 31) == 0) {
-    rk[g.tid >> 5] = best;
-    ((int*)(red + NW))[g.tid >> 5] = bi;
-  }
-  g.sync();
-  best = rk[0];
-  bi = ((int*)(red + NW))[0];
-  for (int w = 1; w < NW; ++w) {
-    const unsigned long long ob = rk[w];
-    const int oi = ((int*)(red + NW))[w];
-    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-  }
-  g.sync();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -245,14 +270,25 @@ struct JacArgs {
   const double* term_coef;
 };
 
+// Right-hand side f(y) and, when Jneg is given, the NEGATED analytic Jacobian -df/dy written into
+// Jneg (N x N, leading dimension LD): the iteration matrix I/(gamma h) - J then only needs its
+// diagonal.  Ends with the group synchronised.
 template <int G>
 __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const WsPtr& w,
                                      const JacArgs& jp, int LD, const double* y, double p,
-                                     double* f, double* Jout, bool jac) {
+                                     double* f, double* Jneg) {
+  constexpr bool kMulti = G > 32;
+  const bool lead = is_lead(g);
+  const bool jac = Jneg != nullptr;
   const int ns = m.ns, nr = m.nr;
   const double T = y[0];
-  const double lnT = log(T);
-  const double invT = 1.0 / T;
+  double lnT = 0.0, invT = 0.0;
+  if (lead) { lnT = log(T); invT = 1.0 / T; }
+  if (kMulti) {
+    if (g.tid == 0) { w.sc[S_LNT] = lnT; w.sc[S_INVT] = invT; }
+    g.sync();
+    lnT = w.sc[S_LNT]; invT = w.sc[S_INVT];
+  }
   const int rg = (T < TMID) ? 0 : 1;
 
   // species thermo (A2): NASA-7 cp/R, h/RT, g/RT sharing T powers and ln T
@@ -272,21 +308,37 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
     acc[0] += yw;
     acc[1] += yw * cp;
     if (jac) {
-      const double* dc = m.dcpc + (rg * ns + k) * 4;
-      const double d = dc[0] + T * (dc[1] + T * (dc[2] + T * dc[3]));
+      // d(cp/R)/dT = a2 + 2 a3 T + 3 a4 T^2 + 4 a5 T^3
+      const double d = cc[1] + T * (2.0 * cc[2] + T * (3.0 * cc[3] + T * (4.0 * cc[4])));
       w.dcpR[k] = d;
       acc[2] += yw * d;
     }
   }
-  gsum<G, 4>(g, acc, w.red);
-  const double S = acc[0];                 // sum Y/W
-  const double cp = RU * acc[1];           // mixture cp (mass)
-  const double dcpdT = RU * acc[2];
-  const double gshift = acc[3] / ns;       // mean g/RT: keeps exp(g/RT - gshift) in range
-  const double rho = p / (RU * T * S);
-  const double invrho = 1.0 / rho;
-  // per-species exp(g/RT - gshift) and its inverse: 1/Kc of every reaction becomes a product
-  // (w.rk / w.Hm are free until the Jacobian section)
+  gsum_lead<G, 4>(g, acc, w.red);
+  // mixture scalars: sum Y/W, cp, d(cp)/dT, mean g/RT (keeps exp(g/RT - gshift) in range),
+  // density, and exp(gshift - ln(p_atm / (R T))) for the equilibrium constants
+  double S = 0.0, cp = 0.0, dcpdT = 0.0, gshift = 0.0, rho = 0.0, invrho = 0.0, ep1 = 0.0, iep1 = 0.0;
+  if (lead) {
+    S = acc[0];
+    cp = RU * acc[1];
+    dcpdT = RU * acc[2];
+    gshift = acc[3] * m.cst[kC_INVNS];
+    rho = p / (RU * T * S);
+    invrho = 1.0 / rho;
+    ep1 = exp(gshift - (m.cst[kC_LNPR0] - lnT));
+    iep1 = 1.0 / ep1;
+  }
+  if (kMulti) {
+    if (g.tid == 0) {
+      w.sc[S_S] = S; w.sc[S_CP] = cp; w.sc[S_DCP] = dcpdT; w.sc[S_GSHIFT] = gshift;
+      w.sc[S_RHO] = rho; w.sc[S_INVRHO] = invrho; w.sc[S_EP1] = ep1; w.sc[S_IEP1] = iep1;
+    }
+    g.sync();
+    S = w.sc[S_S]; cp = w.sc[S_CP]; dcpdT = w.sc[S_DCP]; gshift = w.sc[S_GSHIFT];
+    rho = w.sc[S_RHO]; invrho = w.sc[S_INVRHO]; ep1 = w.sc[S_EP1]; iep1 = w.sc[S_IEP1];
+  }
+  // concentrations; per-species exp(g/RT - gshift) and its inverse: 1/Kc of every reaction
+  // becomes a product (w.rk / w.Hm are free until the Jacobian section)
   double* eg = w.rk;
   double* ieg = w.Hm;
   for (int k = g.tid; k < ns; k += G) {
@@ -299,10 +351,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
 
   // rates of progress (A3)
   const double Ctot = rho * S;
-  const double lnPR = log(PATM / RU) - lnT;     // ln(p_atm / (R T))
-  // 1/Kc = exp(dG - dnu lnPR) = prod_products eg * prod_reactants ieg * ep1^dnu
-  const double ep1 = exp(gshift - lnPR);
-  const double iep1 = 1.0 / ep1;
+  const double lnPR = m.cst[kC_LNPR0] - lnT;     // ln(p_atm / (R T)), range fallback only
   for (int j = g.tid; j < nr; j += G) {
     const short4 ri = m.rinfo[j];
     const short4 re = m.reac[j];
@@ -317,12 +366,6 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
     const double cp2 = pr.z >= 0 ? w.C[pr.z] : 1.0;
     Pf = cr0 * cr1 * cr2;
     Pr = cp0 * cp1 * cp2;
-    if (re.x >= 0) { dG -= w.gRT[re.x]; if (jac) dH -= w.hRT[re.x]; }
-    if (re.y >= 0) { dG -= w.gRT[re.y]; if (jac) dH -= w.hRT[re.y]; }
-    if (re.z >= 0) { dG -= w.gRT[re.z]; if (jac) dH -= w.hRT[re.z]; }
-    if (pr.x >= 0) { dG += w.gRT[pr.x]; if (jac) dH += w.hRT[pr.x]; }
-    if (pr.y >= 0) { dG += w.gRT[pr.y]; if (jac) dH += w.hRT[pr.y]; }
-    if (pr.z >= 0) { dG += w.gRT[pr.z]; if (jac) dH += w.hRT[pr.z]; }
     double Mc = 0.0;
     if (ri.x != 0) {
       Mc = Ctot;
@@ -376,12 +419,12 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
       }
     }
     double invKc = 1.0;                                   // 1 / Kc
-    if (re.x >= 0) invKc *= ieg[re.x];
-    if (re.y >= 0) invKc *= ieg[re.y];
-    if (re.z >= 0) invKc *= ieg[re.z];
-    if (pr.x >= 0) invKc *= eg[pr.x];
-    if (pr.y >= 0) invKc *= eg[pr.y];
-    if (pr.z >= 0) invKc *= eg[pr.z];
+    if (re.x >= 0) { invKc *= ieg[re.x]; dG -= w.gRT[re.x]; }
+    if (re.y >= 0) { invKc *= ieg[re.y]; dG -= w.gRT[re.y]; }
+    if (re.z >= 0) { invKc *= ieg[re.z]; dG -= w.gRT[re.z]; }
+    if (pr.x >= 0) { invKc *= eg[pr.x]; dG += w.gRT[pr.x]; }
+    if (pr.y >= 0) { invKc *= eg[pr.y]; dG += w.gRT[pr.y]; }
+    if (pr.z >= 0) { invKc *= eg[pr.z]; dG += w.gRT[pr.z]; }
     for (int d = ri.y; d > 0; --d) invKc *= ep1;
     for (int d = ri.y; d < 0; ++d) invKc *= iep1;
     if (!(invKc > 0.0 && invKc < 1.0e300)) invKc = exp(dG - (double)ri.y * lnPR);   // range fallback
@@ -390,6 +433,12 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
     const double mult = (ri.x == 1) ? Mc : 1.0;
     w.q[j] = (fwd - rev) * mult;
     if (jac) {
+      if (re.x >= 0) dH -= w.hRT[re.x];
+      if (re.y >= 0) dH -= w.hRT[re.y];
+      if (re.z >= 0) dH -= w.hRT[re.z];
+      if (pr.x >= 0) dH += w.hRT[pr.x];
+      if (pr.y >= 0) dH += w.hRT[pr.y];
+      if (pr.z >= 0) dH += w.hRT[pr.z];
       const double dlnKc = (dH - (double)ri.y) * invT;
       w.dqdT[j] = mult * (fwd * dlnkf - rev * (dlnkf - dlnKc));
       double* dq = w.dq + 6 * j;
@@ -411,9 +460,11 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
   for (int k = g.tid; k < ns; k += G) {
     double wk = 0.0, dwk = 0.0;
     for (int e = m.woff[k]; e < m.woff[k + 1]; ++e) {
-      const int j = m.wrx[e];
-      wk += m.wnu[e] * w.q[j];
-      if (jac) dwk += m.wnu[e] * w.dqdT[j];
+      const int pk = m.wpk[e];
+      const double nu = m.cst[kC_NU + (pk & 15)];
+      const int j = pk >> 4;
+      wk += nu * w.q[j];
+      if (jac) dwk += nu * w.dqdT[j];
     }
     w.wdot[k] = wk;
     const double hk = RT * w.hRT[k];
@@ -425,132 +476,170 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
       r3[2] += hk * dwk;
     }
   }
-  gsum<G, 3>(g, r3, w.red);
-  const double Q = r3[0];
-  const double rcp = rho * cp;
-  if (g.tid == 0) f[0] = -Q / rcp;
   if (!jac) {
+    double q1[1] = {r3[0]};
+    gsum_lead<G, 1>(g, q1, w.red);
+    if (g.tid == 0) f[0] = -q1[0] / (rho * cp);
     g.sync();
     return;
   }
+  gsum_lead<G, 3>(g, r3, w.red);
+  const double Q = r3[0];
+  const double rcp = rho * cp;
+  double ircp = 0.0;
+  if (lead) ircp = 1.0 / rcp;
+  if (g.tid == 0) f[0] = -Q / rcp;
 
   // analytic Jacobian (A5): d(wdot)/dC by the precomputed assembly program ...
-  const int N = m.N;
-  double* J = Jout;
-  for (int e = g.tid; e < ns * ns; e += G) J[(1 + e / ns) * LD + 1 + e % ns] = 0.0;
+  double* Jm = Jneg;
+  for (int e = g.tid; e < ns * ns; e += G) Jm[(1 + e / ns) * LD + 1 + e % ns] = 0.0;
   g.sync();
   for (int e = g.tid; e < jp.nent; e += G) {
     double s = 0.0;
     const int t1 = __ldg(jp.ent_off + e + 1);
     for (int t = __ldg(jp.ent_off + e); t < t1; ++t) s += __ldg(jp.term_coef + t) * w.dq[__ldg(jp.term_src + t)];
-    J[(1 + __ldg(jp.ent_row + e)) * LD + 1 + __ldg(jp.ent_col + e)] = s;
+    Jm[(1 + __ldg(jp.ent_row + e)) * LD + 1 + __ldg(jp.ent_col + e)] = s;
   }
+  if (kMulti && g.tid == 0) w.sc[S_IRCP] = ircp;
   g.sync();
-  // ... then the chain rule through C(T, Y) and rho(T, Y)
+  if (kMulti) ircp = w.sc[S_IRCP];
+  // ... then the chain rule through C(T, Y) and rho(T, Y):
+  //   r_k = sum_m dw_k/dC_m C_m,  H_m = RT sum_k h_k/RT dw_k/dC_m,  R_h = RT sum_k h_k/RT r_k
+  //   J_km = W_k / W_m (dw_k/dC_m - (r_k - w_k) rho^-1 / S)              (species rows)
+  //   J_k0 = W_k / rho (dw_k/dT - (r_k - w_k) / T)
+  //   J_0m = (-(rho H_m - R_h / S) / (rho cp) + Q / (rho cp)^2 rho (R cp_m/R - cp / S)) / W_m
+  const double rS = invrho / S;
+  double rh[1] = {0.0};
   for (int k = g.tid; k < ns; k += G) {
     double s = 0.0;
-    for (int mm = 0; mm < ns; ++mm) s += J[(1 + k) * LD + 1 + mm] * w.C[mm];
-    w.rk[k] = s;
+    for (int mm = 0; mm < ns; ++mm) s += Jm[(1 + k) * LD + 1 + mm] * w.C[mm];
+    rh[0] += RT * w.hRT[k] * s;
+    const double dk = s - w.wdot[k];
+    w.rk[k] = dk * rS;                               // (r_k - w_k) / (rho S)
+    Jm[(1 + k) * LD] = -(m.W[k] * invrho * (w.dwdT[k] - dk * invT));
   }
   for (int mm = g.tid; mm < ns; mm += G) {
     double s = 0.0;
-    for (int k = 0; k < ns; ++k) s += w.hRT[k] * J[(1 + k) * LD + 1 + mm];
+    for (int k = 0; k < ns; ++k) s += w.hRT[k] * Jm[(1 + k) * LD + 1 + mm];
     w.Hm[mm] = RT * s;
   }
-  g.sync();
-  double rh[1] = {0.0};
-  for (int k = g.tid; k < ns; k += G) rh[0] += RT * w.hRT[k] * w.rk[k];
-  gsum<G, 1>(g, rh, w.red);
-  const double Rh = rh[0];
-  const double rS = invrho / S;
+  gsum_lead<G, 1>(g, rh, w.red);
+  double RhS = 0.0, cpS = 0.0, QoR2r = 0.0;
+  if (lead) {
+    const double Rh = rh[0];
+    RhS = Rh / S;
+    cpS = cp / S;
+    QoR2r = Q * ircp * ircp * rho;
+    if (g.tid == 0)
+      Jm[0] = (RU * r3[1] + r3[2] - Rh * invT) * ircp - QoR2r * (-cp * invT + dcpdT);
+  }
+  if (kMulti) {
+    if (g.tid == 0) { w.sc[S_RHS] = RhS; w.sc[S_CPS] = cpS; w.sc[S_QOR2R] = QoR2r; }
+    g.sync();
+    RhS = w.sc[S_RHS]; cpS = w.sc[S_CPS]; QoR2r = w.sc[S_QOR2R];
+  } else {
+    g.sync();
+  }
   for (int e = g.tid; e < ns * ns; e += G) {
     const int k = e / ns, mm = e % ns;
-    double* Jkm = J + (1 + k) * LD + 1 + mm;
-    *Jkm = m.W[k] * m.invW[mm] * (*Jkm) - m.W[k] * (w.rk[k] - w.wdot[k]) * rS * m.invW[mm];
+    double* Jkm = Jm + (1 + k) * LD + 1 + mm;
+    *Jkm = m.W[k] * m.invW[mm] * (w.rk[k] - *Jkm);
   }
-  const double QoR2 = Q / (rcp * rcp);
-  for (int k = g.tid; k < ns; k += G)
-    J[(1 + k) * LD] = m.W[k] * invrho * (w.dwdT[k] - (w.rk[k] - w.wdot[k]) * invT);
   for (int mm = g.tid; mm < ns; mm += G)
-    J[1 + mm] = m.invW[mm] * (-(rho * w.Hm[mm] - Rh / S) / rcp +
-                              QoR2 * rho * (RU * w.cpR[mm] - cp / S));
-  if (g.tid == 0)
-    J[0] = -(RU * r3[1] + r3[2] - Rh * invT) / rcp + QoR2 * (-rho * cp * invT + rho * dcpdT);
-  (void)N;
+    Jm[1 + mm] = m.invW[mm] * ((rho * w.Hm[mm] - RhS) * ircp - QoR2r * (RU * w.cpR[mm] - cpS));
   g.sync();
 }
 
 // ---------------------------------------------------------------------------------------
 // dense LU with partial pivoting (A6) and triangular solves
 // ---------------------------------------------------------------------------------------
+// LU factorisation with partial pivoting, rows pivoted implicitly: perm[i] is the physical row
+// of logical row i.  On return, for logical row i and column j, L[i][j] = M[perm[i]][j] (j < i,
+// unit diagonal implied) and U[i][j] = M[perm[i]][j] (j >= i); invd[j] = 1 / U[j][j].
+// Step k: (1) every thread merges the per-warp pivot candidates of column k; (2) the first warp
+// forms the reciprocal of the pivot and the multipliers of column k and records the row swap in
+// perm; (3) all threads update the trailing block and, on the way, collect the candidates of
+// column k + 1.  Two group barriers per step.  Returns false on an exactly singular matrix.
 template <int G>
-__device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* piv, double* invd,
-                          double* lcol, double* red) {
+__device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* perm, double* invd,
+                          double* red) {
+  constexpr int NW = G > 32 ? G / 32 : 1;
+  constexpr int W = G < 32 ? G : 32;
+  unsigned long long* rkey = (unsigned long long*)red;
+  int* ridx = (int*)(red + NW);
+  for (int i = g.tid; i < N; i += G) perm[i] = i;
+  unsigned long long best = 0ull;
+  int bi = 0;
+  for (int i = g.tid; i < N; i += G) argmax_merge(best, bi, pivot_key(M[i * LD]), i);
+  warp_argmax<G>(g, best, bi);
+  if (G > 32 && (g.tid & 31) == 0) { rkey[g.tid >> 5] = best; ridx[g.tid >> 5] = bi; }
+  g.sync();
   for (int k = 0; k < N; ++k) {
-    unsigned long long best = 0ull;
-    int bi = k;
-    bool any = false;
-    for (int i = k + g.tid; i < N; i += G) {
-      const unsigned long long v = pivot_key(M[i * LD + k]);
-      if (!any || v > best) { best = v; bi = i; any = true; }
+    if (G > 32) {
+      best = rkey[0];
+      bi = ridx[0];
+      for (int w = 1; w < NW; ++w) argmax_merge(best, bi, rkey[w], ridx[w]);
     }
-    gargmax<G>(g, best, bi, red);
     if (best == 0ull) return false;
-    const double pv = M[bi * LD + k];
-    const double ip = 1.0 / pv;
-    // phase A: swap rows k and bi (columns != k); multipliers from column k
-    if (bi != k)
-      for (int j = g.tid; j < N; j += G)
-        if (j != k) {
-          const double t = M[k * LD + j];
-          M[k * LD + j] = M[bi * LD + j];
-          M[bi * LD + j] = t;
-        }
-    for (int i = k + 1 + g.tid; i < N; i += G) lcol[i] = M[((i == bi) ? k : i) * LD + k] * ip;
+    if (is_lead(g)) {
+      const int pk = perm[bi], pb = perm[k];
+      const double ip = 1.0 / M[pk * LD + k];
+      for (int i = k + 1 + g.tid; i < N; i += W) {
+        const int ph = (i == bi) ? pb : perm[i];
+        M[ph * LD + k] *= ip;
+      }
+      if (G <= 32) __syncwarp(g.mask); else __syncwarp();
+      if (g.tid == 0) {
+        invd[k] = ip;
+        perm[k] = pk;
+        perm[bi] = pb;
+      }
+    }
     g.sync();
-    // phase B: trailing update and column k
     const int n = N - k - 1;
+    if (n == 0) break;
+    const int pk = perm[k];
+    best = 0ull;
+    bi = k + 1;
     for (int e = g.tid; e < n * n; e += G) {
       const int i = k + 1 + e / n, j = k + 1 + e % n;
-      M[i * LD + j] -= lcol[i] * M[k * LD + j];
+      const int ph = perm[i];
+      const double v = M[ph * LD + j] - M[ph * LD + k] * M[pk * LD + j];
+      M[ph * LD + j] = v;
+      if (j == k + 1) argmax_merge(best, bi, pivot_key(v), i);
     }
-    for (int i = k + 1 + g.tid; i < N; i += G) M[i * LD + k] = lcol[i];
-    if (g.tid == 0) {
-      M[k * LD + k] = pv;
-      invd[k] = ip;
-      piv[k] = bi;
-    }
+    warp_argmax<G>(g, best, bi);
+    if (G > 32 && (g.tid & 31) == 0) { rkey[g.tid >> 5] = best; ridx[g.tid >> 5] = bi; }
     g.sync();
   }
   return true;
 }
 
+// Solves A x = b with the factors of lu_factor; b (length N) is overwritten with x.  t: N-double
+// scratch holding the permuted right-hand side during the two triangular sweeps.  The division
+// by the diagonal of U happens once per row, in the thread that finishes that row.
 template <int G>
-__device__ void lu_solve(const Grp<G>& g, const double* M, int N, int LD, const int* piv,
-                         const double* invd, double* x) {
-  if (g.tid == 0)
-    for (int k = 0; k < N; ++k)
-      if (piv[k] != k) {
-        const double t = x[k];
-        x[k] = x[piv[k]];
-        x[piv[k]] = t;
-      }
+__device__ void lu_solve(const Grp<G>& g, const double* M, int N, int LD, const int* perm,
+                         const double* invd, double* b, double* t) {
+  for (int i = g.tid; i < N; i += G) t[i] = b[perm[i]];
   g.sync();
-  for (int k = 0; k < N - 1; ++k) {
-    const double xk = x[k];
-    for (int i = k + 1 + g.tid; i < N; i += G) x[i] -= M[i * LD + k] * xk;
+  for (int k = 0; k < N - 1; ++k) {          // L y = P b (unit diagonal)
+    const double xk = t[k];
+    for (int i = k + 1 + g.tid; i < N; i += G) t[i] -= M[perm[i] * LD + k] * xk;
     g.sync();
   }
-  double prev = 0.0;
-  for (int k = N - 1; k >= 0; --k) {
-    const double xk = x[k] * invd[k];
-    if (g.tid == 0 && k < N - 1) x[k + 1] = prev;
-    for (int i = g.tid; i < k; i += G) x[i] -= M[i * LD + k] * xk;
-    prev = xk;
+  if (g.tid == 0) t[N - 1] *= invd[N - 1];
+  g.sync();
+  for (int k = N - 1; k >= 0; --k) {         // U x = y, column by column
+    const double xk = t[k];
+    if (g.tid == 0) b[k] = xk;
+    for (int i = g.tid; i < k; i += G) {
+      double v = t[i] - M[perm[i] * LD + k] * xk;
+      if (i == k - 1) v *= invd[i];
+      t[i] = v;
+    }
     g.sync();
   }
-  if (g.tid == 0) x[0] = prev;
-  g.sync();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -593,22 +682,24 @@ __device__ __forceinline__ void stage_mech(const unsigned char* src, unsigned ch
   for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-// one Rodas4 attempt from w.y with step h; J(y) and f(y) are (re)evaluated when need_j.
-// Returns false on an exactly singular iteration matrix; *en receives the error norm.
+// One Rodas4 attempt from w.y with step h (f and J re-evaluated at w.y).  Returns false on an
+// exactly singular iteration matrix; otherwise *en receives the error norm and *fac the step-size
+// factor 0.9 en^(-1/4) (clamped below at 0.2; 0.2 for a non-finite norm), evaluated once per
+// group.
 template <int G>
 __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& w,
-                               const AdvanceParams& P, double p, double h, bool need_j,
-                               double rtol, double atol, double* en) {
+                               const AdvanceParams& P, double p, double h, double rtol, double atol,
+                               double* en, double* fac) {
+  constexpr bool kMulti = G > 32;
   const int N = m.N, LD = P.ws.LD;
-  if (need_j) eval_fj<G>(g, m, w, P.jp, LD, w.y, p, w.f0, w.J, true);
-  const double ig = 1.0 / (kGamma * h);
-  for (int e = g.tid; e < N * N; e += G) {
-    const int i = e / N, j = e % N;
-    w.M[i * LD + j] = (i == j ? ig : 0.0) - w.J[i * LD + j];
-  }
+  double ig = 0.0, invh = 0.0;
+  if (is_lead(g)) { ig = 1.0 / (kGamma * h); invh = 1.0 / h; }
+  if (kMulti && g.tid == 0) { w.sc[S_IG] = ig; w.sc[S_INVH] = invh; }
+  eval_fj<G>(g, m, w, P.jp, LD, w.y, p, w.f0, w.M);      // M = -J; synchronises
+  if (kMulti) { ig = w.sc[S_IG]; invh = w.sc[S_INVH]; }
+  for (int i = g.tid; i < N; i += G) w.M[i * LD + i] += ig;   // M = I / (gamma h) - J
   g.sync();
-  if (!lu_factor<G>(g, w.M, N, LD, w.piv, w.invd, w.lcol, w.red)) return false;
-  const double invh = 1.0 / h;
+  if (!lu_factor<G>(g, w.M, N, LD, w.perm, w.invd, w.red)) return false;
   for (int s = 0; s < 6; ++s) {
     const double* src = w.f0;
     if (s > 0) {
@@ -618,7 +709,7 @@ __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& 
         w.ys[i] = v;
       }
       g.sync();
-      eval_fj<G>(g, m, w, P.jp, LD, w.ys, p, w.fs, nullptr, false);
+      eval_fj<G>(g, m, w, P.jp, LD, w.ys, p, w.fs, nullptr);
       src = w.fs;
     }
     double* us = w.u + s * N;
@@ -628,7 +719,7 @@ __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& 
       us[i] = v;
     }
     g.sync();
-    lu_solve<G>(g, w.M, N, LD, w.piv, w.invd, us);
+    lu_solve<G>(g, w.M, N, LD, w.perm, w.invd, us, w.tmp);
   }
   double acc[1] = {0.0};
   for (int i = g.tid; i < N; i += G) {
@@ -640,8 +731,23 @@ __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& 
     const double r = w.u[5 * N + i] / sc;
     acc[0] += r * r;
   }
-  gsum<G, 1>(g, acc, w.red);
-  *en = sqrt(acc[0] / (double)N);
+  gsum_lead<G, 1>(g, acc, w.red);
+  double e = 0.0, f = 0.0;
+  if (is_lead(g)) {
+    e = sqrt(acc[0] / (double)N);
+    f = 0.2;
+    if (isfinite(e)) {
+      f = 0.9 * pow(e, -0.25);
+      if (f < 0.2) f = 0.2;
+    }
+  }
+  if (kMulti) {
+    if (g.tid == 0) { w.sc[S_EN] = e; w.sc[S_FAC] = f; }
+    g.sync();
+    e = w.sc[S_EN]; f = w.sc[S_FAC];
+  }
+  *en = e;
+  *fac = f;
   return true;
 }
 
@@ -747,7 +853,7 @@ __global__ void __launch_bounds__(512) advance_kernel(const __grid_constant__ Ad
   if (P.ncells_dev)
     total = (min((long long)*P.ncells_dev, (long long)P.segs[0].ncells) + CHUNK - 1) / CHUNK;
   ChunkPos q{&P.segs[0], 0, 0, 0, false, total};
-  bool active = false, have_j = false;
+  bool active = false;
   double dt = 1.0, rtol = 1e-6, atol = 1e-10;
   double p = 1.0e6, t = 0.0, h = dt, facmax = 6.0;
   int attempts = 0, nacc = 0, nrej = 0;
@@ -776,7 +882,6 @@ __global__ void __launch_bounds__(512) advance_kernel(const __grid_constant__ Ad
         continue;
       }
       active = true;
-      have_j = false;
       dt = q.seg->dt; rtol = q.seg->rtol; atol = q.seg->atol;
       t = 0.0; h = dt; facmax = 6.0;
       attempts = 0; nacc = 0; nrej = 0;
@@ -801,11 +906,9 @@ __global__ void __launch_bounds__(512) advance_kernel(const __grid_constant__ Ad
     const bool run = active && !stop;
     bool finished = false;
     if (run || G < 32) {
-      double en = 0.0;
-      const bool need_j = (G < 32) || !have_j;
-      const bool ok = rodas4_attempt<G>(g, m, w, P, p, run ? h : dt, need_j, rtol, atol, &en);
+      double en = 0.0, fac = 0.2;
+      const bool ok = rodas4_attempt<G>(g, m, w, P, p, run ? h : dt, rtol, atol, &en, &fac);
       if (run) {
-        have_j = true;
         if (!ok) {
           stop = true; status = CHEM_CELL_SINGULAR_LU;
         } else {
@@ -813,25 +916,16 @@ __global__ void __launch_bounds__(512) advance_kernel(const __grid_constant__ Ad
           if (en <= 1.0) {
             for (int i = g.tid; i < N; i += G) w.y[i] = w.ynew[i];
             g.sync();
-            have_j = false;
             ++nacc;
             if (last) {
               finished = true;
             } else {
               t += h;
-              double fac = 0.9 * pow(en, -0.25);
-              if (fac < 0.2) fac = 0.2;
-              if (fac > facmax) fac = facmax;
-              h = h * fac;
+              h = h * fmin(fac, facmax);
               facmax = 6.0;
             }
           } else {
             ++nrej;
-            double fac = 0.2;
-            if (isfinite(en)) {
-              fac = 0.9 * pow(en, -0.25);
-              if (fac < 0.2) fac = 0.2;
-            }
             h = h * fac;
             facmax = 1.0;
           }
@@ -883,11 +977,11 @@ __global__ void __launch_bounds__(512) eval_kernel(const EvalParams P) {
   for (int64_t c = (int64_t)blockIdx.x * gpb + g.gid; c < P.ncells; c += (int64_t)gridDim.x * gpb) {
     for (int i = g.tid; i < N; i += G) w.y[i] = i == 0 ? P.T[c] : P.Y[(int64_t)(i - 1) * P.ld + c];
     g.sync();
-    eval_fj<G>(g, m, w, P.jp, LD, w.y, P.p[c], w.f0, w.J, P.J != nullptr);
+    eval_fj<G>(g, m, w, P.jp, LD, w.y, P.p[c], w.f0, P.J ? w.M : nullptr);
     for (int i = g.tid; i < N; i += G) P.f[(int64_t)i * P.ld + c] = w.f0[i];
-    if (P.J)
+    if (P.J)     // the kernel assembles -J (exact negation back)
       for (int e = g.tid; e < N * N; e += G)
-        P.J[(int64_t)e * P.ld + c] = w.J[(e / N) * LD + e % N];
+        P.J[(int64_t)e * P.ld + c] = -w.M[(e / N) * LD + e % N];
     g.sync();
   }
 }

@@ -50,7 +50,45 @@ struct Builder {
   template <class T> T* at(int off) { return reinterpret_cast<T*>(buf.data() + off); }
 };
 
-int build(const chem_mech_desc* d, chem_mech_s* m) {
+// Copy of a mechanism description whose reactions are reordered fall-off first, then
+// third-body, then elementary (stable within each class).  The rate loop hands consecutive
+// reactions to consecutive threads, so the long fall-off branch runs in as few warps as possible.
+struct Reordered {
+  chem_mech_desc d{};
+  std::vector<int> rtype, reac, prod, has_t2;
+  std::vector<double> A, b, Ea, troe, eff;
+};
+
+void reorder_reactions(const chem_mech_desc* in, Reordered* o) {
+  const int ns = in->n_species, nr = in->n_reactions;
+  std::vector<int> order;
+  for (int cls : {2, 1, 0})
+    for (int j = 0; j < nr; ++j)
+      if (in->rtype[j] == cls) order.push_back(j);
+  o->d = *in;
+  o->rtype.resize(nr); o->reac.resize(3 * nr); o->prod.resize(3 * nr); o->has_t2.resize(nr);
+  o->A.resize(nr); o->b.resize(nr); o->Ea.resize(nr); o->troe.resize(7 * (size_t)nr);
+  o->eff.resize((size_t)nr * ns);
+  for (int jn = 0; jn < nr; ++jn) {
+    const int j = order[jn];
+    o->rtype[jn] = in->rtype[j];
+    for (int i = 0; i < 3; ++i) { o->reac[3 * jn + i] = in->reac[3 * j + i]; o->prod[3 * jn + i] = in->prod[3 * j + i]; }
+    o->has_t2[jn] = in->has_t2[j];
+    o->A[jn] = in->A[j]; o->b[jn] = in->b[j]; o->Ea[jn] = in->Ea[j];
+    for (int i = 0; i < 7; ++i) o->troe[7 * (size_t)jn + i] = in->troe[7 * (size_t)j + i];
+    for (int k = 0; k < ns; ++k) o->eff[(size_t)jn * ns + k] = in->eff[(size_t)j * ns + k];
+  }
+  if (nr > 0) {
+    o->d.rtype = o->rtype.data(); o->d.reac = o->reac.data(); o->d.prod = o->prod.data();
+    o->d.has_t2 = o->has_t2.data(); o->d.A = o->A.data(); o->d.b = o->b.data(); o->d.Ea = o->Ea.data();
+    o->d.troe = o->troe.data(); o->d.eff = o->eff.data();
+  }
+}
+
+int build(const chem_mech_desc* din, chem_mech_s* m) {
+  Reordered ro;
+  reorder_reactions(din, &ro);
+  const chem_mech_desc* d = &ro.d;
   const int ns = d->n_species, ne = d->n_elements, nr = d->n_reactions;
   m->ns = ns; m->ne = ne; m->nr = nr;
   m->elem_mass.assign(d->elem_mass, d->elem_mass + ne);
@@ -101,18 +139,17 @@ int build(const chem_mech_desc* d, chem_mech_s* m) {
   L.o_hc = B.add(8 * 2 * ns * 6);
   L.o_sc = B.add(8 * 2 * ns * 6);
   L.o_cpc = B.add(8 * 2 * ns * 5);
-  L.o_dcpc = B.add(8 * 2 * ns * 4);
   L.o_lnA = B.add(8 * nr);
   L.o_beta = B.add(8 * nr);
   L.o_Ta = B.add(8 * nr);
   L.o_troe = B.add(8 * 8 * ntroe);
   L.o_effv = B.add(8 * neff);
-  L.o_wnu = B.add(8 * nprod);
+  L.o_const = B.add(8 * kConsts);
   L.o_reac = B.add(2 * 4 * nr);
   L.o_prod = B.add(2 * 4 * nr);
   L.o_rinfo = B.add(2 * 4 * nr);
   L.o_effidx = B.add(2 * neff);
-  L.o_wrx = B.add(2 * nprod);
+  L.o_wpk = B.add(4 * nprod);
   L.o_effoff = B.add(4 * (ntb + 1));
   L.o_woff = B.add(4 * (ns + 1));
   L.bytes = (int)B.buf.size();
@@ -127,11 +164,9 @@ int build(const chem_mech_desc* d, chem_mech_s* m) {
       double* hc = B.at<double>(L.o_hc) + (r * ns + k) * 6;
       double* sc = B.at<double>(L.o_sc) + (r * ns + k) * 6;
       double* cc = B.at<double>(L.o_cpc) + (r * ns + k) * 5;
-      double* dc = B.at<double>(L.o_dcpc) + (r * ns + k) * 4;
       hc[0] = a[0]; hc[1] = a[1] / 2.0; hc[2] = a[2] / 3.0; hc[3] = a[3] / 4.0; hc[4] = a[4] / 5.0; hc[5] = a[5];
       sc[0] = a[0]; sc[1] = a[1]; sc[2] = a[2] / 2.0; sc[3] = a[3] / 3.0; sc[4] = a[4] / 4.0; sc[5] = a[6];
       for (int i = 0; i < 5; ++i) cc[i] = a[i];
-      dc[0] = a[1]; dc[1] = 2.0 * a[2]; dc[2] = 3.0 * a[3]; dc[3] = 4.0 * a[4];
     }
   }
   for (int j = 0; j < nr; ++j) {
@@ -165,9 +200,17 @@ int build(const chem_mech_desc* d, chem_mech_s* m) {
   for (int k = 0; k <= ns; ++k) B.at<int>(L.o_woff)[k] = woff[k];
   for (int k = 0; k < ns; ++k)
     for (int i = 0; i < (int)plist[k].size(); ++i) {
-      B.at<int16_t>(L.o_wrx)[woff[k] + i] = (int16_t)plist[k][i].first;
-      B.at<double>(L.o_wnu)[woff[k] + i] = (double)plist[k][i].second;
+      const int nuk = plist[k][i].second;
+      if (nuk < -8 || nuk > 7) {
+        set_error("reaction %d: stoichiometric coefficient %d of species %d out of range", plist[k][i].first, nuk, k);
+        return CHEM_EINVAL;
+      }
+      B.at<int>(L.o_wpk)[woff[k] + i] = (plist[k][i].first << 4) | (nuk + 8);
     }
+  double* cst = B.at<double>(L.o_const);
+  for (int c = 0; c < 16; ++c) cst[kC_NU + c] = (double)(c - 8);
+  cst[kC_LNPR0] = std::log(PATM / RU);
+  cst[kC_INVNS] = 1.0 / ns;
   m->lay = L;
 
   // Jacobian-assembly program for d(wdot_k)/dC_m
