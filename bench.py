@@ -167,11 +167,32 @@ def run_reference(args, rank, world):
 
 
 def run_case(args):
-    """Integrator only, on a small case: the quasi-DNS H2 field or the LES CH4 field."""
+    """One kernel family on a small case (profiling): the integrator on the quasi-DNS H2 field or
+    the LES CH4 field, or the surrogate step on the quasi-DNS H2 field."""
     import torch
     import paper_2312_13513_gb300 as cg
     from synth.mechanism import ch4_mechanism, h2_mechanism
     from synth.states import les_field, load_table
+    if args.case == "surrogate":
+        dm = cg.Mechanism(h2_mechanism())
+        model = cg.Surrogate(dm, path=MODEL_PATH)
+        f = make_field(0, args.cells)
+        T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+        Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+        ms = []
+        for k in range(args.warmup + args.steps):
+            T = T0.clone(); Y = Y0.clone()
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            cg.surrogate_advance(model, T, p, Y, DT, RTOL, ATOL)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        print(json.dumps({"case": args.case, "cells": args.cells, "ms": ms,
+                          "cells_per_s": args.cells / (float(np.mean(ms)) * 1e-3)}), flush=True)
+        return
     if args.case == "h2":
         mech, f, dt = h2_mechanism(), make_field(0, args.cells), DT
     else:
@@ -356,8 +377,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["h2", "ch4"], default=None,
-                    help="time only the integrator on a small case (profiling)")
+    ap.add_argument("--case", choices=["h2", "ch4", "surrogate"], default=None,
+                    help="time one kernel family on a small case (profiling)")
     ap.add_argument("--cells", type=int, default=65536)
     ap.add_argument("--group", type=int, default=0, help="threads per cell (profiling mode; 0 = auto)")
     args = ap.parse_args()

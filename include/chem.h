@@ -273,8 +273,12 @@ int chem_train_normalize(const float* x, int64_t n, int c, const float* mean, co
  * Serving: chemistry sub-steps from many concurrent flow solvers on one GPU.  Solvers register
  * their resident device states once and submit one request per sub-step; a server thread admits
  * requests under a device-memory budget (resident states + per-request workspace), batches the
- * admitted FP64 requests of a mechanism into one persistent launch and overlaps launches on a
- * small stream pool (continuous batching).  Latency = submission to completion.
+ * admitted FP64 requests of a mechanism into one job of the persistent integrator and overlaps
+ * launches on a small stream pool (continuous batching).  An FP64 job runs as time slices of
+ * slice_ms: each slice stops claiming cells after that time and the next continues the same work
+ * queue, so launches on other streams get the SMs in between.  A request completes when the
+ * queue passes its last cell.  Latency = submission to completion.  No counterpart in the paper,
+ * whose solver owns the GPU alone (§3.1). 
  * ------------------------------------------------------------------------------------- */
 enum { CHEM_ROUTE_FP64 = 0, CHEM_ROUTE_SURROGATE = 1 };
 enum { CHEM_REQ_QUEUED = 0, CHEM_REQ_RUNNING = 1, CHEM_REQ_DONE = 2, CHEM_REQ_FAILED = 3 };
@@ -282,6 +286,7 @@ enum { CHEM_REQ_QUEUED = 0, CHEM_REQ_RUNNING = 1, CHEM_REQ_DONE = 2, CHEM_REQ_FA
 typedef struct chem_serve_options {
   int32_t n_streams;         /* concurrent launches (0 -> 4) */
   double idle_poll_us;       /* polling interval while launches are in flight (0 -> 20 us) */
+  double slice_ms;           /* FP64 time slice (0 -> 20 ms; negative: no slicing) */
 } chem_serve_options;
 
 int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_options* opt, chem_server_t* out);
@@ -299,7 +304,8 @@ int chem_serve_submit(chem_server_t s, int state_id, int route, double dt, doubl
 int chem_serve_poll(chem_server_t s, uint64_t req_id, int* state, double* latency_s);
 /* Block until the request is done or timeout_s passes (CHEM_ETIMEOUT); never hangs. */
 int chem_serve_wait(chem_server_t s, uint64_t req_id, double timeout_s);
-/* out[6]: completed, failed, launches, requests launched, max concurrent launches, bytes in use */
+/* out[8]: completed, failed, launches (jobs and surrogate launches), requests launched, max
+ * concurrent launches, bytes in use, FP64 time slices issued, 0 */
 int chem_serve_stats(chem_server_t s, int64_t* out);
 /* Stops the server after its launches finish; queued requests fail. */
 int chem_serve_destroy(chem_server_t s);

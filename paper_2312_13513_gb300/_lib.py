@@ -51,7 +51,7 @@ class Segment(ctypes.Structure):
 
 
 class ServeOptions(ctypes.Structure):
-    _fields_ = [("n_streams", I32), ("idle_poll_us", D)]
+    _fields_ = [("n_streams", I32), ("idle_poll_us", D), ("slice_ms", D)]
 
 
 class SurrogateDesc(ctypes.Structure):

@@ -29,6 +29,7 @@ int cuda_fail(cudaError_t e, const char* what);
 // All arrays are 16-byte aligned.  Doubles first, then 16-bit and 32-bit integers.
 struct MechLayout {
   int ns, nr, N, ntb, ntroe, nprod;     // nprod: entries of the species production lists
+  int npieces;                          // balanced pieces of the production lists
   int bytes;                            // total blob size (multiple of 16)
   int o_W, o_invW;                      // [ns]
   int o_hc;                             // [2][ns][6]  h/RT:  a1, a2/2, a3/3, a4/4, a5/5, a6
@@ -44,6 +45,8 @@ struct MechLayout {
   int o_wpk;                            // [nprod] int32 production term: reaction << 4 | (nu + 8)
   int o_effoff;                         // [ntb + 1] int32
   int o_woff;                           // [ns + 1] int32
+  int o_pterm;                          // [npieces + 1] int32: term range of each piece
+  int o_poff;                           // [ns + 1] int32: pieces of each species
 };
 
 // constants block of the blob: the stoichiometric-coefficient table indexed by the 4-bit code of
@@ -83,6 +86,9 @@ struct chem_mech_s {
 namespace chem {
 // integrator launch (used by the public entry points, the surrogate fallback and the server)
 int launch_advance_batch(chem_mech_s* m, const chem_segment* segs, int nseg, cudaStream_t stream);
+constexpr int kMaxSegsPerLaunch = 32;
+int launch_advance_slice(chem_mech_s* m, const chem_segment* segs, int nseg, unsigned long long budget_ns,
+                         unsigned long long* counter, long long* seg_end, cudaStream_t stream);
 int launch_advance(chem_mech_s* m, double* T, const double* p, double* Y, int64_t ld, double dt,
                    int64_t ncells, double rtol, double atol, const int32_t* idx, int8_t* status,
                    int32_t* nsub, int32_t* nrej, const chem_options* opt, cudaStream_t stream,

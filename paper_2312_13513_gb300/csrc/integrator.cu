@@ -29,7 +29,10 @@
 
 namespace chem {
 
-constexpr int CHUNK = 8;   // cells claimed per queue access
+// Cells claimed per work-queue access: eight consecutive cells (64-byte rows of the SoA state)
+// for sub-warp groups, one cell for groups of a warp or more, whose cells take milliseconds each
+// (a time-sliced launch then overruns its budget by at most one cell).
+__host__ __device__ constexpr int chunk_cells(int G) { return G >= 32 ? 1 : 8; }
 
 // Rodas4 coefficients, transformed (u-variable) form:
 //   (I/(gamma h) - J) u_s = f(y + sum_j A[s][j] u_j) + sum_j (C[s][j]/h) u_j,
@@ -57,16 +60,16 @@ constexpr double kGamma = 0.25;
 // mechanism view (shared memory)
 // ---------------------------------------------------------------------------------------
 struct MechView {
-  int ns, nr, N;
+  int ns, nr, N, npieces;
   const double *W, *invW, *hc, *sc, *cpc, *lnA, *beta, *Ta, *troe, *effv, *cst;
   const short4 *reac, *prod, *rinfo;
   const int16_t* effidx;
-  const int *wpk, *effoff, *woff;
+  const int *wpk, *effoff, *woff, *pterm, *poff;
 };
 
 __device__ __forceinline__ MechView bind_mech(const unsigned char* s, const MechLayout& L) {
   MechView m;
-  m.ns = L.ns; m.nr = L.nr; m.N = L.N;
+  m.ns = L.ns; m.nr = L.nr; m.N = L.N; m.npieces = L.npieces;
   m.W = (const double*)(s + L.o_W);
   m.invW = (const double*)(s + L.o_invW);
   m.hc = (const double*)(s + L.o_hc);
@@ -85,6 +88,8 @@ __device__ __forceinline__ MechView bind_mech(const unsigned char* s, const Mech
   m.wpk = (const int*)(s + L.o_wpk);
   m.effoff = (const int*)(s + L.o_effoff);
   m.woff = (const int*)(s + L.o_woff);
+  m.pterm = (const int*)(s + L.o_pterm);
+  m.poff = (const int*)(s + L.o_poff);
   return m;
 }
 
@@ -102,11 +107,11 @@ struct WsLayout {
   int LD;                  // leading dimension of the N x N matrix (odd: no bank conflicts)
   int y, ynew, ys, fs, f0, u, M, invd, tmp;
   int C, hRT, gRT, cpR, dcpR, wdot, dwdT, rk, Hm;
-  int q, dqdT, dq, red, sc, stage, ctl, perm;
+  int q, dqdT, dq, wpart, dwpart, red, sc, stage, ctl, perm;
   int total;               // doubles
 };
 
-inline WsLayout make_ws(int ns, int nr, int G) {
+inline WsLayout make_ws(int ns, int nr, int npieces, int G) {
   WsLayout w{};
   const int N = ns + 1;
   w.LD = (N % 2 == 0) ? N + 1 : N;
@@ -117,9 +122,11 @@ inline WsLayout make_ws(int ns, int nr, int G) {
   w.C = take(ns); w.hRT = take(ns); w.gRT = take(ns); w.cpR = take(ns); w.dcpR = take(ns);
   w.wdot = take(ns); w.dwdT = take(ns); w.rk = take(ns); w.Hm = take(ns);
   w.q = take(nr); w.dqdT = take(nr); w.dq = take(7 * nr);
+  // partial production sums of the balanced pieces (groups wider than a warp)
+  w.wpart = take(G > 32 ? npieces : 0); w.dwpart = take(G > 32 ? npieces : 0);
   w.red = take(8 * (G >= 32 ? G / 32 : 1) + 8);
   w.sc = take(S_NSC);
-  w.stage = take(CHUNK * (N + 1));
+  w.stage = take(chunk_cells(G) * (N + 1));
   w.ctl = take(2);
   w.perm = take((N + 1) / 2);      // ints
   w.total = o;
@@ -129,7 +136,7 @@ inline WsLayout make_ws(int ns, int nr, int G) {
 struct WsPtr {
   double *y, *ynew, *ys, *fs, *f0, *u, *M, *invd, *tmp;
   double *C, *hRT, *gRT, *cpR, *dcpR, *wdot, *dwdT, *rk, *Hm;
-  double *q, *dqdT, *dq, *red, *sc, *stage;
+  double *q, *dqdT, *dq, *wpart, *dwpart, *red, *sc, *stage;
   unsigned long long* ctl;
   int* perm;
 };
@@ -141,6 +148,7 @@ __device__ __forceinline__ WsPtr bind_ws(double* b, const WsLayout& w) {
   p.C = b + w.C; p.hRT = b + w.hRT; p.gRT = b + w.gRT; p.cpR = b + w.cpR; p.dcpR = b + w.dcpR;
   p.wdot = b + w.wdot; p.dwdT = b + w.dwdT; p.rk = b + w.rk; p.Hm = b + w.Hm;
   p.q = b + w.q; p.dqdT = b + w.dqdT; p.dq = b + w.dq; p.red = b + w.red; p.sc = b + w.sc;
+  p.wpart = b + w.wpart; p.dwpart = b + w.dwpart;
   p.stage = b + w.stage;
   p.ctl = (unsigned long long*)(b + w.ctl);
   p.perm = (int*)(b + w.perm);
@@ -212,23 +220,31 @@ template <int G>
 __device__ __forceinline__ bool is_lead(const Grp<G>& g) { return G <= 32 || g.tid < 32; }
 
 // Sum of K values over the group, delivered to the lead threads only (all threads for G <= 32).
+// Only threads below nact hold non-zero values: warps entirely above it skip the reduction.
 // Ends with the group synchronised once (G > 32); the caller publishes derived scalars through
 // w.sc and synchronises again.
 template <int G, int K>
-__device__ __forceinline__ void gsum_lead(const Grp<G>& g, double (&v)[K], double* red) {
+__device__ __forceinline__ void gsum_lead(const Grp<G>& g, double (&v)[K], double* red, int nact) {
+  if (G <= 32) {
 #pragma unroll
-  for (int i = 0; i < K; ++i) v[i] = sub_sum<G>(v[i], g.mask);
-  if (G <= 32) return;
+    for (int i = 0; i < K; ++i) v[i] = sub_sum<G>(v[i], g.mask);
+    return;
+  }
   constexpr int NW = G / 32;
-  if ((g.tid & 31) == 0)
+  const int nw = min(NW, (nact + 31) >> 5);
+  if ((g.tid >> 5) < nw) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) red[i * NW + (g.tid >> 5)] = v[i];
+    for (int i = 0; i < K; ++i) v[i] = sub_sum<G>(v[i], g.mask);
+    if ((g.tid & 31) == 0)
+#pragma unroll
+      for (int i = 0; i < K; ++i) red[i * NW + (g.tid >> 5)] = v[i];
+  }
   g.sync();
   if (g.tid < 32) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       double s = red[i * NW];
-      for (int w = 1; w < NW; ++w) s += red[i * NW + w];
+      for (int w = 1; w < nw; ++w) s += red[i * NW + w];
       v[i] = s;
     }
   }
@@ -314,7 +330,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
       acc[2] += yw * d;
     }
   }
-  gsum_lead<G, 4>(g, acc, w.red);
+  gsum_lead<G, 4>(g, acc, w.red, ns);
   // mixture scalars: sum Y/W, cp, d(cp)/dT, mean g/RT (keeps exp(g/RT - gshift) in range),
   // density, and exp(gshift - ln(p_atm / (R T))) for the equilibrium constants
   double S = 0.0, cp = 0.0, dcpdT = 0.0, gshift = 0.0, rho = 0.0, invrho = 0.0, ep1 = 0.0, iep1 = 0.0;
@@ -419,15 +435,23 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
       }
     }
     double invKc = 1.0;                                   // 1 / Kc
-    if (re.x >= 0) { invKc *= ieg[re.x]; dG -= w.gRT[re.x]; }
-    if (re.y >= 0) { invKc *= ieg[re.y]; dG -= w.gRT[re.y]; }
-    if (re.z >= 0) { invKc *= ieg[re.z]; dG -= w.gRT[re.z]; }
-    if (pr.x >= 0) { invKc *= eg[pr.x]; dG += w.gRT[pr.x]; }
-    if (pr.y >= 0) { invKc *= eg[pr.y]; dG += w.gRT[pr.y]; }
-    if (pr.z >= 0) { invKc *= eg[pr.z]; dG += w.gRT[pr.z]; }
+    if (re.x >= 0) invKc *= ieg[re.x];
+    if (re.y >= 0) invKc *= ieg[re.y];
+    if (re.z >= 0) invKc *= ieg[re.z];
+    if (pr.x >= 0) invKc *= eg[pr.x];
+    if (pr.y >= 0) invKc *= eg[pr.y];
+    if (pr.z >= 0) invKc *= eg[pr.z];
     for (int d = ri.y; d > 0; --d) invKc *= ep1;
     for (int d = ri.y; d < 0; ++d) invKc *= iep1;
-    if (!(invKc > 0.0 && invKc < 1.0e300)) invKc = exp(dG - (double)ri.y * lnPR);   // range fallback
+    if (!(invKc > 0.0 && invKc < 1.0e300)) {            // range fallback: exp of dG directly
+      if (re.x >= 0) dG -= w.gRT[re.x];
+      if (re.y >= 0) dG -= w.gRT[re.y];
+      if (re.z >= 0) dG -= w.gRT[re.z];
+      if (pr.x >= 0) dG += w.gRT[pr.x];
+      if (pr.y >= 0) dG += w.gRT[pr.y];
+      if (pr.z >= 0) dG += w.gRT[pr.z];
+      invKc = exp(dG - (double)ri.y * lnPR);
+    }
     const double kr = kf * invKc;
     const double fwd = kf * Pf, rev = kr * Pr;
     const double mult = (ri.x == 1) ? Mc : 1.0;
@@ -454,17 +478,40 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
   }
   g.sync();
 
-  // production rates and right-hand side (A4)
+  // production rates and right-hand side (A4).  A multi-warp group first sums balanced pieces
+  // of the production lists (similar loop lengths in every lane), then adds each species' pieces.
+  if (kMulti) {
+    for (int pc = g.tid; pc < m.npieces; pc += G) {
+      double a = 0.0, b = 0.0;
+      for (int e = m.pterm[pc]; e < m.pterm[pc + 1]; ++e) {
+        const int pk = m.wpk[e];
+        const double nu = m.cst[kC_NU + (pk & 15)];
+        const int j = pk >> 4;
+        a += nu * w.q[j];
+        if (jac) b += nu * w.dqdT[j];
+      }
+      w.wpart[pc] = a;
+      if (jac) w.dwpart[pc] = b;
+    }
+    g.sync();
+  }
   double r3[3] = {0.0, 0.0, 0.0};
   const double RT = RU * T;
   for (int k = g.tid; k < ns; k += G) {
     double wk = 0.0, dwk = 0.0;
-    for (int e = m.woff[k]; e < m.woff[k + 1]; ++e) {
-      const int pk = m.wpk[e];
-      const double nu = m.cst[kC_NU + (pk & 15)];
-      const int j = pk >> 4;
-      wk += nu * w.q[j];
-      if (jac) dwk += nu * w.dqdT[j];
+    if (kMulti) {
+      for (int pc = m.poff[k]; pc < m.poff[k + 1]; ++pc) {
+        wk += w.wpart[pc];
+        if (jac) dwk += w.dwpart[pc];
+      }
+    } else {
+      for (int e = m.woff[k]; e < m.woff[k + 1]; ++e) {
+        const int pk = m.wpk[e];
+        const double nu = m.cst[kC_NU + (pk & 15)];
+        const int j = pk >> 4;
+        wk += nu * w.q[j];
+        if (jac) dwk += nu * w.dqdT[j];
+      }
     }
     w.wdot[k] = wk;
     const double hk = RT * w.hRT[k];
@@ -478,12 +525,12 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
   }
   if (!jac) {
     double q1[1] = {r3[0]};
-    gsum_lead<G, 1>(g, q1, w.red);
+    gsum_lead<G, 1>(g, q1, w.red, ns);
     if (g.tid == 0) f[0] = -q1[0] / (rho * cp);
     g.sync();
     return;
   }
-  gsum_lead<G, 3>(g, r3, w.red);
+  gsum_lead<G, 3>(g, r3, w.red, ns);
   const double Q = r3[0];
   const double rcp = rho * cp;
   double ircp = 0.0;
@@ -523,7 +570,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
     for (int k = 0; k < ns; ++k) s += w.hRT[k] * Jm[(1 + k) * LD + 1 + mm];
     w.Hm[mm] = RT * s;
   }
-  gsum_lead<G, 1>(g, rh, w.red);
+  gsum_lead<G, 1>(g, rh, w.red, ns);
   double RhS = 0.0, cpS = 0.0, QoR2r = 0.0;
   if (lead) {
     const double Rh = rh[0];
@@ -661,7 +708,7 @@ struct Segment {
   long long chunk_begin;           // first queue entry of this segment
 };
 
-constexpr int kMaxSegs = 32;       // segments per launch (kernel-parameter space)
+constexpr int kMaxSegs = kMaxSegsPerLaunch;   // segments per launch (kernel-parameter space)
 
 struct AdvanceParams {
   MechLayout lay;
@@ -674,7 +721,14 @@ struct AdvanceParams {
   int max_steps;
   unsigned long long* counter;
   const unsigned int* ncells_dev;  // single segment: cell count read from device memory
+  unsigned long long budget_ns = 0;  // > 0: stop claiming chunks this long after the group started
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ void stage_mech(const unsigned char* src, unsigned char* dst, int bytes) {
   const int4* s = (const int4*)src;
@@ -731,7 +785,7 @@ __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& 
     const double r = w.u[5 * N + i] / sc;
     acc[0] += r * r;
   }
-  gsum_lead<G, 1>(g, acc, w.red);
+  gsum_lead<G, 1>(g, acc, w.red, N);
   double e = 0.0, f = 0.0;
   if (is_lead(g)) {
     e = sqrt(acc[0] / (double)N);
@@ -751,7 +805,7 @@ __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& 
   return true;
 }
 
-// Chunk bookkeeping of one group: the current chunk of up to CHUNK consecutive cells of one
+// Chunk bookkeeping of one group: the current chunk of up to chunk_cells(G) consecutive cells of one
 // segment, staged in shared memory, and the position of the cell being integrated.
 struct ChunkPos {
   const Segment* seg;
@@ -759,6 +813,7 @@ struct ChunkPos {
   int nloc, c;
   bool exhausted;
   long long total;      // queue entries (chunks) of the launch
+  unsigned long long t0;  // group start time (time-sliced launches)
 };
 
 __device__ __forceinline__ int64_t cell_of(const Segment* S, long long base, int c) {
@@ -776,6 +831,7 @@ __device__ __forceinline__ const Segment* segment_of(const AdvanceParams& P, lon
 template <int G>
 __device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
                           const AdvanceParams& P, ChunkPos& q, double* p) {
+  constexpr int CHUNK = chunk_cells(G);
   const int N = m.N;
   for (;;) {
     if (q.c + 1 < q.nloc) {
@@ -800,14 +856,18 @@ __device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
       g.sync();
     }
     if (q.exhausted) return false;
-    if (g.tid == 0) w.ctl[0] = atomicAdd(P.counter, 1ull);
+    // a time-sliced launch stops claiming once its budget is spent: the chunks claimed so far
+    // are exactly the prefix [0, counter) of the queue, and the next slice continues from there
+    if (g.tid == 0)
+      w.ctl[0] = (P.budget_ns > 0 && global_ns() - q.t0 > P.budget_ns) ? ~0ull : atomicAdd(P.counter, 1ull);
     g.sync();
-    const long long chunk = (long long)w.ctl[0];
+    const unsigned long long claimed = w.ctl[0];      // ~0 when the time budget is spent
     g.sync();
-    if (chunk >= q.total) {
+    if (claimed >= (unsigned long long)q.total) {
       q.exhausted = true;
       return false;
     }
+    const long long chunk = (long long)claimed;
     const Segment* S = segment_of(P, chunk);
     const long long ncs = P.ncells_dev ? min((long long)*P.ncells_dev, (long long)S->ncells)
                                        : (long long)S->ncells;
@@ -849,10 +909,11 @@ __global__ void __launch_bounds__(512) advance_kernel(const __grid_constant__ Ad
   for (int i = g.tid; i < N; i += G) w.y[i] = i == 0 ? 1000.0 : 1.0 / m.ns;
   g.sync();
 
+  constexpr int CHUNK = chunk_cells(G);
   long long total = P.total_chunks;
   if (P.ncells_dev)
     total = (min((long long)*P.ncells_dev, (long long)P.segs[0].ncells) + CHUNK - 1) / CHUNK;
-  ChunkPos q{&P.segs[0], 0, 0, 0, false, total};
+  ChunkPos q{&P.segs[0], 0, 0, 0, false, total, P.budget_ns > 0 ? global_ns() : 0ull};
   bool active = false;
   double dt = 1.0, rtol = 1e-6, atol = 1e-10;
   double p = 1.0e6, t = 0.0, h = dt, facmax = 6.0;
@@ -1007,7 +1068,7 @@ int pick_shape(const chem_mech_s* m, const chem_options* opt, LaunchShape* s) {
     return CHEM_EINVAL;
   }
   s->G = G;
-  s->ws = make_ws(m->ns, m->nr, G);
+  s->ws = make_ws(m->ns, m->nr, m->lay.npieces, G);
   int dev = 0;
   CHEM_CUDA_TRY(cudaGetDevice(&dev));
   int smem_max = 0;
@@ -1110,10 +1171,11 @@ int launch_advance(chem_mech_s* m, double* T, const double* p, double* Y, int64_
   P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
   P.segs[0] = Segment{T, p, Y, ld, ncells, idx, status, nsub, nrej, dt, rtol, atol, 0};
   P.nseg = 1;
-  P.total_chunks = (ncells + CHUNK - 1) / CHUNK;
+  P.total_chunks = (ncells + chunk_cells(s.G) - 1) / chunk_cells(s.G);
   P.max_steps = (opt && opt->max_steps > 0) ? opt->max_steps : 100000;
   P.counter = counter;
   P.ncells_dev = nullptr;
+  P.budget_ns = 0;
   rc = dispatch_adv(s, P, opt, stream);
   cudaError_t fe = cudaFreeAsync(counter, stream);
   if (rc) return rc;
@@ -1138,10 +1200,11 @@ int launch_advance_counted(chem_mech_s* m, double* T, const double* p, double* Y
   P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
   P.segs[0] = Segment{T, p, Y, ld, capacity, idx, nullptr, nullptr, nullptr, dt, rtol, atol, 0};
   P.nseg = 1;
-  P.total_chunks = (capacity + CHUNK - 1) / CHUNK;
+  P.total_chunks = (capacity + chunk_cells(s.G) - 1) / chunk_cells(s.G);
   P.max_steps = 100000;
   P.counter = counter;
   P.ncells_dev = count_dev;
+  P.budget_ns = 0;
   rc = dispatch_adv(s, P, nullptr, stream);
   cudaError_t fe = cudaFreeAsync(counter, stream);
   if (rc) return rc;
@@ -1173,13 +1236,14 @@ int launch_advance_batch(chem_mech_s* m, const chem_segment* segs, int nseg, cud
     for (int i = 0; i < cnt; ++i) {
       const chem_segment& a = segs[first + i];
       P.segs[i] = Segment{a.T, a.p, a.Y, a.ld, a.ncells, a.idx, a.status, a.nsub, a.nrej, a.dt, a.rtol, a.atol, total};
-      total += (a.ncells + CHUNK - 1) / CHUNK;
+      total += (a.ncells + chunk_cells(s.G) - 1) / chunk_cells(s.G);
     }
     if (total == 0) continue;
     P.nseg = cnt;
     P.total_chunks = total;
     P.max_steps = 100000;
     P.ncells_dev = nullptr;
+    P.budget_ns = 0;
     unsigned long long* counter = nullptr;
     CHEM_CUDA_TRY(cudaMallocAsync((void**)&counter, sizeof(unsigned long long), stream));
     CHEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream));
@@ -1190,6 +1254,41 @@ int launch_advance_batch(chem_mech_s* m, const chem_segment* segs, int nseg, cud
     CHEM_CUDA_TRY(fe);
   }
   return CHEM_OK;
+}
+
+// One time slice of a batched launch whose work-queue counter the caller owns (zeroed before the
+// first slice).  Groups stop claiming chunks budget_ns after they start; the chunks claimed so far
+// form the prefix [0, counter) of the queue, so re-issuing the same slice continues the work and
+// a segment is complete once the counter reaches seg_end[i] (its last chunk + 1, written here).
+// A slice issued after the counter reached the total returns at once.
+int launch_advance_slice(chem_mech_s* m, const chem_segment* segs, int nseg, unsigned long long budget_ns,
+                         unsigned long long* counter, long long* seg_end, cudaStream_t stream) {
+  if (!m || !segs || nseg < 1 || nseg > kMaxSegs || !counter) { set_error("bad slice arguments"); return CHEM_EINVAL; }
+  LaunchShape s;
+  int rc = pick_shape(m, nullptr, &s);
+  if (rc) return rc;
+  AdvanceParams P;
+  P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
+  long long total = 0;
+  for (int i = 0; i < nseg; ++i) {
+    const chem_segment& a = segs[i];
+    if (a.ncells < 0 || !(a.dt > 0.0) || !(a.rtol > 0.0) || !(a.atol > 0.0) || !std::isfinite(a.dt) ||
+        (a.ncells > 0 && (!a.T || !a.p || !a.Y)) || (!a.idx && a.ld < a.ncells)) {
+      set_error("segment %d: invalid arguments", i);
+      return CHEM_EINVAL;
+    }
+    P.segs[i] = Segment{a.T, a.p, a.Y, a.ld, a.ncells, a.idx, a.status, a.nsub, a.nrej, a.dt, a.rtol, a.atol, total};
+    total += (a.ncells + chunk_cells(s.G) - 1) / chunk_cells(s.G);
+    if (seg_end) seg_end[i] = total;
+  }
+  if (total == 0) return CHEM_OK;
+  P.nseg = nseg;
+  P.total_chunks = total;
+  P.max_steps = 100000;
+  P.counter = counter;
+  P.ncells_dev = nullptr;
+  P.budget_ns = budget_ns;
+  return dispatch_adv(s, P, nullptr, stream);
 }
 
 // FP64 FMA throughput probe: 8 independent dependency chains per thread
@@ -1272,10 +1371,11 @@ int launch_advance_noalloc(chem_mech_s* m, double* T, const double* p, double* Y
   P.lay = m->lay; P.ws = s.ws; P.jp = jac_args(m); P.blob = (const unsigned char*)m->d_blob;
   P.segs[0] = Segment{T, p, Y, ld, ncells, nullptr, status, nsub, nrej, dt, rtol, atol, 0};
   P.nseg = 1;
-  P.total_chunks = (ncells + CHUNK - 1) / CHUNK;
+  P.total_chunks = (ncells + chunk_cells(s.G) - 1) / chunk_cells(s.G);
   P.max_steps = 100000;
   P.counter = counter;
   P.ncells_dev = nullptr;
+  P.budget_ns = 0;
   return dispatch_adv(s, P, nullptr, stream);
 }
 

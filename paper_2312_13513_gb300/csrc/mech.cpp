@@ -6,6 +6,7 @@
 // constants.  This file precomputes everything that does not depend on the state (scaled
 // polynomial coefficients, Ta = Ea/Rc, ln A, sparse efficiency lists, species production lists)
 // into one blob that every CTA stages into shared memory once.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -129,10 +130,30 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   std::vector<int> woff(ns + 1, 0);
   for (int k = 0; k < ns; ++k) woff[k + 1] = woff[k] + (int)plist[k].size();
   const int nprod = woff[ns];
+  // Balanced pieces of the production lists for groups wider than a warp: each species' list
+  // is cut into pieces of at most plen terms, plen the smallest that gives at most kPieceTarget
+  // pieces, so that one pass of a 128-thread group covers them with similar loop lengths.
+  constexpr int kPieceTarget = 128;
+  int plen = 1;
+  auto count_pieces = [&](int len) {
+    int c = 0;
+    for (int k = 0; k < ns; ++k) c += std::max(1, ((int)plist[k].size() + len - 1) / len);
+    return c;
+  };
+  while (count_pieces(plen) > kPieceTarget && plen < std::max(1, nprod)) ++plen;
+  std::vector<int> pterm(1, 0), poff(ns + 1, 0);
+  for (int k = 0; k < ns; ++k) {
+    const int len = (int)plist[k].size();
+    const int np = std::max(1, (len + plen - 1) / plen);
+    for (int i = 0; i < np; ++i) pterm.push_back(woff[k] + std::min(len, (i + 1) * plen));
+    poff[k + 1] = poff[k] + np;
+  }
+  const int npieces = poff[ns];
   const int neff = (int)eff_idx.size();
 
   MechLayout L{};
   L.ns = ns; L.nr = nr; L.N = ns + 1; L.ntb = ntb; L.ntroe = ntroe; L.nprod = nprod;
+  L.npieces = npieces;
   Builder B;
   L.o_W = B.add(8 * ns);
   L.o_invW = B.add(8 * ns);
@@ -152,6 +173,8 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   L.o_wpk = B.add(4 * nprod);
   L.o_effoff = B.add(4 * (ntb + 1));
   L.o_woff = B.add(4 * (ns + 1));
+  L.o_pterm = B.add(4 * (npieces + 1));
+  L.o_poff = B.add(4 * (ns + 1));
   L.bytes = (int)B.buf.size();
 
   double* W = B.at<double>(L.o_W);
@@ -198,6 +221,8 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   }
   for (int i = 0; i <= ntb; ++i) B.at<int>(L.o_effoff)[i] = eff_off[i];
   for (int k = 0; k <= ns; ++k) B.at<int>(L.o_woff)[k] = woff[k];
+  for (int i = 0; i <= npieces; ++i) B.at<int>(L.o_pterm)[i] = pterm[i];
+  for (int k = 0; k <= ns; ++k) B.at<int>(L.o_poff)[k] = poff[k];
   for (int k = 0; k < ns; ++k)
     for (int i = 0; i < (int)plist[k].size(); ++i) {
       const int nuk = plist[k][i].second;
@@ -236,7 +261,14 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   std::vector<int16_t> rows, cols;
   std::vector<int> src;
   std::vector<double> coef;
-  for (auto& kv : ent) {
+  // entries with many terms first: threads take consecutive entries, so a warp's entries have
+  // similar term counts and its lanes stay busy for the same number of iterations
+  std::vector<const std::pair<const std::pair<int, int>, std::vector<std::pair<int, double>>>*> order;
+  for (auto& kv : ent) order.push_back(&kv);
+  std::stable_sort(order.begin(), order.end(),
+                   [](const auto* a, const auto* b) { return a->second.size() > b->second.size(); });
+  for (auto* kvp : order) {
+    const auto& kv = *kvp;
     rows.push_back((int16_t)kv.first.first);
     cols.push_back((int16_t)kv.first.second);
     for (auto& t : kv.second) { src.push_back(t.first); coef.push_back(t.second); }

@@ -7,13 +7,18 @@
 //   * admits queued requests in arrival order, skipping ahead to requests that fit, while the
 //     resident states plus the workspace of the requests in flight stay within the device-memory
 //     budget, and at most one request per state is in flight;
-//   * batches the admitted FP64 requests of each mechanism into one persistent integrator launch
-//     (chem_advance_batch: their cells share one work queue), surrogate requests into their own
-//     launches, each launch on the next free stream of a small pool so that launches overlap on
-//     the device;
-//   * retires launches when their CUDA event completes, records the latency from submission to
-//     completion and frees their budget, so requests arriving meanwhile are admitted as slots and
-//     memory free up (continuous batching).
+//   * batches the admitted FP64 requests of each mechanism into one job of the persistent
+//     integrator (their cells share one work queue), surrogate requests into their own launches,
+//     each on the next free stream of a small pool so that launches overlap on the device;
+//   * runs an FP64 job as time slices: every slice stops claiming cells after slice_ms, the
+//     server reads the queue counter back and re-issues the slice until the queue is drained.
+//     Cells are claimed in queue order, so the claimed part is a prefix of the queue and a request
+//     is complete as soon as the counter passes its last chunk.  Between slices the other streams'
+//     launches get the SMs: a small request is not stuck behind a persistent launch that would
+//     otherwise hold every SM for seconds;
+//   * retires requests when their launch or slice completes, records the latency from submission
+//     to completion and frees their budget, so requests arriving meanwhile are admitted as slots
+//     and memory free up (continuous batching).
 // chem_serve_poll never blocks; chem_serve_wait blocks at most the given timeout.
 #include <cuda_runtime.h>
 
@@ -62,6 +67,13 @@ struct Launch {
   int stream;
   std::vector<uint64_t> reqs;
   size_t bytes;
+  // FP64 job run as time slices: its segments, the queue end of each request's chunks, and how
+  // many of its requests (in queue order) have completed
+  bool sliced = false;
+  chem_mech_t mech = nullptr;
+  std::vector<chem_segment> segs;
+  std::vector<long long> seg_end;
+  size_t ndone = 0;
 };
 
 }  // namespace
@@ -85,8 +97,11 @@ struct chem_server_s {
   std::condition_variable cv_work, cv_done;
   std::thread th;
   bool stop = false;
-  int64_t n_launches = 0, n_batched = 0, n_done = 0, n_failed = 0, max_concurrent = 0;
+  int64_t n_launches = 0, n_batched = 0, n_done = 0, n_failed = 0, max_concurrent = 0, n_slices = 0;
   double idle_poll_us = 20.0;
+  unsigned long long slice_ns = 20000000ull;   // 0: FP64 jobs run unsliced
+  unsigned long long* d_counter = nullptr;     // one work-queue counter per stream (device)
+  unsigned long long* h_counter = nullptr;     // its read-back copy (pinned host memory)
 };
 
 namespace {
@@ -108,10 +123,41 @@ void server_loop(chem_server_s* S) {
       cudaError_t q = cudaEventQuery(L.ev);
       if (q == cudaErrorNotReady) { ++i; continue; }
       const Clock::time_point now = Clock::now();
-      for (uint64_t id : L.reqs) {
+      if (q == cudaSuccess && L.sliced) {
+        const long long total = L.seg_end.back();
+        const long long done = std::min<long long>((long long)S->h_counter[L.stream], total);
+        while (L.ndone < L.reqs.size() && L.seg_end[L.ndone] <= done) {
+          Req& r = S->reqs[L.reqs[L.ndone]];
+          r.status = Q_DONE;
+          r.t_done = now;
+          S->states[r.state].busy = false;
+          ++S->n_done;
+          ++L.ndone;
+          progressed = true;
+        }
+        if (done < total) {
+          // next slice of the same job, continuing the same queue
+          cudaStream_t strm = S->streams[L.stream];
+          int rc = chem::launch_advance_slice(L.mech, L.segs.data(), (int)L.segs.size(), S->slice_ns,
+                                              S->d_counter + L.stream, nullptr, strm);
+          if (rc == CHEM_OK &&
+              cudaMemcpyAsync(S->h_counter + L.stream, S->d_counter + L.stream, sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, strm) == cudaSuccess &&
+              cudaEventRecord(L.ev, strm) == cudaSuccess) {
+            ++S->n_slices;
+            ++i;
+            continue;
+          }
+          q = cudaErrorLaunchFailure;    // the job's remaining requests fail below
+        }
+      }
+      const std::string err = q == cudaErrorLaunchFailure && L.sliced ? std::string(chem_last_error())
+                                                                      : std::string(cudaGetErrorString(q));
+      for (size_t k = L.sliced ? L.ndone : 0; k < L.reqs.size(); ++k) {
+        const uint64_t id = L.reqs[k];
         Req& r = S->reqs[id];
         r.status = q == cudaSuccess ? Q_DONE : Q_FAILED;
-        if (q != cudaSuccess) r.error = cudaGetErrorString(q);
+        if (q != cudaSuccess) r.error = err;
         r.t_done = now;
         S->states[r.state].busy = false;
         if (r.status == Q_DONE) ++S->n_done; else ++S->n_failed;
@@ -152,7 +198,12 @@ void server_loop(chem_server_s* S) {
       S->pending.swap(keep);
       // build launches; each needs a free stream, the rest go back to the queue front
       std::vector<std::vector<uint64_t>> groups;
-      for (auto& kv : fp64) groups.push_back(kv.second);
+      for (auto& kv : fp64) {
+        // one job per mechanism holds at most kMaxSegsPerLaunch requests; the rest wait
+        std::vector<uint64_t>& v = kv.second;
+        for (size_t b = 0; b < v.size(); b += chem::kMaxSegsPerLaunch)
+          groups.push_back(std::vector<uint64_t>(v.begin() + b, v.begin() + std::min(v.size(), b + chem::kMaxSegsPerLaunch)));
+      }
       for (uint64_t id : sur) groups.push_back({id});
       std::vector<uint64_t> back;
       for (auto& grp : groups) {
@@ -168,17 +219,29 @@ void server_loop(chem_server_s* S) {
         cudaStream_t strm = S->streams[sidx];
         int rc = CHEM_OK;
         const Req& r0 = S->reqs[grp[0]];
+        Launch L;
         if (r0.route == CHEM_ROUTE_FP64) {
-          std::vector<chem_segment> segs;
           for (uint64_t id : grp) {
             const Req& r = S->reqs[id];
             const StateRec& st = S->states[r.state];
             chem_segment g{};
             g.T = st.T; g.p = st.p; g.Y = st.Y; g.ld = st.ld; g.ncells = st.ncells;
             g.dt = r.dt; g.rtol = r.rtol; g.atol = r.atol;
-            segs.push_back(g);
+            L.segs.push_back(g);
           }
-          rc = chem::launch_advance_batch(S->states[r0.state].mech, segs.data(), (int)segs.size(), strm);
+          L.sliced = true;
+          L.mech = S->states[r0.state].mech;
+          L.seg_end.assign(L.segs.size(), 0);
+          if (cudaMemsetAsync(S->d_counter + sidx, 0, sizeof(unsigned long long), strm) != cudaSuccess) {
+            rc = chem::cuda_fail(cudaGetLastError(), "cudaMemsetAsync(server counter)");
+          } else {
+            rc = chem::launch_advance_slice(L.mech, L.segs.data(), (int)L.segs.size(), S->slice_ns,
+                                            S->d_counter + sidx, L.seg_end.data(), strm);
+          }
+          if (rc == CHEM_OK &&
+              cudaMemcpyAsync(S->h_counter + sidx, S->d_counter + sidx, sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, strm) != cudaSuccess)
+            rc = chem::cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(server counter)");
         } else {
           const StateRec& st = S->states[r0.state];
           rc = chem_surrogate_advance(st.model, st.mech, st.T, st.p, st.Y, st.ld, r0.dt, st.ncells, r0.rtol,
@@ -198,7 +261,6 @@ void server_loop(chem_server_s* S) {
           S->cv_done.notify_all();
           continue;
         }
-        Launch L;
         L.stream = sidx;
         L.reqs = grp;
         L.bytes = bytes;
@@ -209,6 +271,7 @@ void server_loop(chem_server_s* S) {
         S->stream_busy[sidx] = true;
         S->launches.push_back(L);
         ++S->n_launches;
+        if (L.sliced) ++S->n_slices;
         S->n_batched += (int64_t)grp.size();
         S->max_concurrent = std::max<int64_t>(S->max_concurrent, (int64_t)S->launches.size());
       }
@@ -237,12 +300,25 @@ extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_optio
   S->budget = hbm_budget_bytes;
   const int ns = (opt && opt->n_streams > 0) ? opt->n_streams : 4;
   if (opt && opt->idle_poll_us > 0) S->idle_poll_us = opt->idle_poll_us;
+  if (opt && opt->slice_ms != 0.0)
+    S->slice_ns = opt->slice_ms < 0.0 ? 0ull : (unsigned long long)(opt->slice_ms * 1e6);
   if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; return cuda_fail(cudaGetLastError(), "cudaGetDevice"); }
+  cudaError_t ea = cudaMalloc((void**)&S->d_counter, ns * sizeof(unsigned long long));
+  cudaError_t eh = ea == cudaSuccess ? cudaHostAlloc((void**)&S->h_counter, ns * sizeof(unsigned long long),
+                                                     cudaHostAllocDefault)
+                                     : ea;
+  if (ea != cudaSuccess || eh != cudaSuccess) {
+    if (S->d_counter) cudaFree(S->d_counter);
+    delete S;
+    return cuda_fail(ea != cudaSuccess ? ea : eh, "server counters");
+  }
   for (int i = 0; i < ns; ++i) {
     cudaStream_t st;
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+      cudaFree(S->d_counter);
+      cudaFreeHost(S->h_counter);
       delete S;
       return cuda_fail(e, "cudaStreamCreate");
     }
@@ -332,11 +408,12 @@ extern "C" int chem_serve_wait(chem_server_t S, uint64_t req_id, double timeout_
   return CHEM_OK;
 }
 
-extern "C" int chem_serve_stats(chem_server_t S, int64_t* out /*[6]*/) {
+extern "C" int chem_serve_stats(chem_server_t S, int64_t* out /*[8]*/) {
   if (!S || !out) { set_error("bad arguments"); return CHEM_EINVAL; }
   std::lock_guard<std::mutex> lk(S->mu);
   out[0] = S->n_done; out[1] = S->n_failed; out[2] = S->n_launches; out[3] = S->n_batched;
   out[4] = S->max_concurrent; out[5] = (int64_t)(S->resident + S->inflight);
+  out[6] = S->n_slices; out[7] = 0;
   return CHEM_OK;
 }
 
@@ -356,6 +433,8 @@ extern "C" int chem_serve_destroy(chem_server_t S) {
   S->cv_work.notify_all();
   if (S->th.joinable()) S->th.join();
   for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+  cudaFree(S->d_counter);
+  cudaFreeHost(S->h_counter);
   delete S;
   return CHEM_OK;
 }

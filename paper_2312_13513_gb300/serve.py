@@ -26,9 +26,10 @@ def advance_batch(mech, segments, stream=None):
 
 
 class Server:
-    def __init__(self, budget_bytes, n_streams=4, idle_poll_us=20.0):
+    def __init__(self, budget_bytes, n_streams=4, idle_poll_us=20.0, slice_ms=0.0):
+        """slice_ms: FP64 time slice (0: library default, negative: unsliced jobs)."""
         h = ctypes.c_void_p()
-        opt = _lib.ServeOptions(n_streams, idle_poll_us)
+        opt = _lib.ServeOptions(n_streams, idle_poll_us, slice_ms)
         check(_lib.load().chem_serve_create(int(budget_bytes), ctypes.byref(opt), ctypes.byref(h)))
         self.handle = h
         self._keep = []
@@ -57,9 +58,10 @@ class Server:
         return check(_lib.load().chem_serve_wait(self.handle, req_id, float(timeout_s)))
 
     def stats(self):
-        out = (ctypes.c_int64 * 6)()
+        out = (ctypes.c_int64 * 8)()
         check(_lib.load().chem_serve_stats(self.handle, out))
-        keys = ("completed", "failed", "launches", "requests_launched", "max_concurrent", "bytes_in_use")
+        keys = ("completed", "failed", "launches", "requests_launched", "max_concurrent", "bytes_in_use",
+                "slices")
         return dict(zip(keys, list(out)))
 
     def close(self):

@@ -157,3 +157,44 @@ def test_failed_request_does_not_poison_others(h2):
     st = srv.stats()
     srv.close()
     assert st["failed"] == 1 and st["completed"] == 2
+
+
+def test_time_sliced_job_equals_single_launch(ch4):
+    """An FP64 job run as many short slices gives bitwise the result of one launch."""
+    dm = cg.Mechanism(ch4)
+    f = les_field(load_table("ch4_flamelet.npz"), n=6000, seed=31)
+    a = to_dev(f["T"], f["p"], f["Y"])
+    b = to_dev(f["T"], f["p"], f["Y"])
+    cg.advance(dm, b[0], b[1], b[2], 1e-6)
+    srv = serve.Server(8 << 30, slice_ms=2.0)
+    sid = srv.register(dm, *a)
+    srv.wait(srv.submit(sid, serve.ROUTE_FP64, 1e-6), 120.0)
+    st = srv.stats()
+    srv.close()
+    torch.cuda.synchronize()
+    assert st["slices"] > 1
+    assert torch.equal(a[0], b[0]) and torch.equal(a[2], b[2])
+
+
+def test_small_request_is_not_stuck_behind_a_long_fp64_job(h2, ch4):
+    """A long CH4 FP64 job runs in time slices; a small H2 surrogate request submitted after it
+    completes while the job is still running."""
+    dm_h2, dm_ch4 = cg.Mechanism(h2), cg.Mechanism(ch4)
+    f = les_field(load_table("ch4_flamelet.npz"), n=65536, seed=32)
+    big = to_dev(f["T"], f["p"], f["Y"])
+    small = to_dev(*_h2_state(20000, 33))
+    model = _identity_model(dm_h2, h2, *[x.cpu().numpy() for x in small])
+    srv = serve.Server(8 << 30, slice_ms=10.0)
+    s_big = srv.register(dm_ch4, *big)
+    s_small = srv.register(dm_h2, *small, model=model)
+    r_big = srv.submit(s_big, serve.ROUTE_FP64, 1e-6)
+    time.sleep(0.02)
+    r_small = srv.submit(s_small, serve.ROUTE_SURROGATE, 5e-7)
+    srv.wait(r_small, 60.0)
+    state_big, _ = srv.poll(r_big)
+    srv.wait(r_big, 120.0)
+    lat_small = srv.poll(r_small)[1]
+    lat_big = srv.poll(r_big)[1]
+    srv.close()
+    assert state_big in (serve.QUEUED, serve.RUNNING), "the long job finished before the small request"
+    assert lat_small < 0.5 * lat_big, (lat_small, lat_big)
