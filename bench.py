@@ -36,9 +36,10 @@ METRIC = "chem cell-updates/s, FP64 Rosenbrock vs BF16 MLP at stated error; p50/
 WORKLOAD = ("FP64 Rodas4 chemistry advance, 2^20 cells of a 128^3 quasi-DNS H2/air field "
             "(9 species, 25 reactions), dt=5e-7 s, rtol=1e-6, atol=1e-10")
 
-# DRAM traffic of one integrator launch from an ncu capture (profiles/), valid only for the
-# kernel source it was measured on.
-TRAFFIC = {"bytes_per_launch": None, "source_sha1": None}
+# DRAM traffic of one integrator launch from an ncu capture (profiles/integrator_h2_quasi_dns.md:
+# 8.01 MB for 65536 cells of the same field and launch shape, scaled by cells to 2^20), valid only
+# for the kernel source it was measured on.
+TRAFFIC = {"bytes_per_launch": 16 * (7475200 + 537344), "source_sha1": "7be44160ce2b9160ac848bf6689db2c4c7221dca"}
 
 
 def _sha1_of_kernel():
@@ -127,9 +128,16 @@ def cpu_baseline(field, mech, budget_s=12.0):
         om.advance(field["T"][s], field["p"][s], field["Y"][:, s], DT, RTOL, ATOL, nthreads=cores)
         done += s.size
     el = time.perf_counter() - t0
+    # single-thread rate on a small sample of the same cells
+    s1 = np.sort(order[:1024])
+    t1 = time.perf_counter()
+    om.advance(field["T"][s1], field["p"][s1], field["Y"][:, s1], DT, RTOL, ATOL, nthreads=1)
+    el1 = time.perf_counter() - t1
     return {"value": done / el, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} seeded-uniform cells of the same 2^20-cell field, {el:.1f} s, "
-                      f"OpenMP over cells on {cores} threads; rate extrapolates per cell"}
+                      f"OpenMP over cells on {cores} threads; rate extrapolates per cell",
+            "single_thread_value": s1.size / el1,
+            "single_thread_sample": f"{s1.size} cells of the same sample, 1 thread, {el1:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -312,6 +320,10 @@ def extra_surrogate(peaks, steps=3):
     qr = cg.heat_release(dm, T0, p, Y0, Yr, DT)
     qs = cg.heat_release(dm, T0, p, Y0, Ys, DT)
     err = float(((qs - qr).abs().sum() / qr.abs().sum()).item())
+    err_sum = float(((qs.sum() - qr.sum()).abs() / qr.sum().abs()).item())
+    big = qr.abs() > 1e-3 * qr.abs().max()
+    rel = ((qs - qr).abs() / qr.abs())[big]
+    p99_rel = float(torch.quantile(rel.float()[torch.randperm(rel.numel(), device=rel.device)[:1 << 24]], 0.99).item())
     flop = 2.0 * (11 * 512 + 3 * 512 * 512 + 512 * 9) * n
     tf = flop / (ms_fwd * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
@@ -320,6 +332,7 @@ def extra_surrogate(peaks, steps=3):
             "surrogate_ms": ms_sur, "surrogate_cell_updates_per_s": n / (ms_sur * 1e-3),
             "fp64_ms": ms_fp64, "fp64_cell_updates_per_s": n / (ms_fp64 * 1e-3),
             "speedup_vs_fp64": ms_fp64 / ms_sur, "hrr_l1_rel_error_vs_fp64": err,
+            "hrr_sum_rel_error_vs_fp64": err_sum, "hrr_p99_cell_rel_error_vs_fp64": p99_rel,
             "fallback_fraction": float((route == 1).float().mean().item()),
             "forward_kernel_ms": ms_fwd, "tensor_tflops": tf,
             "tensor_frac_of_sustained": tf / peak, "model_trained_in_this_run": trained_here}
@@ -352,17 +365,27 @@ def extra_serving(duration_s=10.0, seed=12349):
         Y = torch.tensor(np.ascontiguousarray(f["Y"][:, off:off + n]), device="cuda")
         route = serve.ROUTE_SURROGATE if (is_h2 and sur and model is not None) else serve.ROUTE_FP64
         sid = srv.register(dm_h2 if is_h2 else dm_ch4, T, p, Y, model=model if is_h2 else None)
+        label = ("h2" if is_h2 else "ch4") + ("_surrogate" if route == serve.ROUTE_SURROGATE else "_fp64")
         solvers.append({"state_id": sid, "route": route, "dt": DT if is_h2 else 1e-6, "cells": n,
-                        "mech": "h2" if is_h2 else "ch4"})
+                        "mech": "h2" if is_h2 else "ch4", "label": label})
     res = serve.run_closed_loop(srv, solvers, duration_s=duration_s, mean_gap_s=2e-3, seed=seed)
     st = srv.stats()
     srv.close()
     lat = np.array(res["latencies"]) * 1e3
+    labels = np.array(res["labels"])
+    by_class = {}
+    for c in sorted(set(labels.tolist())):
+        lc = lat[labels == c]
+        by_class[c] = {"requests": int(lc.size), "p50_ms": float(np.percentile(lc, 50)),
+                       "p99_ms": float(np.percentile(lc, 99)),
+                       "solvers": int(sum(1 for s_ in solvers if s_["label"] == c))}
     return {"workload": "64 closed-loop solvers, Exp(2 ms) gaps, 1e4-2e6 cells log-uniform, "
-                        "70/30 H2/CH4, routes 50/50 (H2 only), 150 GB budget, 10 s",
+                        "70/30 H2/CH4, routes 50/50 (H2 only), 150 GB budget, 10 s of submissions, "
+                        "FP64 jobs in 20 ms time slices",
             "requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "cell_updates_per_s": res["cells"] / res["wall_s"], "wall_s": res["wall_s"],
+            "by_class": by_class, "fp64_time_slices": st["slices"],
             "launches": st["launches"], "requests_per_launch": st["requests_launched"] / max(1, st["launches"]),
             "max_concurrent_launches": st["max_concurrent"], "failed": st["failed"],
             "cells_h2": int(sum(s["cells"] for s in solvers if s["mech"] == "h2")),

@@ -81,8 +81,8 @@ def run_closed_loop(server, solvers, duration_s=10.0, mean_gap_s=2e-3, seed=0, m
     previous result completes, for duration_s seconds or max_requests requests; requests still
     in flight at the end are waited for.
 
-    solvers: list of dicts(state_id, route, dt, cells).  Returns dict with per-request latencies
-    (s), cells advanced and the wall time of the run.
+    solvers: list of dicts(state_id, route, dt, cells[, label]).  Returns dict with per-request
+    latencies (s) and the label of each request's solver, cells advanced and the wall time.
     """
     import heapq
     import random
@@ -92,7 +92,7 @@ def run_closed_loop(server, solvers, duration_s=10.0, mean_gap_s=2e-3, seed=0, m
     due = [(t0 + rng.expovariate(1.0 / mean_gap_s), i) for i in range(len(solvers))]
     heapq.heapify(due)
     inflight = {}
-    lat, cells, submitted = [], 0, 0
+    lat, labels, cells, submitted = [], [], 0, 0
     end = t0 + duration_s
     while True:
         now = _time.perf_counter()
@@ -108,10 +108,11 @@ def run_closed_loop(server, solvers, duration_s=10.0, mean_gap_s=2e-3, seed=0, m
                 i = inflight.pop(rid)
                 if st == DONE:
                     lat.append(l)
+                    labels.append(solvers[i].get("label", ""))
                     cells += solvers[i]["cells"]
                 heapq.heappush(due, (_time.perf_counter() + rng.expovariate(1.0 / mean_gap_s), i))
         if (now >= end or submitted >= max_requests) and not inflight:
             break
         _time.sleep(1e-4)
     wall = _time.perf_counter() - t0
-    return {"latencies": lat, "cells": cells, "wall_s": wall, "submitted": submitted}
+    return {"latencies": lat, "labels": labels, "cells": cells, "wall_s": wall, "submitted": submitted}
