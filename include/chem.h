@@ -284,7 +284,8 @@ enum { CHEM_ROUTE_FP64 = 0, CHEM_ROUTE_SURROGATE = 1 };
 enum { CHEM_REQ_QUEUED = 0, CHEM_REQ_RUNNING = 1, CHEM_REQ_DONE = 2, CHEM_REQ_FAILED = 3 };
 
 typedef struct chem_serve_options {
-  int32_t n_streams;         /* concurrent launches (0 -> 4) */
+  int32_t n_streams;         /* concurrent FP64 jobs and, on as many high-priority streams,
+                                concurrent surrogate launches (0 -> 4 each) */
   double idle_poll_us;       /* polling interval while launches are in flight (0 -> 20 us) */
   double slice_ms;           /* FP64 time slice (0 -> 20 ms; negative: no slicing) */
 } chem_serve_options;

@@ -29,10 +29,11 @@
 
 namespace chem {
 
-// Cells claimed per work-queue access: eight consecutive cells (64-byte rows of the SoA state)
-// for sub-warp groups, one cell for groups of a warp or more, whose cells take milliseconds each
+// Cells claimed per work-queue access: four consecutive cells (one 32-byte sector per row of the
+// SoA state) for sub-warp groups, one cell for groups of a warp or more, whose cells take
+// milliseconds each
 // (a time-sliced launch then overruns its budget by at most one cell).
-__host__ __device__ constexpr int chunk_cells(int G) { return G >= 32 ? 1 : 8; }
+__host__ __device__ constexpr int chunk_cells(int G) { return G >= 32 ? 1 : 4; }
 
 // Rodas4 coefficients, transformed (u-variable) form:
 //   (I/(gamma h) - J) u_s = f(y + sum_j A[s][j] u_j) + sum_j (C[s][j]/h) u_j,
@@ -106,7 +107,7 @@ enum : int {
 struct WsLayout {
   int LD;                  // leading dimension of the N x N matrix (odd: no bank conflicts)
   int y, ynew, ys, fs, f0, u, M, invd, tmp;
-  int C, hRT, gRT, cpR, dcpR, wdot, dwdT, rk, Hm;
+  int C, hRT, gRT, cpR, wdot, dwdT, rk, Hm;
   int q, dqdT, dq, wpart, dwpart, red, sc, stage, ctl, perm;
   int total;               // doubles
 };
@@ -117,15 +118,18 @@ inline WsLayout make_ws(int ns, int nr, int npieces, int G) {
   w.LD = (N % 2 == 0) ? N + 1 : N;
   int o = 0;
   auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };   // keep 16-byte alignment
-  w.y = take(N); w.ynew = take(N); w.ys = take(N); w.fs = take(N); w.f0 = take(N);
-  w.u = take(6 * N); w.M = take(N * w.LD); w.invd = take(N); w.tmp = take(N);
-  w.C = take(ns); w.hRT = take(ns); w.gRT = take(ns); w.cpR = take(ns); w.dcpR = take(ns);
+  // ys (a stage argument) is dead while a stage's solve runs and after the last stage, so the
+  // solve's scratch and the new state share its storage
+  w.y = take(N); w.ys = take(N); w.ynew = w.ys; w.tmp = w.ys; w.fs = take(N); w.f0 = take(N);
+  w.u = take(6 * N); w.M = take(N * w.LD); w.invd = take(N);
+  w.C = take(ns); w.hRT = take(ns); w.gRT = take(ns); w.cpR = take(ns);
   w.wdot = take(ns); w.dwdT = take(ns); w.rk = take(ns); w.Hm = take(ns);
   w.q = take(nr); w.dqdT = take(nr); w.dq = take(7 * nr);
   // partial production sums of the balanced pieces (groups wider than a warp)
   w.wpart = take(G > 32 ? npieces : 0); w.dwpart = take(G > 32 ? npieces : 0);
-  w.red = take(8 * (G >= 32 ? G / 32 : 1) + 8);
-  w.sc = take(S_NSC);
+  // cross-warp reductions and shared scalars exist only for groups wider than a warp
+  w.red = take(G > 32 ? 8 * (G / 32) + 8 : 0);
+  w.sc = take(G > 32 ? S_NSC : 0);
   w.stage = take(chunk_cells(G) * (N + 1));
   w.ctl = take(2);
   w.perm = take((N + 1) / 2);      // ints
@@ -135,7 +139,7 @@ inline WsLayout make_ws(int ns, int nr, int npieces, int G) {
 
 struct WsPtr {
   double *y, *ynew, *ys, *fs, *f0, *u, *M, *invd, *tmp;
-  double *C, *hRT, *gRT, *cpR, *dcpR, *wdot, *dwdT, *rk, *Hm;
+  double *C, *hRT, *gRT, *cpR, *wdot, *dwdT, *rk, *Hm;
   double *q, *dqdT, *dq, *wpart, *dwpart, *red, *sc, *stage;
   unsigned long long* ctl;
   int* perm;
@@ -145,7 +149,7 @@ __device__ __forceinline__ WsPtr bind_ws(double* b, const WsLayout& w) {
   WsPtr p;
   p.y = b + w.y; p.ynew = b + w.ynew; p.ys = b + w.ys; p.fs = b + w.fs; p.f0 = b + w.f0;
   p.u = b + w.u; p.M = b + w.M; p.invd = b + w.invd; p.tmp = b + w.tmp;
-  p.C = b + w.C; p.hRT = b + w.hRT; p.gRT = b + w.gRT; p.cpR = b + w.cpR; p.dcpR = b + w.dcpR;
+  p.C = b + w.C; p.hRT = b + w.hRT; p.gRT = b + w.gRT; p.cpR = b + w.cpR;
   p.wdot = b + w.wdot; p.dwdT = b + w.dwdT; p.rk = b + w.rk; p.Hm = b + w.Hm;
   p.q = b + w.q; p.dqdT = b + w.dqdT; p.dq = b + w.dq; p.red = b + w.red; p.sc = b + w.sc;
   p.wpart = b + w.wpart; p.dwpart = b + w.dwpart;
@@ -326,7 +330,6 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
     if (jac) {
       // d(cp/R)/dT = a2 + 2 a3 T + 3 a4 T^2 + 4 a5 T^3
       const double d = cc[1] + T * (2.0 * cc[2] + T * (3.0 * cc[3] + T * (4.0 * cc[4])));
-      w.dcpR[k] = d;
       acc[2] += yw * d;
     }
   }

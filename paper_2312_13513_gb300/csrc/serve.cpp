@@ -85,8 +85,9 @@ extern "C" int chem_surrogate_advance(chem_model_t md, chem_mech_t mech, double*
 struct chem_server_s {
   size_t budget = 0, resident = 0, inflight = 0;
   int device = 0;
-  std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> streams;   // [0, n_fp64): FP64 jobs; the rest: surrogate launches
   std::vector<bool> stream_busy;
+  int n_fp64 = 4;
   std::map<int, StateRec> states;
   int next_state = 1;
   std::map<uint64_t, Req> reqs;
@@ -176,6 +177,7 @@ void server_loop(chem_server_s* S) {
     for (size_t k = 0; k < S->streams.size(); ++k)
       if (!S->stream_busy[k]) { free_stream = (int)k; break; }
     if (!S->stop && free_stream >= 0 && !S->pending.empty()) {
+      const size_t n_sur_streams = S->streams.size() - (size_t)S->n_fp64;
       // FP64 requests grouped by mechanism (one batched launch each) and surrogate requests
       std::map<chem_mech_t, std::vector<uint64_t>> fp64;
       std::vector<uint64_t> sur;
@@ -185,7 +187,7 @@ void server_loop(chem_server_s* S) {
         Req& r = S->reqs[id];
         StateRec& st = S->states[r.state];
         const bool take = !st.busy && r.bytes <= avail &&
-                          (r.route == CHEM_ROUTE_FP64 || sur.size() < S->streams.size());
+                          (r.route == CHEM_ROUTE_FP64 || sur.size() < n_sur_streams);
         if (take) {
           avail -= r.bytes;
           st.busy = true;
@@ -207,8 +209,12 @@ void server_loop(chem_server_s* S) {
       for (uint64_t id : sur) groups.push_back({id});
       std::vector<uint64_t> back;
       for (auto& grp : groups) {
+        // FP64 jobs on the low-priority streams, surrogate launches on the high-priority ones: when
+        // a slice's blocks retire, the block scheduler starts a waiting surrogate launch first
+        const bool is_fp64 = S->reqs[grp[0]].route == CHEM_ROUTE_FP64;
         int sidx = -1;
-        for (size_t k = 0; k < S->streams.size(); ++k)
+        const size_t k0 = is_fp64 ? 0 : (size_t)S->n_fp64, k1 = is_fp64 ? (size_t)S->n_fp64 : S->streams.size();
+        for (size_t k = k0; k < k1; ++k)
           if (!S->stream_busy[k]) { sidx = (int)k; break; }
         if (sidx < 0) {
           for (uint64_t id : grp) { S->states[S->reqs[id].state].busy = false; back.push_back(id); }
@@ -298,7 +304,11 @@ extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_optio
   *out = nullptr;
   chem_server_s* S = new chem_server_s();
   S->budget = hbm_budget_bytes;
-  const int ns = (opt && opt->n_streams > 0) ? opt->n_streams : 4;
+  const int nfp = (opt && opt->n_streams > 0) ? opt->n_streams : 4;
+  const int ns = 2 * nfp;          // nfp low-priority FP64 streams + nfp high-priority surrogate streams
+  S->n_fp64 = nfp;
+  int prio_low = 0, prio_high = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
   if (opt && opt->idle_poll_us > 0) S->idle_poll_us = opt->idle_poll_us;
   if (opt && opt->slice_ms != 0.0)
     S->slice_ns = opt->slice_ms < 0.0 ? 0ull : (unsigned long long)(opt->slice_ms * 1e6);
@@ -314,7 +324,7 @@ extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_optio
   }
   for (int i = 0; i < ns; ++i) {
     cudaStream_t st;
-    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i < nfp ? prio_low : prio_high);
     if (e != cudaSuccess) {
       for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
       cudaFree(S->d_counter);
