@@ -58,14 +58,18 @@ constexpr int kConsts = 18;
 
 // Jacobian-assembly program of d(wdot)/dC (global memory, read-only): entry e covers row
 // ent_row[e], column ent_col[e]; its value is sum over terms t in [ent_off[e], ent_off[e+1]) of
-// term_coef[t] * dq[term_src[t]], where dq holds per-reaction slot derivatives (6 per reaction:
-// 3 reactant, 3 product) followed by the per-reaction collision-partner factor X_j.
+// term_coef[t] * d_t.  Per reaction j the rate pass keeps three numbers: a_j = mult kf,
+// b_j = -mult kr and the collision-partner factor X_j.  term_src[t] = j << 3 | c: for c = 7,
+// d_t = X_j; for a reactant slot c < 3 (product slot c - 3), d_t = a_j (b_j) times the
+// concentrations of the other two species of that side, term_oth[t] = o1 | o2 << 16 (ns for an
+// empty slot, whose concentration reads as 1).
 struct JacProgram {
   int nent = 0, nterm = 0;
   int* ent_off = nullptr;       // [nent + 1]
   int16_t* ent_row = nullptr;   // [nent]
   int16_t* ent_col = nullptr;   // [nent]
   int* term_src = nullptr;      // [nterm]
+  int* term_oth = nullptr;      // [nterm]
   double* term_coef = nullptr;  // [nterm]
 };
 

@@ -122,9 +122,11 @@ inline WsLayout make_ws(int ns, int nr, int npieces, int G) {
   // solve's scratch and the new state share its storage
   w.y = take(N); w.ys = take(N); w.ynew = w.ys; w.tmp = w.ys; w.fs = take(N); w.f0 = take(N);
   w.u = take(6 * N); w.M = take(N * w.LD); w.invd = take(N);
-  w.C = take(ns); w.hRT = take(ns); w.gRT = take(ns); w.cpR = take(ns);
+  w.C = take(ns + 1); w.hRT = take(ns); w.gRT = take(ns); w.cpR = take(ns);
   w.wdot = take(ns); w.dwdT = take(ns); w.rk = take(ns); w.Hm = take(ns);
-  w.q = take(nr); w.dqdT = take(nr); w.dq = take(7 * nr);
+  // dq/dT per reaction is only needed inside a Jacobian evaluation, before the assembly writes the
+  // matrix buffer (whose previous content, the last LU, is dead by then): it borrows that buffer
+  w.q = take(nr); w.dqdT = nr <= N * w.LD ? w.M : take(nr); w.dq = take(3 * nr);
   // partial production sums of the balanced pieces (groups wider than a warp)
   w.wpart = take(G > 32 ? npieces : 0); w.dwpart = take(G > 32 ? npieces : 0);
   // cross-warp reductions and shared scalars exist only for groups wider than a warp
@@ -287,6 +289,7 @@ struct JacArgs {
   const int16_t* ent_row;
   const int16_t* ent_col;
   const int* term_src;
+  const int* term_oth;
   const double* term_coef;
 };
 
@@ -360,6 +363,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
   // becomes a product (w.rk / w.Hm are free until the Jacobian section)
   double* eg = w.rk;
   double* ieg = w.Hm;
+  if (g.tid == 0) w.C[ns] = 1.0;           // the concentration of an empty reaction slot
   for (int k = g.tid; k < ns; k += G) {
     w.C[k] = rho * y[1 + k] * m.invW[k];
     const double e = exp(w.gRT[k] - gshift);
@@ -468,15 +472,12 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
       if (pr.z >= 0) dH += w.hRT[pr.z];
       const double dlnKc = (dH - (double)ri.y) * invT;
       w.dqdT[j] = mult * (fwd * dlnkf - rev * (dlnkf - dlnKc));
-      double* dq = w.dq + 6 * j;
-      const double a = mult * kf, b = -mult * kr;
-      dq[0] = re.x >= 0 ? a * cr1 * cr2 : 0.0;
-      dq[1] = re.y >= 0 ? a * cr0 * cr2 : 0.0;
-      dq[2] = re.z >= 0 ? a * cr0 * cr1 : 0.0;
-      dq[3] = pr.x >= 0 ? b * cp1 * cp2 : 0.0;
-      dq[4] = pr.y >= 0 ? b * cp0 * cp2 : 0.0;
-      dq[5] = pr.z >= 0 ? b * cp0 * cp1 : 0.0;
-      w.dq[6 * nr + j] = (ri.x == 1) ? (fwd - rev) : (ri.x == 2 ? dkfdM * (Pf - Pr * invKc) : 0.0);
+      // slot derivatives dq/dC = a (b) times the other concentrations of the side, formed by
+      // the assembly program; the collision-partner factor X completes the reaction's share
+      double* dq = w.dq + 3 * j;
+      dq[0] = mult * kf;
+      dq[1] = -mult * kr;
+      dq[2] = (ri.x == 1) ? (fwd - rev) : (ri.x == 2 ? dkfdM * (Pf - Pr * invKc) : 0.0);
     }
   }
   g.sync();
@@ -547,7 +548,18 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
   for (int e = g.tid; e < jp.nent; e += G) {
     double s = 0.0;
     const int t1 = __ldg(jp.ent_off + e + 1);
-    for (int t = __ldg(jp.ent_off + e); t < t1; ++t) s += __ldg(jp.term_coef + t) * w.dq[__ldg(jp.term_src + t)];
+    for (int t = __ldg(jp.ent_off + e); t < t1; ++t) {
+      const int src = __ldg(jp.term_src + t);
+      const double* dq = w.dq + 3 * (src >> 3);
+      double d;
+      if ((src & 7) == 7) {
+        d = dq[2];
+      } else {
+        const int oth = __ldg(jp.term_oth + t);
+        d = dq[(src & 7) >= 3 ? 1 : 0] * w.C[oth & 0xffff] * w.C[oth >> 16];
+      }
+      s += __ldg(jp.term_coef + t) * d;
+    }
     Jm[(1 + __ldg(jp.ent_row + e)) * LD + 1 + __ldg(jp.ent_col + e)] = s;
   }
   if (kMulti && g.tid == 0) w.sc[S_IRCP] = ircp;
@@ -1146,6 +1158,7 @@ JacArgs jac_args(const chem_mech_s* m) {
   j.ent_row = m->jac.ent_row;
   j.ent_col = m->jac.ent_col;
   j.term_src = m->jac.term_src;
+  j.term_oth = m->jac.term_oth;
   j.term_coef = m->jac.term_coef;
   return j;
 }

@@ -238,20 +238,26 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   cst[kC_INVNS] = 1.0 / ns;
   m->lay = L;
 
-  // Jacobian-assembly program for d(wdot_k)/dC_m
-  std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> ent;
+  // Jacobian-assembly program for d(wdot_k)/dC_m; a term is (src, oth, coef)
+  struct Term { int src, oth; double coef; };
+  std::map<std::pair<int, int>, std::vector<Term>> ent;
   for (int j = 0; j < nr; ++j) {
     for (int k = 0; k < ns; ++k) {
       if (nu[j][k] == 0) continue;
       for (int s = 0; s < 6; ++s) {
-        int sp = s < 3 ? d->reac[3 * j + s] : d->prod[3 * j + s - 3];
+        const int* side = s < 3 ? d->reac + 3 * j : d->prod + 3 * j;
+        const int sl = s % 3;
+        const int sp = side[sl];
         if (sp < 0) continue;
-        ent[{k, sp}].push_back({j * 6 + s, (double)nu[j][k]});
+        // the other two slots of the same side, in slot order
+        const int a1 = sl == 0 ? 1 : 0, a2 = sl == 2 ? 1 : 2;
+        const int o1 = side[a1] >= 0 ? side[a1] : ns, o2 = side[a2] >= 0 ? side[a2] : ns;
+        ent[{k, sp}].push_back({(j << 3) | s, o1 | (o2 << 16), (double)nu[j][k]});
       }
       if (d->rtype[j] != 0)
         for (int mm = 0; mm < ns; ++mm) {
           double e = d->eff[(size_t)j * ns + mm];
-          if (e != 0.0) ent[{k, mm}].push_back({6 * nr + j, nu[j][k] * e});
+          if (e != 0.0) ent[{k, mm}].push_back({(j << 3) | 7, 0, nu[j][k] * e});
         }
     }
   }
@@ -259,11 +265,11 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   P.nent = (int)ent.size();
   std::vector<int> off(1, 0);
   std::vector<int16_t> rows, cols;
-  std::vector<int> src;
+  std::vector<int> src, oth;
   std::vector<double> coef;
   // entries with many terms first: threads take consecutive entries, so a warp's entries have
   // similar term counts and its lanes stay busy for the same number of iterations
-  std::vector<const std::pair<const std::pair<int, int>, std::vector<std::pair<int, double>>>*> order;
+  std::vector<const std::pair<const std::pair<int, int>, std::vector<Term>>*> order;
   for (auto& kv : ent) order.push_back(&kv);
   std::stable_sort(order.begin(), order.end(),
                    [](const auto* a, const auto* b) { return a->second.size() > b->second.size(); });
@@ -271,7 +277,7 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
     const auto& kv = *kvp;
     rows.push_back((int16_t)kv.first.first);
     cols.push_back((int16_t)kv.first.second);
-    for (auto& t : kv.second) { src.push_back(t.first); coef.push_back(t.second); }
+    for (auto& t : kv.second) { src.push_back(t.src); oth.push_back(t.oth); coef.push_back(t.coef); }
     off.push_back((int)src.size());
   }
   P.nterm = (int)src.size();
@@ -283,7 +289,8 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   size_t o_row = align16((int)(o_off + 4 * (P.nent + 1)));
   size_t o_col = o_row + align16(2 * P.nent);
   size_t o_src = o_col + align16(2 * P.nent);
-  size_t o_coef = o_src + align16(4 * P.nterm);
+  size_t o_oth = o_src + align16(4 * P.nterm);
+  size_t o_coef = o_oth + align16(4 * P.nterm);
   size_t tot = o_coef + 8 * (size_t)P.nterm + 16;
   std::vector<unsigned char> jb(tot, 0);
   memcpy(jb.data() + o_off, off.data(), 4 * off.size());
@@ -293,6 +300,7 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   }
   if (P.nterm) {
     memcpy(jb.data() + o_src, src.data(), 4 * src.size());
+    memcpy(jb.data() + o_oth, oth.data(), 4 * oth.size());
     memcpy(jb.data() + o_coef, coef.data(), 8 * coef.size());
   }
   CHEM_CUDA_TRY(cudaMalloc(&m->d_jac, tot));
@@ -302,6 +310,7 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   P.ent_row = (int16_t*)(base + o_row);
   P.ent_col = (int16_t*)(base + o_col);
   P.term_src = (int*)(base + o_src);
+  P.term_oth = (int*)(base + o_oth);
   P.term_coef = (double*)(base + o_coef);
   return CHEM_OK;
 }
