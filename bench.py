@@ -338,6 +338,49 @@ def extra_surrogate(peaks, steps=3):
             "tensor_frac_of_sustained": tf / peak, "model_trained_in_this_run": trained_here}
 
 
+def extra_graph(n=4096, reps=20):
+    """A small chemistry step (n quasi-DNS H2 cells) issued directly and as a captured CUDA-graph
+    replay: per-step time of each (the launch and allocation overhead the graph removes)."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from synth.mechanism import h2_mechanism
+    dm = cg.Mechanism(h2_mechanism())
+    f = make_field(0, n)
+    T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+    Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+    T, Y = T0.clone(), Y0.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        cg.advance(dm, T, p, Y, DT, RTOL, ATOL, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        cg.advance(dm, T, p, Y, DT, RTOL, ATOL, stream=s)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        out = []
+        for _ in range(reps):
+            T.copy_(T0); Y.copy_(Y0)
+            torch.cuda.synchronize()
+            a.record(s); fn(); b.record(s)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return float(np.median(out))
+
+    def replay():
+        with torch.cuda.stream(s):        # a graph replays on the current stream
+            g.replay()
+
+    ms_direct = timed(lambda: cg.advance(dm, T, p, Y, DT, RTOL, ATOL, stream=s))
+    ms_graph = timed(replay)
+    return {"workload": f"FP64 integrator step on {n} quasi-DNS H2 cells: direct call vs captured "
+                        f"CUDA-graph replay, median of {reps}",
+            "direct_ms": ms_direct, "graph_ms": ms_graph}
+
+
 def extra_serving(duration_s=10.0, seed=12349):
     """Config 4: 64 closed-loop solvers (Exp(2 ms) think time), 70 % H2 / 30 % CH4, routes 50/50
     (CH4 solvers use the FP64 route: no CH4 surrogate), 1e4-2e6 cells log-uniform."""
@@ -547,6 +590,7 @@ def main():
         extras = {}
         for name, fn in (("ch4_les", lambda: extra_ch4(fp64_peak)),
                          ("surrogate", lambda: extra_surrogate(_peaks())),
+                         ("graph_small_step", extra_graph),
                          ("serving", extra_serving)):
             try:
                 extras[name] = fn()

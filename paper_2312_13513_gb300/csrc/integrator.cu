@@ -120,13 +120,18 @@ inline WsLayout make_ws(int ns, int nr, int npieces, int G) {
   auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };   // keep 16-byte alignment
   // ys (a stage argument) is dead while a stage's solve runs and after the last stage, so the
   // solve's scratch and the new state share its storage
-  w.y = take(N); w.ys = take(N); w.ynew = w.ys; w.tmp = w.ys; w.fs = take(N); w.f0 = take(N);
+  w.y = take(N); w.f0 = take(N); w.ys = take(N); w.ynew = w.ys; w.tmp = w.ys; w.fs = take(N);
   w.u = take(6 * N); w.M = take(N * w.LD); w.invd = take(N);
   w.C = take(ns + 1); w.hRT = take(ns); w.gRT = take(ns); w.cpR = take(ns);
   w.wdot = take(ns); w.dwdT = take(ns); w.rk = take(ns); w.Hm = take(ns);
   // dq/dT per reaction is only needed inside a Jacobian evaluation, before the assembly writes the
   // matrix buffer (whose previous content, the last LU, is dead by then): it borrows that buffer
-  w.q = take(nr); w.dqdT = nr <= N * w.LD ? w.M : take(nr); w.dq = take(3 * nr);
+  w.q = take(nr); w.dqdT = nr <= N * w.LD ? w.M : take(nr);
+  // the per-reaction derivative numbers live from the rate pass to the assembly of one Jacobian
+  // evaluation, at the start of an attempt, when the stage buffers ys, fs and u (contiguous
+  // above) are dead: small mechanisms keep them there
+  const int stage_span = w.M - w.ys;
+  w.dq = 3 * nr <= stage_span ? w.ys : take(3 * nr);
   // partial production sums of the balanced pieces (groups wider than a warp)
   w.wpart = take(G > 32 ? npieces : 0); w.dwpart = take(G > 32 ? npieces : 0);
   // cross-warp reductions and shared scalars exist only for groups wider than a warp
