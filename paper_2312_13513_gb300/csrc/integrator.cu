@@ -29,11 +29,12 @@
 
 namespace chem {
 
-// Cells claimed per work-queue access: four consecutive cells (one 32-byte sector per row of the
-// SoA state) for sub-warp groups, one cell for groups of a warp or more, whose cells take
-// milliseconds each
+// Cells claimed per work-queue access: two consecutive cells for sub-warp groups (16 bytes per
+// row of the SoA state: the state traffic is far below HBM bandwidth, shared memory per cell is
+// what limits residency), one cell for groups of a warp or more, whose cells take milliseconds
+// each
 // (a time-sliced launch then overruns its budget by at most one cell).
-__host__ __device__ constexpr int chunk_cells(int G) { return G >= 32 ? 1 : 4; }
+__host__ __device__ constexpr int chunk_cells(int G) { return G >= 32 ? 1 : 2; }
 
 // Rodas4 coefficients, transformed (u-variable) form:
 //   (I/(gamma h) - J) u_s = f(y + sum_j A[s][j] u_j) + sum_j (C[s][j]/h) u_j,
@@ -105,7 +106,7 @@ enum : int {
 // assembled (negated) straight into the iteration-matrix buffer M and re-evaluated at every
 // attempt, so a group holds one N x N matrix.
 struct WsLayout {
-  int LD;                  // leading dimension of the N x N matrix (odd: no bank conflicts)
+  int LD;                  // leading dimension of the N x N matrix
   int y, ynew, ys, fs, f0, u, M, invd, tmp;
   int C, hRT, gRT, cpR, wdot, dwdT, rk, Hm;
   int q, dqdT, dq, wpart, dwpart, red, sc, stage, ctl, perm;
@@ -115,7 +116,9 @@ struct WsLayout {
 inline WsLayout make_ws(int ns, int nr, int npieces, int G) {
   WsLayout w{};
   const int N = ns + 1;
-  w.LD = (N % 2 == 0) ? N + 1 : N;
+  // a group wider than a warp reads matrix columns across rows: an odd leading dimension keeps
+  // those rows in different banks; sub-warp groups have at most 4 rows in flight and no padding
+  w.LD = (G > 32 && N % 2 == 0) ? N + 1 : N;
   int o = 0;
   auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };   // keep 16-byte alignment
   // ys (a stage argument) is dead while a stage's solve runs and after the last stage, so the
