@@ -9,16 +9,18 @@
 // W_lo x_hi (the W_lo x_lo term is below FP32 accumulation noise).  Reaction rates depend
 // exponentially on T, and a plain BF16 T feature (8-bit mantissa) is off by several kelvin.
 //
-// surrogate_forward_kernel (persistent, one CTA per SM, 6 warps):
-//   warps 0-3  per 128-cell tile: build the input tile (FP64 state -> features -> BF16, written
-//              straight into shared memory in the 128-byte swizzled K-major layout the MMA reads),
-//              then after every layer read the FP32 accumulator from TMEM (tcgen05.ld), add the
-//              bias, apply GELU, round to BF16 and write the next layer's input tile in place;
-//              after the last layer apply the inverse transform (de-normalise, add to BC(Y0),
-//              invert Box-Cox) and write Y' (FP32).  The trust-region test (training box) is
-//              done on the features.
-//   warp 4     one lane streams weight tiles (256 x 64 BF16, 32 KB) with TMA into a 3-stage ring.
-//   warp 5     one lane issues tcgen05.mma (M = 128, N = 256 or 16, K = 16) into 512 TMEM columns.
+// surrogate_forward_kernel (persistent, one CTA per SM, 10 warps):
+//   warps 0-7  epilogue: after every hidden layer read the FP32 accumulator from TMEM
+//              (tcgen05.ld), add the bias, apply GELU, round to BF16 and write the next layer's
+//              input tile in place (128-byte swizzled K-major layout).  Warp w reads TMEM lanes
+//              32 (w % 4) .. + 31 (its cells) and columns 256 (w / 4) .. + 255, so two warps per
+//              SM sub-partition share a layer's 512 columns.
+//              Warps 0-3 also build the input tile (FP64 state -> features -> BF16) and, after
+//              the last layer, apply the inverse transform (de-normalise, add to BC(Y0), invert
+//              Box-Cox) and write Y' (FP32).  The trust-region test (training box) is done on
+//              the features.
+//   warp 8     one lane streams weight tiles (256 x 64 BF16, 32 KB) with TMA into a 3-stage ring.
+//   warp 9     one lane issues tcgen05.mma (M = 128, N = 256 or 16, K = 16) into 512 TMEM columns.
 // surrogate_post_kernel (FP64, one thread per cell): element-conservation projection, clip,
 //   temperature from enthalpy by Newton (the paper's Thermo class, §3.1), acceptance tests, and
 //   compaction of rejected cells into a fallback list that the FP64 integrator then advances
@@ -83,7 +85,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // layer 4: 8 K-chunks of W5 (16 rows)
 constexpr int CHUNKS_PER_TILE = 2 + 3 * 16 + 8;
 
-__global__ void __launch_bounds__(192, 1)
+constexpr int kEpiWarps = 8;
+constexpr int kFwdThreads = 32 * (kEpiWarps + 2);
+constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+// CTAs of a cluster work on different tiles but walk the same weight sequence: each loads half of
+// every weight stage with a TMA multicast into both, so each SM pulls half the weight bytes from L2
+constexpr int kCluster = 2;
+constexpr uint16_t kClusterMask = (1u << kCluster) - 1;
+constexpr int WHALF_BYTES = WSTAGE_BYTES / kCluster;
+
+__global__ void __launch_bounds__(kFwdThreads, 1)
     surrogate_forward_kernel(const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
                              const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4,
                              const __grid_constant__ CUtensorMap tW5, const SurParams P) {
@@ -99,50 +110,60 @@ __global__ void __launch_bounds__(192, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ntiles = (P.ncells + TM - 1) / TM;
+  // every CTA makes the same number of rounds (a CTA past the last tile runs a masked dummy tile)
+  // so that the two CTAs of a cluster consume the same weight stages
+  const long long rounds = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t crank = cluster_ctarank();
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < WSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    // a stage is free again once the MMAs of both CTAs of the cluster have read it
+    for (int s = 0; s < WSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], kCluster); }
     mbar_init(acc_done, 1);
-    mbar_init(act_ready, 128);
+    mbar_init(act_ready, 32 * kEpiWarps);
     fence_barrier_init();
   }
-  if (warp == 4) tmem_alloc(tmem_slot, 512);
+  if (warp == kTmaWarp) tmem_alloc(tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
+  // the partner CTA's multicast loads and commits target our barriers: initialised cluster-wide first
+  cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == kTmaWarp) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       prefetch_tmap(&tW1); prefetch_tmap(&tW2); prefetch_tmap(&tW3); prefetch_tmap(&tW4); prefetch_tmap(&tW5);
       long long it = 0;
       bool ok = true;
-      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (long long rd = 0; rd < rounds && ok; ++rd) {
         for (int c = 0; c < CHUNKS_PER_TILE; ++c, ++it) {
           const int s = (int)(it % WSTAGES);
           if (!mbar_wait(&empty[s], (uint32_t)((it / WSTAGES) & 1) ^ 1u, P.err)) { ok = false; break; }
-          unsigned char* dst = wst + s * WSTAGE_BYTES;
+          // this CTA loads rows [128 crank, 128 crank + 128) of the 256-row stage into both CTAs;
+          // the stage's full barrier expects both halves
+          unsigned char* dst = wst + s * WSTAGE_BYTES + crank * WHALF_BYTES;
           if (c < 2) {
             mbar_arrive_expect_tx(&full[s], WSTAGE_BYTES);
-            tma_load_2d(dst, &tW1, &full[s], 0, c * 256);
+            tma_load_2d_multicast(dst, &tW1, &full[s], 0, c * 256 + (int)crank * 128, kClusterMask);
           } else if (c < 2 + 48) {
             const int l = (c - 2) / 16, r = (c - 2) % 16, kc = r / 2, nh = r % 2;
             const CUtensorMap* tm = l == 0 ? &tW2 : (l == 1 ? &tW3 : &tW4);
             mbar_arrive_expect_tx(&full[s], WSTAGE_BYTES);
-            tma_load_2d(dst, tm, &full[s], kc * 64, nh * 256);
+            tma_load_2d_multicast(dst, tm, &full[s], kc * 64, nh * 256 + (int)crank * 128, kClusterMask);
           } else {
+            // the 16-row output weights: the first CTA of the cluster loads them for both
             const int kc = c - 50;
             mbar_arrive_expect_tx(&full[s], NOUT * 128);
-            tma_load_2d(dst, &tW5, &full[s], kc * 64, 0);
+            if (crank == 0) tma_load_2d_multicast(wst + s * WSTAGE_BYTES, &tW5, &full[s], kc * 64, 0, kClusterMask);
           }
         }
       }
-      // drain loads still in flight
+      // drain: every issued stage has been read by both CTAs' MMAs (their commits have landed here)
       const long long first = it > WSTAGES ? it - WSTAGES : 0;
-      for (long long k = first; k < it; ++k) mbar_wait(&full[k % WSTAGES], (uint32_t)((k / WSTAGES) & 1), P.err);
+      for (long long k = first; k < it; ++k) mbar_wait(&empty[k % WSTAGES], (uint32_t)((k / WSTAGES) & 1), P.err);
     }
-  } else if (warp == 5) {
+  } else if (warp == kMmaWarp) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       constexpr uint32_t id256 = idesc_bf16_f32(128, 256);
@@ -150,7 +171,7 @@ __global__ void __launch_bounds__(192, 1)
       long long it = 0, nready = 0;
       bool ok = true;
       const uint32_t abase = smem_addr(act);
-      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (long long rd = 0; rd < rounds && ok; ++rd) {
         int c = 0;
         for (int l = 0; l < 5 && ok; ++l) {
           if (!mbar_wait(act_ready, (uint32_t)(nready & 1), P.err)) { ok = false; break; }
@@ -172,81 +193,102 @@ __global__ void __launch_bounds__(192, 1)
             for (int kk = 0; kk < 4; ++kk)
               mma_bf16(d, sdesc_k128(abase + kc * ACT_CHUNK + kk * 32), sdesc_k128(bbase + kk * 32), idesc,
                        (kc > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(&empty[s]);
+            mma_commit_multicast(&empty[s], kClusterMask);     // frees the stage in both CTAs
           }
           if (ok) mma_commit(acc_done);
         }
       }
     }
   } else {
-    // ---------------- feature / epilogue warps 0-3: row r = TMEM lane r ----------------
-    const int r = warp * 32 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    unsigned char* arow = act + r * 128;        // row r inside each 16 KB chunk
+    // ---------------- epilogue warps 0-7; warps 0-3 also do features and output ----------------
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;                 // cell row of the tile = TMEM lane
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+    unsigned char* arow = act + r * 128;               // row r inside each 16 KB chunk
+    const bool io = half == 0;
     long long nacc = 0;
     bool ok = true;
     float bc0[MAXNS];
-    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (long long rd = 0; rd < rounds && ok; ++rd) {
+      const long long tile = blockIdx.x + rd * gridDim.x;
       const long long cell = tile * TM + r;
       const bool valid = cell < P.ncells;
-      // ---- input features ----
-      float x[KIN];
+      if (io) {
+        // ---- input features ----
+        float x[KIN];
 #pragma unroll
-      for (int i = 0; i < KIN; ++i) x[i] = 0.0f;
-      if (valid) {
-        bool outside = false;
-        float f[2 + MAXNS];
-        f[0] = (float)P.T[cell];
-        f[1] = (float)log(P.p[cell]);
-        for (int k = 0; k < P.ns; ++k) {
-          const double yk = P.Y[(int64_t)k * P.ld + cell];
-          const float yf = fmaxf((float)yk, 0.0f);
-          bc0[k] = (powf(yf, BC_LAMBDA) - 1.0f) / BC_LAMBDA;
-          f[2 + k] = bc0[k];
-        }
-        for (int i = 0; i < P.nin; ++i) {
-          if (!(f[i] >= P.lo[i] && f[i] <= P.hi[i])) outside = true;
-          const float v = (f[i] - P.xmu[i]) / P.xsd[i];
-          const float vh = __bfloat162float(__float2bfloat16_rn(v));
-          x[i] = vh;                      // [x_hi | x_lo | x_hi]
-          x[P.nin + i] = v - vh;
-          x[2 * P.nin + i] = vh;
-        }
-        P.outbox[cell] = outside ? 1 : 0;
-      }
+        for (int i = 0; i < KIN; ++i) x[i] = 0.0f;
+        if (valid) {
+          bool outside = false;
+          float f[2 + MAXNS];
+          // all loads of the cell's state first, so their latencies overlap
+          double yv[MAXNS];
+          const double tv = P.T[cell], pv = P.p[cell];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        uint4 v;
-        v.x = pack_bf16(x[8 * u + 0], x[8 * u + 1]);
-        v.y = pack_bf16(x[8 * u + 2], x[8 * u + 3]);
-        v.z = pack_bf16(x[8 * u + 4], x[8 * u + 5]);
-        v.w = pack_bf16(x[8 * u + 6], x[8 * u + 7]);
-        *reinterpret_cast<uint4*>(arow + ((u ^ (r & 7)) << 4)) = v;
+          for (int k = 0; k < MAXNS; ++k)
+            if (k < P.ns) yv[k] = P.Y[(int64_t)k * P.ld + cell];
+          f[0] = (float)tv;
+          f[1] = logf((float)pv);
+#pragma unroll
+          for (int k = 0; k < MAXNS; ++k) {
+            if (k < P.ns) {
+              const float yf = fmaxf((float)yv[k], 0.0f);
+              bc0[k] = (powf(yf, BC_LAMBDA) - 1.0f) / BC_LAMBDA;
+              f[2 + k] = bc0[k];
+            }
+          }
+          for (int i = 0; i < P.nin; ++i) {
+            if (!(f[i] >= P.lo[i] && f[i] <= P.hi[i])) outside = true;
+            const float v = (f[i] - P.xmu[i]) / P.xsd[i];
+            const float vh = __bfloat162float(__float2bfloat16_rn(v));
+            x[i] = vh;                      // [x_hi | x_lo | x_hi]
+            x[P.nin + i] = v - vh;
+            x[2 * P.nin + i] = vh;
+          }
+          P.outbox[cell] = outside ? 1 : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          uint4 v;
+          v.x = pack_bf16(x[8 * u + 0], x[8 * u + 1]);
+          v.y = pack_bf16(x[8 * u + 2], x[8 * u + 3]);
+          v.z = pack_bf16(x[8 * u + 4], x[8 * u + 5]);
+          v.w = pack_bf16(x[8 * u + 6], x[8 * u + 7]);
+          *reinterpret_cast<uint4*>(arow + ((u ^ (r & 7)) << 4)) = v;
+        }
       }
       fence_async_smem();
       mbar_arrive(act_ready);
-      // ---- hidden layers ----
+      // ---- hidden layers: this warp's half of the 512 columns ----
       for (int l = 0; l < 4; ++l) {
         // tcgen05.ld is warp-collective: the warp agrees on the wait's outcome
         if (!__all_sync(0xffffffffu, mbar_wait(acc_done, (uint32_t)(nacc & 1), P.err))) { ok = false; break; }
         ++nacc;
         tc_fence_after();
         const float* bias = P.bias[l];
-        for (int cc = 0; cc < HID / 32; ++cc) {
-          uint32_t a[32];
-          tmem_ld32(trow + cc * 32, a);
+        // 64 columns per step: two TMEM loads in flight behind one wait; the 64 biases are read
+        // once per warp (one per lane) and broadcast by shuffles
+        for (int cc = half * (HID / 64); cc < (half + 1) * (HID / 64); cc += 2) {
+          uint32_t a[2][32];
+          tmem_ld32(trow + cc * 32, a[0]);
+          tmem_ld32(trow + (cc + 1) * 32, a[1]);
+          const float bl[2] = {__ldg(bias + cc * 32 + lane), __ldg(bias + (cc + 1) * 32 + lane)};
           tmem_ld_wait();
+          // columns cc*32 .. cc*32+63 form one 128-byte K chunk of the next layer's input
           unsigned char* chunk = arow + (cc >> 1) * ACT_CHUNK;
-          const int u0 = (cc & 1) * 4;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            float v[8];
+          for (int h = 0; h < 2; ++h) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = gelu_f(__uint_as_float(a[8 * q + e]) + __ldg(bias + cc * 32 + 8 * q + e));
-            uint4 pk;
-            pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
-            pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
-            *reinterpret_cast<uint4*>(chunk + (((u0 + q) ^ (r & 7)) << 4)) = pk;
+            for (int q = 0; q < 4; ++q) {
+              float v[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                v[e] = gelu_f(__uint_as_float(a[h][8 * q + e]) + __shfl_sync(0xffffffffu, bl[h], 8 * q + e));
+              uint4 pk;
+              pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
+              pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
+              *reinterpret_cast<uint4*>(chunk + (((h * 4 + q) ^ (r & 7)) << 4)) = pk;
+            }
           }
         }
         tc_fence_before();
@@ -254,28 +296,32 @@ __global__ void __launch_bounds__(192, 1)
         mbar_arrive(act_ready);
       }
       if (!ok) break;
-      // ---- output layer and inverse transform ----
+      // ---- output layer and inverse transform (every epilogue warp consumes the phase) ----
       if (!__all_sync(0xffffffffu, mbar_wait(acc_done, (uint32_t)(nacc & 1), P.err))) { ok = false; break; }
       ++nacc;
-      tc_fence_after();
-      uint32_t o[16];
-      tmem_ld16(trow, o);
-      tmem_ld_wait();
-      tc_fence_before();
-      if (valid) {
-        for (int k = 0; k < P.ns; ++k) {
-          const float z = __uint_as_float(o[k]) + __ldg(P.bias[4] + k);
-          if (P.zout) P.zout[(int64_t)k * P.ncells + cell] = z;
-          const float d = z * P.ysd[k] + P.ymu[k];
-          const float b1 = bc0[k] + d;
-          P.ynet[(int64_t)k * P.ncells + cell] = powf(fmaxf(1.0f + BC_LAMBDA * b1, 0.0f), 1.0f / BC_LAMBDA);
+      if (io) {
+        tc_fence_after();
+        uint32_t o[16];
+        tmem_ld16(trow, o);
+        tmem_ld_wait();
+        tc_fence_before();
+        if (valid) {
+          for (int k = 0; k < P.ns; ++k) {
+            const float z = __uint_as_float(o[k]) + __ldg(P.bias[4] + k);
+            if (P.zout) P.zout[(int64_t)k * P.ncells + cell] = z;
+            const float d = z * P.ysd[k] + P.ymu[k];
+            const float b1 = bc0[k] + d;
+            P.ynet[(int64_t)k * P.ncells + cell] = powf(fmaxf(1.0f + BC_LAMBDA * b1, 0.0f), 1.0f / BC_LAMBDA);
+          }
         }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 4) tmem_dealloc(tmem, 512);
+  // no CTA leaves while its partner may still deliver multicast data or commits into it
+  cluster_sync_all();
+  if (warp == kTmaWarp) tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -504,14 +550,29 @@ int surrogate_forward(chem_model_s* md, const double* T, const double* p, const 
   P.xmu = md->xmu; P.xsd = md->xsd; P.ymu = md->ymu; P.ysd = md->ysd; P.lo = md->lo; P.hi = md->hi;
   P.ns = md->ns; P.nin = md->nin; P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells;
   P.ynet = ynet; P.zout = zout; P.outbox = outbox; P.err = err;
-  int dev = 0, sms = 0;
-  CHEM_CUDA_TRY(cudaGetDevice(&dev));
-  CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = kCluster;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kFwdThreads);
+  cfg.dynamicSmemBytes = FWD_SMEM;
+  cfg.stream = stream;
+  cfg.attrs = attrs;
+  cfg.numAttrs = 1;
+  // persistent grid: as many clusters as can be resident at once, no more than the tiles need
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    cfg.gridDim = dim3(kCluster);
+    CHEM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_clusters, surrogate_forward_kernel, &cfg));
+    if (max_clusters < 1) { set_error("surrogate kernel: no cluster of %d CTAs fits on the device", kCluster); return CHEM_ECUDA; }
+  }
   const long long ntiles = (ncells + TM - 1) / TM;
-  const int grid = (int)std::min<long long>(ntiles, sms);
-  surrogate_forward_kernel<<<grid, 192, FWD_SMEM, stream>>>(md->tw[0], md->tw[1], md->tw[2], md->tw[3],
-                                                            md->tw[4], P);
-  CHEM_CUDA_TRY(cudaGetLastError());
+  const long long clusters = std::min<long long>((ntiles + kCluster - 1) / kCluster, max_clusters);
+  cfg.gridDim = dim3((unsigned)(clusters * kCluster));
+  CHEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, surrogate_forward_kernel, md->tw[0], md->tw[1], md->tw[2], md->tw[3],
+                                   md->tw[4], P));
   return CHEM_OK;
 }
 
@@ -596,8 +657,10 @@ extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t m
   const float* sd = f + 4 * HID + NOUT;
   md->xmu = sd; md->xsd = sd + KIN; md->ymu = sd + 2 * KIN; md->ysd = sd + 3 * KIN;
   md->lo = sd + 4 * KIN; md->hi = sd + 5 * KIN;
-  int rc = make_tmap_bf16(&md->tw[0], w, HID, KIN, KIN, 256, 64);
-  for (int l = 1; l < 4 && !rc; ++l) rc = make_tmap_bf16(&md->tw[l], w + n1 + (l - 1) * nh, HID, HID, HID, 256, 64);
+  // hidden-layer weight boxes are half a 256-row stage: each CTA of a cluster loads one half
+  int rc = make_tmap_bf16(&md->tw[0], w, HID, KIN, KIN, 256 / kCluster, 64);
+  for (int l = 1; l < 4 && !rc; ++l)
+    rc = make_tmap_bf16(&md->tw[l], w + n1 + (l - 1) * nh, HID, HID, HID, 256 / kCluster, 64);
   if (!rc) rc = make_tmap_bf16(&md->tw[4], w + n1 + 3 * nh, NOUT, HID, HID, NOUT, 64);
   if (rc) return fail(rc);
   *out = md;
