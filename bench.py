@@ -338,6 +338,43 @@ def extra_surrogate(peaks, steps=3):
             "tensor_frac_of_sustained": tf / peak, "model_trained_in_this_run": trained_here}
 
 
+def extra_transport(fp64_peak, reps=3):
+    """Transport and T-from-h kernels on the LES CH4 field (262144 cells) and the quasi-DNS H2
+    field (2^20 cells)."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from paper_2312_13513_gb300 import flops as fl
+    from synth.mechanism import ch4_mechanism, h2_mechanism
+    from synth.states import les_field, load_table
+    from synth.transport import generate_transport
+    out = {}
+    for name, mech, f in (("ch4_les", ch4_mechanism(), les_field(load_table("ch4_flamelet.npz"), n=262144, seed=12347)),
+                          ("h2_quasi_dns", h2_mechanism(), make_field(0, 1 << 20))):
+        dm = cg.Mechanism(mech)
+        gt = cg.Transport(dm, generate_transport(mech))
+        T = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+        Y = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+        n = T.numel()
+        mu = torch.empty_like(T); lam = torch.empty_like(T); D = torch.empty_like(Y)
+        h = torch.empty_like(T); cp = torch.empty_like(T)
+        st = torch.empty(n, dtype=torch.int8, device="cuda")
+        s = torch.cuda.current_stream()
+        gt(T, p, Y, mu, lam, D)
+        ms_tr = min(_time_ms(lambda: gt(T, p, Y, mu, lam, D), s, reps))
+        cg.mixture_thermo(dm, T, Y, h, cp)
+        Tg = T + 100.0
+        ms_T = min(_time_ms(lambda: (Tg.copy_(T + 100.0), cg.temperature_from_enthalpy(dm, h, Y, Tg, st)), s, reps))
+        flo, tr = fl.transport_counts(mech.ns)
+        folded = n * (flo + fl.TRANSCENDENTAL_FLOPS * tr)
+        out[name] = {"cells": n, "transport_ms": ms_tr, "transport_cells_per_s": n / (ms_tr * 1e-3),
+                     "transport_fp64_frac": folded / (ms_tr * 1e-3) / 1e12 / fp64_peak,
+                     "t_from_h_ms": ms_T, "t_from_h_cells_per_s": n / (ms_T * 1e-3),
+                     "t_from_h_converged": int((st == 0).sum())}
+    out["workload"] = ("mixture-averaged viscosity (Wilke), conductivity (Mathur-Saxena), diffusion "
+                       "coefficients from cubic ln T fits; T from h by Newton from T0 + 100 K")
+    return out
+
+
 def extra_graph(n=4096, reps=20):
     """A small chemistry step (n quasi-DNS H2 cells) issued directly and as a captured CUDA-graph
     replay: per-step time of each (the launch and allocation overhead the graph removes)."""
@@ -591,6 +628,7 @@ def main():
         for name, fn in (("ch4_les", lambda: extra_ch4(fp64_peak)),
                          ("surrogate", lambda: extra_surrogate(_peaks())),
                          ("graph_small_step", extra_graph),
+                         ("thermo_transport", lambda: extra_transport(fp64_peak)),
                          ("serving", extra_serving)):
             try:
                 extras[name] = fn()

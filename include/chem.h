@@ -311,6 +311,40 @@ int chem_serve_stats(chem_server_t s, int64_t* out);
 /* Stops the server after its launches finish; queued requests fail. */
 int chem_serve_destroy(chem_server_t s);
 
+/* ---------------------------------------------------------------------------------------
+ * Thermophysical and transport properties per cell (§3.1: the paper's Thermo class computes
+ * them with Newton's method and high-order temperature polynomials on the GPU).  SoA state as
+ * for chem_advance; device pointers; asynchronous on stream.
+ * ------------------------------------------------------------------------------------- */
+/* Mixture enthalpy h (erg/g, formation included) and cp (erg/(g K)) from the NASA-7 fits;
+ * either output may be NULL. */
+int chem_mixture_thermo(chem_mech_t m, const double* T, const double* Y, int64_t ld, int64_t ncells,
+                        double* h, double* cp, chem_stream_t stream);
+/* Temperature from enthalpy: Newton T <- T - (h(T, Y) - h0) / cp(T, Y) from the initial guess in
+ * T, until |dT| < 1e-9 T (at most 50 iterations, T kept in [200, 6000] K).  T is updated only
+ * where it converged; status[c] (nullable, int8) = 0 converged, 1 not. */
+int chem_temperature_from_enthalpy(chem_mech_t m, const double* h0, const double* Y, int64_t ld,
+                                   int64_t ncells, double* T, int8_t* status, chem_stream_t stream);
+
+typedef struct chem_transport_s* chem_transport_t;
+/* Transport data of a mechanism: cubic fits in ln T (T in K) of ln mu_k (g/(cm s)),
+ * ln lambda_k (erg/(cm s K)) and ln D_jk (cm^2/s at p_atm; D_jk(p) = D_jk(p_atm) p_atm / p),
+ * coefficients in ascending powers; host arrays, copied. */
+typedef struct chem_transport_desc {
+  int32_t n_species;
+  const double* mu_poly;       /* [ns][4] */
+  const double* lambda_poly;   /* [ns][4] */
+  const double* diff_poly;     /* [ns][ns][4], symmetric */
+} chem_transport_desc;
+int chem_transport_create(chem_mech_t m, const chem_transport_desc* desc, chem_transport_t* out);
+int chem_transport_free(chem_transport_t t);
+/* Mixture-averaged properties: viscosity by Wilke's rule, conductivity by the Mathur-Saxena
+ * average, D_km = (1 - Y_k) / sum_{j != k} X_j / D_jk (the self-diffusion fit for a cell holding
+ * species k alone).  mu [n], lambda [n], Dmix [ns][ld]: device outputs, each nullable. */
+int chem_transport_eval(chem_transport_t t, const double* T, const double* p, const double* Y,
+                        int64_t ld, int64_t ncells, double* mu, double* lambda, double* Dmix,
+                        chem_stream_t stream);
+
 /* Measured FP64 FMA throughput of the current device (TFLOP/s, 2 flops per FMA) from a
  * register-resident FMA chain kernel; synchronous. */
 int chem_fp64_fma_peak(double* tflops);

@@ -112,6 +112,57 @@ def eval_rhs_jac(mech, T, p, Y, with_jacobian=True, stream=None):
     return f, J
 
 
+# ---------------------------------------------------------------------------------------------
+# thermophysical and transport properties
+# ---------------------------------------------------------------------------------------------
+def mixture_thermo(mech, T, Y, h=None, cp=None, stream=None):
+    """chem_mixture_thermo: mixture h (erg/g) and cp (erg/(g K)) per cell."""
+    import torch
+    _require(T, torch.float64, "T"); _require(Y, torch.float64, "Y")
+    _require(h, torch.float64, "h"); _require(cp, torch.float64, "cp")
+    check(_lib.load().chem_mixture_thermo(mech.handle, _ptr(T), _ptr(Y), Y.shape[1], T.numel(), _ptr(h), _ptr(cp),
+                                          _stream_ptr(stream)))
+
+
+def temperature_from_enthalpy(mech, h, Y, T, status=None, stream=None):
+    """chem_temperature_from_enthalpy: Newton on h(T, Y) = h from the guess in T (in place)."""
+    import torch
+    _require(h, torch.float64, "h"); _require(Y, torch.float64, "Y"); _require(T, torch.float64, "T")
+    _require(status, torch.int8, "status")
+    check(_lib.load().chem_temperature_from_enthalpy(mech.handle, _ptr(h), _ptr(Y), Y.shape[1], T.numel(), _ptr(T),
+                                                     _ptr(status), _stream_ptr(stream)))
+
+
+class Transport:
+    """chem_transport_*: mixture-averaged transport properties from fitted pure-species data."""
+
+    def __init__(self, mech, data):
+        self.mech = mech
+        self._arrays = [np.ascontiguousarray(a, np.float64) for a in (data.mu_poly, data.lambda_poly, data.diff_poly)]
+        d = _lib.TransportDesc(int(data.mu_poly.shape[0]), *[a.ctypes.data for a in self._arrays])
+        h = ctypes.c_void_p()
+        check(_lib.load().chem_transport_create(mech.handle, ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+
+    def __call__(self, T, p, Y, mu=None, lam=None, D=None, stream=None):
+        import torch
+        for a, nm in ((T, "T"), (p, "p"), (Y, "Y"), (mu, "mu"), (lam, "lambda"), (D, "D")):
+            _require(a, torch.float64, nm)
+        check(_lib.load().chem_transport_eval(self.handle, _ptr(T), _ptr(p), _ptr(Y), Y.shape[1], T.numel(), _ptr(mu),
+                                              _ptr(lam), _ptr(D), _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().chem_transport_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def fp64_fma_peak():
     """Measured FP64 FMA throughput of the current GPU in TFLOP/s."""
     v = ctypes.c_double()

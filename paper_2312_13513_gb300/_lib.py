@@ -50,6 +50,10 @@ class Segment(ctypes.Structure):
                 ("status", P), ("nsub", P), ("nrej", P), ("dt", D), ("rtol", D), ("atol", D)]
 
 
+class TransportDesc(ctypes.Structure):
+    _fields_ = [("n_species", I32), ("mu_poly", P), ("lambda_poly", P), ("diff_poly", P)]
+
+
 class ServeOptions(ctypes.Structure):
     _fields_ = [("n_streams", I32), ("idle_poll_us", D), ("slice_ms", D)]
 
@@ -71,6 +75,11 @@ SIGNATURES = {
     "chem_advance_noalloc": (ctypes.c_int, [P, P, P, P, I64, D, I64, D, D, P, P, P, P]),
     "chem_eval_rhs_jac": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P]),
     "chem_fp64_fma_peak": (ctypes.c_int, [P]),
+    "chem_mixture_thermo": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
+    "chem_temperature_from_enthalpy": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
+    "chem_transport_create": (ctypes.c_int, [P, P, P]),
+    "chem_transport_free": (ctypes.c_int, [P]),
+    "chem_transport_eval": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P, P]),
     "chem_surrogate_create": (ctypes.c_int, [P, P, P]),
     "chem_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, P, P]),
     "chem_surrogate_free": (ctypes.c_int, [P]),

@@ -38,6 +38,7 @@
 
 #include "chem_internal.h"
 #include "sm100.h"
+#include "thermo.cuh"
 
 namespace chem {
 
@@ -345,28 +346,6 @@ struct PostParams {
   unsigned int* fb_count;
 };
 
-__device__ __forceinline__ void h_cp_mass(const unsigned char* blob, const MechLayout& L, double T,
-                                          const double* Y, int ld, int64_t cell, const double* Yloc,
-                                          double* h, double* cp) {
-  const int ns = L.ns;
-  const int rg = T < TMID ? 0 : 1;
-  const double* hc = (const double*)(blob + L.o_hc);
-  const double* cc = (const double*)(blob + L.o_cpc);
-  const double* invW = (const double*)(blob + L.o_invW);
-  const double invT = 1.0 / T;
-  double hs = 0.0, cs = 0.0;
-  for (int k = 0; k < ns; ++k) {
-    const double* a = hc + (rg * ns + k) * 6;
-    const double* c = cc + (rg * ns + k) * 5;
-    const double hRT = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4]))) + a[5] * invT;
-    const double cpR = c[0] + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4])));
-    const double yk = Yloc ? Yloc[k] : Y[(int64_t)k * ld + cell];
-    hs += yk * hRT * __ldg(invW + k);
-    cs += yk * cpR * __ldg(invW + k);
-  }
-  *h = RU * T * hs;
-  *cp = RU * cs;
-}
 
 __global__ void surrogate_post_kernel(const PostParams P) {
   const int ns = P.lay.ns;
@@ -444,7 +423,7 @@ __global__ void surrogate_post_kernel(const PostParams P) {
       if (pass) {
         // temperature from enthalpy conservation: h(T, Y'') = h(T0, Y0)
         double h0, cp0;
-        h_cp_mass(P.blob, P.lay, T0, P.Y, (int)0, cell, Y0, &h0, &cp0);
+        h_cp_mass(P.blob, P.lay, T0, P.Y, 0, cell, Y0, &h0, &cp0);
         bool conv = false;
         for (int it = 0; it < 50; ++it) {
           double hh, cp;

@@ -99,3 +99,13 @@ def launch_flops(mech, n_accepted_total, n_attempts_total):
     fl = n_accepted_total * (c["rhs"][0] + c["jac"][0]) + n_attempts_total * c["attempt"][0]
     tr = n_accepted_total * (c["rhs"][1] + c["jac"][1]) + n_attempts_total * c["attempt"][1]
     return float(fl), float(tr), float(fl + TRANSCENDENTAL_FLOPS * tr)
+
+
+def transport_counts(ns):
+    """(flops, transcendentals) of one cell's mixture-averaged properties (chem_transport_eval),
+    counting the diffusion fits once per unordered species pair, as the definition needs."""
+    per_species = 2 * 6 + 2 + 6 + 4          # two cubic fits, X_k, Mathur sums, D_km division
+    pairs = ns * (ns - 1) // 2
+    fl = ns * per_species + pairs * (6 + 2 * 2) + ns * ns * 6 + 8
+    tr = 4 * ns + pairs + 1                   # sqrt(mu), 1/sqrt(mu), lambda, 1/lambda; D fits; ln T
+    return fl, tr
