@@ -8,9 +8,10 @@
 // * chem_transport_eval: mixture-averaged viscosity (Wilke), conductivity (Mathur-Saxena) and
 //   diffusion coefficients D_km = (1 - Y_k) / sum_{j != k} X_j / D_jk from cubic fits in ln T.
 //   A group of G threads owns a cell (G = 4 for small mechanisms, 32 for CH4-sized ones): lanes
-//   split the species rows of the Wilke and diffusion sums (ns^2 terms, one exponential per
-//   diffusion pair), the per-cell scalars are formed once per group.  Fits and the Wilke
-//   weight tables stay in global memory behind the read-only cache.
+//   first evaluate the inverse binary diffusion coefficients once per unordered species pair
+//   (one exponential each, kept in shared memory), then split the species rows of the Wilke and
+//   diffusion sums (ns^2 terms); the per-cell scalars are formed once per group.  Fits, the
+//   pair list and the Wilke weight tables stay in global memory behind the read-only cache.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -34,6 +35,7 @@ struct chem_transport_s {
   const double* invW = nullptr;        // [ns]
   const double* wq = nullptr;          // [ns][ns]: (W_j / W_k)^(1/4) at [j * ns + k]
   const double* cw = nullptr;          // [ns][ns]: (8 (1 + W_k / W_j))^(-1/2) at [k * ns + j]
+  const int* pairs = nullptr;          // [ns (ns - 1) / 2]: j | k << 16, j < k, row-major upper triangle
 };
 
 namespace {
@@ -93,8 +95,12 @@ struct TrParams {
   int64_t ld, n;
   double *mu, *lam, *Dm;
   const double *mu_poly, *lam_poly, *diff_poly, *invW, *wq, *cw;
+  const int* pairs;
   int ns;
 };
+
+// index of the unordered pair (j, k), j < k, in the row-major upper triangle
+__device__ __forceinline__ int pair_index(int j, int k, int ns) { return j * ns - (j * (j + 1)) / 2 + (k - j - 1); }
 
 __device__ __forceinline__ double poly3(const double* c, double x) {
   return __ldg(c) + x * (__ldg(c + 1) + x * (__ldg(c + 2) + x * __ldg(c + 3)));
@@ -108,10 +114,12 @@ __global__ void __launch_bounds__(256) transport_kernel(const TrParams P) {
   g.init();
   const int ns = P.ns;
   const int gpb = blockDim.x / G;
-  double* X = tsm + (size_t)g.gid * 4 * ns;   // mole fractions
+  const int npair = ns * (ns - 1) / 2;
+  double* X = tsm + (size_t)g.gid * (4 * ns + npair);   // mole fractions
   double* s = X + ns;                        // mu_k^(1/2)
   double* is = s + ns;                       // mu_k^(-1/2)
   double* Yc = is + ns;                      // mass fractions of the cell
+  double* E = Yc + ns;                       // 1 / D_jk(p_atm) per unordered pair
   for (int64_t c = (int64_t)blockIdx.x * gpb + g.gid; c < P.n; c += (int64_t)gridDim.x * gpb) {
     const double T = P.T[c];
     const double lnT = log(T);
@@ -138,6 +146,11 @@ __global__ void __launch_bounds__(256) transport_kernel(const TrParams P) {
     }
     lx = g.sum(lx);
     lxi = g.sum(lxi);
+    if (P.Dm)
+      for (int q = g.tid; q < npair; q += G) {
+        const int jk = __ldg(P.pairs + q);
+        E[q] = exp(-poly3(P.diff_poly + 4 * ((jk & 0xffff) * ns + (jk >> 16)), lnT));
+      }
     g.sync();
     // Wilke viscosity and mixture-averaged diffusion: row k per lane
     double num = 0.0;
@@ -148,7 +161,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const TrParams P) {
         const double xj = X[j];
         const double t = 1.0 + sk * is[j] * __ldg(P.wq + j * ns + k);
         den += xj * t * t * __ldg(P.cw + k * ns + j);
-        if (j != k) dsum += xj * exp(-poly3(P.diff_poly + 4 * (k * ns + j), lnT));
+        if (P.Dm && j != k) dsum += xj * E[j < k ? pair_index(j, k, ns) : pair_index(k, j, ns)];
       }
       num += X[k] * sk * sk / den;
       if (P.Dm) {
@@ -210,7 +223,8 @@ extern "C" int chem_transport_create(chem_mech_t m, const chem_transport_desc* d
     return CHEM_EINVAL;
   }
   const size_t n1 = (size_t)ns * 4, n2 = (size_t)ns * ns * 4, nw = (size_t)ns * ns;
-  std::vector<double> h(2 * n1 + n2 + ns + 2 * nw);
+  const size_t npair = (size_t)ns * (ns - 1) / 2;
+  std::vector<double> h(2 * n1 + n2 + ns + 2 * nw + (npair + 1) / 2);   // the pair list rides along as ints
   double* p = h.data();
   for (size_t i = 0; i < n1; ++i) {
     if (!std::isfinite(d->mu_poly[i]) || !std::isfinite(d->lambda_poly[i])) {
@@ -230,6 +244,9 @@ extern "C" int chem_transport_create(chem_mech_t m, const chem_transport_desc* d
       wq[j * ns + k] = std::pow(m->W[j] / m->W[k], 0.25);
       cw[k * ns + j] = 1.0 / std::sqrt(8.0 * (1.0 + m->W[k] / m->W[j]));
     }
+  int* pairs = reinterpret_cast<int*>(cw + nw);
+  for (int j = 0, q = 0; j < ns; ++j)
+    for (int k = j + 1; k < ns; ++k) pairs[q++] = j | (k << 16);
   chem_transport_s* t = new chem_transport_s();
   t->mech = m;
   t->ns = ns;
@@ -246,6 +263,7 @@ extern "C" int chem_transport_create(chem_mech_t m, const chem_transport_desc* d
   t->invW = t->d + 2 * n1 + n2;
   t->wq = t->invW + ns;
   t->cw = t->wq + nw;
+  t->pairs = reinterpret_cast<const int*>(t->cw + nw);
   *out = t;
   return CHEM_OK;
 }
@@ -259,11 +277,18 @@ extern "C" int chem_transport_eval(chem_transport_t t, const double* T, const do
   TrParams P;
   P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.n = ncells; P.mu = mu; P.lam = lambda; P.Dm = Dmix;
   P.mu_poly = t->mu_poly; P.lam_poly = t->lam_poly; P.diff_poly = t->diff_poly; P.invW = t->invW;
-  P.wq = t->wq; P.cw = t->cw; P.ns = t->ns;
+  P.wq = t->wq; P.cw = t->cw; P.pairs = t->pairs; P.ns = t->ns;
   const int G = t->ns + 1 <= 16 ? 4 : 32;
   const int threads = 256, gpb = threads / G;
-  const size_t smem = (size_t)gpb * 4 * t->ns * sizeof(double);
-  if (smem > 48 * 1024) { set_error("mechanism too large for the transport kernel"); return CHEM_EINVAL; }
+  const size_t per_group = (size_t)(4 * t->ns + t->ns * (t->ns - 1) / 2) * sizeof(double);
+  const size_t smem = (size_t)gpb * per_group;
+  static size_t smem_set = 48 * 1024;
+  if (smem > smem_set) {
+    if (smem > 200 * 1024) { set_error("mechanism too large for the transport kernel"); return CHEM_EINVAL; }
+    CHEM_CUDA_TRY(cudaFuncSetAttribute(transport_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CHEM_CUDA_TRY(cudaFuncSetAttribute(transport_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    smem_set = smem;
+  }
   const unsigned grid = grid_cells(ncells, gpb);
   if (G == 4) transport_kernel<4><<<grid, threads, smem, (cudaStream_t)stream>>>(P);
   else transport_kernel<32><<<grid, threads, smem, (cudaStream_t)stream>>>(P);
