@@ -181,6 +181,28 @@ def run_case(args):
     import paper_2312_13513_gb300 as cg
     from synth.mechanism import ch4_mechanism, h2_mechanism
     from synth.states import les_field, load_table
+    if args.case == "transport":
+        from synth.transport import generate_transport
+        mech = ch4_mechanism()
+        f = les_field(load_table("ch4_flamelet.npz"), n=args.cells, seed=12347)
+        dm = cg.Mechanism(mech)
+        gt = cg.Transport(dm, generate_transport(mech))
+        T = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+        Y = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+        mu = torch.empty_like(T); lam = torch.empty_like(T); D = torch.empty_like(Y)
+        ms = []
+        for k in range(args.warmup + args.steps):
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            gt(T, p, Y, mu, lam, D)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        print(json.dumps({"case": args.case, "cells": args.cells, "ms": ms,
+                          "cells_per_s": args.cells / (float(np.mean(ms)) * 1e-3)}), flush=True)
+        return
     if args.case == "surrogate":
         dm = cg.Mechanism(h2_mechanism())
         model = cg.Surrogate(dm, path=MODEL_PATH)
@@ -480,7 +502,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["h2", "ch4", "surrogate"], default=None,
+    ap.add_argument("--case", choices=["h2", "ch4", "surrogate", "transport"], default=None,
                     help="time one kernel family on a small case (profiling)")
     ap.add_argument("--cells", type=int, default=65536)
     ap.add_argument("--group", type=int, default=0, help="threads per cell (profiling mode; 0 = auto)")

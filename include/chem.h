@@ -101,7 +101,7 @@ int chem_mechanism_info(chem_mech_t m, int* n_species, int* n_reactions, int* n_
 
 typedef struct chem_options {
   int32_t max_steps;      /* step attempts per cell before CHEM_CELL_MAX_STEPS; 0 -> 100000 */
-  int32_t group_threads;  /* threads per cell: 0 auto (4 if ns+1 <= 16 else 128); 4, 8, 16, 32, 64, 128, 256 */
+  int32_t group_threads;  /* threads per cell: 0 auto (2 if ns+1 <= 16 else 128); 2, 4, 8, 16, 32, 64, 128, 256 */
   int32_t groups_per_cta; /* 0 auto */
   int32_t max_ctas;       /* 0 auto (SM count x resident CTAs per SM) */
 } chem_options;

@@ -6,15 +6,17 @@
 // dense LU with partial pivoting, six stages, embedded error estimate, adaptive sub-steps.
 //
 // Work decomposition ("group per cell"): a group of G threads owns one cell at a time.
-//   G = 4   (eight cells per warp, sub-warp groups) for small mechanisms (N = ns + 1 <= 16,
+//   G = 2   (sixteen cells per warp, sub-warp groups) for small mechanisms (N = ns + 1 <= 16,
 //           H2-sized): FP64 instructions issue warp-wide whatever the active mask, so a warp per
-//           10-unknown cell would leave most FP64 lanes idle;
+//           10-unknown cell would leave most FP64 lanes idle; two lanes split a 10-long loop
+//           into 5 full rounds (four lanes would idle half a round) and halve the lanes that
+//           sit out per-cell scalar work;
 //   G = 128 (a CTA-sized group per cell, named barriers) for CH4-sized ones (N ~ 54).
 // Inside a group, threads split the species, the reactions, the Jacobian entries, the LU
 // trailing updates and the triangular solves; sums use warp shuffles.  The mechanism (NASA-7
 // coefficients, Arrhenius, fall-off, efficiency lists) is staged once per CTA into shared memory
 // and shared by all groups of the CTA (§3.2 keeps constant coefficients in fast on-chip memory).
-// The kernel is persistent: groups claim chunks of 8 consecutive cells from a device work queue
+// The kernel is persistent: groups claim chunks of consecutive cells from a device work queue
 // (one atomicAdd), load them species-row by species-row (coalesced 64-byte rows of the SoA
 // state, §3.2), integrate them one after another and store them back, so cells needing many
 // sub-steps do not stall the rest of the grid.
@@ -1085,9 +1087,9 @@ constexpr int kMaxThreads = 512;
 
 int pick_shape(const chem_mech_s* m, const chem_options* opt, LaunchShape* s) {
   const int N = m->ns + 1;
-  int G = (opt && opt->group_threads) ? opt->group_threads : (N <= 16 ? 4 : 128);
-  if (G != 4 && G != 8 && G != 16 && G != 32 && G != 64 && G != 128 && G != 256) {
-    set_error("group_threads must be 4, 8, 16, 32, 64, 128 or 256 (got %d)", G);
+  int G = (opt && opt->group_threads) ? opt->group_threads : (N <= 16 ? 2 : 128);
+  if (G != 2 && G != 4 && G != 8 && G != 16 && G != 32 && G != 64 && G != 128 && G != 256) {
+    set_error("group_threads must be 2, 4, 8, 16, 32, 64, 128 or 256 (got %d)", G);
     return CHEM_EINVAL;
   }
   s->G = G;
@@ -1149,6 +1151,7 @@ int launch_eval_t(const LaunchShape& s, const EvalParams& P, cudaStream_t stream
 int dispatch_adv(const LaunchShape& s, const AdvanceParams& P, const chem_options* opt,
                  cudaStream_t stream) {
   switch (s.G) {
+    case 2: return launch_adv_t<2>(s, P, opt, stream);
     case 4: return launch_adv_t<4>(s, P, opt, stream);
     case 8: return launch_adv_t<8>(s, P, opt, stream);
     case 16: return launch_adv_t<16>(s, P, opt, stream);

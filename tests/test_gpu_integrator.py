@@ -94,7 +94,7 @@ def test_parity_ch4_les_subset(om_ch4, ch4, dm_ch4):
     assert out <= 3
 
 
-@pytest.mark.parametrize("G", [4, 16, 32])
+@pytest.mark.parametrize("G", [4, 8, 16, 32])
 def test_parity_h2_other_group_sizes(om_h2, h2, dm_h2, G):
     T, p, Y = prereacted_mixing_states(om_h2, h2, 301, 17)
     Tg, Yg, st, _, _ = _run(dm_h2, T, p, Y, 1e-6, opts=cg.options(group_threads=G))
