@@ -922,6 +922,7 @@ __device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
 template <int G>
 __global__ void __launch_bounds__(512) advance_kernel(const __grid_constant__ AdvanceParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (blockDim.x % G != 0 || blockDim.x < G) return;   // a block of whole groups only
   stage_mech(P.blob, smem, P.lay.bytes);
   __syncthreads();
   const MechView m = bind_mech(smem, P.lay);
@@ -1051,6 +1052,7 @@ struct EvalParams {
 template <int G>
 __global__ void __launch_bounds__(512) eval_kernel(const EvalParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (blockDim.x % G != 0 || blockDim.x < G) return;   // a block of whole groups only
   stage_mech(P.blob, smem, P.lay.bytes);
   __syncthreads();
   const MechView m = bind_mech(smem, P.lay);
@@ -1158,7 +1160,8 @@ int dispatch_adv(const LaunchShape& s, const AdvanceParams& P, const chem_option
     case 32: return launch_adv_t<32>(s, P, opt, stream);
     case 64: return launch_adv_t<64>(s, P, opt, stream);
     case 128: return launch_adv_t<128>(s, P, opt, stream);
-    default: return launch_adv_t<256>(s, P, opt, stream);
+    case 256: return launch_adv_t<256>(s, P, opt, stream);
+    default: set_error("no kernel for group_threads %d", s.G); return CHEM_EINVAL;
   }
 }
 
@@ -1452,13 +1455,15 @@ extern "C" int chem_eval_rhs_jac(chem_mech_t m, const double* T, const double* p
   P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells; P.f = f; P.J = J;
   cudaStream_t st = (cudaStream_t)stream;
   switch (s.G) {
+    case 2: return launch_eval_t<2>(s, P, st);
     case 4: return launch_eval_t<4>(s, P, st);
     case 8: return launch_eval_t<8>(s, P, st);
     case 16: return launch_eval_t<16>(s, P, st);
     case 32: return launch_eval_t<32>(s, P, st);
     case 64: return launch_eval_t<64>(s, P, st);
     case 128: return launch_eval_t<128>(s, P, st);
-    default: return launch_eval_t<256>(s, P, st);
+    case 256: return launch_eval_t<256>(s, P, st);
+    default: set_error("no kernel for group_threads %d", s.G); return CHEM_EINVAL;
   }
 }
 
