@@ -89,11 +89,6 @@ constexpr int CHUNKS_PER_TILE = 2 + 3 * 16 + 8;
 constexpr int kEpiWarps = 8;
 constexpr int kFwdThreads = 32 * (kEpiWarps + 2);
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
-// CTAs of a cluster work on different tiles but walk the same weight sequence: each loads half of
-// every weight stage with a TMA multicast into both, so each SM pulls half the weight bytes from L2
-constexpr int kCluster = 2;
-constexpr uint16_t kClusterMask = (1u << kCluster) - 1;
-constexpr int WHALF_BYTES = WSTAGE_BYTES / kCluster;
 
 __global__ void __launch_bounds__(kFwdThreads, 1)
     surrogate_forward_kernel(const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
@@ -111,14 +106,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ntiles = (P.ncells + TM - 1) / TM;
-  // every CTA makes the same number of rounds (a CTA past the last tile runs a masked dummy tile)
-  // so that the two CTAs of a cluster consume the same weight stages
-  const long long rounds = (ntiles + gridDim.x - 1) / gridDim.x;
-  const uint32_t crank = cluster_ctarank();
+  // tiles blockIdx.x, blockIdx.x + gridDim.x, ...: every role of the CTA walks the same sequence
+  const long long rounds = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
   if (threadIdx.x == 0) {
-    // a stage is free again once the MMAs of both CTAs of the cluster have read it
-    for (int s = 0; s < WSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], kCluster); }
+    for (int s = 0; s < WSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     mbar_init(acc_done, 1);
     mbar_init(act_ready, 32 * kEpiWarps);
     fence_barrier_init();
@@ -126,8 +118,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   if (warp == kTmaWarp) tmem_alloc(tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
-  // the partner CTA's multicast loads and commits target our barriers: initialised cluster-wide first
-  cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -141,26 +131,23 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         for (int c = 0; c < CHUNKS_PER_TILE; ++c, ++it) {
           const int s = (int)(it % WSTAGES);
           if (!mbar_wait(&empty[s], (uint32_t)((it / WSTAGES) & 1) ^ 1u, P.err)) { ok = false; break; }
-          // this CTA loads rows [128 crank, 128 crank + 128) of the 256-row stage into both CTAs;
-          // the stage's full barrier expects both halves
-          unsigned char* dst = wst + s * WSTAGE_BYTES + crank * WHALF_BYTES;
+          unsigned char* dst = wst + s * WSTAGE_BYTES;
           if (c < 2) {
             mbar_arrive_expect_tx(&full[s], WSTAGE_BYTES);
-            tma_load_2d_multicast(dst, &tW1, &full[s], 0, c * 256 + (int)crank * 128, kClusterMask);
+            tma_load_2d(dst, &tW1, &full[s], 0, c * 256);
           } else if (c < 2 + 48) {
             const int l = (c - 2) / 16, r = (c - 2) % 16, kc = r / 2, nh = r % 2;
             const CUtensorMap* tm = l == 0 ? &tW2 : (l == 1 ? &tW3 : &tW4);
             mbar_arrive_expect_tx(&full[s], WSTAGE_BYTES);
-            tma_load_2d_multicast(dst, tm, &full[s], kc * 64, nh * 256 + (int)crank * 128, kClusterMask);
+            tma_load_2d(dst, tm, &full[s], kc * 64, nh * 256);
           } else {
-            // the 16-row output weights: the first CTA of the cluster loads them for both
             const int kc = c - 50;
             mbar_arrive_expect_tx(&full[s], NOUT * 128);
-            if (crank == 0) tma_load_2d_multicast(wst + s * WSTAGE_BYTES, &tW5, &full[s], kc * 64, 0, kClusterMask);
+            tma_load_2d(dst, &tW5, &full[s], kc * 64, 0);
           }
         }
       }
-      // drain: every issued stage has been read by both CTAs' MMAs (their commits have landed here)
+      // drain: every issued stage has been read by the MMAs (their commits have landed)
       const long long first = it > WSTAGES ? it - WSTAGES : 0;
       for (long long k = first; k < it; ++k) mbar_wait(&empty[k % WSTAGES], (uint32_t)((k / WSTAGES) & 1), P.err);
     }
@@ -194,7 +181,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             for (int kk = 0; kk < 4; ++kk)
               mma_bf16(d, sdesc_k128(abase + kc * ACT_CHUNK + kk * 32), sdesc_k128(bbase + kk * 32), idesc,
                        (kc > 0 || kk > 0) ? 1u : 0u);
-            mma_commit_multicast(&empty[s], kClusterMask);     // frees the stage in both CTAs
+            mma_commit(&empty[s]);                             // frees the stage
           }
           if (ok) mma_commit(acc_done);
         }
@@ -320,8 +307,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  // no CTA leaves while its partner may still deliver multicast data or commits into it
-  cluster_sync_all();
   if (warp == kTmaWarp) tmem_dealloc(tmem, 512);
 }
 
@@ -529,29 +514,22 @@ int surrogate_forward(chem_model_s* md, const double* T, const double* p, const 
   P.xmu = md->xmu; P.xsd = md->xsd; P.ymu = md->ymu; P.ysd = md->ysd; P.lo = md->lo; P.hi = md->hi;
   P.ns = md->ns; P.nin = md->nin; P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells;
   P.ynet = ynet; P.zout = zout; P.outbox = outbox; P.err = err;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attrs[1];
-  attrs[0].id = cudaLaunchAttributeClusterDimension;
-  attrs[0].val.clusterDim.x = kCluster;
-  attrs[0].val.clusterDim.y = 1;
-  attrs[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kFwdThreads);
-  cfg.dynamicSmemBytes = FWD_SMEM;
-  cfg.stream = stream;
-  cfg.attrs = attrs;
-  cfg.numAttrs = 1;
-  // persistent grid: as many clusters as can be resident at once, no more than the tiles need
-  static int max_clusters = 0;
-  if (max_clusters == 0) {
-    cfg.gridDim = dim3(kCluster);
-    CHEM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_clusters, surrogate_forward_kernel, &cfg));
-    if (max_clusters < 1) { set_error("surrogate kernel: no cluster of %d CTAs fits on the device", kCluster); return CHEM_ECUDA; }
+  // persistent grid: as many CTAs as can be resident at once (one per SM), no more than the tiles
+  static int max_ctas = 0;
+  if (max_ctas == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    CHEM_CUDA_TRY(cudaGetDevice(&dev));
+    CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CHEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, surrogate_forward_kernel, kFwdThreads,
+                                                                FWD_SMEM));
+    if (per_sm < 1) { set_error("surrogate kernel does not fit on an SM"); return CHEM_ECUDA; }
+    max_ctas = sms * per_sm;
   }
   const long long ntiles = (ncells + TM - 1) / TM;
-  const long long clusters = std::min<long long>((ntiles + kCluster - 1) / kCluster, max_clusters);
-  cfg.gridDim = dim3((unsigned)(clusters * kCluster));
-  CHEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, surrogate_forward_kernel, md->tw[0], md->tw[1], md->tw[2], md->tw[3],
-                                   md->tw[4], P));
+  const long long grid = std::min<long long>(ntiles, max_ctas);
+  surrogate_forward_kernel<<<(unsigned)grid, kFwdThreads, FWD_SMEM, stream>>>(md->tw[0], md->tw[1], md->tw[2],
+                                                                              md->tw[3], md->tw[4], P);
+  CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
 }
 
@@ -636,10 +614,10 @@ extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t m
   const float* sd = f + 4 * HID + NOUT;
   md->xmu = sd; md->xsd = sd + KIN; md->ymu = sd + 2 * KIN; md->ysd = sd + 3 * KIN;
   md->lo = sd + 4 * KIN; md->hi = sd + 5 * KIN;
-  // hidden-layer weight boxes are half a 256-row stage: each CTA of a cluster loads one half
-  int rc = make_tmap_bf16(&md->tw[0], w, HID, KIN, KIN, 256 / kCluster, 64);
+  // hidden-layer weight boxes are one 256-row x 64-column stage (32 KB)
+  int rc = make_tmap_bf16(&md->tw[0], w, HID, KIN, KIN, 256, 64);
   for (int l = 1; l < 4 && !rc; ++l)
-    rc = make_tmap_bf16(&md->tw[l], w + n1 + (l - 1) * nh, HID, HID, HID, 256 / kCluster, 64);
+    rc = make_tmap_bf16(&md->tw[l], w + n1 + (l - 1) * nh, HID, HID, HID, 256, 64);
   if (!rc) rc = make_tmap_bf16(&md->tw[4], w + n1 + 3 * nh, NOUT, HID, HID, NOUT, 64);
   if (rc) return fail(rc);
   *out = md;
