@@ -345,6 +345,13 @@ int chem_transport_eval(chem_transport_t t, const double* T, const double* p, co
                         int64_t ld, int64_t ncells, double* mu, double* lambda, double* Dmix,
                         chem_stream_t stream);
 
+/* The FP64 exponential the integrator's rate evaluation uses (table-driven, after Tang, ACM TOMS
+ * 15(2), 1989: a 64-entry table of 2^(j/64) and a degree-5 polynomial; within a few units in the
+ * last place of exp; |x| >= 700 and NaN take the library exp), applied elementwise:
+ * y[i] = exp(x[i]) for i < n.  x, y: device arrays of n doubles (may alias).  Asynchronous on
+ * stream.  Exposed for testing and measurement. */
+int chem_fast_exp(const double* x, double* y, int64_t n, chem_stream_t stream);
+
 /* Measured FP64 FMA throughput of the current device (TFLOP/s, 2 flops per FMA) from a
  * register-resident FMA chain kernel; synchronous. */
 int chem_fp64_fma_peak(double* tflops);

@@ -163,6 +163,15 @@ class Transport:
             pass
 
 
+def fast_exp(x, y, stream=None):
+    """chem_fast_exp: y = exp(x) elementwise with the integrator's table-driven exponential."""
+    import torch
+    _require(x, torch.float64, "x"); _require(y, torch.float64, "y")
+    if x.numel() != y.numel() or not x.is_contiguous() or not y.is_contiguous():
+        raise ValueError("x and y must be contiguous and of the same size")
+    check(_lib.load().chem_fast_exp(_ptr(x), _ptr(y), x.numel(), _stream_ptr(stream)))
+
+
 def fp64_fma_peak():
     """Measured FP64 FMA throughput of the current GPU in TFLOP/s."""
     v = ctypes.c_double()

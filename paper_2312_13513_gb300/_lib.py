@@ -75,6 +75,7 @@ SIGNATURES = {
     "chem_advance_noalloc": (ctypes.c_int, [P, P, P, P, I64, D, I64, D, D, P, P, P, P]),
     "chem_eval_rhs_jac": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P]),
     "chem_fp64_fma_peak": (ctypes.c_int, [P]),
+    "chem_fast_exp": (ctypes.c_int, [P, P, I64, P]),
     "chem_mixture_thermo": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
     "chem_temperature_from_enthalpy": (ctypes.c_int, [P, P, P, I64, I64, P, P, P]),
     "chem_transport_create": (ctypes.c_int, [P, P, P]),

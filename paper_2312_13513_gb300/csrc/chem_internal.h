@@ -50,11 +50,13 @@ struct MechLayout {
 };
 
 // constants block of the blob: the stoichiometric-coefficient table indexed by the 4-bit code of
-// a production term (value = code - 8), ln(p_atm / R) and 1 / ns
+// a production term (value = code - 8), ln(p_atm / R), 1 / ns, and the 64-entry table 2^(j / 64)
+// of the table-driven exponential (fastexp.cuh)
 constexpr int kC_NU = 0;
 constexpr int kC_LNPR0 = 16;
 constexpr int kC_INVNS = 17;
-constexpr int kConsts = 18;
+constexpr int kC_EXPTAB = 18;
+constexpr int kConsts = 82;
 
 // Jacobian-assembly program of d(wdot)/dC (global memory, read-only): entry e covers row
 // ent_row[e], column ent_col[e]; its value is sum over terms t in [ent_off[e], ent_off[e+1]) of

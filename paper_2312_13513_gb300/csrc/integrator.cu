@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "chem_internal.h"
+#include "fastexp.cuh"
 
 namespace chem {
 
@@ -37,6 +38,11 @@ namespace chem {
 // each
 // (a time-sliced launch then overruns its budget by at most one cell).
 __host__ __device__ constexpr int chunk_cells(int G) { return G >= 32 ? 1 : 2; }
+
+// Threads per CTA at most.  Two-thread groups are few per CTA (shared memory per cell bounds
+// them near 80), so their kernels are compiled for 256 threads, which lifts the register cap
+// from 128 to 255 per thread: the rate evaluation no longer spills.
+__host__ __device__ constexpr int max_threads(int G) { return G == 2 ? 256 : 512; }
 
 // Rodas4 coefficients, transformed (u-variable) form:
 //   (I/(gamma h) - J) u_s = f(y + sum_j A[s][j] u_j) + sum_j (C[s][j]/h) u_j,
@@ -314,6 +320,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
   const bool lead = is_lead(g);
   const bool jac = Jneg != nullptr;
   const int ns = m.ns, nr = m.nr;
+  const double* etab = m.cst + kC_EXPTAB;     // the table-driven exponential's 2^(j/64)
   const double T = y[0];
   double lnT = 0.0, invT = 0.0;
   if (lead) { lnT = log(T); invT = 1.0 / T; }
@@ -357,7 +364,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
     gshift = acc[3] * m.cst[kC_INVNS];
     rho = p / (RU * T * S);
     invrho = 1.0 / rho;
-    ep1 = exp(gshift - (m.cst[kC_LNPR0] - lnT));
+    ep1 = exp_tab(gshift - (m.cst[kC_LNPR0] - lnT), etab);
     iep1 = 1.0 / ep1;
   }
   if (kMulti) {
@@ -376,7 +383,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
   if (g.tid == 0) w.C[ns] = 1.0;           // the concentration of an empty reaction slot
   for (int k = g.tid; k < ns; k += G) {
     w.C[k] = rho * y[1 + k] * m.invW[k];
-    const double e = exp(w.gRT[k] - gshift);
+    const double e = exp_tab(w.gRT[k] - gshift, etab);
     eg[k] = e;
     ieg[k] = 1.0 / e;
   }
@@ -389,7 +396,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
     const short4 ri = m.rinfo[j];
     const short4 re = m.reac[j];
     const short4 pr = m.prod[j];
-    double kf = exp(m.lnA[j] + m.beta[j] * lnT - m.Ta[j] * invT);
+    double kf = exp_tab(m.lnA[j] + m.beta[j] * lnT - m.Ta[j] * invT, etab);
     double Pf = 1.0, Pr = 1.0, dG = 0.0, dH = 0.0;
     const double cr0 = re.x >= 0 ? w.C[re.x] : 1.0;
     const double cr1 = re.y >= 0 ? w.C[re.y] : 1.0;
@@ -410,15 +417,15 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
       // Troe fall-off (Gilbert, Luther & Troe 1983): k = kinf Pr/(1+Pr) F(T, Pr)
       const double* tr = m.troe + 8 * ri.w;
       const double kinf = kf;
-      const double k0 = exp(tr[0] + tr[1] * lnT - tr[2] * invT);
+      const double k0 = exp_tab(tr[0] + tr[1] * lnT - tr[2] * invT, etab);
       if (kinf == 0.0 || k0 == 0.0) {
         kf = 0.0; dlnkf = 0.0; dkfdM = 0.0;
       } else {
-        const double e3 = exp(-T * tr[4]), e1 = exp(-T * tr[5]);
+        const double e3 = exp_tab(-T * tr[4], etab), e1 = exp_tab(-T * tr[5], etab);
         double Fc = (1.0 - tr[3]) * e3 + tr[3] * e1;
         double dFc = -(1.0 - tr[3]) * tr[4] * e3 - tr[3] * tr[5] * e1;
         if (tr[7] != 0.0) {
-          const double e2 = exp(-tr[6] * invT);
+          const double e2 = exp_tab(-tr[6] * invT, etab);
           Fc += e2;
           dFc += tr[6] * invT * invT * e2;
         }
@@ -435,7 +442,7 @@ __device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const W
           const double d = n - 0.14 * u;
           const double f1 = u / d;
           const double den = 1.0 + f1 * f1;
-          const double F = exp(2.302585092994046 * (L / den));
+          const double F = exp_tab(2.302585092994046 * (L / den), etab);
           const double opr = 1.0 / (1.0 + Prr);
           kf = kinf * (Prr * opr) * F;
           if (jac) {
@@ -920,7 +927,7 @@ __device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
 // the attempt body each iteration (an idle group works on a dummy state whose results are
 // discarded), so the warp's FP64 instructions stay converged across its groups.
 template <int G>
-__global__ void __launch_bounds__(512) advance_kernel(const __grid_constant__ AdvanceParams P) {
+__global__ void __launch_bounds__(max_threads(G)) advance_kernel(const __grid_constant__ AdvanceParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (blockDim.x % G != 0 || blockDim.x < G) return;   // a block of whole groups only
   stage_mech(P.blob, smem, P.lay.bytes);
@@ -1050,7 +1057,7 @@ struct EvalParams {
 };
 
 template <int G>
-__global__ void __launch_bounds__(512) eval_kernel(const EvalParams P) {
+__global__ void __launch_bounds__(max_threads(G)) eval_kernel(const EvalParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (blockDim.x % G != 0 || blockDim.x < G) return;   // a block of whole groups only
   stage_mech(P.blob, smem, P.lay.bytes);
@@ -1085,7 +1092,6 @@ struct LaunchShape {
   WsLayout ws;
 };
 
-constexpr int kMaxThreads = 512;
 
 int pick_shape(const chem_mech_s* m, const chem_options* opt, LaunchShape* s) {
   const int N = m->ns + 1;
@@ -1103,8 +1109,8 @@ int pick_shape(const chem_mech_s* m, const chem_options* opt, LaunchShape* s) {
   const size_t per_group = (size_t)s->ws.total * 8;
   const size_t fixed = (size_t)m->lay.bytes;
   const int unit = G < 32 ? 32 / G : 1;          // groups per warp: whole warps only
-  int groups = (opt && opt->groups_per_cta) ? opt->groups_per_cta : kMaxThreads / G;
-  groups = std::min(groups, kMaxThreads / G);
+  int groups = (opt && opt->groups_per_cta) ? opt->groups_per_cta : max_threads(G) / G;
+  groups = std::min(groups, max_threads(G) / G);
   if (G > 32) groups = std::min(groups, 15);     // named barriers 1..15
   while (groups > unit && fixed + per_group * groups > (size_t)smem_max) groups -= unit;
   groups = std::max(unit, (groups / unit) * unit);
@@ -1333,6 +1339,15 @@ __global__ void fma_peak_kernel(double* out, int iters, double a, double b) {
   if (s == 12345.678) out[0] = s;     // keeps the chains live
 }
 
+// The integrator's table-driven exponential applied elementwise (testing and measurement)
+__global__ void fast_exp_kernel(const double* x, double* y, int64_t n) {
+  __shared__ double tab[64];
+  stage_exp_table(tab);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = exp_tab(x[i], tab);
+}
+
 // ---------------------------------------------------------------------------------------
 // Allocation-free variant of the integrator launch.
 //
@@ -1465,6 +1480,19 @@ extern "C" int chem_eval_rhs_jac(chem_mech_t m, const double* T, const double* p
     case 256: return launch_eval_t<256>(s, P, st);
     default: set_error("no kernel for group_threads %d", s.G); return CHEM_EINVAL;
   }
+}
+
+extern "C" int chem_fast_exp(const double* x, double* y, int64_t n, chem_stream_t stream) {
+  if (n < 0) { set_error("negative n"); return CHEM_EINVAL; }
+  if (n == 0) return CHEM_OK;
+  if (!x || !y) { set_error("NULL pointer"); return CHEM_EINVAL; }
+  int dev = 0, sms = 0;
+  CHEM_CUDA_TRY(cudaGetDevice(&dev));
+  CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t grid = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  fast_exp_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
 }
 
 extern "C" int chem_fp64_fma_peak(double* tflops) {

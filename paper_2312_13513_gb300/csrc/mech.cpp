@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "chem_internal.h"
+#include "exp_table.h"
 
 namespace chem {
 
@@ -236,6 +237,7 @@ int build(const chem_mech_desc* din, chem_mech_s* m) {
   for (int c = 0; c < 16; ++c) cst[kC_NU + c] = (double)(c - 8);
   cst[kC_LNPR0] = std::log(PATM / RU);
   cst[kC_INVNS] = 1.0 / ns;
+  for (int j = 0; j < 64; ++j) cst[kC_EXPTAB + j] = kExpTable[j];
   m->lay = L;
 
   // Jacobian-assembly program for d(wdot_k)/dC_m; a term is (src, oth, coef)

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "chem_internal.h"
+#include "fastexp.cuh"
 #include "thermo.cuh"
 
 using namespace chem;
@@ -110,12 +111,15 @@ __device__ __forceinline__ double poly3(const double* c, double x) {
 template <int G>
 __global__ void __launch_bounds__(256) transport_kernel(const TrParams P) {
   extern __shared__ double tsm[];
+  double* etab = tsm;                        // 2^(j/64) of the table-driven exponential
+  stage_exp_table(etab);
+  __syncthreads();
   TGrp<G> g;
   g.init();
   const int ns = P.ns;
   const int gpb = blockDim.x / G;
   const int npair = ns * (ns - 1) / 2;
-  double* X = tsm + (size_t)g.gid * (4 * ns + npair);   // mole fractions
+  double* X = tsm + 64 + (size_t)g.gid * (4 * ns + npair);   // mole fractions
   double* s = X + ns;                        // mu_k^(1/2)
   double* is = s + ns;                       // mu_k^(-1/2)
   double* Yc = is + ns;                      // mass fractions of the cell
@@ -130,8 +134,8 @@ __global__ void __launch_bounds__(256) transport_kernel(const TrParams P) {
       const double y = P.Y[(int64_t)k * P.ld + c];
       Yc[k] = y;
       const double a = 0.5 * poly3(P.mu_poly + 4 * k, lnT);
-      s[k] = exp(a);
-      is[k] = exp(-a);
+      s[k] = exp_tab(a, etab);
+      is[k] = exp_tab(-a, etab);
       X[k] = y * __ldg(P.invW + k);
       yw += X[k];
     }
@@ -141,15 +145,15 @@ __global__ void __launch_bounds__(256) transport_kernel(const TrParams P) {
       const double x = X[k] / S;
       X[k] = x;
       const double pl = poly3(P.lam_poly + 4 * k, lnT);
-      lx += x * exp(pl);
-      lxi += x * exp(-pl);
+      lx += x * exp_tab(pl, etab);
+      lxi += x * exp_tab(-pl, etab);
     }
     lx = g.sum(lx);
     lxi = g.sum(lxi);
     if (P.Dm)
       for (int q = g.tid; q < npair; q += G) {
         const int jk = __ldg(P.pairs + q);
-        E[q] = exp(-poly3(P.diff_poly + 4 * ((jk & 0xffff) * ns + (jk >> 16)), lnT));
+        E[q] = exp_tab(-poly3(P.diff_poly + 4 * ((jk & 0xffff) * ns + (jk >> 16)), lnT), etab);
       }
     g.sync();
     // Wilke viscosity and mixture-averaged diffusion: row k per lane
@@ -281,7 +285,7 @@ extern "C" int chem_transport_eval(chem_transport_t t, const double* T, const do
   const int G = t->ns + 1 <= 16 ? 4 : 32;
   const int threads = 256, gpb = threads / G;
   const size_t per_group = (size_t)(4 * t->ns + t->ns * (t->ns - 1) / 2) * sizeof(double);
-  const size_t smem = (size_t)gpb * per_group;
+  const size_t smem = 64 * sizeof(double) + (size_t)gpb * per_group;
   static size_t smem_set = 48 * 1024;
   if (smem > smem_set) {
     if (smem > 200 * 1024) { set_error("mechanism too large for the transport kernel"); return CHEM_EINVAL; }
