@@ -40,8 +40,8 @@ namespace chem {
 __host__ __device__ constexpr int chunk_cells(int G) { return G >= 32 ? 1 : 2; }
 
 // Threads per CTA at most.  Two-thread groups are few per CTA (shared memory per cell bounds
-// them near 80), so their kernels are compiled for 256 threads, which lifts the register cap
-// from 128 to 255 per thread: the rate evaluation no longer spills.
+// them near 80), so their kernels are compiled for 256 threads and one CTA per SM, which lifts
+// the register cap from 128 to 255 per thread: the inlined rate evaluation does not spill.
 __host__ __device__ constexpr int max_threads(int G) { return G == 2 ? 256 : 512; }
 
 // Rodas4 coefficients, transformed (u-variable) form:
@@ -313,7 +313,7 @@ struct JacArgs {
 // Jneg (N x N, leading dimension LD): the iteration matrix I/(gamma h) - J then only needs its
 // diagonal.  Ends with the group synchronised.
 template <int G>
-__device__ __noinline__ void eval_fj(const Grp<G>& g, const MechView& m, const WsPtr& w,
+__device__ __forceinline__ void eval_fj(const Grp<G>& g, const MechView& m, const WsPtr& w,
                                      const JacArgs& jp, int LD, const double* y, double p,
                                      double* f, double* Jneg) {
   constexpr bool kMulti = G > 32;
@@ -927,7 +927,7 @@ __device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
 // the attempt body each iteration (an idle group works on a dummy state whose results are
 // discarded), so the warp's FP64 instructions stay converged across its groups.
 template <int G>
-__global__ void __launch_bounds__(max_threads(G)) advance_kernel(const __grid_constant__ AdvanceParams P) {
+__global__ void __launch_bounds__(max_threads(G), 1) advance_kernel(const __grid_constant__ AdvanceParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (blockDim.x % G != 0 || blockDim.x < G) return;   // a block of whole groups only
   stage_mech(P.blob, smem, P.lay.bytes);
