@@ -192,8 +192,36 @@ typedef struct chem_surrogate_desc {
  * split into a BF16 pair (hi + lo) and the product keeps the hi*hi, hi*lo and lo*hi terms, about
  * 16 significant bits, because the rates depend exponentially on the temperature feature. */
 int chem_surrogate_create(const chem_surrogate_desc* desc, chem_mech_t m, chem_model_t* out);
-/* Same from a CHEMSUR1 binary file: magic, int32 ns, int32 hidden, double dt, then W[l], b[l]
- * (l = 0..4), x_mean, x_std, y_mean, y_std, box_lo, box_hi as little-endian float32. */
+/* The paper's own surrogate variant (§2): one network per species, each nin -> h1 -> h2 -> h3 -> 1
+ * with GELU (the paper's widths are 1600, 800, 400), on the same features, normalisation and
+ * trust box as the single network.  A species with W[k][0..3] all NULL has no network and keeps
+ * its mass fraction through the network pass (an inert species, y_std[k] = 0); the others need
+ * all four layers.  Weights are host row-major [out x in]: W[k][0] [h1 x nin], W[k][1] [h2 x h1],
+ * W[k][2] [h3 x h2], W[k][3] [1 x h3]; biases b[k][l] of the layer's output width.  The first
+ * layer is compensated as in the single network; the others are rounded to BF16.  The networks
+ * run layer by layer on the tcgen05 GEMM (bias, GELU and BF16 rounding in its epilogue);
+ * chem_surrogate_forward and chem_surrogate_advance accept either kind of model. */
+typedef struct chem_surrogate_ps_desc {
+  int32_t n_species;         /* ns (<= 16) */
+  int32_t hidden[3];         /* h1, h2, h3: multiples of 8 in [128, 8192] */
+  double dt;                 /* step the networks were trained for (s) */
+  const float* W[16][4];     /* per species k < ns, see above */
+  const float* b[16][4];
+  const float* x_mean;       /* as chem_surrogate_desc */
+  const float* x_std;
+  const float* y_mean;
+  const float* y_std;
+  const float* box_lo;
+  const float* box_hi;
+} chem_surrogate_ps_desc;
+int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* desc, chem_mech_t m,
+                                      chem_model_t* out);
+
+/* Same from a binary file.  CHEMSUR1 (one network): magic, int32 ns, int32 hidden, double dt,
+ * then W[l], b[l] (l = 0..4), x_mean, x_std, y_mean, y_std, box_lo, box_hi as little-endian
+ * float32.  CHEMSUR2 (per-species networks): magic, int32 ns, int32 h1, h2, h3, double dt,
+ * int32 nnet, int32 species[nnet], then for each network W1, b1, W2, b2, W3, b3, W4, b4, then
+ * the statistics as in CHEMSUR1. */
 int chem_surrogate_load(const char* path, chem_mech_t m, chem_model_t* out);
 int chem_surrogate_free(chem_model_t model);
 
@@ -227,6 +255,10 @@ int chem_heat_release(chem_mech_t m, const double* T0, const double* p, const do
  * (device int) is set to 1 if a pipeline wait times out. */
 int chem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                    const float* bias, int M, int N, int K, int* err, chem_stream_t stream);
+/* The same product with the activation epilogue of the per-species networks: Cb[M x N] (BF16, row
+ * pitch ldc) = bf16(act(A B^T + bias)) with act = exact-erf GELU if gelu != 0, else identity. */
+int chem_gemm_bf16_act(const void* A, int64_t lda, const void* B, int64_t ldb, void* Cb, int64_t ldc,
+                       const float* bias, int gelu, int M, int N, int K, int* err, chem_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
  * Surrogate training on the GPU (§2: GELU networks trained with Adam).  A trainer holds FP32
@@ -242,6 +274,12 @@ typedef struct chem_trainer_s* chem_trainer_t;
  * a seeded Gaussian initialisation (std 1/sqrt(fan_in), zero biases).  batch: multiple of 128. */
 int chem_mlp_trainer_create(int n_in, int n_out, int batch, const float* const* W_init,
                             const float* const* b_init, uint64_t seed, chem_trainer_t* out);
+/* Same with the caller's hidden widths: n_in -> hidden[0] -> ... -> hidden[n_hidden - 1] -> n_out
+ * (1 <= n_hidden <= 7, widths in [1, 8192]; the per-species networks use 1600, 800, 400);
+ * W_init / b_init hold n_hidden + 1 layers. */
+int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden, const int* hidden, int batch,
+                                   const float* const* W_init, const float* const* b_init,
+                                   uint64_t seed, chem_trainer_t* out);
 int chem_mlp_trainer_free(chem_trainer_t t);
 /* forward pass of one batch, keeping the activations; out (nullable) receives [batch x n_out].
  * X is read again by chem_mlp_backward: it must stay valid until that call's work is done. */

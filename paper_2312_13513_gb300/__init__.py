@@ -189,7 +189,8 @@ class Surrogate:
     """A BF16 MLP surrogate bound to a mechanism (chem_surrogate_create / _load).
 
     params: dict with W (5 FP32 arrays [out, in]), b (5 arrays), x_mean, x_std, y_mean, y_std,
-    box_lo, box_hi, dt.
+    box_lo, box_hi, dt; or, for the per-species variant (chem_surrogate_create_per_species),
+    hidden = [h1, h2, h3] and nets = {species k: {"W": 4 arrays, "b": 4 arrays}} instead of W, b.
     """
 
     def __init__(self, mech, params=None, path=None):
@@ -205,17 +206,29 @@ class Surrogate:
                 keep.append(a)
                 return a.ctypes.data_as(ctypes.c_void_p)
 
-            d = _lib.SurrogateDesc()
-            d.n_species = mech.ns
-            d.hidden = int(np.asarray(params["W"][0]).shape[0])
-            d.dt = float(params["dt"])
-            for l in range(5):
-                d.W[l] = arr(params["W"][l])
-                d.b[l] = arr(params["b"][l])
+            if "nets" in params:
+                d = _lib.SurrogatePsDesc()
+                d.n_species = mech.ns
+                for i in range(3):
+                    d.hidden[i] = int(params["hidden"][i])
+                d.dt = float(params["dt"])
+                for k, net in params["nets"].items():
+                    for l in range(4):
+                        d.W[int(k)][l] = arr(net["W"][l])
+                        d.b[int(k)][l] = arr(net["b"][l])
+            else:
+                d = _lib.SurrogateDesc()
+                d.n_species = mech.ns
+                d.hidden = int(np.asarray(params["W"][0]).shape[0])
+                d.dt = float(params["dt"])
+                for l in range(5):
+                    d.W[l] = arr(params["W"][l])
+                    d.b[l] = arr(params["b"][l])
             d.x_mean = arr(params["x_mean"]); d.x_std = arr(params["x_std"])
             d.y_mean = arr(params["y_mean"]); d.y_std = arr(params["y_std"])
             d.box_lo = arr(params["box_lo"]); d.box_hi = arr(params["box_hi"])
-            check(L.chem_surrogate_create(ctypes.byref(d), mech.handle, ctypes.byref(h)))
+            create = L.chem_surrogate_create_per_species if "nets" in params else L.chem_surrogate_create
+            check(create(ctypes.byref(d), mech.handle, ctypes.byref(h)))
         self.handle = h
         self.mech = mech
 
@@ -265,6 +278,24 @@ def gemm_bf16(A, B, bias=None, err=None, stream=None):
         err = torch.zeros(1, dtype=torch.int32, device=A.device)
     check(_lib.load().chem_gemm_bf16(_ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), C.stride(0),
                                      _ptr(bias), M, N, K, _ptr(err), _stream_ptr(stream)))
+    if own_err:
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        if int(err.item()) != 0:
+            raise ChemError(-3, "gemm pipeline wait timed out")
+    return C
+
+
+def gemm_bf16_act(A, B, bias=None, gelu=True, err=None, stream=None):
+    """chem_gemm_bf16_act: C = bf16(GELU(A @ B.T + bias)) (or without GELU), BF16 [M, N]."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.bfloat16, device=A.device)
+    own_err = err is None
+    if own_err:
+        err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    check(_lib.load().chem_gemm_bf16_act(_ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), C.stride(0),
+                                         _ptr(bias), 1 if gelu else 0, M, N, K, _ptr(err), _stream_ptr(stream)))
     if own_err:
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         if int(err.item()) != 0:

@@ -64,6 +64,12 @@ class SurrogateDesc(ctypes.Structure):
                 ("box_hi", P)]
 
 
+class SurrogatePsDesc(ctypes.Structure):
+    _fields_ = [("n_species", I32), ("hidden", I32 * 3), ("dt", D), ("W", (P * 4) * 16),
+                ("b", (P * 4) * 16), ("x_mean", P), ("x_std", P), ("y_mean", P), ("y_std", P),
+                ("box_lo", P), ("box_hi", P)]
+
+
 # name -> (restype, argtypes); the library must export every one of them
 SIGNATURES = {
     "chem_load_mechanism": (ctypes.c_int, [ctypes.c_char_p, P]),
@@ -83,11 +89,14 @@ SIGNATURES = {
     "chem_transport_eval": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P, P]),
     "chem_surrogate_create": (ctypes.c_int, [P, P, P]),
     "chem_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, P, P]),
+    "chem_surrogate_create_per_species": (ctypes.c_int, [P, P, P]),
     "chem_surrogate_free": (ctypes.c_int, [P]),
     "chem_surrogate_forward": (ctypes.c_int, [P, P, P, P, I64, I64, P, P, P, P]),
     "chem_surrogate_advance": (ctypes.c_int, [P, P, P, P, P, I64, D, I64, D, D, P, P]),
     "chem_mlp_trainer_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
                                                ctypes.c_uint64, P]),
+    "chem_mlp_trainer_create_layers": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                                      ctypes.c_int, P, P, ctypes.c_uint64, P]),
     "chem_mlp_trainer_free": (ctypes.c_int, [P]),
     "chem_mlp_forward": (ctypes.c_int, [P, P, P, P]),
     "chem_mlp_backward": (ctypes.c_int, [P, P, P, P]),
@@ -109,6 +118,8 @@ SIGNATURES = {
     "chem_serve_destroy": (ctypes.c_int, [P]),
     "chem_gemm_bf16": (ctypes.c_int, [P, I64, P, I64, P, I64, P, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, P, P]),
+    "chem_gemm_bf16_act": (ctypes.c_int, [P, I64, P, I64, P, I64, P, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, P, P]),
     "chem_last_error": (ctypes.c_char_p, []),
 }
 

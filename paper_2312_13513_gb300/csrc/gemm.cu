@@ -1,5 +1,7 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) for sm_103a:
-//   C[M x N] (FP32) = A[M x K] * B[N x K]^T (+ bias[N]),  A and B BF16 with K contiguous.
+//   C[M x N] (FP32) = A[M x K] * B[N x K]^T (+ bias[N]),  A and B BF16 with K contiguous,
+// or, with the activation epilogue, C[M x N] (BF16) = bf16(GELU(A B^T + bias)) (exact erf GELU,
+// round to nearest even): the layer-by-layer inference of the per-species networks.
 //
 // Used by the surrogate's training (forward and backward products of §2's MLP, trained with
 // Adam); inference uses the fused kernel in surrogate.cu built from the same primitives.
@@ -74,11 +76,15 @@ constexpr int GEMM_SMEM = STAGES * (TILE_A + TILE_B) + 1024 + 256;
 
 struct GemmArgs {
   float* C;
+  __nv_bfloat16* Cb;       // non-null: BF16 output of the activation epilogue instead of C
+  int gelu;                // activation epilogue: apply GELU before rounding
   const float* bias;
   int M, N, K;
   int64_t ldc;
   int* err;
 };
+
+__device__ __forceinline__ float gelu_erf(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
 
 __global__ void __launch_bounds__(128, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -151,7 +157,18 @@ __global__ void __launch_bounds__(128, 1)
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
       tmem_ld_wait();
-      if (row < a.M) {
+      if (row < a.M && a.Cb) {
+        __nv_bfloat16* out = a.Cb + (int64_t)row * a.ldc + n0 + c0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < a.N) {
+            float v = __uint_as_float(r[j]) + (a.bias ? a.bias[col] : 0.0f);
+            if (a.gelu) v = gelu_erf(v);
+            out[j] = __float2bfloat16_rn(v);
+          }
+        }
+      } else if (row < a.M) {
         float* out = a.C + (int64_t)row * a.ldc + n0 + c0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -168,9 +185,9 @@ __global__ void __launch_bounds__(128, 1)
 
 }  // namespace
 
-int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
-              const float* bias, int M, int N, int K, int* err, cudaStream_t stream) {
-  if (M < BM || N < BN || K <= 0 || !A || !B || !C || !err) {
+static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, void* Cb, int gelu,
+                       int64_t ldc, const float* bias, int M, int N, int K, int* err, cudaStream_t stream) {
+  if (M < BM || N < BN || K <= 0 || !A || !B || (!C && !Cb) || !err) {
     set_error("gemm_bf16: bad arguments (M=%d N=%d K=%d; M and N must be >= 128)", M, N, K);
     return CHEM_EINVAL;
   }
@@ -184,11 +201,21 @@ int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, 
     CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
     attr_set = true;
   }
-  GemmArgs g{C, bias, M, N, K, ldc, err};
+  GemmArgs g{C, (__nv_bfloat16*)Cb, gelu, bias, M, N, K, ldc, err};
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
   gemm_bf16_kernel<<<grid, 128, GEMM_SMEM, stream>>>(ta, tb, g);
   CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
+}
+
+int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+              const float* bias, int M, int N, int K, int* err, cudaStream_t stream) {
+  return gemm_launch(A, lda, B, ldb, C, nullptr, 0, ldc, bias, M, N, K, err, stream);
+}
+
+int gemm_bf16_act(const void* A, int64_t lda, const void* B, int64_t ldb, void* Cb, int64_t ldc,
+                  const float* bias, int gelu, int M, int N, int K, int* err, cudaStream_t stream) {
+  return gemm_launch(A, lda, B, ldb, nullptr, Cb, gelu, ldc, bias, M, N, K, err, stream);
 }
 
 }  // namespace chem
@@ -199,4 +226,10 @@ extern "C" int chem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t
                               int64_t ldc, const float* bias, int M, int N, int K, int* err,
                               chem_stream_t stream) {
   return gemm_bf16(A, lda, B, ldb, C, ldc, bias, M, N, K, err, (cudaStream_t)stream);
+}
+
+extern "C" int chem_gemm_bf16_act(const void* A, int64_t lda, const void* B, int64_t ldb, void* Cb,
+                                  int64_t ldc, const float* bias, int gelu, int M, int N, int K, int* err,
+                                  chem_stream_t stream) {
+  return gemm_bf16_act(A, lda, B, ldb, Cb, ldc, bias, gelu, M, N, K, err, (cudaStream_t)stream);
 }

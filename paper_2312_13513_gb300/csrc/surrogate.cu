@@ -38,6 +38,7 @@
 
 #include "chem_internal.h"
 #include "sm100.h"
+#include "surrogate_model.h"
 #include "thermo.cuh"
 
 namespace chem {
@@ -49,16 +50,16 @@ int make_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t col
 
 constexpr int TM = 128;            // cells per tile
 constexpr int HID = 512;           // hidden width
-constexpr int KIN = 64;            // padded input width (one 128-byte K chunk)
+constexpr int KIN = SUR_KIN;       // padded input width (one 128-byte K chunk)
 constexpr int NOUT = 16;           // padded output width
-constexpr int MAXNS = 16;          // outputs supported
+constexpr int MAXNS = SUR_MAXNS;   // outputs supported
 static_assert(3 * (MAXNS + 2) <= KIN, "the compensated first layer needs 3 n_in <= KIN");
 constexpr int WSTAGES = 3;
 constexpr int WSTAGE_BYTES = 256 * 64 * 2;
 constexpr int ACT_CHUNK = TM * 128;                  // 16 KB: 128 rows x 64 bf16
 constexpr int ACT_BYTES = 8 * ACT_CHUNK;             // 128 KB
 constexpr int FWD_SMEM = ACT_BYTES + WSTAGES * WSTAGE_BYTES + 1024 + 256;
-constexpr float BC_LAMBDA = 0.1f;
+constexpr float BC_LAMBDA = SUR_BC_LAMBDA;
 
 struct SurParams {
   const float* bias[5];
@@ -478,17 +479,6 @@ namespace chem {}
 // ---------------------------------------------------------------------------------------
 // model object and entry points
 // ---------------------------------------------------------------------------------------
-struct chem_model_s {
-  int ns = 0, nin = 0, ne = 0;
-  double dt = 0.0;
-  int device = 0;
-  void* d_w = nullptr;       // all BF16 weights
-  void* d_f = nullptr;       // FP32 biases and statistics
-  double* d_A = nullptr;     // element mass-fraction matrix
-  const float* bias[5] = {};
-  const float *xmu = nullptr, *xsd = nullptr, *ymu = nullptr, *ysd = nullptr, *lo = nullptr, *hi = nullptr;
-  CUtensorMap tw[5];
-};
 
 namespace chem {
 
@@ -503,6 +493,7 @@ static uint16_t f2bf(float f) {
 int surrogate_forward(chem_model_s* md, const double* T, const double* p, const double* Y, int64_t ld,
                       int64_t ncells, float* ynet, float* zout, uint8_t* outbox, int* err,
                       cudaStream_t stream) {
+  if (md->kind == 1) return surrogate_forward_ps(md, T, p, Y, ld, ncells, ynet, zout, outbox, err, stream);
   static bool attr = false;
   if (!attr) {
     CHEM_CUDA_TRY(cudaFuncSetAttribute(surrogate_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -624,6 +615,153 @@ extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t m
   return CHEM_OK;
 }
 
+extern "C" int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* d, chem_mech_t mech,
+                                                 chem_model_t* out) {
+  if (!d || !mech || !out) { set_error("NULL argument"); return CHEM_EINVAL; }
+  *out = nullptr;
+  const int ns = d->n_species, nin = ns + 2;
+  if (ns != mech->ns || ns < 1 || ns > MAXNS || 3 * nin > KIN || mech->ne > NEMAX) {
+    set_error("surrogate shape unsupported (ns=%d, mechanism ns=%d, ne=%d)", ns, mech->ns, mech->ne);
+    return CHEM_EINVAL;
+  }
+  const int h1 = d->hidden[0], h2 = d->hidden[1], h3 = d->hidden[2];
+  for (int i = 0; i < 3; ++i)
+    if (d->hidden[i] < 128 || d->hidden[i] > 8192 || d->hidden[i] % 8) {
+      set_error("per-species hidden widths must be multiples of 8 in [128, 8192] (got %d)", d->hidden[i]);
+      return CHEM_EINVAL;
+    }
+  if (!(d->dt > 0.0)) { set_error("surrogate dt must be positive"); return CHEM_EINVAL; }
+  if (!d->x_mean || !d->x_std || !d->y_mean || !d->y_std || !d->box_lo || !d->box_hi) {
+    set_error("NULL normalisation statistics");
+    return CHEM_EINVAL;
+  }
+  chem_model_s* md = new chem_model_s();
+  md->kind = 1; md->ns = ns; md->nin = nin; md->ne = mech->ne; md->dt = d->dt;
+  md->h[0] = h1; md->h[1] = h2; md->h[2] = h3;
+  // per network: BF16 W1 [h1 x 64] (compensated), W2 [h2 x h1], W3 [h3 x h2], w4 [h3];
+  // FP32 b1 [h1], b2 [h2], b3 [h3], b4 (4 slots); then the statistics block
+  const size_t nw1 = (size_t)h1 * KIN, nw2 = (size_t)h2 * h1, nw3 = (size_t)h3 * h2, nw4 = (size_t)h3;
+  const size_t per_w = nw1 + nw2 + nw3 + nw4, per_f = (size_t)h1 + h2 + h3 + 4;
+  std::vector<int> sp;
+  for (int k = 0; k < ns; ++k) {
+    const bool any = d->W[k][0] || d->W[k][1] || d->W[k][2] || d->W[k][3];
+    if (!any) continue;
+    for (int l = 0; l < 4; ++l)
+      if (!d->W[k][l] || !d->b[k][l]) { set_error("species %d: NULL weight or bias", k); delete md; return CHEM_EINVAL; }
+    sp.push_back(k);
+  }
+  md->nnet = (int)sp.size();
+  std::vector<uint16_t> wb(per_w * std::max<size_t>(sp.size(), 1), 0);
+  std::vector<float> fb(per_f * sp.size() + 6 * KIN, 0.0f);
+  for (size_t s = 0; s < sp.size(); ++s) {
+    const int k = sp[s];
+    uint16_t* w = &wb[s * per_w];
+    for (int o = 0; o < h1; ++o)
+      for (int i = 0; i < nin; ++i) {
+        const float v = d->W[k][0][(size_t)o * nin + i];
+        const uint16_t hi = f2bf(v);
+        const uint32_t hbits = (uint32_t)hi << 16;
+        float vh;
+        memcpy(&vh, &hbits, 4);
+        w[(size_t)o * KIN + i] = hi;
+        w[(size_t)o * KIN + nin + i] = hi;
+        w[(size_t)o * KIN + 2 * nin + i] = f2bf(v - vh);
+      }
+    for (size_t e = 0; e < nw2; ++e) w[nw1 + e] = f2bf(d->W[k][1][e]);
+    for (size_t e = 0; e < nw3; ++e) w[nw1 + nw2 + e] = f2bf(d->W[k][2][e]);
+    for (size_t e = 0; e < nw4; ++e) w[nw1 + nw2 + nw3 + e] = f2bf(d->W[k][3][e]);
+    float* f = &fb[s * per_f];
+    memcpy(f, d->b[k][0], h1 * sizeof(float));
+    memcpy(f + h1, d->b[k][1], h2 * sizeof(float));
+    memcpy(f + h1 + h2, d->b[k][2], h3 * sizeof(float));
+    f[h1 + h2 + h3] = d->b[k][3][0];
+  }
+  float* st = &fb[per_f * sp.size()];
+  for (int i = 0; i < nin; ++i) {
+    st[i] = d->x_mean[i];
+    st[KIN + i] = d->x_std[i] > 0.0f ? d->x_std[i] : 1.0f;
+    st[4 * KIN + i] = d->box_lo[i];
+    st[5 * KIN + i] = d->box_hi[i];
+  }
+  for (int k = 0; k < ns; ++k) {
+    st[2 * KIN + k] = d->y_mean[k];
+    st[3 * KIN + k] = d->y_std[k];
+  }
+  std::vector<double> A((size_t)mech->ne * ns);
+  for (int e = 0; e < mech->ne; ++e)
+    for (int k = 0; k < ns; ++k)
+      A[(size_t)e * ns + k] = mech->comp[(size_t)k * mech->ne + e] * mech->elem_mass[e] / mech->W[k];
+  auto fail = [&](int rc) { chem_surrogate_free(md); return rc; };
+  if (cudaGetDevice(&md->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaGetDevice"));
+  cudaError_t e1 = cudaMalloc(&md->d_w, wb.size() * 2);
+  cudaError_t e2 = cudaMalloc(&md->d_f, fb.size() * 4);
+  cudaError_t e3 = cudaMalloc((void**)&md->d_A, A.size() * 8);
+  if (e1 || e2 || e3) return fail(cuda_fail(e1 ? e1 : (e2 ? e2 : e3), "cudaMalloc(surrogate)"));
+  if (cudaMemcpy(md->d_w, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(md->d_f, fb.data(), fb.size() * 4, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(md->d_A, A.data(), A.size() * 8, cudaMemcpyHostToDevice))
+    return fail(cuda_fail(cudaGetLastError(), "cudaMemcpy(surrogate)"));
+  const uint16_t* w = (const uint16_t*)md->d_w;
+  const float* f = (const float*)md->d_f;
+  for (size_t s = 0; s < sp.size(); ++s) {
+    PsNet& n = md->net[s];
+    n.species = sp[s];
+    const uint16_t* ws = w + s * per_w;
+    n.W1 = ws; n.W2 = ws + nw1; n.W3 = ws + nw1 + nw2; n.w4 = ws + nw1 + nw2 + nw3;
+    const float* fs = f + s * per_f;
+    n.b1 = fs; n.b2 = fs + h1; n.b3 = fs + h1 + h2; n.b4 = fs + h1 + h2 + h3;
+  }
+  const float* sd = f + per_f * sp.size();
+  md->xmu = sd; md->xsd = sd + KIN; md->ymu = sd + 2 * KIN; md->ysd = sd + 3 * KIN;
+  md->lo = sd + 4 * KIN; md->hi = sd + 5 * KIN;
+  *out = md;
+  return CHEM_OK;
+}
+
+// CHEMSUR2 (per-species networks): magic, int32 ns, int32 h1, h2, h3, double dt, int32 nnet,
+// int32 species[nnet], then per network W1, b1, W2, b2, W3, b3, W4, b4, then the statistics
+static int load_per_species(std::ifstream& f, const char* path, chem_mech_t mech, chem_model_t* out) {
+  int32_t ns = 0, h[3] = {0, 0, 0}, nnet = 0;
+  double dt = 0.0;
+  f.read((char*)&ns, 4);
+  f.read((char*)h, 12);
+  f.read((char*)&dt, 8);
+  f.read((char*)&nnet, 4);
+  if (!f || ns < 1 || ns > MAXNS || nnet < 0 || nnet > ns) {
+    set_error("%s: not a per-species surrogate model file", path);
+    return CHEM_EINVAL;
+  }
+  for (int i = 0; i < 3; ++i)
+    if (h[i] < 128 || h[i] > 8192) { set_error("%s: bad hidden width", path); return CHEM_EINVAL; }
+  std::vector<int32_t> sp(nnet);
+  f.read((char*)sp.data(), 4 * (size_t)nnet);
+  const int nin = ns + 2;
+  const size_t wsz[4] = {(size_t)h[0] * nin, (size_t)h[1] * h[0], (size_t)h[2] * h[1], (size_t)h[2]};
+  const size_t bsz[4] = {(size_t)h[0], (size_t)h[1], (size_t)h[2], 1};
+  std::vector<std::vector<float>> W(4 * (size_t)nnet), b(4 * (size_t)nnet);
+  chem_surrogate_ps_desc d{};
+  d.n_species = ns; d.hidden[0] = h[0]; d.hidden[1] = h[1]; d.hidden[2] = h[2]; d.dt = dt;
+  for (int s = 0; s < nnet; ++s) {
+    if (sp[s] < 0 || sp[s] >= ns) { set_error("%s: bad species index", path); return CHEM_EINVAL; }
+    for (int l = 0; l < 4; ++l) {
+      W[4 * s + l].resize(wsz[l]);
+      b[4 * s + l].resize(bsz[l]);
+      f.read((char*)W[4 * s + l].data(), wsz[l] * 4);
+      f.read((char*)b[4 * s + l].data(), bsz[l] * 4);
+      d.W[sp[s]][l] = W[4 * s + l].data();
+      d.b[sp[s]][l] = b[4 * s + l].data();
+    }
+  }
+  std::vector<float> xm(nin), xs(nin), ym(ns), ys(ns), lo(nin), hi(nin);
+  f.read((char*)xm.data(), nin * 4); f.read((char*)xs.data(), nin * 4);
+  f.read((char*)ym.data(), ns * 4); f.read((char*)ys.data(), ns * 4);
+  f.read((char*)lo.data(), nin * 4); f.read((char*)hi.data(), nin * 4);
+  if (!f) { set_error("%s: truncated surrogate model file", path); return CHEM_EINVAL; }
+  d.x_mean = xm.data(); d.x_std = xs.data(); d.y_mean = ym.data(); d.y_std = ys.data();
+  d.box_lo = lo.data(); d.box_hi = hi.data();
+  return chem_surrogate_create_per_species(&d, mech, out);
+}
+
 extern "C" int chem_surrogate_load(const char* path, chem_mech_t mech, chem_model_t* out) {
   if (!path || !mech || !out) { set_error("NULL argument"); return CHEM_EINVAL; }
   std::ifstream f(path, std::ios::binary);
@@ -632,6 +770,7 @@ extern "C" int chem_surrogate_load(const char* path, chem_mech_t mech, chem_mode
   int32_t ns = 0, hid = 0;
   double dt = 0.0;
   f.read(magic, 8);
+  if (f && memcmp(magic, "CHEMSUR2", 8) == 0) return load_per_species(f, path, mech, out);
   f.read((char*)&ns, 4);
   f.read((char*)&hid, 4);
   f.read((char*)&dt, 8);

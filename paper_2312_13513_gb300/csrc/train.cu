@@ -2,9 +2,11 @@
 // trained with Adam).  Every product runs on the tcgen05 GEMM (gemm.cu); the rest are small
 // elementwise / reduction kernels here.
 //
-// Layer l maps in_pad[l] -> out_pad[l] features; training pads the input to 128 columns and the
-// output layer to 128 rows so that every GEMM dimension is at least one 128-wide tile (padding is
-// zero and stays zero: its gradients vanish).  Per step, with batch B:
+// Layer l maps in_pad[l] -> out_pad[l] features; training pads the input to 128 columns, the
+// output layer to 128 rows and every hidden width to at least 128 (a multiple of 8) so that every
+// GEMM dimension is at least one 128-wide tile (padding is zero and stays zero: its gradients
+// vanish).  The hidden widths are the caller's: 4 x 512 for the single network, 1600/800/400 for
+// the paper's per-species networks.  Per step, with batch B:
 //   forward   Z_l = A_l W_l^T + b_l (FP32), A_{l+1} = bf16(GELU(Z_l))
 //   loss      L = mean over B x n_out of (Z_4 - target)^2,  dZ_4 = 2 (Z_4 - target) / (B n_out)
 //   backward  dW_l = dZ_l^T A_l,  db_l = sum_b dZ_l,  dA_{l-1} = dZ_l W_l,
@@ -21,6 +23,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstring>
 #include <random>
 #include <vector>
@@ -38,7 +41,7 @@ namespace {
 
 constexpr int HID = 512;
 constexpr int PADIO = 128;
-constexpr int NL = 5;
+constexpr int MAXL = 8;          // layers at most (hidden layers + output)
 
 __device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float v) {
@@ -257,12 +260,12 @@ inline unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 25
 }  // namespace
 
 struct chem_trainer_s {
-  int nin, nout, B;
-  int in_pad[NL], out_pad[NL];
-  float *W[NL], *b[NL], *mW[NL], *vW[NL], *mb[NL], *vb[NL], *dW[NL], *db[NL];
-  __nv_bfloat16 *Wb[NL], *Wt[NL];
-  float* Z[NL];                    // pre-activations [B x out_pad]
-  __nv_bfloat16* A[NL];            // A[0] = caller's input, A[l] = bf16(GELU(Z[l-1]))
+  int nin, nout, B, nl;
+  int real_in[MAXL], real_out[MAXL], in_pad[MAXL], out_pad[MAXL];
+  float *W[MAXL], *b[MAXL], *mW[MAXL], *vW[MAXL], *mb[MAXL], *vb[MAXL], *dW[MAXL], *db[MAXL];
+  __nv_bfloat16 *Wb[MAXL], *Wt[MAXL];
+  float* Z[MAXL];                  // pre-activations [B x out_pad]
+  __nv_bfloat16* A[MAXL];          // A[0] = caller's input, A[l] = bf16(GELU(Z[l-1]))
   float *dA, *dZf;
   __nv_bfloat16 *dZb, *dZt, *At;
   int* err;
@@ -288,15 +291,37 @@ extern "C" int chem_mlp_trainer_free(chem_trainer_t t) {
 
 extern "C" int chem_mlp_trainer_create(int n_in, int n_out, int batch, const float* const* W_init,
                                        const float* const* b_init, uint64_t seed, chem_trainer_t* out) {
-  if (!out || n_in < 1 || 3 * n_in > PADIO || n_out < 1 || n_out > PADIO || batch < 128 || batch % 128) {
-    set_error("trainer: n_in in [1, 42], n_out in [1, 128], batch a positive multiple of 128 required");
+  const int hidden[4] = {HID, HID, HID, HID};
+  return chem_mlp_trainer_create_layers(n_in, n_out, 4, hidden, batch, W_init, b_init, seed, out);
+}
+
+extern "C" int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden, const int* hidden, int batch,
+                                              const float* const* W_init, const float* const* b_init,
+                                              uint64_t seed, chem_trainer_t* out) {
+  if (!out || n_in < 1 || 3 * n_in > PADIO || n_out < 1 || n_out > PADIO || batch < 128 || batch % 128 ||
+      n_hidden < 1 || n_hidden + 1 > MAXL || !hidden) {
+    set_error("trainer: n_in in [1, 42], n_out in [1, 128], 1..%d hidden layers, batch a positive "
+              "multiple of 128 required", MAXL - 1);
     return CHEM_EINVAL;
   }
+  for (int h = 0; h < n_hidden; ++h)
+    if (hidden[h] < 1 || hidden[h] > 8192) { set_error("trainer: hidden width %d out of range", hidden[h]); return CHEM_EINVAL; }
   *out = nullptr;
   chem_trainer_s* t = new chem_trainer_s();
-  t->nin = n_in; t->nout = n_out; t->B = batch; t->step = 0;
-  const int ins[NL] = {PADIO, HID, HID, HID, HID}, outs[NL] = {HID, HID, HID, HID, PADIO};
-  const int real_in[NL] = {n_in, HID, HID, HID, HID}, real_out[NL] = {HID, HID, HID, HID, n_out};
+  t->nin = n_in; t->nout = n_out; t->B = batch; t->step = 0; t->nl = n_hidden + 1;
+  const int NL = t->nl;
+  auto pad = [](int w) { return std::max(128, (w + 7) / 8 * 8); };
+  int ins[MAXL], outs[MAXL];
+  for (int l = 0; l < NL; ++l) {
+    t->real_in[l] = l == 0 ? n_in : hidden[l - 1];
+    t->real_out[l] = l == NL - 1 ? n_out : hidden[l];
+    ins[l] = l == 0 ? PADIO : pad(hidden[l - 1]);
+    outs[l] = l == NL - 1 ? PADIO : pad(hidden[l]);
+  }
+  const int* real_in = t->real_in;
+  const int* real_out = t->real_out;
+  int maxw = PADIO;
+  for (int l = 0; l < NL; ++l) maxw = std::max(maxw, std::max(ins[l], outs[l]));
   int rc = CHEM_OK;
   std::mt19937_64 rng(seed);
   std::normal_distribution<float> nd(0.0f, 1.0f);
@@ -337,11 +362,11 @@ extern "C" int chem_mlp_trainer_create(int n_in, int n_out, int batch, const flo
     else k_to_bf16<<<grid_for(nw), 256>>>(t->W[l], t->Wb[l], t->Wt[l], outs[l], ins[l]);
   }
   void* p;
-  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 4), t->dA = (float*)p;
-  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 4), t->dZf = (float*)p;
-  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 2), t->dZb = (__nv_bfloat16*)p;
-  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 2), t->dZt = (__nv_bfloat16*)p;
-  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * HID * 2), t->At = (__nv_bfloat16*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 4), t->dA = (float*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 4), t->dZf = (float*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 2), t->dZb = (__nv_bfloat16*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 2), t->dZt = (__nv_bfloat16*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 2), t->At = (__nv_bfloat16*)p;
   if (!rc) rc = tr_alloc(t, &p, 16), t->err = (int*)p;
   if (!rc) rc = tr_alloc(t, &p, 16), t->loss = (double*)p;
   if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "trainer init");
@@ -354,7 +379,7 @@ extern "C" int chem_mlp_forward(chem_trainer_t t, const void* X, float* out, che
   if (!t || !X) { set_error("NULL argument"); return CHEM_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
   t->A[0] = (__nv_bfloat16*)X;
-  const int B = t->B;
+  const int B = t->B, NL = t->nl;
   for (int l = 0; l < NL; ++l) {
     int rc = gemm_bf16(t->A[l], t->in_pad[l], t->Wb[l], t->in_pad[l], t->Z[l], t->out_pad[l], t->b[l], B,
                        t->out_pad[l], t->in_pad[l], t->err, st);
@@ -376,7 +401,7 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
                                  chem_stream_t stream) {
   if (!t || !target) { set_error("NULL argument"); return CHEM_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
-  const int B = t->B;
+  const int B = t->B, NL = t->nl;
   CHEM_CUDA_TRY(cudaMemsetAsync(t->loss, 0, sizeof(double), st));
   k_mse_grad<<<grid_for((int64_t)B * PADIO), 256, 0, st>>>(t->Z[NL - 1], target, t->dZf, t->dZb, t->loss, B,
                                                           t->nout, PADIO);
@@ -408,7 +433,7 @@ extern "C" int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float
   cudaStream_t st = (cudaStream_t)stream;
   t->step += 1;
   const float c1 = 1.0f - powf(beta1, (float)t->step), c2 = 1.0f - powf(beta2, (float)t->step);
-  for (int l = 0; l < NL; ++l) {
+  for (int l = 0; l < t->nl; ++l) {
     const int r = t->out_pad[l], c = t->in_pad[l];
     k_adam<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[l], t->dW[l], t->mW[l], t->vW[l],
                                                       l == 0 ? nullptr : t->Wb[l], t->Wt[l], r, c, lr, beta1,
@@ -425,8 +450,9 @@ extern "C" int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float
 extern "C" int chem_mlp_trainer_get(chem_trainer_t t, int which, float* const* W, float* const* b) {
   if (!t || !W || !b) { set_error("NULL argument"); return CHEM_EINVAL; }
   CHEM_CUDA_TRY(cudaDeviceSynchronize());
-  const int real_in[NL] = {t->nin, HID, HID, HID, HID}, real_out[NL] = {HID, HID, HID, HID, t->nout};
-  for (int l = 0; l < NL; ++l) {
+  const int* real_in = t->real_in;
+  const int* real_out = t->real_out;
+  for (int l = 0; l < t->nl; ++l) {
     const float* sw = which ? t->dW[l] : t->W[l];
     const float* sb = which ? t->db[l] : t->b[l];
     if (W[l])

@@ -25,20 +25,26 @@ PAD = 128
 
 
 class Trainer:
-    """chem_mlp_trainer_*: n_in -> 512 x 4 -> n_out GELU network with Adam."""
+    """chem_mlp_trainer_*: n_in -> hidden... -> n_out GELU network with Adam (hidden defaults to the
+    single network's 512 x 4; the per-species networks use 1600, 800, 400)."""
 
-    def __init__(self, n_in, n_out, batch, W=None, b=None, seed=0):
+    def __init__(self, n_in, n_out, batch, W=None, b=None, seed=0, hidden=(512, 512, 512, 512)):
         L = _lib.load()
         self.n_in, self.n_out, self.batch = n_in, n_out, batch
+        self.hidden = [int(h) for h in hidden]
+        nl = len(self.hidden) + 1
+        hid = (ctypes.c_int * len(self.hidden))(*self.hidden)
         h = ctypes.c_void_p()
         if W is not None:
             self._w = [np.ascontiguousarray(w, np.float32) for w in W]
             self._b = [np.ascontiguousarray(x, np.float32) for x in b]
-            Wp = (ctypes.c_void_p * 5)(*[w.ctypes.data for w in self._w])
-            bp = (ctypes.c_void_p * 5)(*[x.ctypes.data for x in self._b])
-            check(L.chem_mlp_trainer_create(n_in, n_out, batch, Wp, bp, seed, ctypes.byref(h)))
+            Wp = (ctypes.c_void_p * nl)(*[w.ctypes.data for w in self._w])
+            bp = (ctypes.c_void_p * nl)(*[x.ctypes.data for x in self._b])
+            check(L.chem_mlp_trainer_create_layers(n_in, n_out, len(self.hidden), hid, batch, Wp, bp, seed,
+                                                   ctypes.byref(h)))
         else:
-            check(L.chem_mlp_trainer_create(n_in, n_out, batch, None, None, seed, ctypes.byref(h)))
+            check(L.chem_mlp_trainer_create_layers(n_in, n_out, len(self.hidden), hid, batch, None, None, seed,
+                                                   ctypes.byref(h)))
         self.handle = h
 
     def forward(self, X, out=None, stream=None):
@@ -55,11 +61,12 @@ class Trainer:
                                              _stream_ptr(stream)))
 
     def get(self, which=0):
-        dims = [self.n_in, 512, 512, 512, 512, self.n_out]
-        W = [np.zeros((dims[i + 1], dims[i]), np.float32) for i in range(5)]
-        b = [np.zeros(dims[i + 1], np.float32) for i in range(5)]
-        Wp = (ctypes.c_void_p * 5)(*[w.ctypes.data for w in W])
-        bp = (ctypes.c_void_p * 5)(*[x.ctypes.data for x in b])
+        dims = [self.n_in] + self.hidden + [self.n_out]
+        nl = len(dims) - 1
+        W = [np.zeros((dims[i + 1], dims[i]), np.float32) for i in range(nl)]
+        b = [np.zeros(dims[i + 1], np.float32) for i in range(nl)]
+        Wp = (ctypes.c_void_p * nl)(*[w.ctypes.data for w in W])
+        bp = (ctypes.c_void_p * nl)(*[x.ctypes.data for x in b])
         check(_lib.load().chem_mlp_trainer_get(self.handle, which, Wp, bp))
         return W, b
 
@@ -171,6 +178,83 @@ def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5,
     params = dict(data["stats"])
     params.update({"W": W, "b": b, "dt": dt, "history": history})
     return params
+
+
+PER_SPECIES_HIDDEN = (1600, 800, 400)
+
+
+def train_per_species(mech, n_states=1 << 21, epochs=20, batch=4096, lr=3e-4, lr_final=1e-5, dt=5e-7,
+                      seed=7, log=print, time_budget_s=None, front_fraction=0.5, hidden=PER_SPECIES_HIDDEN,
+                      data=None):
+    """The paper's per-species variant (§2): one n_in -> 1600 -> 800 -> 400 -> 1 GELU network per
+    species with a nonzero increment (inert species get none), each trained on its own column of
+    the same normalised targets, on the same data, features and statistics as the single network.
+    The networks train in lockstep (one Adam step of each per batch)."""
+    import torch
+    dm = Mechanism(mech)
+    t0 = time.time()
+    if data is None:
+        data = make_dataset(mech, dm, n_states, dt, seed, front_fraction=front_fraction)
+    log(f"dataset: {data['X'].shape[0]} states in {time.time() - t0:.1f} s")
+    ns = mech.ns
+    species = [k for k in range(ns) if float(data["stats"]["y_std"][k]) > 0.0]
+    trainers = {k: Trainer(ns + 2, 1, batch, seed=seed + 17 * k, hidden=hidden) for k in species}
+    X, Tt = data["X"], data["T"]
+    n = X.shape[0]
+    steps_per_epoch = n // batch
+    total = epochs * steps_per_epoch
+    loss = {k: torch.zeros(1, dtype=torch.float64, device="cuda") for k in species}
+    history = []
+    step = 0
+    t1 = time.time()
+    for ep in range(epochs):
+        perm = torch.randperm(n, device="cuda")
+        acc = 0.0
+        for i in range(steps_per_epoch):
+            idx = perm[i * batch:(i + 1) * batch]
+            xb = X.index_select(0, idx)
+            yb = Tt.index_select(0, idx)
+            frac = step / max(1, total - 1)
+            lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * frac))
+            for k in species:
+                tr = trainers[k]
+                tr.forward(xb)
+                tr.backward(yb[:, k].contiguous(), loss[k])
+                tr.adam(lr_t)
+            step += 1
+            if i % 64 == 0:
+                acc = float(sum(float(loss[k].item()) for k in species) / len(species))
+        history.append(acc)
+        log(f"epoch {ep + 1}/{epochs}: mean loss over {len(species)} networks {acc:.4e}  "
+            f"({time.time() - t1:.1f} s)")
+        if time_budget_s is not None and time.time() - t1 > time_budget_s:
+            log("time budget reached")
+            break
+    params = dict(data["stats"])
+    params.update({"hidden": list(hidden), "dt": dt, "history": history, "nets": {}})
+    for k in species:
+        W, b = trainers[k].get(0)
+        params["nets"][k] = {"W": W, "b": b}
+        trainers[k].close()
+    return params
+
+
+def save_model_per_species(params, path):
+    """CHEMSUR2 file: magic, int32 ns, int32 h1, h2, h3, float64 dt, int32 nnet, int32 species[nnet],
+    then float32 W1, b1, W2, b2, W3, b3, W4, b4 of each network and the statistics."""
+    ns = len(params["y_std"])
+    species = sorted(int(k) for k in params["nets"])
+    with open(path, "wb") as f:
+        f.write(b"CHEMSUR2")
+        f.write(struct.pack("<iiiidi", ns, *[int(h) for h in params["hidden"]], float(params["dt"]), len(species)))
+        f.write(np.asarray(species, np.int32).tobytes())
+        for k in species:
+            net = params["nets"][k]
+            for l in range(4):
+                f.write(np.ascontiguousarray(net["W"][l], np.float32).tobytes())
+                f.write(np.ascontiguousarray(net["b"][l], np.float32).tobytes())
+        for key in ("x_mean", "x_std", "y_mean", "y_std", "box_lo", "box_hi"):
+            f.write(np.ascontiguousarray(params[key], np.float32).tobytes())
 
 
 def save_model(params, path):

@@ -1,0 +1,155 @@
+"""GPU parity of the paper's per-species surrogate variant (one GELU network per species, run layer
+by layer on the tcgen05 GEMM with its activation epilogue) and of the variable-width trainer."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2312_13513_gb300 as cg  # noqa: E402
+from oracle import mlp as omlp  # noqa: E402
+from oracle import surrogate as osur  # noqa: E402
+
+from gpu_common import to_dev  # noqa: E402
+from helpers import random_states  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("M,N,K,gelu", [(300, 200, 192, True), (128, 1600, 64, True), (1000, 400, 800, False)])
+def test_gemm_activation_epilogue_matches_torch(M, N, K, gelu):
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = (torch.randn(N, K, device="cuda", generator=g) / np.sqrt(K)).to(torch.bfloat16)
+    bias = torch.randn(N, device="cuda", generator=g)
+    C = cg.gemm_bf16_act(A, B, bias, gelu=gelu)
+    z = (A.double() @ B.double().T + bias.double()).cpu().numpy()
+    ref = omlp.bf16_round(omlp.gelu(z) if gelu else z)
+    got = C.float().cpu().numpy().astype(np.float64)
+    # one BF16 rounding of nearly the same value: the tensor cores' FP32 sums differ from the FP64
+    # reference by ~1e-4 of the largest entry (as in the FP32-output test), which near zero
+    # dominates; elsewhere values that straddle a rounding boundary land one BF16 ulp apart
+    tol = 2.0 ** -7 * np.maximum(np.abs(ref), np.abs(got)) + 1e-4 * np.max(np.abs(ref))
+    assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) - tol)
+    assert np.mean(got == ref) > 0.95
+
+
+def _ps_params(mech, x, seed, hidden, inert=()):
+    rng = np.random.default_rng(seed)
+    nin = mech.ns + 2
+    dims = [nin] + list(hidden) + [1]
+    nets = {}
+    for k in range(mech.ns):
+        if k in inert:
+            continue
+        W = [rng.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i]) for i in range(4)]
+        b = [0.1 * rng.standard_normal(dims[i + 1]) for i in range(4)]
+        nets[k] = {"W": W, "b": b}
+    sd = x.std(axis=0)
+    sd = np.where(sd > 1e-6 * np.maximum(1.0, np.abs(x.mean(axis=0))), sd, 1.0)
+    y_std = np.array([0.0 if k in inert else 0.05 + 0.01 * k for k in range(mech.ns)])
+    return {"hidden": list(hidden), "nets": nets, "dt": 5e-7, "x_mean": x.mean(axis=0), "x_std": sd,
+            "y_mean": np.where(y_std > 0, 0.01 * np.arange(mech.ns), 0.0), "y_std": y_std,
+            "box_lo": x.min(axis=0) - 1.0, "box_hi": x.max(axis=0) + 1.0}
+
+
+def _oracle_z(prm, T, p, Y, ns):
+    xz = (osur.features(T, p, Y) - prm["x_mean"]) / prm["x_std"]
+    z = np.zeros((ns, T.size))
+    for k, net in prm["nets"].items():
+        W32 = [np.asarray(w, np.float32).astype(np.float64) for w in net["W"]]
+        b32 = [np.asarray(v, np.float32).astype(np.float64) for v in net["b"]]
+        out, _ = omlp.forward(W32, b32, xz, emulate_bf16=True)
+        z[k] = out[:, 0]
+    return z
+
+
+@pytest.mark.parametrize("hidden,n", [((256, 200, 136), 300), ((1600, 800, 400), 1000)])
+def test_per_species_forward_matches_oracle(h2, hidden, n):
+    dm = cg.Mechanism(h2)
+    T, p, Y = random_states(h2, n, 31, "H2", Tlo=300.0, Thi=2500.0)
+    x = osur.features(T, p, Y)
+    inert = (h2.ns - 1,)                                   # N2: no network
+    prm = _ps_params(h2, x, 5, hidden, inert=inert)
+    prm["box_hi"][0] = 2000.0
+    model = cg.Surrogate(dm, prm)
+    ynet, z, box = cg.surrogate_forward(model, *to_dev(T, p, Y), with_z=True)
+    torch.cuda.synchronize()
+    z = z.cpu().numpy().astype(np.float64)
+    zr = _oracle_z(prm, T, p, Y, h2.ns)
+    tol = 1e-2 * np.maximum(1.0, np.abs(zr))
+    assert np.all(np.abs(z - zr) <= tol), np.max(np.abs(z - zr))
+    assert np.all(z[list(inert)] == 0.0)
+    assert np.array_equal(box.cpu().numpy().astype(bool), T > 2000.0)
+    yr = osur.boxcox_inv(osur.boxcox(Y) + zr * prm["y_std"][:, None] + prm["y_mean"][:, None])
+    yg = ynet.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(yg - yr) <= 0.05 * np.abs(yr) + 1e-6)
+
+
+def test_per_species_model_file_roundtrip(h2, tmp_path):
+    from paper_2312_13513_gb300.train import save_model_per_species
+    dm = cg.Mechanism(h2)
+    T, p, Y = random_states(h2, 500, 32, "H2", Tlo=600.0, Thi=2400.0)
+    prm = _ps_params(h2, osur.features(T, p, Y), 6, (256, 128, 128), inert=(h2.ns - 1,))
+    path = str(tmp_path / "ps.chemsur")
+    save_model_per_species(prm, path)
+    a = cg.Surrogate(dm, prm)
+    b = cg.Surrogate(dm, path=path)
+    ya, za, _ = cg.surrogate_forward(a, *to_dev(T, p, Y), with_z=True)
+    yb, zb, _ = cg.surrogate_forward(b, *to_dev(T, p, Y), with_z=True)
+    torch.cuda.synchronize()
+    assert torch.equal(za, zb) and torch.equal(ya, yb)
+
+
+def test_per_species_identity_networks_through_projection_and_newton(h2, om_h2):
+    """Networks that predict no change: every cell takes the network route and keeps its
+    elements, enthalpy and temperature (the same post-processing as the single network)."""
+    dm = cg.Mechanism(h2)
+    T, p, Y = random_states(h2, 600, 33, "H2", Tlo=400.0, Thi=2400.0)
+    prm = _ps_params(h2, osur.features(T, p, Y), 7, (128, 128, 128), inert=(h2.ns - 1,))
+    for net in prm["nets"].values():
+        net["W"][3] = np.zeros_like(net["W"][3])
+        net["b"][3] = np.zeros(1)
+    prm["y_mean"] = np.zeros(h2.ns)
+    model = cg.Surrogate(dm, prm)
+    Td, pd, Yd = to_dev(T, p, Y)
+    route = torch.full((T.size,), -1, dtype=torch.int8, device="cuda")
+    cg.surrogate_advance(model, Td, pd, Yd, prm["dt"], route=route)
+    torch.cuda.synchronize()
+    assert np.all(route.cpu().numpy() == 0)
+    Tg, Yg = Td.cpu().numpy(), Yd.cpu().numpy()
+    A = osur.element_mass_matrix(h2)
+    assert np.max(np.abs(A @ Yg - A @ Y)) <= 1e-9
+    assert np.max(np.abs(Tg - T) / T) <= 1e-5
+
+
+def test_trainer_with_per_species_widths_matches_oracle():
+    """The variable-width trainer (ragged widths 200 and 136 exercise the K and N tile edges):
+    forward, loss and gradients against the FP64 oracle."""
+    from paper_2312_13513_gb300.train import PAD, Trainer
+    rng = np.random.default_rng(41)
+    B, nin, nout = 256, 11, 1
+    hidden = [200, 136, 160]
+    dims = [nin] + hidden + [nout]
+    W = [omlp.bf16_round(rng.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i])) for i in range(4)]
+    b = [np.float32(0.1 * rng.standard_normal(dims[i + 1])).astype(np.float64) for i in range(4)]
+    X = omlp.bf16_round(rng.standard_normal((B, nin)))
+    T = rng.standard_normal((B, nout))
+    tr = Trainer(nin, nout, B, W=W, b=b, hidden=hidden)
+    Xd = torch.zeros((B, PAD), dtype=torch.bfloat16, device="cuda")
+    Xd[:, :nin] = torch.tensor(X, dtype=torch.float32).to(torch.bfloat16)
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    out = torch.empty((B, nout), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tr.forward(Xd, out)
+    tr.backward(Td, loss)
+    dW, db = tr.get(1)
+    o_out, cache = omlp.forward(W, b, X, emulate_bf16=True)
+    assert np.max(np.abs(out.cpu().numpy() - o_out)) <= 1e-2 * max(1.0, np.max(np.abs(o_out)))
+    assert abs(loss.item() - omlp.mse_loss(o_out, T)) <= 1e-3 * omlp.mse_loss(o_out, T)
+    gW, gb = omlp.backward(W, b, cache, o_out, T)
+    for l in range(4):
+        rel = np.linalg.norm(dW[l] - gW[l]) / np.linalg.norm(gW[l])
+        relb = np.linalg.norm(db[l] - gb[l]) / np.linalg.norm(gb[l])
+        assert rel < 2e-2 and relb < 2e-2, (l, rel, relb)
