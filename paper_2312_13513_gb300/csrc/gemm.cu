@@ -6,9 +6,11 @@
 // Used by the surrogate's training (forward and backward products of §2's MLP, trained with
 // Adam); inference uses the fused kernel in surrogate.cu built from the same primitives.
 // One CTA computes a 128 x 128 tile: warp 0 (one lane) streams 128 x 64 tiles of A and B with TMA
-// (128-byte swizzle) through a 4-stage mbarrier ring, warp 1 (one lane) issues
+// (128-byte swizzle) through a 3-stage mbarrier ring, warp 1 (one lane) issues
 // tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16) into a TMEM accumulator, and the
-// four warps read their 32 TMEM lanes back with tcgen05.ld for the epilogue.  Every wait is
+// four warps read their 32 TMEM lanes back with tcgen05.ld for the epilogue, which stages the tile
+// in the (then idle) stage buffers and writes whole rows with 16-byte stores.  Two CTAs share an
+// SM, so one's epilogue overlaps the other's main loop.  Every wait is
 // bounded: a timeout sets a device error flag and the kernel drains and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -69,7 +71,7 @@ int make_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t col
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;   // 97 KB: two CTAs per SM
 constexpr int TILE_A = BM * BK * 2;              // 16 KB
 constexpr int TILE_B = BN * BK * 2;              // 16 KB
 constexpr int GEMM_SMEM = STAGES * (TILE_A + TILE_B) + 1024 + 256;
@@ -78,6 +80,7 @@ struct GemmArgs {
   float* C;
   __nv_bfloat16* Cb;       // non-null: BF16 output of the activation epilogue instead of C
   int gelu;                // activation epilogue: apply GELU before rounding
+  int vec;                 // output base and row pitch allow 16-byte stores
   const float* bias;
   int M, N, K;
   int64_t ldc;
@@ -86,7 +89,7 @@ struct GemmArgs {
 
 __device__ __forceinline__ float gelu_erf(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const GemmArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -147,33 +150,79 @@ __global__ void __launch_bounds__(128, 1)
     mma_commit(acc_done);
   }
   __syncwarp();
-  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31; tcgen05.ld is warp-collective, so
-  // the warp agrees on the wait's outcome first
-  const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_done, 0, a.err));
+  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31.  TMEM -> registers (bias, activation)
+  // -> shared memory (the stage buffers: every MMA, hence every read of them, has completed once
+  // acc_done fires) -> coalesced row stores, 16 bytes per lane.  The wait's outcome is agreed
+  // block-wide first (tcgen05.ld is warp-collective and the staging needs block barriers).
+  const bool ok = __syncthreads_and(mbar_wait(acc_done, 0, a.err)) != 0;
   tc_fence_after();
-  const int row = m0 + warp * 32 + lane;
+  const int rl = warp * 32 + lane;                       // tile row of this thread
   if (ok) {
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
-      tmem_ld_wait();
-      if (row < a.M && a.Cb) {
-        __nv_bfloat16* out = a.Cb + (int64_t)row * a.ldc + n0 + c0;
+    if (a.Cb) {
+      constexpr int SP = BN + 8;                           // BF16 row pitch: 272 B
+      __nv_bfloat16* st = (__nv_bfloat16*)sA;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
+        tmem_ld_wait();
+        uint32_t pk[16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < a.N) {
-            float v = __uint_as_float(r[j]) + (a.bias ? a.bias[col] : 0.0f);
-            if (a.gelu) v = gelu_erf(v);
-            out[j] = __float2bfloat16_rn(v);
-          }
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + 2 * j;
+          float v0 = __uint_as_float(r[2 * j]) + (a.bias && col < a.N ? a.bias[col] : 0.0f);
+          float v1 = __uint_as_float(r[2 * j + 1]) + (a.bias && col + 1 < a.N ? a.bias[col + 1] : 0.0f);
+          if (a.gelu) { v0 = gelu_erf(v0); v1 = gelu_erf(v1); }
+          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+          pk[j] = *reinterpret_cast<uint32_t*>(&h);
         }
-      } else if (row < a.M) {
-        float* out = a.C + (int64_t)row * a.ldc + n0 + c0;
+        uint4* dst = reinterpret_cast<uint4*>(st + rl * SP + c0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < a.N) out[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[col] : 0.0f);
+        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+      }
+      __syncthreads();
+      // 16 lanes per 256-byte row: a warp stores two rows per instruction
+      const int cg = threadIdx.x & 15;
+      for (int rr = threadIdx.x >> 4; rr < BM; rr += 8) {
+        const int row = m0 + rr, col = n0 + 8 * cg;
+        if (row >= a.M || col >= a.N) continue;
+        const __nv_bfloat16* src = st + rr * SP + 8 * cg;
+        __nv_bfloat16* out = a.Cb + (int64_t)row * a.ldc + col;
+        if (a.vec && col + 8 <= a.N) {
+          *reinterpret_cast<uint4*>(out) = *reinterpret_cast<const uint4*>(src);
+        } else {
+          for (int j = 0; j < 8 && col + j < a.N; ++j) out[j] = src[j];
+        }
+      }
+    } else {
+      constexpr int SP = BN + 4;                           // FP32 row pitch: 528 B
+      float* st = (float*)sA;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
+        tmem_ld_wait();
+        float4* dst = reinterpret_cast<float4*>(st + rl * SP + c0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int col = n0 + c0 + 4 * q + j;
+            v[j] = __uint_as_float(r[4 * q + j]) + (a.bias && col < a.N ? a.bias[col] : 0.0f);
+          }
+          dst[q] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+      }
+      __syncthreads();
+      // 32 lanes per 512-byte row: a warp stores one row per instruction
+      for (int rr = warp; rr < BM; rr += 4) {
+        const int row = m0 + rr, col = n0 + 4 * lane;
+        if (row >= a.M || col >= a.N) continue;
+        const float* src = st + rr * SP + 4 * lane;
+        float* out = a.C + (int64_t)row * a.ldc + col;
+        if (a.vec && col + 4 <= a.N) {
+          *reinterpret_cast<float4*>(out) = *reinterpret_cast<const float4*>(src);
+        } else {
+          for (int j = 0; j < 4 && col + j < a.N; ++j) out[j] = src[j];
         }
       }
     }
@@ -201,7 +250,10 @@ static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, f
     CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
     attr_set = true;
   }
-  GemmArgs g{C, (__nv_bfloat16*)Cb, gelu, bias, M, N, K, ldc, err};
+  const uintptr_t obase = C ? (uintptr_t)C : (uintptr_t)Cb;
+  const int64_t opitch = ldc * (C ? 4 : 2);
+  const int vec = (obase % 16 == 0 && opitch % 16 == 0) ? 1 : 0;
+  GemmArgs g{C, (__nv_bfloat16*)Cb, gelu, vec, bias, M, N, K, ldc, err};
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
   gemm_bf16_kernel<<<grid, 128, GEMM_SMEM, stream>>>(ta, tb, g);
   CHEM_CUDA_TRY(cudaGetLastError());
