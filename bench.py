@@ -204,9 +204,23 @@ def run_case(args):
         print(json.dumps({"case": args.case, "cells": args.cells, "ms": ms,
                           "cells_per_s": args.cells / (float(np.mean(ms)) * 1e-3)}), flush=True)
         return
-    if args.case == "surrogate":
+    if args.case in ("surrogate", "surrogate_ps"):
         dm = cg.Mechanism(h2_mechanism())
-        model = cg.Surrogate(dm, path=MODEL_PATH)
+        if args.case == "surrogate":
+            model = cg.Surrogate(dm, path=MODEL_PATH)
+        else:
+            # the per-species networks' shapes with seeded weights (timing only), the single
+            # network's normalisation and trust box
+            from paper_2312_13513_gb300 import train as trn
+            base = trn.load_model_params(MODEL_PATH)
+            rng = np.random.default_rng(3)
+            dims = [dm.ns + 2, 1600, 800, 400, 1]
+            nets = {k: {"W": [rng.standard_normal((dims[i + 1], dims[i])) / np.sqrt(dims[i]) for i in range(4)],
+                        "b": [np.zeros(dims[i + 1]) for i in range(4)]}
+                    for k in range(dm.ns) if base["y_std"][k] > 0}
+            prm = {kk: base[kk] for kk in ("x_mean", "x_std", "y_mean", "y_std", "box_lo", "box_hi", "dt")}
+            prm.update({"hidden": [1600, 800, 400], "nets": nets})
+            model = cg.Surrogate(dm, prm)
         f = make_field(0, args.cells)
         T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
         Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
@@ -361,6 +375,74 @@ def extra_surrogate(peaks, steps=3):
             "tensor_frac_of_sustained": tf / peak, "model_trained_in_this_run": trained_here}
 
 
+def _score_surrogate(cg, dm, model, T0, p, Y0, Yr, stream, steps=3):
+    """Step and forward time, heat-release error against the FP64 result Yr, fallback fraction."""
+    import torch
+    n = T0.numel()
+    Ts, Ys = T0.clone(), Y0.clone()
+    route = torch.empty(n, dtype=torch.int8, device="cuda")
+
+    def sur():
+        Ts.copy_(T0); Ys.copy_(Y0)
+        cg.surrogate_advance(model, Ts, p, Ys, DT, RTOL, ATOL, route=route, stream=stream)
+
+    sur()
+    ms = min(_time_ms(sur, stream, steps))
+    ms_fwd = min(_time_ms(lambda: cg.surrogate_forward(model, T0, p, Y0, stream=stream), stream, steps))
+    qr = cg.heat_release(dm, T0, p, Y0, Yr, DT)
+    qs = cg.heat_release(dm, T0, p, Y0, Ys, DT)
+    err = float(((qs - qr).abs().sum() / qr.abs().sum()).item())
+    return {"step_ms": ms, "forward_ms": ms_fwd, "hrr_l1_rel_error_vs_fp64": err,
+            "fallback_fraction": float((route == 1).float().mean().item())}
+
+
+def extra_surrogate_per_species(peaks, n_states=1 << 20, epochs=12):
+    """The paper's per-species networks (one 11-1600-800-400-1 GELU network per reactive species)
+    against the single 11-512x4-9 network, both trained in this run on the same data with the same
+    schedule and epochs, scored on the 2^22-cell quasi-DNS field."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from paper_2312_13513_gb300 import train as trn
+    from synth.mechanism import h2_mechanism
+    mech = h2_mechanism()
+    dm = cg.Mechanism(mech)
+    data = trn.make_dataset(mech, dm, n_states, DT, 7)
+    quiet = lambda *a: None
+    t0 = time.time()
+    p1 = trn.train(mech, epochs=epochs, log=quiet, data=data)
+    t_single = time.time() - t0
+    t0 = time.time()
+    pps = trn.train_per_species(mech, epochs=epochs, log=quiet, data=data)
+    t_ps = time.time() - t0
+    f = make_field(0, 1 << 22)
+    n = f["T"].size
+    T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+    Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+    stream = torch.cuda.current_stream()
+    Tr, Yr = T0.clone(), Y0.clone()
+    cg.advance(dm, Tr, p, Yr, DT, RTOL, ATOL, stream=stream)
+    out = {"workload": f"single 11-512x4-9 network vs per-species 11-1600-800-400-1 networks "
+                       f"({len(pps['nets'])} reactive species), both trained here on {n_states} states "
+                       f"x {epochs} epochs (same data, schedule, batch 4096), scored on 2^22 quasi-DNS "
+                       f"H2 cells"}
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    for name, prm, secs in (("single_net", p1, t_single), ("per_species", pps, t_ps)):
+        model = cg.Surrogate(dm, prm)
+        r = _score_surrogate(cg, dm, model, T0, p, Y0, Yr, stream)
+        if name == "single_net":
+            flop = 2.0 * (11 * 512 + 3 * 512 * 512 + 512 * 9)
+        else:
+            h1, h2, h3 = prm["hidden"]
+            flop = 2.0 * len(prm["nets"]) * (11 * h1 + h1 * h2 + h2 * h3 + h3)
+        tf = flop * n / (r["forward_ms"] * 1e-3) / 1e12
+        r.update({"train_s": secs, "mflop_per_cell": flop / 1e6, "forward_tensor_tflops": tf,
+                  "forward_tensor_frac_of_sustained": tf / peak,
+                  "cell_updates_per_s": n / (r["step_ms"] * 1e-3)})
+        out[name] = r
+        model.close()
+    return out
+
+
 def extra_transport(fp64_peak, reps=3):
     """Transport and T-from-h kernels on the LES CH4 field (262144 cells) and the quasi-DNS H2
     field (2^20 cells)."""
@@ -503,7 +585,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["h2", "ch4", "surrogate", "transport"], default=None,
+    ap.add_argument("--case", choices=["h2", "ch4", "surrogate", "surrogate_ps", "transport"], default=None,
                     help="time one kernel family on a small case (profiling)")
     ap.add_argument("--cells", type=int, default=65536)
     ap.add_argument("--group", type=int, default=0, help="threads per cell (profiling mode; 0 = auto)")
@@ -650,6 +732,7 @@ def main():
         extras = {}
         for name, fn in (("ch4_les", lambda: extra_ch4(fp64_peak)),
                          ("surrogate", lambda: extra_surrogate(_peaks())),
+                         ("surrogate_per_species", lambda: extra_surrogate_per_species(_peaks())),
                          ("graph_small_step", extra_graph),
                          ("thermo_transport", lambda: extra_transport(fp64_peak)),
                          ("serving", extra_serving)):

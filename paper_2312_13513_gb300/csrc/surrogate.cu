@@ -638,10 +638,12 @@ extern "C" int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* d
   chem_model_s* md = new chem_model_s();
   md->kind = 1; md->ns = ns; md->nin = nin; md->ne = mech->ne; md->dt = d->dt;
   md->h[0] = h1; md->h[1] = h2; md->h[2] = h3;
-  // per network: BF16 W1 [h1 x 64] (compensated), W2 [h2 x h1], W3 [h3 x h2], w4 [h3];
-  // FP32 b1 [h1], b2 [h2], b3 [h3], b4 (4 slots); then the statistics block
+  // BF16: the first layers of all networks stacked, [nnet h1 x 64] (compensated; one GEMM feeds
+  // every network from the shared features), then per network W2 [h2 x h1], W3 [h3 x h2], w4 [h3];
+  // FP32: the stacked b1 [nnet h1], then per network b2 [h2], b3 [h3], b4 (4 slots); then the
+  // statistics block
   const size_t nw1 = (size_t)h1 * KIN, nw2 = (size_t)h2 * h1, nw3 = (size_t)h3 * h2, nw4 = (size_t)h3;
-  const size_t per_w = nw1 + nw2 + nw3 + nw4, per_f = (size_t)h1 + h2 + h3 + 4;
+  const size_t per_w = nw2 + nw3 + nw4, per_f = (size_t)h2 + h3 + 4;
   std::vector<int> sp;
   for (int k = 0; k < ns; ++k) {
     const bool any = d->W[k][0] || d->W[k][1] || d->W[k][2] || d->W[k][3];
@@ -651,11 +653,13 @@ extern "C" int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* d
     sp.push_back(k);
   }
   md->nnet = (int)sp.size();
-  std::vector<uint16_t> wb(per_w * std::max<size_t>(sp.size(), 1), 0);
-  std::vector<float> fb(per_f * sp.size() + 6 * KIN, 0.0f);
+  const size_t nsp = sp.size();
+  std::vector<uint16_t> wb(nw1 * nsp + per_w * std::max<size_t>(nsp, 1), 0);
+  std::vector<float> fb((size_t)h1 * nsp + per_f * nsp + 6 * KIN, 0.0f);
   for (size_t s = 0; s < sp.size(); ++s) {
     const int k = sp[s];
-    uint16_t* w = &wb[s * per_w];
+    uint16_t* w1 = &wb[s * nw1];
+    uint16_t* w = &wb[nw1 * nsp + s * per_w];
     for (int o = 0; o < h1; ++o)
       for (int i = 0; i < nin; ++i) {
         const float v = d->W[k][0][(size_t)o * nin + i];
@@ -663,20 +667,20 @@ extern "C" int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* d
         const uint32_t hbits = (uint32_t)hi << 16;
         float vh;
         memcpy(&vh, &hbits, 4);
-        w[(size_t)o * KIN + i] = hi;
-        w[(size_t)o * KIN + nin + i] = hi;
-        w[(size_t)o * KIN + 2 * nin + i] = f2bf(v - vh);
+        w1[(size_t)o * KIN + i] = hi;
+        w1[(size_t)o * KIN + nin + i] = hi;
+        w1[(size_t)o * KIN + 2 * nin + i] = f2bf(v - vh);
       }
-    for (size_t e = 0; e < nw2; ++e) w[nw1 + e] = f2bf(d->W[k][1][e]);
-    for (size_t e = 0; e < nw3; ++e) w[nw1 + nw2 + e] = f2bf(d->W[k][2][e]);
-    for (size_t e = 0; e < nw4; ++e) w[nw1 + nw2 + nw3 + e] = f2bf(d->W[k][3][e]);
-    float* f = &fb[s * per_f];
-    memcpy(f, d->b[k][0], h1 * sizeof(float));
-    memcpy(f + h1, d->b[k][1], h2 * sizeof(float));
-    memcpy(f + h1 + h2, d->b[k][2], h3 * sizeof(float));
-    f[h1 + h2 + h3] = d->b[k][3][0];
+    for (size_t e = 0; e < nw2; ++e) w[e] = f2bf(d->W[k][1][e]);
+    for (size_t e = 0; e < nw3; ++e) w[nw2 + e] = f2bf(d->W[k][2][e]);
+    for (size_t e = 0; e < nw4; ++e) w[nw2 + nw3 + e] = f2bf(d->W[k][3][e]);
+    memcpy(&fb[s * h1], d->b[k][0], h1 * sizeof(float));
+    float* f = &fb[(size_t)h1 * nsp + s * per_f];
+    memcpy(f, d->b[k][1], h2 * sizeof(float));
+    memcpy(f + h2, d->b[k][2], h3 * sizeof(float));
+    f[h2 + h3] = d->b[k][3][0];
   }
-  float* st = &fb[per_f * sp.size()];
+  float* st = &fb[(size_t)h1 * nsp + per_f * nsp];
   for (int i = 0; i < nin; ++i) {
     st[i] = d->x_mean[i];
     st[KIN + i] = d->x_std[i] > 0.0f ? d->x_std[i] : 1.0f;
@@ -706,12 +710,12 @@ extern "C" int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* d
   for (size_t s = 0; s < sp.size(); ++s) {
     PsNet& n = md->net[s];
     n.species = sp[s];
-    const uint16_t* ws = w + s * per_w;
-    n.W1 = ws; n.W2 = ws + nw1; n.W3 = ws + nw1 + nw2; n.w4 = ws + nw1 + nw2 + nw3;
-    const float* fs = f + s * per_f;
-    n.b1 = fs; n.b2 = fs + h1; n.b3 = fs + h1 + h2; n.b4 = fs + h1 + h2 + h3;
+    const uint16_t* ws = w + nw1 * nsp + s * per_w;
+    n.W1 = w + s * nw1; n.W2 = ws; n.W3 = ws + nw2; n.w4 = ws + nw2 + nw3;
+    const float* fs = f + (size_t)h1 * nsp + s * per_f;
+    n.b1 = f + s * h1; n.b2 = fs; n.b3 = fs + h2; n.b4 = fs + h2 + h3;
   }
-  const float* sd = f + per_f * sp.size();
+  const float* sd = f + (size_t)h1 * nsp + per_f * nsp;
   md->xmu = sd; md->xsd = sd + KIN; md->ymu = sd + 2 * KIN; md->ysd = sd + 3 * KIN;
   md->lo = sd + 4 * KIN; md->hi = sd + 5 * KIN;
   *out = md;

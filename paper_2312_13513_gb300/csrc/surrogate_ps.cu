@@ -5,9 +5,10 @@
 // The widths do not fit the fused single-network kernel (a 128 x 1600 BF16 activation tile alone
 // is 400 KB), so the networks run layer by layer on the tcgen05 GEMM with its activation epilogue
 // (bias, exact-erf GELU and BF16 rounding fused into the accumulator read-back): per chunk of
-// 16384 cells, one feature kernel, then for every species three GEMMs and an output dot product,
-// then one inverse-transform kernel.  At that chunk size a species' activations (52 + 26 + 13 MB)
-// stay in the 129 MB L2 between its layers.  The output layer (400 -> 1) is a warp-per-cell dot
+// 16384 cells, one feature kernel; one grouped GEMM for the first layers of all networks (they
+// share the input, so their weights stack into one [nnet h1 x 64] operand); then for every species
+// two GEMMs reading its column block of that output and an output dot product; then one
+// inverse-transform kernel.  A species' later activations (26 + 13 MB) stay in the 129 MB L2.  The output layer (400 -> 1) is a warp-per-cell dot
 // product of BF16 values with FP32 accumulation, the precision of the single network's output MMA.
 // Everything after the network (projection, Newton on T, fallback) is shared with the single
 // network (surrogate.cu).
@@ -130,7 +131,8 @@ int surrogate_forward_ps(chem_model_s* md, const double* T, const double* p, con
   const int64_t chunk = std::min<int64_t>(ncells, kPsChunk);
   const int64_t Mp = std::max<int64_t>(chunk, 128);           // a GEMM needs at least one 128-row tile
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t bX = al((size_t)Mp * SUR_KIN * 2), bA1 = al((size_t)Mp * h1 * 2), bA2 = al((size_t)Mp * h2 * 2);
+  const int nnet = std::max(md->nnet, 1), ld1 = nnet * h1;     // A1 holds every network's first layer
+  const size_t bX = al((size_t)Mp * SUR_KIN * 2), bA1 = al((size_t)Mp * ld1 * 2), bA2 = al((size_t)Mp * h2 * 2);
   const size_t bA3 = al((size_t)Mp * h3 * 2), bz = al((size_t)std::max(md->nnet, 1) * Mp * 4);
   unsigned char* ws = nullptr;
   CHEM_CUDA_TRY(cudaMallocAsync((void**)&ws, bX + bA1 + bA2 + bA3 + bz, st));
@@ -152,10 +154,12 @@ int surrogate_forward_ps(chem_model_s* md, const double* T, const double* p, con
     F.ns = md->ns; F.nin = md->nin; F.xmu = md->xmu; F.xsd = md->xsd; F.lo = md->lo; F.hi = md->hi;
     F.X = X; F.outbox = outbox + c0;
     k_ps_features<<<blocks_for(M, 256), 256, 0, st>>>(F);
+    if (md->nnet > 0)   // stacked first layers: net s's weights and biases follow net s - 1's
+      rc = gemm_bf16_act(X, SUR_KIN, md->net[0].W1, SUR_KIN, A1, ld1, md->net[0].b1, 1, M, md->nnet * h1, SUR_KIN,
+                         err, st);
     for (int s = 0; s < md->nnet && !rc; ++s) {
       const PsNet& n = md->net[s];
-      rc = gemm_bf16_act(X, SUR_KIN, n.W1, SUR_KIN, A1, h1, n.b1, 1, M, h1, SUR_KIN, err, st);
-      if (!rc) rc = gemm_bf16_act(A1, h1, n.W2, h1, A2, h2, n.b2, 1, M, h2, h1, err, st);
+      rc = gemm_bf16_act(A1 + (size_t)s * h1, ld1, n.W2, h1, A2, h2, n.b2, 1, M, h2, h1, err, st);
       if (!rc) rc = gemm_bf16_act(A2, h2, n.W3, h2, A3, h3, n.b3, 1, M, h3, h2, err, st);
       if (!rc) k_ps_out<<<blocks_for(nc * 32, 256), 256, 0, st>>>(A3, h3, (const __nv_bfloat16*)n.w4, n.b4, nc,
                                                                   z + (int64_t)s * Mp);

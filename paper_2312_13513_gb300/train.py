@@ -137,12 +137,13 @@ def make_dataset(mech, dm, n, dt, seed, rtol=1e-6, atol=1e-10, stats=None, front
 
 
 def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5, dt=5e-7, seed=7,
-          log=print, time_budget_s=None, front_fraction=0.5):
+          log=print, time_budget_s=None, front_fraction=0.5, data=None):
     import torch
     dm = Mechanism(mech)
     t0 = time.time()
-    data = make_dataset(mech, dm, n_states, dt, seed, front_fraction=front_fraction)
-    log(f"dataset: {n_states} states in {time.time() - t0:.1f} s")
+    if data is None:
+        data = make_dataset(mech, dm, n_states, dt, seed, front_fraction=front_fraction)
+    log(f"dataset: {data['X'].shape[0]} states in {time.time() - t0:.1f} s")
     ns = mech.ns
     tr = Trainer(ns + 2, ns, batch, seed=seed)
     X, Tt = data["X"], data["T"]
