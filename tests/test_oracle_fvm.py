@@ -1,0 +1,99 @@
+"""Pins of the oracle's finite-volume species-equation assembly (Alg. 1 and the other terms) and of
+its PaSR factor."""
+import numpy as np
+import pytest
+
+from oracle import fvm
+from synth.mesh import box_mesh
+
+
+def test_uniform_diffusion_is_the_seven_point_stencil():
+    """Unit box, n cells per side, h = 1/n: a_f = gamma h^2 / h = gamma h on internal faces and
+    gamma h^2 / (h/2) = 2 gamma h on the fixed-value x sides."""
+    n, g = 4, 0.7
+    m = box_mesh(n, n, n)
+    A, s = fvm.species_matrix(m, gamma=np.full(m.n_cells, g), gamma_b=np.full(m.b_cell.size, g),
+                              Y_b=np.zeros(m.b_cell.size))
+    h = 1.0 / n
+    for P in range(m.n_cells):
+        i, j, k = P % n, (P // n) % n, P // (n * n)
+        nbrs = [(i + di, j + dj, k + dk) for di, dj, dk in
+                ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))]
+        inside = [c for c in nbrs if all(0 <= x < n for x in c)]
+        d = g * h * len(inside) + (2 * g * h if i in (0, n - 1) else 0.0) * (2 if n == 1 else 1)
+        assert A[P, P] == pytest.approx(d, rel=1e-14)
+        for (a, b, c) in inside:
+            assert A[P, a + n * b + n * n * c] == pytest.approx(-g * h, rel=1e-14)
+        assert np.count_nonzero(A[P]) == 1 + len(inside)
+
+
+def test_linear_field_has_zero_laplacian_on_a_stretched_permuted_mesh():
+    """psi = x with exact fixed values on the x sides and zero gradient elsewhere: the two-point
+    fluxes are exact on an orthogonal mesh, so A psi = s to rounding."""
+    m = box_mesh(5, 4, 3, seed=3, stretch=3.0, permute=True)
+    g = np.full(m.n_cells, 1.3)
+    psi = m.centre[:, 0]
+    A, s = fvm.species_matrix(m, gamma=g, gamma_b=np.full(m.b_cell.size, 1.3), Y_b=m.b_centre[:, 0])
+    assert np.max(np.abs(A @ psi - s)) <= 1e-12 * np.max(np.abs(s))
+
+
+def test_closed_box_conserves_the_species_mass():
+    """Zero-gradient walls and no boundary flux: every face flux (convective and diffusive)
+    enters two rows with opposite signs, so 1^T A Y = sum rho V Y / dt for any Y and phi."""
+    m = box_mesh(4, 3, 3, seed=4, stretch=2.0, permute=True)
+    rng = np.random.default_rng(5)
+    m.b_type[:] = 0
+    nb = m.b_cell.size
+    rho = rng.uniform(0.5, 2.0, m.n_cells)
+    dt = 1e-3
+    A, s = fvm.species_matrix(m, dt=dt, rho=rho, rho_old=rho, Y_old=np.zeros(m.n_cells),
+                              phi=rng.standard_normal(m.owner.size), phi_b=np.zeros(nb),
+                              gamma=rng.uniform(0.1, 1.0, m.n_cells), gamma_b=np.ones(nb), Y_b=np.zeros(nb))
+    Y = rng.uniform(0.0, 1.0, m.n_cells)
+    assert np.sum(A @ Y) == pytest.approx(np.sum(rho * m.volume * Y / dt), rel=1e-12)
+
+
+def test_upwind_convection_of_a_uniform_field_through_a_uniform_flow():
+    """A uniform flow along x through a box with inflow at x = 0 (boundary value 1) and outflow
+    at x = 1: the uniform field Y = 1 is steady (A Y = s without the time term)."""
+    n = 4
+    m = box_mesh(n, 3, 2, seed=6, stretch=2.0, permute=True)
+    u = 2.5
+    # face flux u |S| on x-normal faces, oriented owner -> neighbour
+    d = m.centre[m.neighbour] - m.centre[m.owner]
+    xface = np.abs(d[:, 0]) > 0
+    phi = np.where(xface, u * m.mag_sf * np.sign(d[:, 0]), 0.0)
+    out = m.b_centre[:, 0] > 1.0 - 1e-12
+    inl = m.b_centre[:, 0] < 1e-12
+    phi_b = np.where(out, u * m.b_mag_sf, np.where(inl, -u * m.b_mag_sf, 0.0))
+    A, s = fvm.species_matrix(m, phi=phi, phi_b=phi_b, Y_b=np.ones(m.b_cell.size))
+    assert np.max(np.abs(A @ np.ones(m.n_cells) - s)) <= 1e-13 * u
+    assert np.all(A - np.diag(np.diag(A)) <= 0.0)         # upwind: non-positive off-diagonals
+
+
+def test_ldu_round_trip_and_source_term():
+    m = box_mesh(3, 3, 2, seed=7, permute=True)
+    rng = np.random.default_rng(8)
+    S = rng.standard_normal(m.n_cells)
+    kap = rng.uniform(0.0, 1.0, m.n_cells)
+    A, s = fvm.species_matrix(m, gamma=np.ones(m.n_cells), gamma_b=np.ones(m.b_cell.size),
+                              Y_b=np.zeros(m.b_cell.size), S=S, kappa=kap)
+    assert np.allclose(s, m.volume * kap * S, rtol=1e-15, atol=0)
+    lo, up, dg = fvm.ldu(m, A)
+    B = np.diag(dg)
+    B[m.neighbour, m.owner] = lo
+    B[m.owner, m.neighbour] = up
+    assert np.array_equal(A, B)
+    assert np.array_equal(lo, up)                           # diffusion alone is symmetric
+
+
+def test_pasr_limits():
+    rho, mu, strain, delta = 1.2, 1.8e-4, 500.0, 1e-3
+    nu = (0.17 * delta) ** 2 * strain
+    tmix = 1.0 * np.sqrt((mu + rho * nu) / (rho * nu * strain ** 2))
+    k = fvm.pasr_kappa(np.array([tmix, 1e-30, 1e30]), np.full(3, rho), np.full(3, mu), np.full(3, strain),
+                       np.full(3, delta), 0.17, 1.0)
+    assert k[0] == pytest.approx(0.5, rel=1e-14)
+    assert k[1] < 1e-20 and k[2] == pytest.approx(1.0, rel=1e-12)
+    assert fvm.pasr_kappa(np.array([1e-4]), np.array([rho]), np.array([mu]), np.array([0.0]),
+                          np.array([delta]), 0.17, 1.0)[0] == 1.0
