@@ -182,6 +182,24 @@ def run_case(args):
     import paper_2312_13513_gb300 as cg
     from synth.mechanism import ch4_mechanism, h2_mechanism
     from synth.states import les_field, load_table
+    if args.case == "fvm":
+        side = max(2, int(round(args.cells ** (1.0 / 3.0))))
+        m, kw = _fvm_inputs(side)
+        gm = cg.FvMesh(m)
+        ms = []
+        for k in range(args.warmup + args.steps):
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            gm.assemble(**kw)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        print(json.dumps({"case": args.case, "cells": m.n_cells, "ms": ms,
+                          "gbs": fvm_bytes(m.n_cells, m.owner.size, m.b_cell.size) / (float(np.mean(ms)) * 1e-3) / 1e9}),
+              flush=True)
+        return
     if args.case == "transport":
         from synth.transport import generate_transport
         mech = ch4_mechanism()
@@ -443,6 +461,60 @@ def extra_surrogate_per_species(peaks, n_states=1 << 20, epochs=12):
     return out
 
 
+def _fvm_inputs(n_side, seed=21):
+    """A 128^3-style box in face-addressed form (natural numbering, mildly stretched) and seeded
+    species-equation inputs of realistic magnitude (cgs), all terms on."""
+    import torch
+    from synth.mesh import box_mesh
+    m = box_mesh(n_side, n_side, n_side, seed=seed, stretch=1.5)
+    rng = np.random.default_rng(seed + 1)
+    n, nf, nb = m.n_cells, m.owner.size, m.b_cell.size
+    dev = lambda a: torch.tensor(a, device="cuda")
+    kw = dict(dt=1e-6, rho=dev(rng.uniform(2e-4, 1.2e-3, n)), rho_old=dev(rng.uniform(2e-4, 1.2e-3, n)),
+              Y_old=dev(rng.uniform(0.0, 0.3, n)), phi=dev(rng.standard_normal(nf) * 1e-6),
+              phi_b=dev(rng.standard_normal(nb) * 1e-6), gamma=dev(rng.uniform(1e-4, 1e-3, n)),
+              gamma_b=dev(rng.uniform(1e-4, 1e-3, nb)), Y_b=dev(rng.uniform(0.0, 0.3, nb)),
+              S=dev(rng.standard_normal(n)), kappa=dev(rng.uniform(0.0, 1.0, n)))
+    return m, kw
+
+
+def fvm_bytes(n, nf, nb):
+    """Algorithmic bytes of one assembly with every term: per cell V, rho, rho_old, Y_old, gamma,
+    S, kappa read, diag and source written, its face-index range; per internal face owner,
+    neighbour, w, delta, |S|, phi read once, lower and upper written; per boundary face type,
+    delta, |S|, phi_b, gamma_b, Y_b; the cell-to-face codes."""
+    return n * (7 * 8 + 2 * 8 + 4) + nf * (8 + 4 * 8 + 2 * 8) + nb * (1 + 5 * 8) + (2 * nf + nb) * 4
+
+
+def extra_fvm(hbm_peak, reps=5):
+    """Species-equation assembly (Alg. 1 and the other terms) on a 128^3 box, ldu and CSR, and
+    the PaSR factor on the same cells."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    m, kw = _fvm_inputs(128)
+    gm = cg.FvMesh(m)
+    s = torch.cuda.current_stream()
+    out = gm.assemble(**kw)
+    ms = min(_time_ms(lambda: gm.assemble(**kw), s, reps))
+    lo, up, dg, _ = out
+    ms_csr = min(_time_ms(lambda: gm.to_csr(lo, up, dg), s, reps))
+    n, nf, nb = m.n_cells, m.owner.size, m.b_cell.size
+    byts = fvm_bytes(n, nf, nb)
+    rng = np.random.default_rng(5)
+    pin = [torch.tensor(a, device="cuda") for a in (10.0 ** rng.uniform(-7, -2, n), rng.uniform(2e-4, 1.2e-3, n),
+                                                     rng.uniform(1e-4, 6e-4, n), 10.0 ** rng.uniform(1, 5, n),
+                                                     np.full(n, 1.0 / 128))]
+    kap = torch.empty(n, dtype=torch.float64, device="cuda")
+    ms_pasr = min(_time_ms(lambda: cg.pasr_kappa(*pin, kappa=kap), s, reps))
+    return {"workload": f"species equation (implicit Euler, upwind convection, Alg. 1 Laplacian, fixed-value and "
+                        f"zero-gradient patches, PaSR-scaled source) on a 128^3 box: {n} cells, {nf} internal "
+                        f"faces, {nb} boundary faces",
+            "assemble_ms": ms, "assemble_gbs": byts / (ms * 1e-3) / 1e9,
+            "assemble_frac_of_hbm": byts / (ms * 1e-3) / 1e9 / hbm_peak, "algorithmic_bytes": byts,
+            "to_csr_ms": ms_csr, "csr_nnz": gm.nnz, "pasr_ms": ms_pasr,
+            "pasr_gbs": 6 * 8 * n / (ms_pasr * 1e-3) / 1e9}
+
+
 def extra_transport(fp64_peak, reps=3):
     """Transport and T-from-h kernels on the LES CH4 field (262144 cells) and the quasi-DNS H2
     field (2^20 cells)."""
@@ -585,7 +657,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["h2", "ch4", "surrogate", "surrogate_ps", "transport"], default=None,
+    ap.add_argument("--case", choices=["h2", "ch4", "surrogate", "surrogate_ps", "transport", "fvm"], default=None,
                     help="time one kernel family on a small case (profiling)")
     ap.add_argument("--cells", type=int, default=65536)
     ap.add_argument("--group", type=int, default=0, help="threads per cell (profiling mode; 0 = auto)")
@@ -733,6 +805,7 @@ def main():
         for name, fn in (("ch4_les", lambda: extra_ch4(fp64_peak)),
                          ("surrogate", lambda: extra_surrogate(_peaks())),
                          ("surrogate_per_species", lambda: extra_surrogate_per_species(_peaks())),
+                         ("fvm_species_assembly", lambda: extra_fvm(_peaks().get("hbm_gbs", 6800.0))),
                          ("graph_small_step", extra_graph),
                          ("thermo_transport", lambda: extra_transport(fp64_peak)),
                          ("serving", extra_serving)):

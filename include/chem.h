@@ -394,6 +394,74 @@ int chem_fast_exp(const double* x, double* y, int64_t n, chem_stream_t stream);
  * register-resident FMA chain kernel; synchronous. */
 int chem_fp64_fma_peak(double* tflops);
 
+/* ---------------------------------------------------------------------------------------
+ * Finite-volume species equation (the paper's species PDE, §3.1, with the Laplacian term of
+ * Alg. 1) and the PaSR factor of its LES closure (§2).
+ *
+ * A mesh is face-addressed as in the paper's ldu format: internal faces with owner < neighbour,
+ * per face the owner's linear-interpolation weight w, the delta coefficient (1 / centre
+ * distance) and the area |S|; boundary faces with their cell, patch type (0 zero-gradient,
+ * 1 fixed-value), delta coefficient (1 / face-to-centre distance) and area; cell volumes.
+ * ------------------------------------------------------------------------------------- */
+typedef struct chem_fvmesh_s* chem_fvmesh_t;
+typedef struct chem_fvmesh_desc {
+  int64_t n_cells, n_faces, n_bfaces;
+  const int32_t* owner;      /* [n_faces] host arrays, copied */
+  const int32_t* neighbour;  /* [n_faces], owner < neighbour */
+  const double* weight;      /* [n_faces] owner interpolation weight */
+  const double* delta;       /* [n_faces] */
+  const double* mag_sf;      /* [n_faces] */
+  const int32_t* b_cell;     /* [n_bfaces] */
+  const int8_t* b_type;      /* [n_bfaces] 0 zero-gradient, 1 fixed-value */
+  const double* b_delta;     /* [n_bfaces] */
+  const double* b_mag_sf;    /* [n_bfaces] */
+  const double* volume;      /* [n_cells] */
+} chem_fvmesh_desc;
+/* Upload a mesh; builds the cell-to-face index and the CSR pattern of its matrices.  At most
+ * 2^31 - 1 cells and 2^29 - 1 faces of each kind. */
+int chem_fvmesh_create(const chem_fvmesh_desc* desc, chem_fvmesh_t* out);
+int chem_fvmesh_free(chem_fvmesh_t mesh);
+/* The CSR pattern (device arrays owned by the mesh): row_ptr [n_cells + 1], col_idx [nnz],
+ * columns ascending within a row; the diagonal is always stored. */
+int chem_fvmesh_csr(chem_fvmesh_t mesh, int64_t* nnz, const int32_t** row_ptr, const int32_t** col_idx);
+
+/* Terms of one species equation over one step (device arrays; a NULL input leaves its term out):
+ *   (rho Y - rho_old Y_old) V / dt                                    if dt > 0
+ *   + sum_f F_f(Y)            upwind convection by the face mass flux phi (owner -> neighbour)
+ *                             and the outward boundary flux phi_b (inflow takes Y_b)
+ *   - sum_f a_f (Y_N - Y_P) - sum_{fixed-value b} a_b (Y_b - Y_P)      if gamma (= rho D)
+ *     with a_f = (w gamma_owner + (1 - w) gamma_neighbour) |S_f| delta_f  (Alg. 1) and
+ *     a_b = gamma_b |S_b| delta_b
+ *   = V kappa S               if S (kappa NULL: 1) */
+typedef struct chem_fvm_terms {
+  double dt;
+  const double* rho;         /* [n_cells] */
+  const double* rho_old;     /* [n_cells] */
+  const double* Y_old;       /* [n_cells] */
+  const double* phi;         /* [n_faces] */
+  const double* phi_b;       /* [n_bfaces] */
+  const double* gamma;       /* [n_cells] */
+  const double* gamma_b;     /* [n_bfaces] */
+  const double* Y_b;         /* [n_bfaces] boundary values (fixed-value faces, inflow) */
+  const double* S;           /* [n_cells] source per unit volume */
+  const double* kappa;       /* [n_cells] PaSR factor of S */
+} chem_fvm_terms;
+/* Assemble the matrix in ldu form: upper[f] = A[owner, neighbour], lower[f] = A[neighbour,
+ * owner], diag[c], and the right-hand side source[c] (nullable).  One kernel, no atomics;
+ * bitwise reproducible.  Asynchronous on stream. */
+int chem_fvm_assemble(chem_fvmesh_t mesh, const chem_fvm_terms* terms, double* lower, double* upper,
+                      double* diag, double* source, chem_stream_t stream);
+/* The same matrix as CSR values vals [nnz] on the mesh's pattern (for a linear solver). */
+int chem_fvm_to_csr(chem_fvmesh_t mesh, const double* lower, const double* upper, const double* diag,
+                    double* vals, chem_stream_t stream);
+/* PaSR factor per cell: kappa = tau_c / (tau_c + tau_mix), tau_mix = c_mix sqrt(mu_eff / (rho eps)),
+ * with the Smagorinsky sub-grid viscosity nu = (c_s Delta)^2 |S|, mu_eff = mu + rho nu and
+ * eps = nu |S|^2; kappa = 1 where eps = 0.  tau_c (the chemical time scale), rho, mu, strain
+ * (|S|) and delta (filter width): device arrays of n doubles.  Asynchronous on stream. */
+int chem_pasr_kappa(int64_t n, const double* tau_c, const double* rho, const double* mu,
+                    const double* strain, const double* delta, double c_s, double c_mix,
+                    double* kappa, chem_stream_t stream);
+
 const char* chem_last_error(void);
 
 #ifdef __cplusplus

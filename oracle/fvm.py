@@ -79,6 +79,49 @@ def species_matrix(mesh, dt=0.0, rho=None, rho_old=None, Y_old=None, phi=None, p
     return A, s
 
 
+def species_rows(mesh, cells, dt=0.0, rho=None, rho_old=None, Y_old=None, phi=None, phi_b=None,
+                 gamma=None, gamma_b=None, Y_b=None, S=None, kappa=None):
+    """The same equation for selected cells only (large meshes): {cell: ({column: value}, s)}."""
+    out = {}
+    V = mesh.volume
+    for P in cells:
+        P = int(P)
+        row = {P: 0.0}
+        s = 0.0
+        if dt > 0.0:
+            row[P] += rho[P] * V[P] / dt
+            s += rho_old[P] * Y_old[P] * V[P] / dt
+        for f in np.nonzero((mesh.owner == P) | (mesh.neighbour == P))[0]:
+            o, nb = int(mesh.owner[f]), int(mesh.neighbour[f])
+            other = nb if o == P else o
+            row.setdefault(other, 0.0)
+            if phi is not None:
+                Fout = phi[f] if o == P else -phi[f]
+                if Fout >= 0.0:
+                    row[P] += Fout
+                else:
+                    row[other] += Fout
+            if gamma is not None:
+                g = mesh.weight[f] * gamma[o] + (1.0 - mesh.weight[f]) * gamma[nb]
+                a = g * mesh.mag_sf[f] * mesh.delta[f]
+                row[P] += a
+                row[other] -= a
+        for b in np.nonzero(mesh.b_cell == P)[0]:
+            if phi_b is not None:
+                if phi_b[b] >= 0.0:
+                    row[P] += phi_b[b]
+                else:
+                    s -= phi_b[b] * Y_b[b]
+            if gamma is not None and mesh.b_type[b] == 1:
+                a = gamma_b[b] * mesh.b_mag_sf[b] * mesh.b_delta[b]
+                row[P] += a
+                s += a * Y_b[b]
+        if S is not None:
+            s += V[P] * (1.0 if kappa is None else kappa[P]) * S[P]
+        out[P] = (row, s)
+    return out
+
+
 def ldu(mesh, A):
     """(lower, upper, diag) of a dense matrix on the mesh's addressing."""
     o, nb = mesh.owner.astype(np.int64), mesh.neighbour.astype(np.int64)

@@ -163,6 +163,97 @@ class Transport:
             pass
 
 
+class FvMesh:
+    """chem_fvmesh_*: a face-addressed finite-volume mesh on the device (fields of a
+    synth.mesh.Mesh-like object: owner, neighbour, weight, delta, mag_sf, b_cell, b_type,
+    b_delta, b_mag_sf, volume, n_cells)."""
+
+    def __init__(self, mesh):
+        import torch
+        keep = [np.ascontiguousarray(mesh.owner, np.int32), np.ascontiguousarray(mesh.neighbour, np.int32),
+                np.ascontiguousarray(mesh.weight, np.float64), np.ascontiguousarray(mesh.delta, np.float64),
+                np.ascontiguousarray(mesh.mag_sf, np.float64), np.ascontiguousarray(mesh.b_cell, np.int32),
+                np.ascontiguousarray(mesh.b_type, np.int8), np.ascontiguousarray(mesh.b_delta, np.float64),
+                np.ascontiguousarray(mesh.b_mag_sf, np.float64), np.ascontiguousarray(mesh.volume, np.float64)]
+        d = _lib.FvMeshDesc(int(mesh.n_cells), keep[0].size, keep[5].size,
+                            *[a.ctypes.data_as(ctypes.c_void_p) for a in keep])
+        h = ctypes.c_void_p()
+        check(_lib.load().chem_fvmesh_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.n_cells, self.n_faces, self.n_bfaces = int(mesh.n_cells), keep[0].size, keep[5].size
+        nnz = ctypes.c_int64()
+        rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
+        check(_lib.load().chem_fvmesh_csr(h, ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)))
+        self.nnz = nnz.value
+
+    def assemble(self, dt=0.0, rho=None, rho_old=None, Y_old=None, phi=None, phi_b=None, gamma=None,
+                 gamma_b=None, Y_b=None, S=None, kappa=None, stream=None):
+        """chem_fvm_assemble: returns (lower, upper, diag, source) device tensors."""
+        import torch
+        for a, nm in ((rho, "rho"), (rho_old, "rho_old"), (Y_old, "Y_old"), (phi, "phi"), (phi_b, "phi_b"),
+                      (gamma, "gamma"), (gamma_b, "gamma_b"), (Y_b, "Y_b"), (S, "S"), (kappa, "kappa")):
+            _require(a, torch.float64, nm)
+        t = _lib.FvmTerms(float(dt), *[_ptr(a) for a in (rho, rho_old, Y_old, phi, phi_b, gamma, gamma_b, Y_b,
+                                                          S, kappa)])
+        dev = torch.device("cuda")
+        lower = torch.empty(self.n_faces, dtype=torch.float64, device=dev)
+        upper = torch.empty_like(lower)
+        diag = torch.empty(self.n_cells, dtype=torch.float64, device=dev)
+        source = torch.empty_like(diag)
+        check(_lib.load().chem_fvm_assemble(self.handle, ctypes.byref(t), _ptr(lower), _ptr(upper), _ptr(diag),
+                                            _ptr(source), _stream_ptr(stream)))
+        return lower, upper, diag, source
+
+    def to_csr(self, lower, upper, diag, stream=None):
+        """chem_fvm_to_csr: CSR values [nnz] on the mesh's pattern."""
+        import torch
+        vals = torch.empty(self.nnz, dtype=torch.float64, device=diag.device)
+        check(_lib.load().chem_fvm_to_csr(self.handle, _ptr(lower), _ptr(upper), _ptr(diag), _ptr(vals),
+                                          _stream_ptr(stream)))
+        return vals
+
+    def csr_pattern(self):
+        """(row_ptr, col_idx) of the mesh's CSR pattern, copied to host numpy arrays."""
+        import torch
+        nnz = ctypes.c_int64()
+        rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
+        check(_lib.load().chem_fvmesh_csr(self.handle, ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)))
+        row_ptr = torch.as_tensor(_DeviceArray(rp.value, self.n_cells + 1, "<i4"), device="cuda")
+        col = torch.as_tensor(_DeviceArray(ci.value, nnz.value, "<i4"), device="cuda")
+        return row_ptr.cpu().numpy(), col.cpu().numpy()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().chem_fvmesh_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """A library-owned device array exposed through __cuda_array_interface__ (to be copied, not written)."""
+
+    def __init__(self, ptr, count, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def pasr_kappa(tau_c, rho, mu, strain, delta, c_s=0.17, c_mix=1.0, kappa=None, stream=None):
+    """chem_pasr_kappa: PaSR factor per cell (device tensors)."""
+    import torch
+    for a, nm in ((tau_c, "tau_c"), (rho, "rho"), (mu, "mu"), (strain, "strain"), (delta, "delta")):
+        _require(a, torch.float64, nm)
+    if kappa is None:
+        kappa = torch.empty_like(tau_c)
+    check(_lib.load().chem_pasr_kappa(tau_c.numel(), _ptr(tau_c), _ptr(rho), _ptr(mu), _ptr(strain), _ptr(delta),
+                                      float(c_s), float(c_mix), _ptr(kappa), _stream_ptr(stream)))
+    return kappa
+
+
 def fast_exp(x, y, stream=None):
     """chem_fast_exp: y = exp(x) elementwise with the integrator's table-driven exponential."""
     import torch

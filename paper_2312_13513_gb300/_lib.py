@@ -64,6 +64,17 @@ class SurrogateDesc(ctypes.Structure):
                 ("box_hi", P)]
 
 
+class FvMeshDesc(ctypes.Structure):
+    _fields_ = [("n_cells", I64), ("n_faces", I64), ("n_bfaces", I64), ("owner", P), ("neighbour", P),
+                ("weight", P), ("delta", P), ("mag_sf", P), ("b_cell", P), ("b_type", P), ("b_delta", P),
+                ("b_mag_sf", P), ("volume", P)]
+
+
+class FvmTerms(ctypes.Structure):
+    _fields_ = [("dt", D), ("rho", P), ("rho_old", P), ("Y_old", P), ("phi", P), ("phi_b", P),
+                ("gamma", P), ("gamma_b", P), ("Y_b", P), ("S", P), ("kappa", P)]
+
+
 class SurrogatePsDesc(ctypes.Structure):
     _fields_ = [("n_species", I32), ("hidden", I32 * 3), ("dt", D), ("W", (P * 4) * 16),
                 ("b", (P * 4) * 16), ("x_mean", P), ("x_std", P), ("y_mean", P), ("y_std", P),
@@ -120,6 +131,12 @@ SIGNATURES = {
                                       ctypes.c_int, P, P]),
     "chem_gemm_bf16_act": (ctypes.c_int, [P, I64, P, I64, P, I64, P, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, P, P]),
+    "chem_fvmesh_create": (ctypes.c_int, [P, P]),
+    "chem_fvmesh_free": (ctypes.c_int, [P]),
+    "chem_fvmesh_csr": (ctypes.c_int, [P, P, P, P]),
+    "chem_fvm_assemble": (ctypes.c_int, [P, P, P, P, P, P, P]),
+    "chem_fvm_to_csr": (ctypes.c_int, [P, P, P, P, P, P]),
+    "chem_pasr_kappa": (ctypes.c_int, [I64, P, P, P, P, P, D, D, P, P]),
     "chem_last_error": (ctypes.c_char_p, []),
 }
 

@@ -97,3 +97,20 @@ def test_pasr_limits():
     assert k[1] < 1e-20 and k[2] == pytest.approx(1.0, rel=1e-12)
     assert fvm.pasr_kappa(np.array([1e-4]), np.array([rho]), np.array([mu]), np.array([0.0]),
                           np.array([delta]), 0.17, 1.0)[0] == 1.0
+
+
+def test_row_form_matches_the_dense_matrix():
+    m = box_mesh(4, 3, 3, seed=9, stretch=2.0, permute=True)
+    rng = np.random.default_rng(10)
+    nb = m.b_cell.size
+    kw = dict(dt=1e-3, rho=rng.uniform(0.5, 2, m.n_cells), rho_old=rng.uniform(0.5, 2, m.n_cells),
+              Y_old=rng.uniform(0, 1, m.n_cells), phi=rng.standard_normal(m.owner.size),
+              phi_b=rng.standard_normal(nb), gamma=rng.uniform(0.1, 1, m.n_cells), gamma_b=rng.uniform(0.1, 1, nb),
+              Y_b=rng.uniform(0, 1, nb), S=rng.standard_normal(m.n_cells), kappa=rng.uniform(0, 1, m.n_cells))
+    A, s = fvm.species_matrix(m, **kw)
+    rows = fvm.species_rows(m, range(m.n_cells), **kw)
+    for P, (row, sp) in rows.items():
+        dense = np.zeros(m.n_cells)
+        for c, v in row.items():
+            dense[c] = v
+        assert np.allclose(dense, A[P], rtol=1e-13, atol=1e-300) and sp == pytest.approx(s[P], rel=1e-13)
