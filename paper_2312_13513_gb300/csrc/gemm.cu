@@ -1,7 +1,8 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) for sm_103a:
 //   C[M x N] (FP32) = A[M x K] * B[N x K]^T (+ bias[N]),  A and B BF16 with K contiguous,
-// or, with the activation epilogue, C[M x N] (BF16) = bf16(GELU(A B^T + bias)) (exact erf GELU,
-// round to nearest even): the layer-by-layer inference of the per-species networks.
+// or, with the activation epilogue, C[M x N] (BF16) = bf16(GELU(A B^T + bias)) (the erf form of
+// GELU to 5e-7, gelu.cuh; round to nearest even): the layer-by-layer inference of the per-species
+// networks.
 //
 // Used by the surrogate's training (forward and backward products of §2's MLP, trained with
 // Adam); inference uses the fused kernel in surrogate.cu built from the same primitives.
@@ -20,6 +21,7 @@
 #include <mutex>
 
 #include "chem_internal.h"
+#include "gelu.cuh"
 #include "sm100.h"
 
 namespace chem {
@@ -87,7 +89,7 @@ struct GemmArgs {
   int* err;
 };
 
-__device__ __forceinline__ float gelu_erf(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+
 
 __global__ void __launch_bounds__(128, 2)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(128, 2)
           const int col = n0 + c0 + 2 * j;
           float v0 = __uint_as_float(r[2 * j]) + (a.bias && col < a.N ? a.bias[col] : 0.0f);
           float v1 = __uint_as_float(r[2 * j + 1]) + (a.bias && col + 1 < a.N ? a.bias[col + 1] : 0.0f);
-          if (a.gelu) { v0 = gelu_erf(v0); v1 = gelu_erf(v1); }
+          if (a.gelu) { v0 = gelu_f(v0); v1 = gelu_f(v1); }
           __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
           pk[j] = *reinterpret_cast<uint32_t*>(&h);
         }

@@ -38,6 +38,7 @@
 
 #include "chem_internal.h"
 #include "sm100.h"
+#include "gelu.cuh"
 #include "surrogate_model.h"
 #include "thermo.cuh"
 
@@ -74,8 +75,6 @@ struct SurParams {
   uint8_t* outbox;      // [ncells] 1 = features outside the training box
   int* err;
 };
-
-__device__ __forceinline__ float gelu_f(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -255,13 +254,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         ++nacc;
         tc_fence_after();
         const float* bias = P.bias[l];
-        // 64 columns per step: two TMEM loads in flight behind one wait; the 64 biases are read
-        // once per warp (one per lane) and broadcast by shuffles
+        // 64 columns per step: two TMEM loads in flight behind one wait; every lane needs the same
+        // 64 biases, read as warp-uniform 32-byte loads (one L1 transaction each, broadcast)
         for (int cc = half * (HID / 64); cc < (half + 1) * (HID / 64); cc += 2) {
           uint32_t a[2][32];
           tmem_ld32(trow + cc * 32, a[0]);
           tmem_ld32(trow + (cc + 1) * 32, a[1]);
-          const float bl[2] = {__ldg(bias + cc * 32 + lane), __ldg(bias + (cc + 1) * 32 + lane)};
           tmem_ld_wait();
           // columns cc*32 .. cc*32+63 form one 128-byte K chunk of the next layer's input
           unsigned char* chunk = arow + (cc >> 1) * ACT_CHUNK;
@@ -269,10 +267,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           for (int h = 0; h < 2; ++h) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+              // the eight biases of these columns: one uniform 32-byte load for the whole warp
+              const float4* b4 = reinterpret_cast<const float4*>(bias + (cc + h) * 32 + 8 * q);
+              const float4 b0 = __ldg(b4), b1 = __ldg(b4 + 1);
+              const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
               float v[8];
 #pragma unroll
-              for (int e = 0; e < 8; ++e)
-                v[e] = gelu_f(__uint_as_float(a[h][8 * q + e]) + __shfl_sync(0xffffffffu, bl[h], 8 * q + e));
+              for (int e = 0; e < 8; ++e) v[e] = gelu_f(__uint_as_float(a[h][8 * q + e]) + bv[e]);
               uint4 pk;
               pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
               pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
