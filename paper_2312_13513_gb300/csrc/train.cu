@@ -97,16 +97,36 @@ __global__ void k_transpose(const __nv_bfloat16* in, __nv_bfloat16* out, int R, 
   }
 }
 
-// column sums of a [R x C] FP32 matrix
-__global__ void k_colsum(const float* A, float* s, int R, int C) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  double acc = 0.0;
-  for (int r = 0; r < R; ++r) acc += A[(int64_t)r * C + c];
-  s[c] = (float)acc;
+// column sums of a [R x C] FP32 matrix, in two deterministic passes spread over the whole GPU:
+// block (x, y) sums rows [y * kColRows, ...) of 32 columns (8 thread rows, FP32, then the 8
+// partials in FP64) into part[y][c]; k_colsum_finish adds the row-block partials of a column.
+constexpr int kColRows = 64;
+__global__ void k_colsum_part(const float* A, double* part, int R, int C) {
+  __shared__ double red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int r0 = blockIdx.y * kColRows;
+  float acc = 0.0f;
+  if (c < C)
+    for (int r = r0 + threadIdx.y; r < min(R, r0 + kColRows); r += 8) acc += A[(int64_t)r * C + c];
+  red[threadIdx.y][threadIdx.x] = (double)acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < C) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+    part[(int64_t)blockIdx.y * C + c] = t;
+  }
 }
 
-// Adam on a [rows x cols] parameter block (cols = 1 for biases); writes BF16 W and W^T if given
+__global__ void k_colsum_finish(const double* part, float* s, int nparts, int C) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double t = 0.0;
+  for (int i = 0; i < nparts; ++i) t += part[(int64_t)i * C + c];
+  s[c] = (float)t;
+}
+
+// Adam on a [rows x cols] parameter block (cols = 1 for biases); writes the BF16 copy of W if given
+// (its transpose follows by the tiled k_transpose)
 __global__ void k_adam(float* W, const float* G, float* m, float* v, __nv_bfloat16* Wb, __nv_bfloat16* Wt,
                        int rows, int cols, float lr, float b1, float b2, float eps, float c1, float c2) {
   const int64_t n = (int64_t)rows * cols;
@@ -118,12 +138,7 @@ __global__ void k_adam(float* W, const float* G, float* m, float* v, __nv_bfloat
     v[i] = vi;
     const float w = W[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     W[i] = w;
-    if (Wb) {
-      const __nv_bfloat16 wb = __float2bfloat16_rn(w);
-      Wb[i] = wb;
-      const int r = (int)(i / cols), c = (int)(i % cols);
-      Wt[(int64_t)c * rows + r] = wb;
-    }
+    if (Wb) Wb[i] = __float2bfloat16_rn(w);
   }
 }
 
@@ -267,6 +282,7 @@ struct chem_trainer_s {
   float* Z[MAXL];                  // pre-activations [B x out_pad]
   __nv_bfloat16* A[MAXL];          // A[0] = caller's input, A[l] = bf16(GELU(Z[l-1]))
   float *dA, *dZf;
+  double* colpart;                 // row-block partial column sums [B / 64 x max width]
   __nv_bfloat16 *dZb, *dZt, *At;
   int* err;
   double* loss;
@@ -367,6 +383,7 @@ extern "C" int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden,
   if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 2), t->dZb = (__nv_bfloat16*)p;
   if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 2), t->dZt = (__nv_bfloat16*)p;
   if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 2), t->At = (__nv_bfloat16*)p;
+  if (!rc) rc = tr_alloc(t, &p, (size_t)((batch + kColRows - 1) / kColRows) * maxw * 8), t->colpart = (double*)p;
   if (!rc) rc = tr_alloc(t, &p, 16), t->err = (int*)p;
   if (!rc) rc = tr_alloc(t, &p, 16), t->loss = (double*)p;
   if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "trainer init");
@@ -414,7 +431,11 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
     int rc = gemm_bf16(t->dZt, B, t->At, B, t->dW[l], nin, nullptr, nout, nin, B, t->err, st);
     if (rc) return rc;
     if (l == 0) k_fold_split_grad<<<(nout + 127) / 128, 128, 0, st>>>(t->dW[0], nout, nin, t->nin);
-    k_colsum<<<(nout + 127) / 128, 128, 0, st>>>(t->dZf, t->db[l], B, nout);
+    {
+      const int nparts = (B + kColRows - 1) / kColRows;
+      k_colsum_part<<<dim3((nout + 31) / 32, nparts), dim3(32, 8), 0, st>>>(t->dZf, t->colpart, B, nout);
+      k_colsum_finish<<<(nout + 127) / 128, 128, 0, st>>>(t->colpart, t->db[l], nparts, nout);
+    }
     if (l > 0) {
       rc = gemm_bf16(t->dZb, nout, t->Wt[l], nout, t->dA, nin, nullptr, B, nin, nout, t->err, st);
       if (rc) return rc;
@@ -436,8 +457,9 @@ extern "C" int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float
   for (int l = 0; l < t->nl; ++l) {
     const int r = t->out_pad[l], c = t->in_pad[l];
     k_adam<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[l], t->dW[l], t->mW[l], t->vW[l],
-                                                      l == 0 ? nullptr : t->Wb[l], t->Wt[l], r, c, lr, beta1,
+                                                      l == 0 ? nullptr : t->Wb[l], nullptr, r, c, lr, beta1,
                                                       beta2, eps, c1, c2);
+    if (l > 0) k_transpose<<<dim3((c + 31) / 32, (r + 31) / 32), dim3(32, 8), 0, st>>>(t->Wb[l], t->Wt[l], r, c);
     if (l == 0) k_split_bf16<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[0], t->Wb[0], r, c, t->nin);
     k_adam<<<grid_for(r), 256, 0, st>>>(t->b[l], t->db[l], t->mb[l], t->vb[l], nullptr, nullptr, r, 1, lr, beta1,
                                         beta2, eps, c1, c2);
