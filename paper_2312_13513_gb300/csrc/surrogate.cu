@@ -64,6 +64,7 @@ constexpr float BC_LAMBDA = SUR_BC_LAMBDA;
 
 struct SurParams {
   const float* bias[5];
+  float hb[4][HID];     // hidden-layer biases by value: read from the parameter (constant) bank
   const float *xmu, *xsd, *ymu, *ysd, *lo, *hi;
   int ns, nin;
   const double* T;
@@ -93,7 +94,7 @@ constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 __global__ void __launch_bounds__(kFwdThreads, 1)
     surrogate_forward_kernel(const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
                              const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4,
-                             const __grid_constant__ CUtensorMap tW5, const SurParams P) {
+                             const __grid_constant__ CUtensorMap tW5, const __grid_constant__ SurParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* act = smem;
@@ -253,9 +254,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         if (!__all_sync(0xffffffffu, mbar_wait(acc_done, (uint32_t)(nacc & 1), P.err))) { ok = false; break; }
         ++nacc;
         tc_fence_after();
-        const float* bias = P.bias[l];
+        const float* bias = P.hb[l];
         // 64 columns per step: two TMEM loads in flight behind one wait; every lane needs the same
-        // 64 biases, read as warp-uniform 32-byte loads (one L1 transaction each, broadcast)
+        // 64 biases, warp-uniform reads of the kernel's parameter bank (constant cache)
         for (int cc = half * (HID / 64); cc < (half + 1) * (HID / 64); cc += 2) {
           uint32_t a[2][32];
           tmem_ld32(trow + cc * 32, a[0]);
@@ -267,10 +268,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           for (int h = 0; h < 2; ++h) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              // the eight biases of these columns: one uniform 32-byte load for the whole warp
-              const float4* b4 = reinterpret_cast<const float4*>(bias + (cc + h) * 32 + 8 * q);
-              const float4 b0 = __ldg(b4), b1 = __ldg(b4 + 1);
-              const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+              // the eight biases of these columns, warp-uniform reads of the parameter bank
+              const float* bq = bias + (cc + h) * 32 + 8 * q;
+              const float bv[8] = {bq[0], bq[1], bq[2], bq[3], bq[4], bq[5], bq[6], bq[7]};
               float v[8];
 #pragma unroll
               for (int e = 0; e < 8; ++e) v[e] = gelu_f(__uint_as_float(a[h][8 * q + e]) + bv[e]);
@@ -503,6 +503,7 @@ int surrogate_forward(chem_model_s* md, const double* T, const double* p, const 
   }
   SurParams P;
   for (int l = 0; l < 5; ++l) P.bias[l] = md->bias[l];
+  memcpy(P.hb, md->hbias, sizeof(P.hb));
   P.xmu = md->xmu; P.xsd = md->xsd; P.ymu = md->ymu; P.ysd = md->ysd; P.lo = md->lo; P.hi = md->hi;
   P.ns = md->ns; P.nin = md->nin; P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells;
   P.ynet = ynet; P.zout = zout; P.outbox = outbox; P.err = err;
@@ -573,6 +574,7 @@ extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t m
   // FP32: 4 hidden biases, padded output bias, statistics
   std::vector<float> fb(4 * HID + NOUT + 6 * KIN, 0.0f);
   for (int l = 0; l < 4; ++l) memcpy(&fb[l * HID], d->b[l], HID * sizeof(float));
+  for (int l = 0; l < 4; ++l) memcpy(md->hbias[l], d->b[l], HID * sizeof(float));
   memcpy(&fb[4 * HID], d->b[4], ns * sizeof(float));
   float* st = &fb[4 * HID + NOUT];
   for (int i = 0; i < nin; ++i) {

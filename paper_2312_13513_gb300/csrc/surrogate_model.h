@@ -40,6 +40,7 @@ struct chem_model_s {
   const float* bias[5] = {};
   const float *xmu = nullptr, *xsd = nullptr, *ymu = nullptr, *ysd = nullptr, *lo = nullptr, *hi = nullptr;
   CUtensorMap tw[5];
+  float hbias[4][512];       // host copy of the hidden-layer biases (single network)
   // per-species networks (kind 1)
   int h[3] = {0, 0, 0};
   int nnet = 0;
