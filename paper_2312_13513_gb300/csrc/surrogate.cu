@@ -411,10 +411,17 @@ __global__ void surrogate_post_kernel(const PostParams P) {
         // temperature from enthalpy conservation: h(T, Y'') = h(T0, Y0)
         double h0, cp0;
         h_cp_mass(P.blob, P.lay, T0, P.Y, 0, cell, Y0, &h0, &cp0);
+        // the new composition is fixed during the iteration: its mixture polynomial once per
+        // temperature range visited
+        double Ah[6], Ac[5];
+        int rg = Tn < TMID ? 0 : 1;
+        mixture_nasa(P.blob, P.lay, rg, Y1, Ah, Ac);
         bool conv = false;
         for (int it = 0; it < 50; ++it) {
+          const int r = Tn < TMID ? 0 : 1;
+          if (r != rg) { rg = r; mixture_nasa(P.blob, P.lay, rg, Y1, Ah, Ac); }
           double hh, cp;
-          h_cp_mass(P.blob, P.lay, Tn, P.Y, 0, cell, Y1, &hh, &cp);
+          h_cp_from_mixture(Ah, Ac, Tn, &hh, &cp);
           const double dT = (hh - h0) / cp;
           Tn -= dT;
           if (!(Tn >= 200.0 && Tn <= 6000.0)) break;

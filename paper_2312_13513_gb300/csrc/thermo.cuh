@@ -34,4 +34,33 @@ __device__ __forceinline__ void h_cp_mass(const unsigned char* blob, const MechL
   *cp = RU * cs;
 }
 
+// The mixture's NASA-7 polynomials for one temperature range: for mass fractions Yloc,
+// Ah[i] = sum_k Y_k / W_k a_ik (the h/RT coefficients, a6 included) and Ac[i] likewise for cp/R,
+// so that h = R T (Ah0 + Ah1 T + ... + Ah4 T^4 + Ah5 / T) and cp = R (Ac0 + ... + Ac4 T^4): a
+// Newton iteration on T at fixed composition then costs one polynomial instead of one per
+// species (the same sums, reordered).
+__device__ __forceinline__ void mixture_nasa(const unsigned char* blob, const MechLayout& L, int rg,
+                                             const double* Yloc, double Ah[6], double Ac[5]) {
+  const int ns = L.ns;
+  const double* hc = (const double*)(blob + L.o_hc);
+  const double* cc = (const double*)(blob + L.o_cpc);
+  const double* invW = (const double*)(blob + L.o_invW);
+  for (int i = 0; i < 6; ++i) Ah[i] = 0.0;
+  for (int i = 0; i < 5; ++i) Ac[i] = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    const double yw = Yloc[k] * __ldg(invW + k);
+    const double* a = hc + (rg * ns + k) * 6;
+    const double* c = cc + (rg * ns + k) * 5;
+    for (int i = 0; i < 6; ++i) Ah[i] = fma(yw, a[i], Ah[i]);
+    for (int i = 0; i < 5; ++i) Ac[i] = fma(yw, c[i], Ac[i]);
+  }
+}
+
+__device__ __forceinline__ void h_cp_from_mixture(const double Ah[6], const double Ac[5], double T, double* h,
+                                                  double* cp) {
+  const double hRT = Ah[0] + T * (Ah[1] + T * (Ah[2] + T * (Ah[3] + T * Ah[4]))) + Ah[5] / T;
+  *h = RU * T * hRT;
+  *cp = RU * (Ac[0] + T * (Ac[1] + T * (Ac[2] + T * (Ac[3] + T * Ac[4]))));
+}
+
 }  // namespace chem
