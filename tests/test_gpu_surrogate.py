@@ -336,3 +336,37 @@ def test_trained_surrogate_heat_release_error_vs_oracle(h2, om_h2):
     Tn = Td.cpu().numpy()
     h1 = np.array([om_h2.enthalpy_mass(Tn[i], Ys[:, i]) for i in net])
     assert np.max(np.abs(h1 - h0) / np.abs(h0).max()) <= 1e-8
+
+
+def test_trained_network_gains_over_frozen_chemistry_and_an_untrained_network(h2, om_h2):
+    """What the training buys: on held-out quasi-DNS cells the shipped model's heat-release error
+    is <= 1 %, frozen chemistry (no change over the step) is off by 100 % by construction, and a
+    network with the same shape, statistics and trust box but untrained weights is at least ten
+    times worse than the trained one."""
+    from paper_2312_13513_gb300 import train as trn
+    f = quasi_dns_field(load_table("h2_flamelet.npz"), n=1 << 21, seed=4343)
+    rng = np.random.default_rng(6)
+    s = np.sort(rng.choice(f["T"].size, 5000, replace=False))
+    T0, p, Y0 = f["T"][s], f["p"][s], f["Y"][:, s]
+    dm = cg.Mechanism(h2)
+    T1, Y1 = om_h2.advance(T0, p, Y0, 5e-7, 1e-6, 1e-10)[:2]
+    q_ref = np.array([osur.heat_release(om_h2, T0[i], p[i], Y0[:, i], Y1[:, i], 5e-7) for i in range(T0.size)])
+
+    def err_of(model):
+        Td, pd, Yd = to_dev(T0, p, Y0)
+        cg.surrogate_advance(model, Td, pd, Yd, 5e-7)
+        torch.cuda.synchronize()
+        Ys = Yd.cpu().numpy()
+        q = np.array([osur.heat_release(om_h2, T0[i], p[i], Y0[:, i], Ys[:, i], 5e-7) for i in range(T0.size)])
+        return osur.hrr_error(q, q_ref)
+
+    trained = err_of(cg.Surrogate(dm, path=MODEL))
+    prm = trn.load_model_params(MODEL)
+    r = np.random.default_rng(7)
+    prm["W"] = [r.standard_normal(w.shape) / np.sqrt(w.shape[1]) for w in prm["W"]]
+    prm["b"] = [np.zeros_like(b) for b in prm["b"]]
+    untrained = err_of(cg.Surrogate(dm, prm))
+    frozen = osur.hrr_error(np.zeros_like(q_ref), q_ref)
+    assert trained <= 0.01, trained
+    assert frozen == pytest.approx(1.0)
+    assert untrained >= 10.0 * trained, (untrained, trained)
