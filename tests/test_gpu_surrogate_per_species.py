@@ -65,7 +65,9 @@ def _oracle_z(prm, T, p, Y, ns):
     return z
 
 
-@pytest.mark.parametrize("hidden,n", [((256, 200, 136), 300), ((1600, 800, 400), 1000)])
+@pytest.mark.parametrize("hidden,n", [((256, 200, 136), 300), ((1600, 800, 400), 1000),
+                                      ((128, 136, 128), 5),              # below one 128-row tile
+                                      ((256, 200, 136), 16384 + 77)])    # two chunks, ragged tail
 def test_per_species_forward_matches_oracle(h2, hidden, n):
     dm = cg.Mechanism(h2)
     T, p, Y = random_states(h2, n, 31, "H2", Tlo=300.0, Thi=2500.0)
