@@ -320,7 +320,8 @@ constexpr int NEMAX = 8;
 struct PostParams {
   const unsigned char* blob;   // mechanism blob (global memory)
   MechLayout lay;
-  const double* Aem;           // [ne][ns] element mass fractions a_ek M_e / W_k
+  const double* Aem;           // [ne][ns] element mass fractions a_ek M_e / W_k, then the pair
+                               // products A_ek A_fk, e >= f ([ne (ne + 1) / 2][ns])
   int ne;
   double* T;
   const double* p;
@@ -361,10 +362,13 @@ __global__ void surrogate_post_kernel(const PostParams P) {
         b[e] = sb;
         rr[e] = sr - sb;
       }
+      double Yp[MAXNS];
+      for (int k = 0; k < ns; ++k) Yp[k] = Y1[k] + 1e-12;
+      const double* AA = P.Aem + ne * ns;
       for (int e = 0; e < ne; ++e)
-        for (int f = 0; f <= e; ++f) {
+        for (int f = 0; f <= e; ++f, AA += ns) {
           double s = 0.0;
-          for (int k = 0; k < ns; ++k) s += P.Aem[e * ns + k] * (Y1[k] + 1e-12) * P.Aem[f * ns + k];
+          for (int k = 0; k < ns; ++k) s = fma(AA[k], Yp[k], s);
           G[e][f] = s;
           G[f][e] = s;
         }
@@ -541,6 +545,22 @@ int launch_advance_counted(chem_mech_s* m, double* T, const double* p, double* Y
 
 using namespace chem;
 
+// Element mass fractions A[e][k] = a_ek M_e / W_k ([ne][ns]), followed by the products
+// A[e][k] A[f][k] of every pair e <= f ([ne (ne + 1) / 2][ns], pairs in row order), which the
+// projection's normal matrix sum_k A_ek A_fk (Y_k + 1e-12) needs per cell.
+static std::vector<double> element_matrices(chem_mech_t mech, int ns) {
+  const int ne = mech->ne;
+  std::vector<double> A((size_t)ne * ns + (size_t)ne * (ne + 1) / 2 * ns);
+  for (int e = 0; e < ne; ++e)
+    for (int k = 0; k < ns; ++k)
+      A[(size_t)e * ns + k] = mech->comp[(size_t)k * ne + e] * mech->elem_mass[e] / mech->W[k];
+  size_t o = (size_t)ne * ns;
+  for (int e = 0; e < ne; ++e)
+    for (int f = 0; f <= e; ++f, o += ns)
+      for (int k = 0; k < ns; ++k) A[o + k] = A[(size_t)e * ns + k] * A[(size_t)f * ns + k];
+  return A;
+}
+
 extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t mech, chem_model_t* out) {
   if (!d || !mech || !out) { set_error("NULL argument"); return CHEM_EINVAL; }
   *out = nullptr;
@@ -594,10 +614,7 @@ extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t m
     st[2 * KIN + k] = d->y_mean[k];
     st[3 * KIN + k] = d->y_std[k];
   }
-  std::vector<double> A((size_t)mech->ne * ns);
-  for (int e = 0; e < mech->ne; ++e)
-    for (int k = 0; k < ns; ++k)
-      A[(size_t)e * ns + k] = mech->comp[(size_t)k * mech->ne + e] * mech->elem_mass[e] / mech->W[k];
+  std::vector<double> A = element_matrices(mech, ns);
   auto fail = [&](int rc) { chem_surrogate_free(md); return rc; };
   if (cudaGetDevice(&md->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaGetDevice"));
   cudaError_t e1 = cudaMalloc(&md->d_w, wb.size() * 2);
@@ -701,10 +718,7 @@ extern "C" int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* d
     st[2 * KIN + k] = d->y_mean[k];
     st[3 * KIN + k] = d->y_std[k];
   }
-  std::vector<double> A((size_t)mech->ne * ns);
-  for (int e = 0; e < mech->ne; ++e)
-    for (int k = 0; k < ns; ++k)
-      A[(size_t)e * ns + k] = mech->comp[(size_t)k * mech->ne + e] * mech->elem_mass[e] / mech->W[k];
+  std::vector<double> A = element_matrices(mech, ns);
   auto fail = [&](int rc) { chem_surrogate_free(md); return rc; };
   if (cudaGetDevice(&md->device) != cudaSuccess) return fail(cuda_fail(cudaGetLastError(), "cudaGetDevice"));
   cudaError_t e1 = cudaMalloc(&md->d_w, wb.size() * 2);
