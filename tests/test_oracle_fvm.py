@@ -114,3 +114,28 @@ def test_row_form_matches_the_dense_matrix():
         for c, v in row.items():
             dense[c] = v
         assert np.allclose(dense, A[P], rtol=1e-13, atol=1e-300) and sp == pytest.approx(s[P], rel=1e-13)
+
+
+@pytest.mark.parametrize("shape,permute", [((5, 4, 3), True), ((1, 1, 1), False), ((8, 1, 1), True)])
+def test_mesh_generator_geometry(shape, permute):
+    """Face counts, owner < neighbour in upper-triangular order, interpolation weights in (0, 1)
+    that reproduce the face position, volumes and boundary areas of the unit box."""
+    nx, ny, nz = shape
+    m = box_mesh(nx, ny, nz, seed=21, stretch=3.0, permute=permute)
+    n = nx * ny * nz
+    assert m.n_cells == n
+    assert m.owner.size == (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1)
+    assert m.b_cell.size == 2 * (ny * nz + nx * nz + nx * ny)
+    assert np.all(m.owner < m.neighbour)
+    assert np.all(np.diff(m.owner) >= 0)
+    assert np.all((m.weight > 0.0) & (m.weight < 1.0))
+    assert m.volume.sum() == pytest.approx(1.0, rel=1e-13)
+    assert m.b_mag_sf.sum() == pytest.approx(6.0, rel=1e-13)
+    d = m.centre[m.neighbour] - m.centre[m.owner]
+    assert np.allclose(1.0 / np.linalg.norm(d, axis=1), m.delta, rtol=1e-13)
+    # w x_owner + (1 - w) x_neighbour lies on the face between them (along the connecting axis)
+    xf = m.weight[:, None] * m.centre[m.owner] + (1.0 - m.weight[:, None]) * m.centre[m.neighbour]
+    ax = np.argmax(np.abs(d), axis=1)
+    lo = np.minimum(m.centre[m.owner, ax], m.centre[m.neighbour, ax])
+    hi = np.maximum(m.centre[m.owner, ax], m.centre[m.neighbour, ax])
+    assert np.all((xf[np.arange(ax.size), ax] > lo) & (xf[np.arange(ax.size), ax] < hi))
