@@ -467,7 +467,9 @@ __device__ __forceinline__ void eval_fj(const Grp<G>& g, const MechView& m, cons
     if (pr.z >= 0) invKc *= eg[pr.z];
     for (int d = ri.y; d > 0; --d) invKc *= ep1;
     for (int d = ri.y; d < 0; ++d) invKc *= iep1;
-    if (!(invKc > 0.0 && invKc < 1.0e300)) {            // range fallback: exp of dG directly
+    // range fallback (exp of dG directly) unless invKc is a positive normal number below 2^995;
+    // the test reads the exponent bits (integer work, no FP64 compare)
+    if ((unsigned)__double2hiint(invKc) - 0x00100000u >= 0x7e200000u - 0x00100000u) {
       if (re.x >= 0) dG -= w.gRT[re.x];
       if (re.y >= 0) dG -= w.gRT[re.y];
       if (re.z >= 0) dG -= w.gRT[re.z];
@@ -476,11 +478,16 @@ __device__ __forceinline__ void eval_fj(const Grp<G>& g, const MechView& m, cons
       if (pr.z >= 0) dG += w.gRT[pr.z];
       invKc = exp(dG - (double)ri.y * lnPR);
     }
+    const double mult = (ri.x == 1) ? Mc : 1.0;
+    if (!jac) {
+      // q = kf (Pf - Pr / Kc): one FMA for the difference of the two directions
+      w.q[j] = kf * fma(-invKc, Pr, Pf) * mult;
+      continue;
+    }
     const double kr = kf * invKc;
     const double fwd = kf * Pf, rev = kr * Pr;
-    const double mult = (ri.x == 1) ? Mc : 1.0;
     w.q[j] = (fwd - rev) * mult;
-    if (jac) {
+    {                                                     // the Jacobian's per-reaction numbers
       if (re.x >= 0) dH -= w.hRT[re.x];
       if (re.y >= 0) dH -= w.hRT[re.y];
       if (re.z >= 0) dH -= w.hRT[re.z];
