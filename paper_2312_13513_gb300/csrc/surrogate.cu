@@ -413,8 +413,7 @@ __global__ void surrogate_post_kernel(const PostParams P) {
       }
       if (pass) {
         // temperature from enthalpy conservation: h(T, Y'') = h(T0, Y0)
-        double h0, cp0;
-        h_cp_mass(P.blob, P.lay, T0, P.Y, 0, cell, Y0, &h0, &cp0);
+        const double h0 = h_mass(P.blob, P.lay, T0, Y0);
         // the new composition is fixed during the iteration: its mixture polynomial once per
         // temperature range visited
         double Ah[6], Ac[5];

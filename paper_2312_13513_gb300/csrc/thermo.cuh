@@ -34,6 +34,23 @@ __device__ __forceinline__ void h_cp_mass(const unsigned char* blob, const MechL
   *cp = RU * cs;
 }
 
+// Mass-specific enthalpy alone (erg/g, formation included) of the composition Yloc at T.
+__device__ __forceinline__ double h_mass(const unsigned char* blob, const MechLayout& L, double T,
+                                         const double* Yloc) {
+  const int ns = L.ns;
+  const int rg = T < TMID ? 0 : 1;
+  const double* hc = (const double*)(blob + L.o_hc);
+  const double* invW = (const double*)(blob + L.o_invW);
+  const double invT = 1.0 / T;
+  double hs = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    const double* a = hc + (rg * ns + k) * 6;
+    const double hRT = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4]))) + a[5] * invT;
+    hs += Yloc[k] * hRT * __ldg(invW + k);
+  }
+  return RU * T * hs;
+}
+
 // The mixture's NASA-7 polynomials for one temperature range: for mass fractions Yloc,
 // Ah[i] = sum_k Y_k / W_k a_ik (the h/RT coefficients, a6 included) and Ac[i] likewise for cp/R,
 // so that h = R T (Ah0 + Ah1 T + ... + Ah4 T^4 + Ah5 / T) and cp = R (Ac0 + ... + Ac4 T^4): a
