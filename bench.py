@@ -42,6 +42,27 @@ WORKLOAD = ("FP64 Rodas4 chemistry advance, 2^20 cells of a 128^3 quasi-DNS H2/a
 # was measured on.
 TRAFFIC = {"bytes_per_launch": 16 * (6013952 + 0), "source_sha1": "d641dd08253098b82348cc5a0efac85caa814942"}
 
+# The paper's chemistry time per step for its H2-air case (Table 1, Section 3.2), in seconds:
+# CVODE on one CPU core and DNN inference on one GPU card, on uniform meshes of 32^3, 64^3 and
+# 128^3 cells.  Neither the card nor the CPU is named beside the table (the roofline figure of the
+# same section shows V100 and T4).  Quoted in the output as context, never used as a target.
+PAPER_TABLE1_CHEMISTRY_S = {32: (4.7, 0.007), 64: (34.24, 0.053), 128: (253.86, 0.41)}
+
+
+def paper_context():
+    """Table 1's chemistry columns as rates: cells advanced per second by each side of the
+    paper's comparison, and their quotient (the paper's chemistry speedup)."""
+    rows = {}
+    for side, (cpu_s, gpu_s) in PAPER_TABLE1_CHEMISTRY_S.items():
+        n = side ** 3
+        rows[f"{side}^3"] = {"cpu_cvode_s": cpu_s, "gpu_dnn_s": gpu_s,
+                             "cpu_cvode_cell_updates_per_s_per_core": n / cpu_s,
+                             "gpu_dnn_cell_updates_per_s": n / gpu_s, "chemistry_speedup": cpu_s / gpu_s}
+    return {"source": "Table 1 (Section 3.2): H2-air, 9 species, per-step chemistry time",
+            "hardware": "one GPU card, not named (V100 and T4 in the same section's roofline figure), "
+                        "against one CPU core, not named",
+            "rows": rows}
+
 
 def _sha1_of_kernel():
     p = os.path.join(ROOT, "paper_2312_13513_gb300", "csrc", "integrator.cu")
@@ -797,6 +818,7 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clk,
         "substeps": {"accepted_mean": acc / n, "attempts_mean": att / n, "non_ok_cells": bad},
+        "paper_context": paper_context(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(field, mech)

@@ -184,6 +184,13 @@ def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5,
 PER_SPECIES_HIDDEN = (1600, 800, 400)
 
 
+def networked_species(y_std):
+    """Species that get a network of their own (§2: none for inert species).  The training
+    statistics give y_std = 0 exactly to a species whose increment over dt is zero in every state,
+    which is what an inert species (one that no reaction produces or consumes) shows."""
+    return [k for k in range(len(y_std)) if float(y_std[k]) > 0.0]
+
+
 def train_per_species(mech, n_states=1 << 21, epochs=20, batch=4096, lr=3e-4, lr_final=1e-5, dt=5e-7,
                       seed=7, log=print, time_budget_s=None, front_fraction=0.5, hidden=PER_SPECIES_HIDDEN,
                       data=None):
@@ -198,7 +205,7 @@ def train_per_species(mech, n_states=1 << 21, epochs=20, batch=4096, lr=3e-4, lr
         data = make_dataset(mech, dm, n_states, dt, seed, front_fraction=front_fraction)
     log(f"dataset: {data['X'].shape[0]} states in {time.time() - t0:.1f} s")
     ns = mech.ns
-    species = [k for k in range(ns) if float(data["stats"]["y_std"][k]) > 0.0]
+    species = networked_species(data["stats"]["y_std"])
     trainers = {k: Trainer(ns + 2, 1, batch, seed=seed + 17 * k, hidden=hidden) for k in species}
     X, Tt = data["X"], data["T"]
     n = X.shape[0]
