@@ -41,31 +41,35 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB_PATH)
-        P = ctypes.c_void_p
-        d = ctypes.c_double
-        i = ctypes.c_int
-        i64 = ctypes.c_int64
-        L.or_mech_new.restype = P
-        L.or_mech_new.argtypes = [i, i, i] + [P] * 13
-        L.or_mech_free.argtypes = [P]
-        L.or_species_thermo.argtypes = [P, d, P, P, P, P]
-        L.or_rates.argtypes = [P, d, d, P, P, P, P, P]
-        L.or_rhs.argtypes = [P, d, P, P]
-        L.or_rhs_complex.argtypes = [P, d, P, P, P, P]
-        L.or_jacobian.argtypes = [P, d, P, P]
-        L.or_jacobian_complex_step.argtypes = [P, d, P, P]
-        L.or_rodas4.argtypes = [P, d, P, d, d, d, i, P, P]
-        L.or_rodas4.restype = i
-        L.or_advance.argtypes = [P, i64, P, P, P, i64, d, d, d, P, P, i]
-        L.or_advance_dt.argtypes = [P, i64, P, P, P, i64, P, d, d, P, i]
-        L.or_rk4.argtypes = [P, d, P, d, i64]
-        L.or_rodas4_tableau.argtypes = [P, P, P, P, P]
-        L.or_rodas4_linear.argtypes = [i, P, P, d, i, P]
-        L.or_count_ops.argtypes = [P, d, P, d, d, d, P, P, P]
-        L.or_count_ops.restype = i
-        _lib = L
+        _lib = declare(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+def declare(L):
+    """Set the argument and result types of the oracle's C functions on a loaded library."""
+    P = ctypes.c_void_p
+    d = ctypes.c_double
+    i = ctypes.c_int
+    i64 = ctypes.c_int64
+    L.or_mech_new.restype = P
+    L.or_mech_new.argtypes = [i, i, i] + [P] * 13
+    L.or_mech_free.argtypes = [P]
+    L.or_species_thermo.argtypes = [P, d, P, P, P, P]
+    L.or_rates.argtypes = [P, d, d, P, P, P, P, P]
+    L.or_rhs.argtypes = [P, d, P, P]
+    L.or_rhs_complex.argtypes = [P, d, P, P, P, P]
+    L.or_jacobian.argtypes = [P, d, P, P]
+    L.or_jacobian_complex_step.argtypes = [P, d, P, P]
+    L.or_rodas4.argtypes = [P, d, P, d, d, d, i, P, P]
+    L.or_rodas4.restype = i
+    L.or_advance.argtypes = [P, i64, P, P, P, i64, d, d, d, P, P, i]
+    L.or_advance_dt.argtypes = [P, i64, P, P, P, i64, P, d, d, P, i]
+    L.or_rk4.argtypes = [P, d, P, d, i64]
+    L.or_rodas4_tableau.argtypes = [P, P, P, P, P]
+    L.or_rodas4_linear.argtypes = [i, P, P, d, i, P]
+    L.or_count_ops.argtypes = [P, d, P, d, d, d, P, P, P]
+    L.or_count_ops.restype = i
+    return L
 
 
 def _p(a):

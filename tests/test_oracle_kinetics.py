@@ -166,3 +166,90 @@ def test_planted_jacobian_error_is_caught(om_h2, h2):
     bad[1:, 2] -= f[1:] / (np.sum(y[1:] / om_h2.W) * om_h2.W[1])
     scale = np.max(np.abs(Jc[:, 2]))
     assert np.max(np.abs(bad[:, 2] - Jc[:, 2])) > 1e-10 * scale
+
+
+RC_CAL = 8.314462618 / 4.184     # gas constant in cal/(mol K) (thermochemical calorie)
+
+
+def _reactant_state(om, mech, j):
+    """Equal mass fractions of reaction j's distinct reactants and nothing else."""
+    Y = np.zeros(mech.ns)
+    ks = sorted({int(k) for k in mech.reac[j] if k >= 0})
+    Y[ks] = 1.0 / len(ks)
+    return Y
+
+
+@pytest.mark.parametrize("which", ["h2", "ch4"])
+def test_reaction_order_in_pressure(which, request):
+    """Law of mass action: with only its reactants present (no reverse flux) and T fixed, every
+    concentration scales with p, so a reaction of n reactant molecules runs at a rate
+    proportional to p^n, and p^(n+1) with a third body; a fall-off reaction tends to p^(n+1) at
+    low pressure and to p^n at high pressure (checked to 0.01 in the exponent at 1e-25 and 1e25
+    dyn/cm^2: the broadening factor approaches its limits slowly)."""
+    om = request.getfixturevalue("om_" + which)
+    mech = om.mech
+    T = 1350.0
+    for j in range(mech.nr):
+        Y = _reactant_state(om, mech, j)
+        n = int(np.sum(mech.reac[j] >= 0))
+        order = n + (1 if mech.rtype[j] == 1 else 0)
+        if mech.rtype[j] == 2:
+            for p, want in ((1e-25, n + 1), (1e25, n)):
+                q1 = om.rates(T, p, Y)[1][j]
+                q2 = om.rates(T, 2 * p, Y)[1][j]
+                assert abs(np.log2(q2 / q1) - want) < 1e-2, (j, p, np.log2(q2 / q1))
+            continue
+        q1 = om.rates(T, PATM, Y)[1][j]
+        q2 = om.rates(T, 2 * PATM, Y)[1][j]
+        assert q1 > 0.0
+        assert q2 / q1 == pytest.approx(2.0 ** order, rel=1e-13), (j, q2 / q1, order)
+
+
+@pytest.mark.parametrize("which", ["h2", "ch4"])
+def test_arrhenius_apparent_activation_energy(which, request):
+    """The apparent activation energy R T^2 d ln k/dT of k = A T^b exp(-Ea/(R T)) is Ea + b R T,
+    with Ea in cal/mol; the derivative is taken by central differences of the oracle's kf."""
+    om = request.getfixturevalue("om_" + which)
+    mech = om.mech
+    Y = np.full(mech.ns, 1.0 / mech.ns)
+    for T in (800.0, 1250.0, 2100.0):
+        e = 1e-5 * T
+        kp = om.rates(T + e, PATM, Y)[2]
+        km = om.rates(T - e, PATM, Y)[2]
+        for j in range(mech.nr):
+            if mech.rtype[j] == 2:
+                continue
+            Eapp = RC_CAL * T * T * (np.log(kp[j]) - np.log(km[j])) / (2 * e)
+            want = mech.Ea[j] + mech.b[j] * RC_CAL * T
+            assert abs(Eapp - want) <= 1e-6 * (abs(mech.Ea[j]) + abs(mech.b[j]) * RC_CAL * T) + 1e-4, (j, T)
+
+
+def test_troe_broadening_centre_and_half_widths(ch4):
+    """Troe's broadening factor (Gilbert, Luther & Troe 1983): with c = -0.4 - 0.67 log Fcent,
+    N = 0.75 - 1.27 log Fcent and u = log Pr + c, log F = log Fcent / (1 + (u / (N - 0.14 u))^2).
+    F equals Fcent at the centre u = 0, where it is extremal, and Fcent^(1/2) at u = N / 1.14 and
+    u = -N / 0.86.  F is read from the oracle's kf as kf / (kinf Pr / (1 + Pr))."""
+    om = oracle.OracleMech(ch4)
+    RCv = 8.314462618e7 / 4.184e7
+    for j in np.nonzero(ch4.rtype == TROE)[0][:8]:
+        Y = _reactant_state(om, ch4, j)
+        for T in (900.0, 1700.0):
+            a, T3, T1, T2 = ch4.troe[j, 3:7]
+            Fc = (1 - a) * np.exp(-T / T3) + a * np.exp(-T / T1) + (np.exp(-T2 / T) if ch4.has_t2[j] else 0.0)
+            L = np.log10(Fc)
+            c, N = -0.4 - 0.67 * L, 0.75 - 1.27 * L
+            kinf = ch4.A[j] * T ** ch4.b[j] * np.exp(-ch4.Ea[j] / (RCv * T))
+            k0 = ch4.troe[j, 0] * T ** ch4.troe[j, 1] * np.exp(-ch4.troe[j, 2] / (RCv * T))
+            M1 = np.dot(ch4.eff[j], om.density(T, PATM, Y) * Y / om.W)
+            Pr1 = k0 * M1 / kinf            # Pr at 1 atm; Pr is proportional to p
+
+            def F_at(u):
+                Pr = 10.0 ** (u - c)
+                kf = om.rates(T, PATM * Pr / Pr1, Y)[2][j]
+                return kf / (kinf * Pr / (1 + Pr))
+
+            assert F_at(0.0) == pytest.approx(Fc, rel=1e-11)
+            assert F_at(N / 1.14) == pytest.approx(np.sqrt(Fc), rel=1e-11)
+            assert F_at(-N / 0.86) == pytest.approx(np.sqrt(Fc), rel=1e-11)
+            for du in (-0.05, 0.05):
+                assert (F_at(du) - Fc) * np.sign(L) < 0.0 or Fc == 1.0
