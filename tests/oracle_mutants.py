@@ -1,13 +1,17 @@
-"""Planted mistakes in the oracle's C source, for the mutation tests (test infrastructure).
+"""Planted mistakes in the oracle, for the mutation tests (test infrastructure).
 
 Each entry names a plausible mistake (a dropped term, a wrong sign, constant or index, a
-transposed operand) as text replacements in a copy of chem_oracle.cpp, applied in every place
-the same arithmetic appears, so that the copy stays self-consistent where the original is (a
+transposed operand) as text replacements in a copy of an oracle source (chem_oracle.cpp, or one
+of the Python modules fvm.py, transport.py, mlp.py, surrogate.py), applied in every place the
+same arithmetic appears, so that the copy stays self-consistent where the original is (a
 mistake made the same way in the rates and in the analytic Jacobian is the hard case for the
-pins).  Every replacement stays inside the arrays it touches."""
+pins).  Every replacement stays inside the arrays it touches.  The C copies are compiled beside
+the oracle's own build; the Python copies are executed as fresh module objects.  The oracle's
+files are never changed."""
 import ctypes
 import os
 import subprocess
+import types
 from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -114,3 +118,96 @@ def build_all(names=None, workers=None):
 def load(path):
     import oracle
     return oracle.declare(ctypes.CDLL(path))
+
+
+# Python oracle modules: name -> (module, what is wrong, [(original, planted, occurrences)])
+PY_MUTANTS = {
+    "fvm_interpolation_weight_swapped": ("fvm", "face gamma with the owner's weight on the neighbour",
+        [("g = mesh.weight[f] * gamma[o] + (1.0 - mesh.weight[f]) * gamma[nb]",
+          "g = mesh.weight[f] * gamma[nb] + (1.0 - mesh.weight[f]) * gamma[o]", 2)]),
+    "fvm_downwind": ("fvm", "convected value taken from the downwind cell",
+        [("up = o if F >= 0.0 else nb", "up = nb if F >= 0.0 else o", 1),
+         ("if Fout >= 0.0:\n                    row[P] += Fout\n                else:\n                    row[other] += Fout",
+          "if Fout >= 0.0:\n                    row[other] += Fout\n                else:\n                    row[P] += Fout", 1)]),
+    "fvm_neighbour_flux_sign": ("fvm", "the neighbour's row gains the face flux instead of losing it",
+        [("A[nb, up] -= F", "A[nb, up] += F", 1),
+         ("Fout = phi[f] if o == P else -phi[f]", "Fout = phi[f]", 1)]),
+    "fvm_delta_dropped": ("fvm", "diffusion coefficient without the delta coefficient",
+        [("a = g * mesh.mag_sf[f] * mesh.delta[f]", "a = g * mesh.mag_sf[f]", 2)]),
+    "fvm_boundary_value_dropped": ("fvm", "fixed-value boundary diffusion without the boundary value",
+        [("            s[P] += a * Y_b[b]", "            s[P] += 0.0 * a * Y_b[b]", 1),
+         ("                s += a * Y_b[b]", "                s += 0.0 * a * Y_b[b]", 1)]),
+    "fvm_inflow_convects_cell_value": ("fvm", "an inflow face convects the cell's value",
+        [("                s[P] -= phi_b[b] * Y_b[b]", "                A[P, P] += phi_b[b]", 1),
+         ("                    s -= phi_b[b] * Y_b[b]", "                    row[P] += phi_b[b]", 1)]),
+    "fvm_old_mass_new_density": ("fvm", "old species mass with the new density",
+        [("s[P] += rho_old[P] * Y_old[P] * V[P] / dt", "s[P] += rho[P] * Y_old[P] * V[P] / dt", 1),
+         ("s += rho_old[P] * Y_old[P] * V[P] / dt", "s += rho[P] * Y_old[P] * V[P] / dt", 1)]),
+    "fvm_source_without_volume": ("fvm", "chemistry source not integrated over the cell volume",
+        [("s += V * k * S", "s += k * S", 1),
+         ("s += V[P] * (1.0 if kappa is None else kappa[P]) * S[P]",
+          "s += (1.0 if kappa is None else kappa[P]) * S[P]", 1)]),
+    "fvm_ldu_lower_upper_swapped": ("fvm", "lower and upper exchanged in the ldu split",
+        [("return A[nb, o].copy(), A[o, nb].copy(), np.diag(A).copy()",
+          "return A[o, nb].copy(), A[nb, o].copy(), np.diag(A).copy()", 1)]),
+    "pasr_mixing_time_without_sqrt": ("fvm", "mixing time without the square root",
+        [("tmix = c_mix * np.sqrt(mu_eff[i] / (rho[i] * eps[i]))",
+          "tmix = c_mix * mu_eff[i] / (rho[i] * eps[i])", 1)]),
+    "pasr_factor_inverted": ("fvm", "kappa = tau_mix / (tau_c + tau_mix)",
+        [("kappa[i] = tau_c[i] / (tau_c[i] + tmix)", "kappa[i] = tmix / (tau_c[i] + tmix)", 1)]),
+    "wilke_mass_ratio_inverted": ("transport", "Wilke's factor with (W_k / W_j)^(1/4)",
+        [("(W[j] / W[k]) ** 0.25", "(W[k] / W[j]) ** 0.25", 1)]),
+    "wilke_denominator_inverted": ("transport", "Wilke's factor with (8 (1 + W_j / W_k))^(1/2)",
+        [("np.sqrt(8.0 * (1.0 + W[k] / W[j]))", "np.sqrt(8.0 * (1.0 + W[j] / W[k]))", 1)]),
+    "wilke_numerator_without_X": ("transport", "mixture viscosity sums mu_k / den without X_k",
+        [("mu = float(np.sum(X * mu_k / mu_den))", "mu = float(np.sum(mu_k / mu_den))", 1)]),
+    "mathur_harmonic_not_inverted": ("transport", "Mathur average with sum X / lambda not inverted",
+        [("1.0 / float(np.sum(X / lam_k))", "float(np.sum(X / lam_k))", 1)]),
+    "diffusion_mole_fraction": ("transport", "D_km = (1 - X_k) / ... instead of (1 - Y_k)",
+        [("Dm[k] = (1.0 - Y[k]) / s", "Dm[k] = (1.0 - X[k]) / s", 1)]),
+    "diffusion_pressure_inverted": ("transport", "D proportional to p instead of 1 / p",
+        [("* (PATM / p)", "* (p / PATM)", 1)]),
+    "mole_fractions_are_mass_fractions": ("transport", "X = Y",
+        [("X = (Y / W) / np.sum(Y / W)", "X = Y / np.sum(Y)", 1)]),
+    "gelu_grad_sign": ("mlp", "GELU derivative with the density term's sign flipped",
+        [("+ x * np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)",
+          "- x * np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)", 1)]),
+    "backward_derivative_at_activation": ("mlp", "GELU derivative taken at the activation",
+        [('dz = da * gelu_grad(cache["z"][l - 1])', 'dz = da * gelu_grad(cache["a"][l])', 1)]),
+    "loss_gradient_scale": ("mlp", "loss gradient divided by the batch only",
+        [("dz = 2.0 * (out - target) / (M * n_out)", "dz = 2.0 * (out - target) / M", 1)]),
+    "adam_no_bias_correction": ("mlp", "Adam's first moment without bias correction",
+        [("mh = m[i] / (1.0 - beta1 ** step)", "mh = m[i]", 1)]),
+    "bf16_ties_down": ("mlp", "BF16 rounding with ties always down",
+        [("bias = ((u >> 16) & 1) + 0x7FFF", "bias = 0x7FFF + 0 * u", 1)]),
+    "first_layer_drops_weight_correction": ("mlp", "compensated first layer without x_hi W_lo",
+        [("return xh @ wh.T + xl @ wh.T + xh @ wl.T", "return xh @ wh.T + xl @ wh.T", 1)]),
+    "boxcox_inverse_exponent": ("surrogate", "Box-Cox inverse with exponent lambda",
+        [("np.power(base, 1.0 / lam)", "np.power(base, lam)", 1)]),
+    "projection_unweighted": ("surrogate", "projection without the D weighting, consistently",
+        [("G = (A * D[None, :]) @ A.T", "G = A @ A.T", 1),
+         ("Ypp = Yp - D * (A.T @ lam)", "Ypp = Yp - (A.T @ lam)", 1)]),
+    "projection_normal_matrix_unweighted": ("surrogate", "normal matrix without D, update with D",
+        [("G = (A * D[None, :]) @ A.T", "G = A @ A.T", 1)]),
+    "newton_step_sign": ("surrogate", "Newton on T stepping the wrong way",
+        [("        T -= dT", "        T += dT", 1)]),
+    "heat_release_without_W": ("surrogate", "heat release with molar enthalpies times mass fractions",
+        [("hk * (np.asarray(Y1) - np.asarray(Y0)) / om.W", "hk * (np.asarray(Y1) - np.asarray(Y0))", 1)]),
+}
+
+
+def planted_module(name):
+    """A fresh module object holding the planted copy of one Python oracle module."""
+    mod, _, reps = PY_MUTANTS[name]
+    path = os.path.join(ROOT, "oracle", mod + ".py")
+    text = open(path).read()
+    for old, new, count in reps:
+        found = text.count(old)
+        if found != count:
+            raise ValueError(f"{name}: {old!r} occurs {found} times, expected {count}")
+        text = text.replace(old, new)
+    m = types.ModuleType(f"oracle.{mod}")
+    m.__file__ = path
+    m.__package__ = "oracle"
+    exec(compile(text, f"{path} [{name}]", "exec"), m.__dict__)
+    return m

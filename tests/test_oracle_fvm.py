@@ -54,8 +54,9 @@ def test_closed_box_conserves_the_species_mass():
 
 
 def test_upwind_convection_of_a_uniform_field_through_a_uniform_flow():
-    """A uniform flow along x through a box with inflow at x = 0 (boundary value 1) and outflow
-    at x = 1: the uniform field Y = 1 is steady (A Y = s without the time term)."""
+    """A uniform flow along x through a box with inflow at x = 0 (boundary value c) and outflow
+    at x = 1: the uniform field Y = c is steady (A Y = s without the time term).  c is not 1, so
+    that an inflow face that convected the cell's value instead of the boundary value fails."""
     n = 4
     m = box_mesh(n, 3, 2, seed=6, stretch=2.0, permute=True)
     u = 2.5
@@ -66,25 +67,83 @@ def test_upwind_convection_of_a_uniform_field_through_a_uniform_flow():
     out = m.b_centre[:, 0] > 1.0 - 1e-12
     inl = m.b_centre[:, 0] < 1e-12
     phi_b = np.where(out, u * m.b_mag_sf, np.where(inl, -u * m.b_mag_sf, 0.0))
-    A, s = fvm.species_matrix(m, phi=phi, phi_b=phi_b, Y_b=np.ones(m.b_cell.size))
-    assert np.max(np.abs(A @ np.ones(m.n_cells) - s)) <= 1e-13 * u
+    c = 0.37
+    A, s = fvm.species_matrix(m, phi=phi, phi_b=phi_b, Y_b=np.full(m.b_cell.size, c))
+    assert np.max(np.abs(A @ np.full(m.n_cells, c) - s)) <= 1e-13 * u
     assert np.all(A - np.diag(np.diag(A)) <= 0.0)         # upwind: non-positive off-diagonals
 
 
 def test_ldu_round_trip_and_source_term():
+    """lower_f = A[neighbour, owner] and upper_f = A[owner, neighbour] rebuild A; the round trip
+    runs on a convective (unsymmetric) matrix so that exchanging lower and upper fails."""
     m = box_mesh(3, 3, 2, seed=7, permute=True)
     rng = np.random.default_rng(8)
     S = rng.standard_normal(m.n_cells)
     kap = rng.uniform(0.0, 1.0, m.n_cells)
-    A, s = fvm.species_matrix(m, gamma=np.ones(m.n_cells), gamma_b=np.ones(m.b_cell.size),
-                              Y_b=np.zeros(m.b_cell.size), S=S, kappa=kap)
+    nb = m.b_cell.size
+    A, s = fvm.species_matrix(m, gamma=np.ones(m.n_cells), gamma_b=np.ones(nb), Y_b=np.zeros(nb), S=S, kappa=kap,
+                              phi=rng.standard_normal(m.owner.size), phi_b=np.zeros(nb))
     assert np.allclose(s, m.volume * kap * S, rtol=1e-15, atol=0)
+    assert not np.array_equal(A, A.T)
     lo, up, dg = fvm.ldu(m, A)
     B = np.diag(dg)
     B[m.neighbour, m.owner] = lo
     B[m.owner, m.neighbour] = up
     assert np.array_equal(A, B)
+    Ad, _ = fvm.species_matrix(m, gamma=np.ones(m.n_cells), gamma_b=np.ones(nb), Y_b=np.zeros(nb))
+    lo, up, _ = fvm.ldu(m, Ad)
     assert np.array_equal(lo, up)                           # diffusion alone is symmetric
+
+
+def test_linear_diffusivity_is_interpolated_exactly_to_the_faces():
+    """Alg. 1 interpolates gamma linearly to each face: for gamma linear in space, sampled at the
+    cell centres of a stretched mesh, the face value is gamma at the face itself, which lies half
+    the owner's width (its volume over the face area) from the owner's centre."""
+    m = box_mesh(6, 5, 4, seed=31, stretch=3.0, permute=True)
+    lin = lambda x: 0.5 + 2.0 * x[..., 0] + 0.7 * x[..., 1] - 0.3 * x[..., 2]
+    nb = m.b_cell.size
+    A, _ = fvm.species_matrix(m, gamma=lin(m.centre), gamma_b=np.ones(nb), Y_b=np.zeros(nb))
+    d = m.centre[m.neighbour] - m.centre[m.owner]
+    ax = np.argmax(np.abs(d), axis=1)
+    xf = m.centre[m.owner].copy()
+    f = np.arange(ax.size)
+    xf[f, ax] += np.sign(d[f, ax]) * 0.5 * m.volume[m.owner] / m.mag_sf
+    want = -lin(xf) * m.mag_sf * m.delta
+    assert np.allclose(A[m.owner, m.neighbour], want, rtol=1e-13, atol=0)
+    assert np.allclose(A[m.neighbour, m.owner], want, rtol=1e-13, atol=0)
+    assert np.max(np.abs(m.weight - 0.5)) > 0.1             # the mesh really is stretched
+
+
+def test_time_term_alone_carries_each_cells_species_mass():
+    """With the time derivative alone, A Y = s gives rho Y = rho_old Y_old in every cell."""
+    m = box_mesh(4, 3, 2, seed=32, stretch=2.0, permute=True)
+    rng = np.random.default_rng(33)
+    rho, rho_old = rng.uniform(0.3, 1.5, m.n_cells), rng.uniform(0.3, 1.5, m.n_cells)
+    Y_old = rng.uniform(0.0, 0.3, m.n_cells)
+    A, s = fvm.species_matrix(m, dt=2e-4, rho=rho, rho_old=rho_old, Y_old=Y_old)
+    Y = np.linalg.solve(A, s)
+    assert np.allclose(rho * Y, rho_old * Y_old, rtol=1e-14, atol=0)
+
+
+def test_open_box_species_budget():
+    """Over the whole box, storage plus the net convective outflow through the boundary equals
+    the source, whatever the flux field: sum V (rho Y - rho_old Y_old) / dt + sum_b phi_b Y_b' =
+    sum V kappa S, where a boundary face carries its cell's value out (phi_b >= 0) and the boundary
+    value in (phi_b < 0); internal faces, convective and diffusive, cancel.  Zero-gradient walls,
+    so that no diffusive flux crosses the boundary."""
+    m = box_mesh(5, 4, 3, seed=34, stretch=2.0, permute=True)
+    rng = np.random.default_rng(35)
+    m.b_type[:] = 0
+    n, nf, nb = m.n_cells, m.owner.size, m.b_cell.size
+    kw = dict(dt=1e-3, rho=rng.uniform(0.5, 2, n), rho_old=rng.uniform(0.5, 2, n), Y_old=rng.uniform(0, 1, n),
+              phi=rng.standard_normal(nf), phi_b=rng.standard_normal(nb), gamma=rng.uniform(0.1, 1, n),
+              gamma_b=np.ones(nb), Y_b=rng.uniform(0, 1, nb), S=rng.standard_normal(n), kappa=rng.uniform(0, 1, n))
+    A, s = fvm.species_matrix(m, **kw)
+    Y = np.linalg.solve(A, s)
+    face = np.where(kw["phi_b"] >= 0.0, Y[m.b_cell], kw["Y_b"])
+    terms = np.r_[m.volume * (kw["rho"] * Y - kw["rho_old"] * kw["Y_old"]) / kw["dt"], kw["phi_b"] * face,
+                  -m.volume * kw["kappa"] * kw["S"]]
+    assert abs(terms.sum()) <= 1e-11 * np.abs(terms).sum()
 
 
 def test_pasr_limits():

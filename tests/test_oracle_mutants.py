@@ -1,16 +1,20 @@
-"""Mutation tests of the oracle's pins: each plausible mistake planted in a copy of the oracle's
-C source (tests/oracle_mutants.py) must make the pins named for it fail, so that the pins are
-known to detect a dropped term, a wrong sign, constant or index, or a transposed operand in every
-part of the kinetics and the integrator, including mistakes made consistently in the rates and
-in the analytic Jacobian.  The mistakes are planted on the CPU, in copies built beside the
-oracle; the oracle itself is untouched."""
+"""Mutation tests of the oracle's pins: each plausible mistake planted in a copy of an oracle
+source (tests/oracle_mutants.py) must make the pins named for it fail, so that the pins are known
+to detect a dropped term, a wrong sign, constant or index, or a transposed operand in every part
+of the kinetics and the integrator (including mistakes made consistently in the rates and in the
+analytic Jacobian), the species-equation assembly and PaSR factor, the transport mixture rules,
+and the surrogate's network, training step and post-processing.  The mistakes are planted on the
+CPU, in copies; the oracle itself is untouched."""
 import numpy as np
 import pytest
 
 import oracle
+import test_oracle_fvm as F
 import test_oracle_integrator as I
 import test_oracle_kinetics as K
-from oracle_mutants import MUTANTS, build_all, load
+import test_oracle_surrogate as S
+import test_oracle_transport as TT
+from oracle_mutants import MUTANTS, PY_MUTANTS, build_all, load, planted_module
 
 # the pins that must fail for each planted mistake (others may fail too)
 CAUGHT_BY = {
@@ -38,6 +42,84 @@ CAUGHT_BY = {
     "lu_forward_transposed": ["linear_convergence", "isomerisation"],
     "rk4_weight": ["rk4_brute_force"],
 }
+
+
+# the same for the Python oracle modules
+PY_CAUGHT_BY = {
+    "fvm_interpolation_weight_swapped": ["linear_diffusivity"],
+    "fvm_downwind": ["uniform_flow"],
+    "fvm_neighbour_flux_sign": ["closed_box", "budget"],
+    "fvm_delta_dropped": ["seven_point", "linear_field"],
+    "fvm_boundary_value_dropped": ["linear_field"],
+    "fvm_inflow_convects_cell_value": ["budget"],
+    "fvm_old_mass_new_density": ["time_term", "budget"],
+    "fvm_source_without_volume": ["ldu_round_trip", "budget"],
+    "fvm_ldu_lower_upper_swapped": ["ldu_round_trip"],
+    "pasr_mixing_time_without_sqrt": ["pasr_limits"],
+    "pasr_factor_inverted": ["pasr_limits"],
+    "wilke_mass_ratio_inverted": ["wilke_reciprocity"],
+    "wilke_denominator_inverted": ["wilke_reciprocity"],
+    "wilke_numerator_without_X": ["pure_limit", "wilke_identical"],
+    "mathur_harmonic_not_inverted": ["pure_limit"],
+    "diffusion_mole_fraction": ["binary_diffusion"],
+    "diffusion_pressure_inverted": ["pressure_scaling"],
+    "mole_fractions_are_mass_fractions": ["binary_diffusion", "wilke_reciprocity"],
+    "gelu_grad_sign": ["gelu_forms", "finite_differences"],
+    "backward_derivative_at_activation": ["finite_differences"],
+    "loss_gradient_scale": ["finite_differences"],
+    "adam_no_bias_correction": ["adam"],
+    "bf16_ties_down": ["bf16_known"],
+    "first_layer_drops_weight_correction": ["first_layer"],
+    "boxcox_inverse_exponent": ["boxcox"],
+    "projection_unweighted": ["projection"],
+    "projection_normal_matrix_unweighted": ["projection"],
+    "newton_step_sign": ["T_from_h"],
+    "heat_release_without_W": ["heat_release"],
+}
+
+# where each pin module holds the oracle module it checks
+_PY_TARGET = {"fvm": (F, "fvm"), "transport": (TT, "ot"), "mlp": (S, "mlp"), "surrogate": (S, "sur")}
+
+
+def _py_pins(om, h2, h2_tr):
+    return {
+        "seven_point": F.test_uniform_diffusion_is_the_seven_point_stencil,
+        "linear_field": F.test_linear_field_has_zero_laplacian_on_a_stretched_permuted_mesh,
+        "closed_box": F.test_closed_box_conserves_the_species_mass,
+        "uniform_flow": F.test_upwind_convection_of_a_uniform_field_through_a_uniform_flow,
+        "ldu_round_trip": F.test_ldu_round_trip_and_source_term,
+        "linear_diffusivity": F.test_linear_diffusivity_is_interpolated_exactly_to_the_faces,
+        "time_term": F.test_time_term_alone_carries_each_cells_species_mass,
+        "budget": F.test_open_box_species_budget,
+        "pasr_limits": F.test_pasr_limits,
+        "pure_limit": lambda: TT.test_pure_species_limit(h2_tr),
+        "wilke_identical": TT.test_wilke_reduces_to_pure_value_for_identical_species,
+        "binary_diffusion": lambda: TT.test_binary_mixture_diffusion_identity(h2_tr),
+        "pressure_scaling": lambda: TT.test_diffusion_scales_inversely_with_pressure_and_viscosity_does_not(h2_tr),
+        "wilke_reciprocity": lambda: TT.test_wilke_interaction_factors_obey_reciprocity(h2_tr),
+        "bf16_known": S.test_bf16_rounding_known_values,
+        "gelu_forms": S.test_gelu_closed_forms,
+        "first_layer": S.test_compensated_first_layer_error_bound,
+        "finite_differences": S.test_backward_matches_finite_differences,
+        "adam": S.test_adam_first_step_is_signed_lr,
+        "boxcox": S.test_boxcox_roundtrip_and_log_limit,
+        "projection": lambda: S.test_projection_conserves_and_is_weighted_least_squares(h2, om),
+        "T_from_h": lambda: S.test_temperature_from_enthalpy(h2, om),
+        "heat_release": lambda: S.test_heat_release_matches_energy_equation(h2, om),
+    }
+
+
+def _failing(pins, names):
+    """The named pins that pass (should be empty)."""
+    survived = []
+    for pin in names:
+        try:
+            with np.errstate(all="ignore"):
+                pins[pin]()
+        except Exception:      # an assertion, or a pin's own solver giving up on the wrong arithmetic
+            continue
+        survived.append(pin)
+    return survived
 
 
 class _Fixtures:
@@ -75,9 +157,11 @@ def mutant_libs():
 
 
 def test_every_mutant_has_catching_pins():
-    assert set(CAUGHT_BY) == set(MUTANTS)
+    assert set(CAUGHT_BY) == set(MUTANTS) and set(PY_CAUGHT_BY) == set(PY_MUTANTS)
     known = set(_pins(None, None, None))
     assert all(CAUGHT_BY[n] and set(CAUGHT_BY[n]) <= known for n in CAUGHT_BY)
+    known = set(_py_pins(None, None, None))
+    assert all(PY_CAUGHT_BY[n] and set(PY_CAUGHT_BY[n]) <= known for n in PY_CAUGHT_BY)
 
 
 @pytest.mark.parametrize("name", list(MUTANTS))
@@ -86,16 +170,22 @@ def test_planted_mistake_is_caught(name, mutant_libs, h2, ch4, monkeypatch):
     monkeypatch.setattr(oracle, "_lib", L)
     om = oracle.OracleMech(h2)
     try:
-        pins = _pins(om, h2, ch4)
-        survived = []
-        for pin in CAUGHT_BY[name]:
-            try:
-                with np.errstate(all="ignore"):
-                    pins[pin]()
-            except Exception:      # an assertion, or a pin's own solver giving up on the wrong arithmetic
-                continue
-            survived.append(pin)
+        survived = _failing(_pins(om, h2, ch4), CAUGHT_BY[name])
         assert not survived, f"{name} ({MUTANTS[name][0]}) passes {survived}"
     finally:
         L.or_mech_free(om.h)
         om.h = None
+
+
+@pytest.fixture(scope="module")
+def h2_transport(h2):
+    from synth.transport import generate_transport
+    return h2, generate_transport(h2)
+
+
+@pytest.mark.parametrize("name", list(PY_MUTANTS))
+def test_planted_mistake_in_python_oracle_is_caught(name, h2, om_h2, h2_transport, monkeypatch):
+    module, attr = _PY_TARGET[PY_MUTANTS[name][0]]
+    monkeypatch.setattr(module, attr, planted_module(name))
+    survived = _failing(_py_pins(om_h2, h2, h2_transport), PY_CAUGHT_BY[name])
+    assert not survived, f"{name} ({PY_MUTANTS[name][1]}) passes {survived}"

@@ -104,3 +104,32 @@ def test_trace_species_continuity(h2_tr):
     near = ot.mixture(tr, m.W, 1500.0, PATM, Y2 / Y2.sum())
     assert near[0] == pytest.approx(base[0], rel=1e-9)
     assert near[1] == pytest.approx(base[1], rel=1e-9)
+
+
+def test_wilke_interaction_factors_obey_reciprocity(h2_tr):
+    """Wilke's interaction factors satisfy Phi_jk / Phi_kj = (mu_j / mu_k)(W_k / W_j), a property of
+    their form (1 + (mu_k/mu_j)^(1/2) (W_j/W_k)^(1/4))^2 / (8 (1 + W_k/W_j))^(1/2).  For a binary
+    mixture the rule mu = X1 mu1 / (X1 + X2 Phi12) + X2 mu2 / (X1 Phi21 + X2) at three compositions
+    determines Phi12 and Phi21; fitted to the oracle's mixture viscosities of H2 with N2 (molar
+    masses 14 times apart), they obey the identity."""
+    from scipy.optimize import least_squares
+    m, tr = h2_tr
+    W = np.asarray(m.W)
+    i, j = m.species.index("H2"), m.species.index("N2")
+    T = 1500.0
+    mu_k, _, _ = ot.pure_species(tr, T, PATM)
+    data = []
+    for y2 in (0.2, 0.5, 0.8):
+        Y = np.zeros(m.ns)
+        Y[i], Y[j] = 1.0 - y2, y2
+        X = (Y / W) / np.sum(Y / W)
+        data.append((X[i], X[j], ot.mixture(tr, W, T, PATM, Y)[0]))
+
+    def resid(v):
+        a, b = v
+        return [(x1 * mu_k[i] / (x1 + x2 * a) + x2 * mu_k[j] / (x1 * b + x2)) / mu - 1.0 for x1, x2, mu in data]
+
+    fit = least_squares(resid, [1.0, 1.0], bounds=([1e-3, 1e-3], [1e3, 1e3]), xtol=1e-15, ftol=1e-15, gtol=1e-15)
+    assert np.max(np.abs(resid(fit.x))) < 1e-12
+    a, b = fit.x
+    assert b / a == pytest.approx((mu_k[j] / mu_k[i]) * (W[i] / W[j]), rel=1e-8)
