@@ -88,7 +88,11 @@ typedef struct chem_mech_desc {
 int chem_load_mechanism(const char* path, chem_mech_t* out);
 /* Same from an in-memory description. */
 int chem_load_mechanism_desc(const chem_mech_desc* desc, chem_mech_t* out);
+/* Release a mechanism's device copy (cudaFree, which waits for device work still using it); the
+ * handle is invalid afterwards.  CHEM_EINVAL for NULL. */
 int chem_free_mechanism(chem_mech_t m);
+/* Species, reaction and element counts of a loaded mechanism (host ints, each nullable).
+ * CHEM_EINVAL for a NULL handle; no device work. */
 int chem_mechanism_info(chem_mech_t m, int* n_species, int* n_reactions, int* n_elements);
 
 /* ---------------------------------------------------------------------------------------
@@ -214,6 +218,11 @@ typedef struct chem_surrogate_ps_desc {
   const float* box_lo;
   const float* box_hi;
 } chem_surrogate_ps_desc;
+/* Copy the per-species networks (host arrays, read during the call) to the device, bound to
+ * mechanism m.  *out receives a handle owned by the caller (chem_surrogate_free).  CHEM_EINVAL
+ * for NULL arguments or statistics, ns different from the mechanism's or above 16, widths outside
+ * the stated range, dt <= 0, or a species given some but not all of its four layers;
+ * CHEM_ENOMEM / CHEM_ECUDA if the upload fails. */
 int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* desc, chem_mech_t m,
                                       chem_model_t* out);
 
@@ -223,6 +232,8 @@ int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* desc, chem_m
  * int32 nnet, int32 species[nnet], then for each network W1, b1, W2, b2, W3, b3, W4, b4, then
  * the statistics as in CHEMSUR1. */
 int chem_surrogate_load(const char* path, chem_mech_t m, chem_model_t* out);
+/* Release a model's device memory (cudaFree, which waits for device work still using it); the
+ * handle is invalid afterwards.  CHEM_EINVAL for NULL. */
 int chem_surrogate_free(chem_model_t model);
 
 /* Network pass only (features, MLP, inverse transform): ynet[k * ncells + c] = predicted Y_k
@@ -280,6 +291,8 @@ int chem_mlp_trainer_create(int n_in, int n_out, int batch, const float* const* 
 int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden, const int* hidden, int batch,
                                    const float* const* W_init, const float* const* b_init,
                                    uint64_t seed, chem_trainer_t* out);
+/* Release a trainer's parameters, optimiser state and activations (cudaFree, which waits for
+ * device work still using them).  CHEM_EINVAL for NULL. */
 int chem_mlp_trainer_free(chem_trainer_t t);
 /* forward pass of one batch, keeping the activations; out (nullable) receives [batch x n_out].
  * X is read again by chem_mlp_backward: it must stay valid until that call's work is done. */
@@ -328,6 +341,12 @@ typedef struct chem_serve_options {
   double slice_ms;           /* FP64 time slice (0 -> 20 ms; negative: no slicing) */
 } chem_serve_options;
 
+/* Start a server on the current device: its streams (half low-priority FP64, half high-priority
+ * surrogate), its device work-queue counters and one host thread that admits, batches and
+ * launches requests.  hbm_budget_bytes (> 0) bounds the device memory of registered states plus
+ * running requests' workspaces; opt nullable (defaults).  *out receives a handle owned by the
+ * caller (chem_serve_destroy).  CHEM_EINVAL for a zero budget or NULL out; CHEM_ECUDA if a
+ * stream or the counters cannot be created. */
 int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_options* opt, chem_server_t* out);
 /* Register a solver's resident state (device arrays owned by the caller, valid until the server
  * is destroyed); model (nullable) enables the surrogate route.  CHEM_EBUSY if the state alone
@@ -374,7 +393,12 @@ typedef struct chem_transport_desc {
   const double* lambda_poly;   /* [ns][4] */
   const double* diff_poly;     /* [ns][ns][4], symmetric */
 } chem_transport_desc;
+/* Copy a mechanism's transport fits to the device.  *out receives a handle owned by the caller
+ * (chem_transport_free).  CHEM_EINVAL for NULL arguments, a NULL table or n_species different from
+ * the mechanism's; CHEM_ENOMEM / CHEM_ECUDA if the upload fails. */
 int chem_transport_create(chem_mech_t m, const chem_transport_desc* desc, chem_transport_t* out);
+/* Release the device copy (cudaFree, which waits for device work still using it).  CHEM_EINVAL
+ * for NULL. */
 int chem_transport_free(chem_transport_t t);
 /* Mixture-averaged properties: viscosity by Wilke's rule, conductivity by the Mathur-Saxena
  * average, D_km = (1 - Y_k) / sum_{j != k} X_j / D_jk (the self-diffusion fit for a cell holding
@@ -420,6 +444,8 @@ typedef struct chem_fvmesh_desc {
 /* Upload a mesh; builds the cell-to-face index and the CSR pattern of its matrices.  At most
  * 2^31 - 1 cells and 2^29 - 1 faces of each kind. */
 int chem_fvmesh_create(const chem_fvmesh_desc* desc, chem_fvmesh_t* out);
+/* Release the mesh's device arrays, the CSR pattern included (cudaFree, which waits for device
+ * work still using them).  CHEM_EINVAL for NULL. */
 int chem_fvmesh_free(chem_fvmesh_t mesh);
 /* The CSR pattern (device arrays owned by the mesh): row_ptr [n_cells + 1], col_idx [nnz],
  * columns ascending within a row; the diagonal is always stored. */
@@ -462,6 +488,8 @@ int chem_pasr_kappa(int64_t n, const double* tau_c, const double* rho, const dou
                     const double* strain, const double* delta, double c_s, double c_mix,
                     double* kappa, chem_stream_t stream);
 
+/* Message of the last failure on the calling thread (empty if none); the string stays valid
+ * until the thread's next failing call.  Never fails. */
 const char* chem_last_error(void);
 
 #ifdef __cplusplus
