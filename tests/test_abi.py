@@ -36,3 +36,30 @@ def test_last_error_is_callable_without_gpu():
     rc = L.chem_mechanism_info(None, None, None, None)
     assert rc == _lib.CHEM_EINVAL
     assert b"NULL" in L.chem_last_error()
+
+
+def test_every_entry_point_rejects_null_arguments_before_device_work():
+    """The header's error contract on a host without a GPU: called with NULL handles and pointers
+    (sizes 1, scalars 1.0), every entry point returns CHEM_EINVAL and leaves a message, without
+    touching the device.  The two calls that take no handle (the FMA-peak probe, the error
+    query) are left out."""
+    import ctypes
+    from paper_2312_13513_gb300 import _lib
+    L = _lib.load()
+    checked = 0
+    for name, (_, argtypes) in _lib.SIGNATURES.items():
+        if name in ("chem_fp64_fma_peak", "chem_last_error"):
+            continue
+        args = []
+        for a in argtypes:
+            if a in (ctypes.c_double, ctypes.c_float):
+                args.append(1.0)
+            elif a in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(a, ctypes._Pointer):
+                args.append(None)
+            else:
+                args.append(1)
+        rc = getattr(L, name)(*args)
+        assert rc == _lib.CHEM_EINVAL, (name, rc)
+        assert L.chem_last_error(), name
+        checked += 1
+    assert checked >= 45
