@@ -330,9 +330,17 @@ int validate(const chem_mech_desc* d) {
     set_error("NULL array in mechanism description");
     return CHEM_EINVAL;
   }
+  for (int e = 0; e < ne; ++e)
+    if (!(d->elem_mass[e] > 0.0) || !std::isfinite(d->elem_mass[e])) {
+      set_error("element %d has a non-positive or non-finite atomic mass", e);
+      return CHEM_EINVAL;
+    }
   for (int k = 0; k < ns; ++k) {
     double W = 0.0;
-    for (int e = 0; e < ne; ++e) W += d->comp[(size_t)k * ne + e] * d->elem_mass[e];
+    for (int e = 0; e < ne; ++e) {
+      if (d->comp[(size_t)k * ne + e] < 0) { set_error("species %d has a negative element count", k); return CHEM_EINVAL; }
+      W += d->comp[(size_t)k * ne + e] * d->elem_mass[e];
+    }
     if (!(W > 0.0)) { set_error("species %d has non-positive molar mass", k); return CHEM_EINVAL; }
     for (int i = 0; i < 7; ++i)
       if (!std::isfinite(d->nasa_lo[7 * k + i]) || !std::isfinite(d->nasa_hi[7 * k + i])) {
@@ -356,9 +364,20 @@ int validate(const chem_mech_desc* d) {
       set_error("reaction %d: bad Arrhenius parameters", j);
       return CHEM_EINVAL;
     }
+    if (d->rtype[j] != 0)
+      for (int k = 0; k < ns; ++k) {
+        const double e = d->eff[(size_t)j * ns + k];
+        if (!(e >= 0.0) || !std::isfinite(e)) {
+          set_error("reaction %d: third-body efficiency of species %d is negative or not finite", j, k);
+          return CHEM_EINVAL;
+        }
+      }
     if (d->rtype[j] == 2) {
       const double* t = d->troe + 7 * j;
-      if (!(t[0] >= 0.0) || !(t[4] > 0.0) || !(t[5] > 0.0)) {
+      bool finite = true;
+      for (int i = 0; i < 7; ++i) finite = finite && std::isfinite(t[i]);
+      if (!finite || !(t[0] >= 0.0) || !(t[4] > 0.0) || !(t[5] > 0.0) ||
+          (d->has_t2[j] != 0 && d->has_t2[j] != 1)) {
         set_error("reaction %d: bad Troe parameters", j);
         return CHEM_EINVAL;
       }

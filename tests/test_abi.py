@@ -63,3 +63,64 @@ def test_every_entry_point_rejects_null_arguments_before_device_work():
         assert L.chem_last_error(), name
         checked += 1
     assert checked >= 45
+
+
+def _desc(mech, **bad):
+    """A chem_mech_desc of mech's arrays, with the named arrays replaced."""
+    import ctypes
+    import numpy as np
+    from paper_2312_13513_gb300 import _lib
+    fields = {"elem_mass": (mech.elem_mass, np.float64), "comp": (mech.comp, np.int32),
+              "nasa_lo": (mech.nasa_lo, np.float64), "nasa_hi": (mech.nasa_hi, np.float64),
+              "rtype": (mech.rtype, np.int32), "reac": (mech.reac, np.int32), "prod": (mech.prod, np.int32),
+              "A": (mech.A, np.float64), "b": (mech.b, np.float64), "Ea": (mech.Ea, np.float64),
+              "troe": (mech.troe, np.float64), "has_t2": (mech.has_t2, np.int32), "eff": (mech.eff, np.float64)}
+    keep = {k: np.ascontiguousarray(bad.get(k, v), dtype=t) for k, (v, t) in fields.items()}
+    d = _lib.MechDesc(mech.ns, mech.ne, mech.nr, *[keep[k].ctypes.data_as(ctypes.c_void_p) for k in fields])
+    return d, keep
+
+
+def test_mechanism_descriptions_are_validated_on_the_host():
+    """chem_load_mechanism_desc checks the description before any device work: each corruption
+    below is CHEM_EINVAL with a message naming it; the intact H2 and CH4 descriptions pass the
+    checks (on a host without a GPU they then fail at the upload, CHEM_ECUDA)."""
+    import ctypes
+    import numpy as np
+    from paper_2312_13513_gb300 import _lib
+    from synth.mechanism import ch4_mechanism, h2_mechanism
+    L = _lib.load()
+    m = h2_mechanism()
+    j3 = int(np.nonzero(m.rtype == 1)[0][0])     # a third-body reaction
+    jt = int(np.nonzero(m.rtype == 2)[0][0])     # the fall-off reaction
+
+    def with_(arr, idx, v):
+        a = np.array(arr, copy=True)
+        a[idx] = v
+        return a
+
+    cases = {
+        "efficiency": dict(eff=with_(m.eff, (j3, 0), -0.5)),
+        "efficiency NaN": dict(eff=with_(m.eff, (j3, 1), np.nan)),
+        "Troe NaN": dict(troe=with_(m.troe, (jt, 3), np.nan)),
+        "Troe T3": dict(troe=with_(m.troe, (jt, 4), 0.0)),
+        "has_t2": dict(has_t2=with_(m.has_t2, jt, 2)),
+        "element count": dict(comp=with_(m.comp, (0, 0), -1)),
+        "atomic mass": dict(elem_mass=with_(m.elem_mass, 0, np.inf)),
+        "species index": dict(reac=with_(m.reac, (0, 0), m.ns)),
+        "empty side": dict(prod=with_(m.prod, 0, -1)),
+        "Arrhenius": dict(A=with_(m.A, 0, -1.0)),
+        "reaction type": dict(rtype=with_(m.rtype, 0, 3)),
+        "NASA": dict(nasa_hi=with_(m.nasa_hi, (0, 2), np.inf)),
+    }
+    h = ctypes.c_void_p()
+    for what, bad in cases.items():
+        d, _ = _desc(m, **bad)
+        rc = L.chem_load_mechanism_desc(ctypes.byref(d), ctypes.byref(h))
+        assert rc == _lib.CHEM_EINVAL, what
+        assert L.chem_last_error(), what
+    for mech in (m, ch4_mechanism()):
+        d, _ = _desc(mech)
+        rc = L.chem_load_mechanism_desc(ctypes.byref(d), ctypes.byref(h))
+        assert rc != _lib.CHEM_EINVAL, L.chem_last_error()
+        if rc == _lib.CHEM_OK:
+            L.chem_free_mechanism(h)
