@@ -86,7 +86,14 @@ typedef struct chem_mech_desc {
 /* Parse a CHEMMECH text file (format written by synth.mechanism.Mechanism.to_text) and upload
  * it to the current device.  *out receives a handle owned by the caller (chem_free_mechanism). */
 int chem_load_mechanism(const char* path, chem_mech_t* out);
-/* Same from an in-memory description. */
+/* Same from an in-memory description.  The description is checked on the host before any device
+ * work; CHEM_EINVAL (with the offending species or reaction in chem_last_error) for sizes out of
+ * range (1 <= ns <= 4096, 1 <= ne <= 64, 0 <= nr <= 30000), a NULL array, a non-positive or
+ * non-finite atomic mass, a negative element count, a species of non-positive molar mass,
+ * non-finite NASA coefficients, a reaction type outside 0..2, a species index outside [-1, ns),
+ * an empty side, A < 0 or non-finite b / Ea, a negative or non-finite third-body efficiency, or
+ * Troe parameters that are non-finite, have A0 < 0, T3 <= 0 or T1 <= 0, or has_t2 outside
+ * {0, 1}.  CHEM_ECUDA / CHEM_ENOMEM if the upload fails. */
 int chem_load_mechanism_desc(const chem_mech_desc* desc, chem_mech_t* out);
 /* Release a mechanism's device copy (cudaFree, which waits for device work still using it); the
  * handle is invalid afterwards.  CHEM_EINVAL for NULL. */
@@ -354,7 +361,9 @@ int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_options* opt, ch
 int chem_serve_register_state(chem_server_t s, chem_mech_t m, chem_model_t model, double* T,
                               double* p, double* Y, int64_t ld, int64_t ncells, int* state_id);
 /* Queue one sub-step of a registered state.  CHEM_EBUSY if the request could never be admitted
- * (its workspace exceeds the budget left by the resident states). */
+ * (its workspace exceeds the budget left by the resident states).  A queued request that stops
+ * fitting because states registered after it took the budget fails (CHEM_REQ_FAILED) as soon as
+ * nothing else is running, instead of waiting forever. */
 int chem_serve_submit(chem_server_t s, int state_id, int route, double dt, double rtol,
                       double atol, uint64_t* req_id);
 /* Non-blocking: *state = CHEM_REQ_*, *latency_s (nullable) = seconds from submission to
@@ -365,7 +374,8 @@ int chem_serve_wait(chem_server_t s, uint64_t req_id, double timeout_s);
 /* out[8]: completed, failed, launches (jobs and surrogate launches), requests launched, max
  * concurrent launches, bytes in use, FP64 time slices issued, 0 */
 int chem_serve_stats(chem_server_t s, int64_t* out);
-/* Stops the server after its launches finish; queued requests fail. */
+/* Stops the server after its launches finish; queued requests fail and callers blocked in
+ * chem_serve_wait on them return.  No call on the server may start once this is entered. */
 int chem_serve_destroy(chem_server_t s);
 
 /* ---------------------------------------------------------------------------------------

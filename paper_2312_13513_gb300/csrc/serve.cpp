@@ -98,6 +98,7 @@ struct chem_server_s {
   std::condition_variable cv_work, cv_done;
   std::thread th;
   bool stop = false;
+  uint64_t n_submitted = 0;                    // submissions so far: the idle server waits for a new one
   int64_t n_launches = 0, n_batched = 0, n_done = 0, n_failed = 0, max_concurrent = 0, n_slices = 0;
   double idle_poll_us = 20.0;
   unsigned long long slice_ns = 20000000ull;   // 0: FP64 jobs run unsliced
@@ -117,6 +118,7 @@ void server_loop(chem_server_s* S) {
   cudaSetDevice(S->device);
   std::unique_lock<std::mutex> lk(S->mu);
   for (;;) {
+    const uint64_t submitted = S->n_submitted;
     // ---- retire finished launches ----
     bool progressed = false;
     for (size_t i = 0; i < S->launches.size();) {
@@ -181,7 +183,8 @@ void server_loop(chem_server_s* S) {
       // FP64 requests grouped by mechanism (one batched launch each) and surrogate requests
       std::map<chem_mech_t, std::vector<uint64_t>> fp64;
       std::vector<uint64_t> sur;
-      size_t avail = S->budget - S->resident - S->inflight;
+      // states registered while requests run can take resident + inflight past the budget
+      size_t avail = S->resident + S->inflight < S->budget ? S->budget - S->resident - S->inflight : 0;
       std::deque<uint64_t> keep;
       for (uint64_t id : S->pending) {
         Req& r = S->reqs[id];
@@ -208,6 +211,7 @@ void server_loop(chem_server_s* S) {
       }
       for (uint64_t id : sur) groups.push_back({id});
       std::vector<uint64_t> back;
+      bool launched = false;             // a group was launched or failed: look again right away
       for (auto& grp : groups) {
         // FP64 jobs on the low-priority streams, surrogate launches on the high-priority ones: when
         // a slice's blocks retire, the block scheduler starts a waiting surrogate launch first
@@ -265,6 +269,7 @@ void server_loop(chem_server_s* S) {
             ++S->n_failed;
           }
           S->cv_done.notify_all();
+          launched = true;
           continue;
         }
         L.stream = sidx;
@@ -280,13 +285,29 @@ void server_loop(chem_server_s* S) {
         if (L.sliced) ++S->n_slices;
         S->n_batched += (int64_t)grp.size();
         S->max_concurrent = std::max<int64_t>(S->max_concurrent, (int64_t)S->launches.size());
+        launched = true;
       }
       for (auto it = back.rbegin(); it != back.rend(); ++it) S->pending.push_front(*it);
-      if (!groups.empty()) continue;    // look again right away
+      // groups that found no free stream wait (below) for a launch to retire, with the lock released
+      if (launched) continue;
     }
     // ---- wait ----
     if (S->launches.empty()) {
-      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+      // nothing runs, so every queued request that fits was just launched: what is left can never
+      // fit (states registered after it took the budget) and fails rather than waiting forever
+      if (!S->stop && !S->pending.empty()) {
+        const Clock::time_point now = Clock::now();
+        for (uint64_t id : S->pending) {
+          Req& r = S->reqs[id];
+          r.status = Q_FAILED;
+          r.error = "request no longer fits the memory budget left by the resident states";
+          r.t_done = now;
+          ++S->n_failed;
+        }
+        S->pending.clear();
+        S->cv_done.notify_all();
+      }
+      S->cv_work.wait(lk, [&] { return S->stop || S->n_submitted != submitted; });
     } else {
       lk.unlock();
       std::this_thread::sleep_for(std::chrono::microseconds((int)S->idle_poll_us));
@@ -387,6 +408,7 @@ extern "C" int chem_serve_submit(chem_server_t S, int state_id, int route, doubl
   r.t_submit = Clock::now();
   S->reqs[r.id] = r;
   S->pending.push_back(r.id);
+  ++S->n_submitted;
   *req_id = r.id;
   S->cv_work.notify_one();
   return CHEM_OK;
@@ -433,14 +455,18 @@ extern "C" int chem_serve_destroy(chem_server_t S) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
     // queued requests that never started are dropped as failed
+    const Clock::time_point now = Clock::now();
     for (uint64_t id : S->pending) {
       Req& r = S->reqs[id];
       r.status = Q_FAILED;
       r.error = "server destroyed";
+      r.t_done = now;
+      ++S->n_failed;
     }
     S->pending.clear();
   }
   S->cv_work.notify_all();
+  S->cv_done.notify_all();
   if (S->th.joinable()) S->th.join();
   for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
   cudaFree(S->d_counter);
