@@ -452,7 +452,10 @@ typedef struct chem_fvmesh_desc {
   const double* volume;      /* [n_cells] */
 } chem_fvmesh_desc;
 /* Upload a mesh; builds the cell-to-face index and the CSR pattern of its matrices.  At most
- * 2^31 - 1 cells and 2^29 - 1 faces of each kind. */
+ * 2^31 - 1 cells and 2^29 - 1 faces of each kind, and n_cells + 2 n_faces (the matrix entries)
+ * at most 2^31 - 1.  Checked on the host before any device work: CHEM_EINVAL for sizes out of
+ * range, a NULL array, a face whose owner is not below its neighbour or whose cells are outside
+ * the mesh, or a boundary face with a cell outside the mesh or a patch type other than 0 or 1. */
 int chem_fvmesh_create(const chem_fvmesh_desc* desc, chem_fvmesh_t* out);
 /* Release the mesh's device arrays, the CSR pattern included (cudaFree, which waits for device
  * work still using them).  CHEM_EINVAL for NULL. */

@@ -174,6 +174,10 @@ extern "C" int chem_fvmesh_create(const chem_fvmesh_desc* d, chem_fvmesh_t* out)
     set_error("bad mesh description");
     return CHEM_EINVAL;
   }
+  if (n + 2 * nf > INT32_MAX) {      // the CSR pattern's row pointers are 32-bit
+    set_error("mesh too large: %lld matrix entries exceed 2^31 - 1", (long long)(n + 2 * nf));
+    return CHEM_EINVAL;
+  }
   for (int64_t f = 0; f < nf; ++f)
     if (d->owner[f] < 0 || d->neighbour[f] >= n || d->owner[f] >= d->neighbour[f]) {
       set_error("face %lld: owner must be below neighbour, both cells of the mesh", (long long)f);

@@ -124,3 +124,36 @@ def test_mechanism_descriptions_are_validated_on_the_host():
         assert rc != _lib.CHEM_EINVAL, L.chem_last_error()
         if rc == _lib.CHEM_OK:
             L.chem_free_mechanism(h)
+
+
+def test_mesh_descriptions_are_validated_on_the_host():
+    """chem_fvmesh_create checks face addressing and patch types before any device work; the
+    intact mesh passes the checks (on a host without a GPU it then fails at the upload)."""
+    import copy
+    import paper_2312_13513_gb300 as cg
+    from paper_2312_13513_gb300 import _lib
+    from synth.mesh import box_mesh
+    m = box_mesh(4, 3, 2, seed=1, permute=True)
+
+    def bad(**kw):
+        b = copy.deepcopy(m)
+        for k, (i, v) in kw.items():
+            getattr(b, k)[i] = v
+        return b
+
+    cases = {"owner not below neighbour": bad(owner=(0, int(m.neighbour[0]))),
+             "neighbour outside": bad(neighbour=(1, m.n_cells)),
+             "owner negative": bad(owner=(2, -1)),
+             "boundary cell outside": bad(b_cell=(0, m.n_cells)),
+             "patch type": bad(b_type=(3, 2))}
+    for what, mesh in cases.items():
+        try:
+            cg.FvMesh(mesh)
+        except cg.ChemError as e:
+            assert e.code == _lib.CHEM_EINVAL, what
+        else:
+            raise AssertionError(f"{what}: accepted")
+    try:
+        cg.FvMesh(m).close()
+    except cg.ChemError as e:
+        assert e.code != _lib.CHEM_EINVAL, str(e)
