@@ -125,9 +125,11 @@ int chem_advance(chem_mech_t m, double* T, const double* p, double* Y, double dt
 
 /* Extended form.  idx (device, nullable): advance only cells idx[0..ncells) of arrays whose
  * leading dimension is ld (indexed mode, used for surrogate fallback); otherwise cells
- * [0, ncells).  status (int8), nsub (accepted sub-steps), nrej (rejected attempts): device
- * arrays indexed like the cells they describe (by idx[c] in indexed mode), each nullable.
- * opt nullable (defaults). */
+ * [0, ncells).  The indices must be distinct and lie in [0, ld): they live on the device and are
+ * not checked (an index outside is an out-of-bounds device access, a repeated one a data race).
+ * status (int8), nsub (accepted sub-steps), nrej (rejected attempts): device arrays indexed like
+ * the cells they describe (by idx[c] in indexed mode), each nullable.  opt nullable
+ * (defaults). */
 int chem_advance_ex(chem_mech_t m, double* T, const double* p, double* Y, int64_t ld,
                     double dt, int64_t ncells, double rtol, double atol, const int32_t* idx,
                     int8_t* status, int32_t* nsub, int32_t* nrej, const chem_options* opt,
