@@ -142,7 +142,7 @@ typedef struct chem_segment {
   const double* p;
   double* Y;
   int64_t ld, ncells;
-  const int32_t* idx;        /* nullable: cells idx[0..ncells) */
+  const int32_t* idx;        /* nullable: cells idx[0..ncells), distinct and in [0, ld) (unchecked) */
   int8_t* status;            /* nullable outputs, as for chem_advance_ex */
   int32_t* nsub;
   int32_t* nrej;
