@@ -101,11 +101,14 @@ def build(name):
     lib = os.path.join(OUT, f"{name}.so")
     text = planted_source(name)
     if not (os.path.exists(src) and open(src).read() == text and os.path.exists(lib)):
-        with open(src, "w") as f:
+        # private names while building, so that concurrent test processes never share a file
+        tag = f".{os.getpid()}"
+        with open(src + tag, "w") as f:
             f.write(text)
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
-                               "-I", os.path.join(ROOT, "oracle"), "-o", lib + ".tmp", src])
-        os.replace(lib + ".tmp", lib)
+                               "-I", os.path.join(ROOT, "oracle"), "-x", "c++", "-o", lib + tag, src + tag])
+        os.replace(lib + tag, lib)
+        os.replace(src + tag, src)
     return lib
 
 
