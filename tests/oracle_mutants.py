@@ -196,6 +196,15 @@ PY_MUTANTS = {
         [("        T -= dT", "        T += dT", 1)]),
     "heat_release_without_W": ("surrogate", "heat release with molar enthalpies times mass fractions",
         [("hk * (np.asarray(Y1) - np.asarray(Y0)) / om.W", "hk * (np.asarray(Y1) - np.asarray(Y0))", 1)]),
+    "equilibrium_pressure_sign": ("equilibrium", "Gibbs function with - ln(p / p_atm)",
+        [("g = (h_RT - s_R)[keep] + np.log(p / om.PATM)", "g = (h_RT - s_R)[keep] - np.log(p / om.PATM)", 1)]),
+    "equilibrium_mole_fractions_as_mass": ("equilibrium", "equilibrium mole fractions returned as mass fractions",
+        [("    Y = x_full * om.W\n", "    Y = x_full * 1.0\n", 1)]),
+    "equilibrium_entropy_dropped": ("equilibrium", "Gibbs function h/RT without - s/R",
+        [("g = (h_RT - s_R)[keep] + np.log(p / om.PATM)", "g = (h_RT - 0.0 * s_R)[keep] + np.log(p / om.PATM)", 1)]),
+    "hp_frozen_composition": ("equilibrium", "adiabatic temperature from the initial composition's enthalpy",
+        [("        r = om.enthalpy_mass(T, Y) - h0\n", "        r = om.enthalpy_mass(T, Y0) - h0\n", 1),
+         ("        return om.enthalpy_mass(T, Y) - h0\n", "        return om.enthalpy_mass(T, Y0) - h0\n", 1)]),
 }
 
 

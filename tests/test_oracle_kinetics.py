@@ -88,6 +88,25 @@ def test_detailed_balance_at_gibbs_equilibrium(which, fuel, request):
                 assert abs(q[j]) <= 1e-8 * fwd, (j, q[j], fwd)
 
 
+@pytest.mark.parametrize("p_atm", [0.05, 40.0])
+def test_detailed_balance_away_from_one_atmosphere(p_atm, om_h2, h2):
+    """The same at 0.05 and 40 atm: the pressure enters the Gibbs minimisation through
+    ln(p / p_atm) and the kinetics through Kc's (p_atm / RT)^dnu, independently."""
+    T, _, Y = random_states(h2, 3, 13, "H2", Tlo=1500.0, Thi=2500.0)
+    p = p_atm * PATM
+    for i in range(T.size):
+        Yeq, _, info = equilibrate_tp(om_h2, T[i], p, element_moles(om_h2, Y[:, i]))
+        assert info["resid"] < 1e-12
+        w, q, kf, kr = om_h2.rates(T[i], p, Yeq)
+        C = om_h2.density(T[i], p, Yeq) * Yeq / om_h2.W
+        for j in range(h2.nr):
+            fwd = kf[j] * np.prod([C[k] for k in h2.reac[j] if k >= 0])
+            if h2.rtype[j] == 1:
+                fwd *= np.dot(h2.eff[j], C)
+            if fwd > 1e-250:
+                assert abs(q[j]) <= 1e-8 * fwd, (p_atm, j, q[j], fwd)
+
+
 def _troe_mech(mech):
     j = int(np.nonzero(mech.rtype == TROE)[0][0])
     return j

@@ -75,10 +75,18 @@ PY_CAUGHT_BY = {
     "projection_normal_matrix_unweighted": ["projection"],
     "newton_step_sign": ["T_from_h"],
     "heat_release_without_W": ["heat_release"],
+    "equilibrium_pressure_sign": ["detailed_balance_off_1atm"],
+    "equilibrium_mole_fractions_as_mass": ["detailed_balance"],
+    "equilibrium_entropy_dropped": ["detailed_balance"],
+    "hp_frozen_composition": ["long_time_equilibrium"],
 }
 
-# where each pin module holds the oracle module it checks
-_PY_TARGET = {"fvm": (F, "fvm"), "transport": (TT, "ot"), "mlp": (S, "mlp"), "surrogate": (S, "sur")}
+# where the pin modules hold what they use of each oracle module: (pin module, name there, name
+# in the oracle module, or None for the module itself)
+_PY_TARGET = {"fvm": [(F, "fvm", None)], "transport": [(TT, "ot", None)], "mlp": [(S, "mlp", None)],
+              "surrogate": [(S, "sur", None)],
+              "equilibrium": [(K, "equilibrate_tp", "equilibrate_tp"), (K, "element_moles", "element_moles"),
+                              (I, "equilibrate_hp", "equilibrate_hp")]}
 
 
 def _py_pins(om, h2, h2_tr):
@@ -106,6 +114,11 @@ def _py_pins(om, h2, h2_tr):
         "projection": lambda: S.test_projection_conserves_and_is_weighted_least_squares(h2, om),
         "T_from_h": lambda: S.test_temperature_from_enthalpy(h2, om),
         "heat_release": lambda: S.test_heat_release_matches_energy_equation(h2, om),
+        "detailed_balance": lambda: K.test_detailed_balance_at_gibbs_equilibrium(
+            "h2", "H2", _Fixtures(om_h2=om, h2=h2)),
+        "detailed_balance_off_1atm": lambda: [K.test_detailed_balance_away_from_one_atmosphere(pa, om, h2)
+                                              for pa in (0.05, 40.0)],
+        "long_time_equilibrium": lambda: I.test_long_time_limit_is_gibbs_equilibrium(om, h2),
     }
 
 
@@ -185,7 +198,8 @@ def h2_transport(h2):
 
 @pytest.mark.parametrize("name", list(PY_MUTANTS))
 def test_planted_mistake_in_python_oracle_is_caught(name, h2, om_h2, h2_transport, monkeypatch):
-    module, attr = _PY_TARGET[PY_MUTANTS[name][0]]
-    monkeypatch.setattr(module, attr, planted_module(name))
+    planted = planted_module(name)
+    for module, attr, fn in _PY_TARGET[PY_MUTANTS[name][0]]:
+        monkeypatch.setattr(module, attr, planted if fn is None else getattr(planted, fn))
     survived = _failing(_py_pins(om_h2, h2, h2_transport), PY_CAUGHT_BY[name])
     assert not survived, f"{name} ({PY_MUTANTS[name][1]}) passes {survived}"
