@@ -108,26 +108,35 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        with open(self.path) as f:
+            out = parse_clock_samples(f)
         os.unlink(self.path)
-        if not rows:
-            return out
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        out["samples"] = len(rows)
-        out["sm_mhz"] = statistics.median(sm) if sm else None
-        try:
-            out["sm_max_mhz"] = float(rows[0][2])
-        except ValueError:
-            pass
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for i, nm in enumerate(names):
-            if any(r[5 + i].lower() == "active" for r in rows):
-                out["reasons"].append(nm)
         return out
+
+
+def parse_clock_samples(lines):
+    """Summary of nvidia-smi samples in ClockSampler.Q's column order (csv, noheader, nounits):
+    median SM clock, maximum SM clock, and each throttle reason that was Active in any sample."""
+    out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) >= 9:
+            rows.append(parts)
+    if not rows:
+        return out
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    out["samples"] = len(rows)
+    out["sm_mhz"] = statistics.median(sm) if sm else None
+    try:
+        out["sm_max_mhz"] = float(rows[0][2])
+    except ValueError:
+        pass
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for i, nm in enumerate(names):
+        if any(r[5 + i].lower() == "active" for r in rows):
+            out["reasons"].append(nm)
+    return out
 
 
 def make_field(rank=0, n=NCELLS):

@@ -42,3 +42,19 @@ def test_reference_arm_under_torchrun_prints_once_from_rank_zero():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_clock_samples_summary():
+    """The timed region's clock record: median SM clock, the maximum, and every throttle reason
+    seen Active in any sample (the reasons a run is rejected for, and sw_power_cap, which is kept
+    and noted)."""
+    import bench
+    rows = ["0, 1965, 2070, 1010.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 1980, 2070, 1050.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 2010, 2070, 990.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    d = bench.parse_clock_samples(rows)
+    assert d == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = rows[:1] + ["0, 1200, 2070, 900.0, 0x0000000000000040, Not Active, Active, Not Active, Not Active"]
+    assert bench.parse_clock_samples(hot)["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert bench.parse_clock_samples([])["samples"] == 0
