@@ -196,6 +196,8 @@ PY_MUTANTS = {
         [("        T -= dT", "        T += dT", 1)]),
     "heat_release_without_W": ("surrogate", "heat release with molar enthalpies times mass fractions",
         [("hk * (np.asarray(Y1) - np.asarray(Y0)) / om.W", "hk * (np.asarray(Y1) - np.asarray(Y0))", 1)]),
+    "features_pressure_not_logarithm": ("surrogate", "pressure feature p instead of ln p",
+        [("np.log(np.asarray(p))[:, None]", "np.asarray(p, np.float64)[:, None]", 1)]),
     "equilibrium_pressure_sign": ("equilibrium", "Gibbs function with - ln(p / p_atm)",
         [("g = (h_RT - s_R)[keep] + np.log(p / om.PATM)", "g = (h_RT - s_R)[keep] - np.log(p / om.PATM)", 1)]),
     "equilibrium_mole_fractions_as_mass": ("equilibrium", "equilibrium mole fractions returned as mass fractions",

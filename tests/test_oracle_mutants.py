@@ -75,6 +75,7 @@ PY_CAUGHT_BY = {
     "projection_normal_matrix_unweighted": ["projection"],
     "newton_step_sign": ["T_from_h"],
     "heat_release_without_W": ["heat_release"],
+    "features_pressure_not_logarithm": ["features"],
     "equilibrium_pressure_sign": ["detailed_balance_off_1atm"],
     "equilibrium_mole_fractions_as_mass": ["detailed_balance"],
     "equilibrium_entropy_dropped": ["detailed_balance"],
@@ -111,6 +112,7 @@ def _py_pins(om, h2, h2_tr):
         "finite_differences": S.test_backward_matches_finite_differences,
         "adam": S.test_adam_first_step_is_signed_lr,
         "boxcox": S.test_boxcox_roundtrip_and_log_limit,
+        "features": S.test_features_are_T_log_p_and_boxcox,
         "projection": lambda: S.test_projection_conserves_and_is_weighted_least_squares(h2, om),
         "T_from_h": lambda: S.test_temperature_from_enthalpy(h2, om),
         "heat_release": lambda: S.test_heat_release_matches_energy_equation(h2, om),

@@ -152,3 +152,19 @@ def test_heat_release_matches_energy_equation(h2, om_h2):
         f = om_h2.rhs(p[i], y0)
         q_ref = om_h2.density(T[i], p[i], Y[:, i]) * om_h2.cp_mass(T[i], Y[:, i]) * f[0]
         assert abs(q - q_ref) <= 1e-5 * abs(q_ref)
+
+
+def test_features_are_T_log_p_and_boxcox():
+    """The feature row [T, ln p, BC(Y_1..Y_ns)]: the pressure feature of p^2 is twice that of p
+    (a logarithm), T passes through, and the composition columns are the Box-Cox transforms
+    checked above."""
+    rng = np.random.default_rng(4)
+    n, ns = 5, 4
+    T = rng.uniform(300, 2500, n)
+    p = rng.uniform(2.0, 50.0, n)
+    Y = rng.dirichlet(np.ones(ns), n).T
+    x1, x2 = sur.features(T, p, Y), sur.features(T, p * p, Y)
+    assert x1.shape == (n, ns + 2)
+    assert np.array_equal(x1[:, 0], T)
+    assert np.allclose(x2[:, 1], 2.0 * x1[:, 1], rtol=1e-14, atol=0)
+    assert np.array_equal(x1[:, 2:], sur.boxcox(Y).T)
