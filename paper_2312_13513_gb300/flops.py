@@ -23,6 +23,17 @@ def _rxn_sides(mech):
     return nre, npr
 
 
+def lu_flops(N):
+    """Dense LU with partial pivoting of an N x N matrix: per column k, N-k-1 multipliers and a
+    rank-one update of (N-k-1)^2 multiply-adds, plus the N pivot reciprocals."""
+    return sum((N - k - 1) + 2 * (N - k - 1) ** 2 for k in range(N)) + N
+
+
+def solve_flops(N):
+    """Forward (unit lower) and backward substitution with the factors: 2 N^2 - N."""
+    return 2 * N * N - N
+
+
 def counts(mech):
     """dict of per-event (flops, transcendentals) for one cell of this mechanism."""
     ns, nr = mech.ns, mech.nr
@@ -81,8 +92,8 @@ def counts(mech):
     jac_tr = ntroe * 2
 
     # ---- one Rodas4 attempt ----------------------------------------------------------------
-    lu = sum((N - k - 1) + 2 * (N - k - 1) ** 2 for k in range(N)) + N
-    solve = 2 * N * N - N
+    lu = lu_flops(N)
+    solve = solve_flops(N)
     att = 3 + N * N + lu + 6 * solve
     att += sum(N * 2 * s for s in range(1, 6))            # stage arguments
     att += sum(N * 2 * s + s for s in range(1, 6))        # stage right-hand sides
