@@ -167,6 +167,12 @@ def _pins(om, h2, ch4):
 
 
 @pytest.fixture(scope="module")
+def h2_transport(h2):
+    from synth.transport import generate_transport
+    return h2, generate_transport(h2)
+
+
+@pytest.fixture(scope="module")
 def mutant_libs():
     return build_all()
 
@@ -177,6 +183,17 @@ def test_every_mutant_has_catching_pins():
     assert all(CAUGHT_BY[n] and set(CAUGHT_BY[n]) <= known for n in CAUGHT_BY)
     known = set(_py_pins(None, None, None))
     assert all(PY_CAUGHT_BY[n] and set(PY_CAUGHT_BY[n]) <= known for n in PY_CAUGHT_BY)
+
+
+def test_every_pin_passes_through_the_harness_on_the_real_oracle(h2, ch4, om_h2, h2_transport):
+    """The control: called through the same harness on the untouched oracle, no pin fails, so a
+    failure under a planted mistake is the mistake's doing and not the harness's."""
+    om = oracle.OracleMech(h2)
+    failed = [pin for pin in _pins(om, h2, ch4) if not _failing(_pins(om, h2, ch4), [pin])]
+    assert not failed, failed
+    failed = [pin for pin in _py_pins(om_h2, h2, h2_transport)
+              if not _failing(_py_pins(om_h2, h2, h2_transport), [pin])]
+    assert not failed, failed
 
 
 @pytest.mark.parametrize("name", list(MUTANTS))
@@ -190,12 +207,6 @@ def test_planted_mistake_is_caught(name, mutant_libs, h2, ch4, monkeypatch):
     finally:
         L.or_mech_free(om.h)
         om.h = None
-
-
-@pytest.fixture(scope="module")
-def h2_transport(h2):
-    from synth.transport import generate_transport
-    return h2, generate_transport(h2)
 
 
 @pytest.mark.parametrize("name", list(PY_MUTANTS))
