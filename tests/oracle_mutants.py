@@ -179,6 +179,10 @@ PY_MUTANTS = {
         [('dz = da * gelu_grad(cache["z"][l - 1])', 'dz = da * gelu_grad(cache["a"][l])', 1)]),
     "loss_gradient_scale": ("mlp", "loss gradient divided by the batch only",
         [("dz = 2.0 * (out - target) / (M * n_out)", "dz = 2.0 * (out - target) / M", 1)]),
+    "hidden_activations_not_rounded": ("mlp", "BF16 emulation leaves the hidden activations unrounded",
+        [("            a = rnd(gelu(z))\n            acts.append(a)\n", "            a = gelu(z)\n            acts.append(a)\n", 1)]),
+    "hidden_weights_not_rounded": ("mlp", "BF16 emulation leaves the weights of layers 2-5 unrounded",
+        [("        W = rnd(Ws[l])\n", "        W = np.asarray(Ws[l], np.float64)\n", 1)]),
     "adam_no_bias_correction": ("mlp", "Adam's first moment without bias correction",
         [("mh = m[i] / (1.0 - beta1 ** step)", "mh = m[i]", 1)]),
     "bf16_ties_down": ("mlp", "BF16 rounding with ties always down",

@@ -67,6 +67,8 @@ PY_CAUGHT_BY = {
     "gelu_grad_sign": ["gelu_forms", "finite_differences"],
     "backward_derivative_at_activation": ["finite_differences"],
     "loss_gradient_scale": ["finite_differences"],
+    "hidden_activations_not_rounded": ["bf16_points"],
+    "hidden_weights_not_rounded": ["bf16_points"],
     "adam_no_bias_correction": ["adam"],
     "bf16_ties_down": ["bf16_known"],
     "first_layer_drops_weight_correction": ["first_layer"],
@@ -111,6 +113,7 @@ def _py_pins(om, h2, h2_tr):
         "first_layer": S.test_compensated_first_layer_error_bound,
         "finite_differences": S.test_backward_matches_finite_differences,
         "adam": S.test_adam_first_step_is_signed_lr,
+        "bf16_points": S.test_bf16_emulation_rounds_where_the_gpu_holds_bf16,
         "boxcox": S.test_boxcox_roundtrip_and_log_limit,
         "features": S.test_features_are_T_log_p_and_boxcox,
         "projection": lambda: S.test_projection_conserves_and_is_weighted_least_squares(h2, om),

@@ -168,3 +168,20 @@ def test_features_are_T_log_p_and_boxcox():
     assert np.array_equal(x1[:, 0], T)
     assert np.allclose(x2[:, 1], 2.0 * x1[:, 1], rtol=1e-14, atol=0)
     assert np.array_equal(x1[:, 2:], sur.boxcox(Y).T)
+
+
+def test_bf16_emulation_rounds_where_the_gpu_holds_bf16():
+    """With BF16 emulation, every hidden activation is a BF16 value (a fixed point of the
+    rounding), the weights of layers 2-5 enter rounded (rounding them beforehand changes
+    nothing), and the first layer is compensated (rounding its weights beforehand does change
+    the output)."""
+    rng = np.random.default_rng(6)
+    Ws, bs = _net(rng, [11, 32, 32, 32, 32, 9])
+    x = rng.standard_normal((8, 11)) * 3.0
+    out, cache = mlp.forward(Ws, bs, x, emulate_bf16=True)
+    for a in cache["a"][1:]:
+        assert np.array_equal(mlp.bf16_round(a), a)
+    pre = [Ws[0]] + [mlp.bf16_round(W) for W in Ws[1:]]
+    assert np.array_equal(mlp.forward(pre, bs, x, emulate_bf16=True)[0], out)
+    pre0 = [mlp.bf16_round(Ws[0])] + Ws[1:]
+    assert not np.array_equal(mlp.forward(pre0, bs, x, emulate_bf16=True)[0], out)
