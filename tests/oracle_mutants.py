@@ -202,6 +202,9 @@ PY_MUTANTS = {
         [("hk * (np.asarray(Y1) - np.asarray(Y0)) / om.W", "hk * (np.asarray(Y1) - np.asarray(Y0))", 1)]),
     "features_pressure_not_logarithm": ("surrogate", "pressure feature p instead of ln p",
         [("np.log(np.asarray(p))[:, None]", "np.asarray(p, np.float64)[:, None]", 1)]),
+    "hrr_error_normalised_by_surrogate": ("surrogate", "heat-release error divided by the surrogate's field",
+        [("return float(np.sum(np.abs(q_sur - q_ref)) / np.sum(np.abs(q_ref)))",
+          "return float(np.sum(np.abs(q_sur - q_ref)) / np.sum(np.abs(q_sur)))", 1)]),
     "equilibrium_pressure_sign": ("equilibrium", "Gibbs function with - ln(p / p_atm)",
         [("g = (h_RT - s_R)[keep] + np.log(p / om.PATM)", "g = (h_RT - s_R)[keep] - np.log(p / om.PATM)", 1)]),
     "equilibrium_mole_fractions_as_mass": ("equilibrium", "equilibrium mole fractions returned as mass fractions",

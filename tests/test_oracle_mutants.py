@@ -78,6 +78,7 @@ PY_CAUGHT_BY = {
     "newton_step_sign": ["T_from_h"],
     "heat_release_without_W": ["heat_release"],
     "features_pressure_not_logarithm": ["features"],
+    "hrr_error_normalised_by_surrogate": ["hrr_error"],
     "equilibrium_pressure_sign": ["detailed_balance_off_1atm"],
     "equilibrium_mole_fractions_as_mass": ["detailed_balance"],
     "equilibrium_entropy_dropped": ["detailed_balance"],
@@ -116,6 +117,7 @@ def _py_pins(om, h2, h2_tr):
         "bf16_points": S.test_bf16_emulation_rounds_where_the_gpu_holds_bf16,
         "boxcox": S.test_boxcox_roundtrip_and_log_limit,
         "features": S.test_features_are_T_log_p_and_boxcox,
+        "hrr_error": S.test_heat_release_error_closed_forms,
         "projection": lambda: S.test_projection_conserves_and_is_weighted_least_squares(h2, om),
         "T_from_h": lambda: S.test_temperature_from_enthalpy(h2, om),
         "heat_release": lambda: S.test_heat_release_matches_energy_equation(h2, om),

@@ -185,3 +185,16 @@ def test_bf16_emulation_rounds_where_the_gpu_holds_bf16():
     assert np.array_equal(mlp.forward(pre, bs, x, emulate_bf16=True)[0], out)
     pre0 = [mlp.bf16_round(Ws[0])] + Ws[1:]
     assert not np.array_equal(mlp.forward(pre0, bs, x, emulate_bf16=True)[0], out)
+
+
+def test_heat_release_error_closed_forms():
+    """The field L1-relative heat-release error sum |q - q_ref| / sum |q_ref|: zero for the
+    reference itself, exactly 1 for twice the reference and for a zero field, 2 for its negation
+    (a sign flip counts in full), and 1/2 against a reference twice the field: it normalises by
+    the reference, not by the surrogate."""
+    q_ref = np.array([3.0, -1.0, 0.5, 8.0])
+    assert sur.hrr_error(q_ref, q_ref) == 0.0
+    assert sur.hrr_error(2.0 * q_ref, q_ref) == pytest.approx(1.0, rel=1e-15)
+    assert sur.hrr_error(np.zeros(4), q_ref) == pytest.approx(1.0, rel=1e-15)
+    assert sur.hrr_error(-q_ref, q_ref) == pytest.approx(2.0, rel=1e-15)
+    assert sur.hrr_error(q_ref, 2.0 * q_ref) == pytest.approx(0.5, rel=1e-15)
