@@ -79,6 +79,8 @@ MUTANTS = {
     "lu_forward_transposed": ("forward substitution reads the upper triangle (transposed index)",
                               [("for (int j = 0; j < i; ++j) x[i] -= a[(size_t)i * N + j] * x[j];",
                                 "for (int j = 0; j < i; ++j) x[i] -= a[(size_t)j * N + i] * x[j];", 1)]),
+    "step_acceptance_loose": ("steps accepted with an error norm up to 100 instead of 1",
+                              [("if (env <= 1.0) {", "if (env <= 100.0) {", 1)]),
     "rk4_weight": ("brute-force RK4 with weight 1 on k3 instead of 2",
                    [("2.0 * k2[i] + 2.0 * k3[i] + k4[i]", "2.0 * k2[i] + k3[i] + k4[i]", 1)]),
 }

@@ -106,6 +106,26 @@ def test_isomerisation_closed_form():
         assert y[0] == pytest.approx(T0, abs=1e-9)
 
 
+def test_global_error_stays_within_the_requested_tolerance():
+    """The adaptive control delivers the accuracy it is asked for: on the isomerisation with its
+    closed-form solution, over one and five relaxation times and at rtol from 1e-3 to 1e-6, the
+    global error of Y_B stays below rtol (Y_B is of order one)."""
+    m = _isomer_mech()
+    om = oracle.OracleMech(m)
+    T0, p = 1300.0, PATM
+    Y0 = np.array([0.8, 0.2])
+    _, _, kf, kr = om.rates(T0, p, Y0)
+    ksum = kf[0] + kr[0]
+    Yeq = kr[0] / ksum
+    for n_tau in (1.0, 5.0):
+        dt = n_tau / ksum
+        exact = Yeq + (Y0[0] - Yeq) * np.exp(-ksum * dt)
+        for rtol in (1e-3, 1e-4, 1e-5, 1e-6):
+            y, st, _, _ = om.rodas4(p, np.r_[T0, Y0], dt, rtol, 1e-20)
+            assert st == 0
+            assert abs(y[1] - exact) <= rtol, (n_tau, rtol, abs(y[1] - exact))
+
+
 def test_rodas4_matches_rk4_brute_force(om_h2, h2):
     T, p, Y = prereacted_mixing_states(om_h2, h2, 16, 12345)
     dt = 1e-6
