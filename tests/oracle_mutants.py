@@ -81,6 +81,9 @@ MUTANTS = {
                                 "for (int j = 0; j < i; ++j) x[i] -= a[(size_t)j * N + i] * x[j];", 1)]),
     "step_acceptance_loose": ("steps accepted with an error norm up to 100 instead of 1",
                               [("if (env <= 1.0) {", "if (env <= 100.0) {", 1)]),
+    "final_step_not_clipped": ("the last step runs its full length past the end of the interval",
+                               [("if (re(h) >= dt - re(t)) { h = S(dt) - t; last = true; }",
+                                 "if (re(h) >= dt - re(t)) { last = true; }", 1)]),
     "rk4_weight": ("brute-force RK4 with weight 1 on k3 instead of 2",
                    [("2.0 * k2[i] + 2.0 * k3[i] + k4[i]", "2.0 * k2[i] + k3[i] + k4[i]", 1)]),
 }

@@ -41,6 +41,7 @@ CAUGHT_BY = {
     "rodas4_gamma_dropped": ["linear_convergence", "isomerisation"],
     "lu_forward_transposed": ["linear_convergence", "isomerisation"],
     "step_acceptance_loose": ["tolerance"],
+    "final_step_not_clipped": ["isomerisation", "tolerance"],
     "rk4_weight": ["rk4_brute_force"],
 }
 
