@@ -158,6 +158,8 @@ PY_MUTANTS = {
     "fvm_ldu_lower_upper_swapped": ("fvm", "lower and upper exchanged in the ldu split",
         [("return A[nb, o].copy(), A[o, nb].copy(), np.diag(A).copy()",
           "return A[o, nb].copy(), A[nb, o].copy(), np.diag(A).copy()", 1)]),
+    "fvm_rows_diffusion_sign": ("fvm", "the row form adds the neighbour's diffusion coefficient",
+        [("                row[other] -= a\n", "                row[other] += a\n", 1)]),
     "pasr_mixing_time_without_sqrt": ("fvm", "mixing time without the square root",
         [("tmix = c_mix * np.sqrt(mu_eff[i] / (rho[i] * eps[i]))",
           "tmix = c_mix * mu_eff[i] / (rho[i] * eps[i])", 1)]),

@@ -57,6 +57,7 @@ PY_CAUGHT_BY = {
     "fvm_old_mass_new_density": ["time_term", "budget"],
     "fvm_source_without_volume": ["ldu_round_trip", "budget"],
     "fvm_ldu_lower_upper_swapped": ["ldu_round_trip"],
+    "fvm_rows_diffusion_sign": ["row_form"],
     "pasr_mixing_time_without_sqrt": ["pasr_limits"],
     "pasr_factor_inverted": ["pasr_limits"],
     "wilke_mass_ratio_inverted": ["wilke_reciprocity"],
@@ -105,6 +106,7 @@ def _py_pins(om, h2, h2_tr):
         "linear_diffusivity": F.test_linear_diffusivity_is_interpolated_exactly_to_the_faces,
         "time_term": F.test_time_term_alone_carries_each_cells_species_mass,
         "budget": F.test_open_box_species_budget,
+        "row_form": F.test_row_form_matches_the_dense_matrix,
         "pasr_limits": F.test_pasr_limits,
         "pure_limit": lambda: TT.test_pure_species_limit(h2_tr),
         "wilke_identical": TT.test_wilke_reduces_to_pure_value_for_identical_species,
