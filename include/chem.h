@@ -317,14 +317,17 @@ int chem_mlp_trainer_get(chem_trainer_t t, int which, float* const* W, float* co
 
 /* Training data: raw features x [n x (ns + 2)] = [T, ln p, BC(Y0)] and targets
  * t [n x ns] = BC(Y1) - BC(Y0) (difference formed in FP64) from states before (T0, p, Y0) and
- * after (Y1) a step. */
+ * after (Y1) a step.  Device arrays; CHEM_EINVAL for a NULL array, n < 0, ld < n or ns outside
+ * [1, 62].  Asynchronous on stream. */
 int chem_train_features(const double* T0, const double* p, const double* Y0, const double* Y1,
                         int64_t ld, int64_t n, int ns, float* x_raw, float* t_raw,
                         chem_stream_t stream);
-/* stats[4 x c] (device doubles): column sums, sums of squares, minima, maxima of A [n x c] */
+/* stats[4 x c] (device doubles): column sums, sums of squares, minima, maxima of A [n x c].
+ * CHEM_EINVAL for a NULL array, n < 1 or c outside [1, 64].  Asynchronous on stream. */
 int chem_column_stats(const float* A, int64_t n, int c, double* stats, chem_stream_t stream);
 /* v = (x - mean) / sd;  X row = [bf16(v) | bf16(v - bf16(v)) | bf16(v) | 0] (c columns each, zero
- * padded to ldx >= 3 c); Tn = (t - tmean) / tsd (t nullable) */
+ * padded to ldx >= 3 c); Tn = (t - tmean) / tsd (t nullable).  CHEM_EINVAL for a NULL array,
+ * n < 0, c < 1, ldx < 3 c, or t without tmean, tsd and Tn.  Asynchronous on stream. */
 int chem_train_normalize(const float* x, int64_t n, int c, const float* mean, const float* sd,
                          void* X, int ldx, const float* t, int ct, const float* tmean,
                          const float* tsd, float* Tn, chem_stream_t stream);
