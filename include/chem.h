@@ -84,7 +84,9 @@ typedef struct chem_mech_desc {
 } chem_mech_desc;
 
 /* Parse a CHEMMECH text file (format written by synth.mechanism.Mechanism.to_text) and upload
- * it to the current device.  *out receives a handle owned by the caller (chem_free_mechanism). */
+ * it to the current device.  *out receives a handle owned by the caller (chem_free_mechanism).
+ * CHEM_ENOTFOUND if the file cannot be opened; CHEM_EINVAL if it does not parse or fails the checks
+ * of chem_load_mechanism_desc; CHEM_ECUDA / CHEM_ENOMEM if the upload fails. */
 int chem_load_mechanism(const char* path, chem_mech_t* out);
 /* Same from an in-memory description.  The description is checked on the host before any device
  * work; CHEM_EINVAL (with the offending species or reaction in chem_last_error) for sizes out of
@@ -129,7 +131,10 @@ int chem_advance(chem_mech_t m, double* T, const double* p, double* Y, double dt
  * not checked (an index outside is an out-of-bounds device access, a repeated one a data race).
  * status (int8), nsub (accepted sub-steps), nrej (rejected attempts): device arrays indexed like
  * the cells they describe (by idx[c] in indexed mode), each nullable.  opt nullable
- * (defaults). */
+ * (defaults).
+ * The errors of chem_advance (ld < ncells only without idx), and CHEM_EINVAL for options the
+ * integrator cannot run: group_threads other than 0, 2, 4, ..., 256, or a mechanism too large for
+ * the launch's shared memory. */
 int chem_advance_ex(chem_mech_t m, double* T, const double* p, double* Y, int64_t ld,
                     double dt, int64_t ncells, double rtol, double atol, const int32_t* idx,
                     int8_t* status, int32_t* nsub, int32_t* nrej, const chem_options* opt,
@@ -153,7 +158,9 @@ typedef struct chem_segment {
  * persistent launch: their 8-cell chunks share one work queue, so small requests fill the GPU
  * together (iteration-level batching, used by the serving loop).  segs is a host array read
  * during the call; the call returns once the descriptors are on the device (it synchronises
- * the stream). */
+ * the stream).
+ * CHEM_EINVAL for a NULL mechanism or segment list, nseg < 1, or a segment with arguments
+ * chem_advance rejects. */
 int chem_advance_batch(chem_mech_t m, const chem_segment* segs, int nseg, chem_stream_t stream);
 
 /* Allocation-free form of chem_advance_ex (cells [0, ncells), default options).  It calls no
@@ -167,14 +174,16 @@ int chem_advance_batch(chem_mech_t m, const chem_segment* segs, int nseg, chem_s
  * must therefore happen outside any stream capture.  All calls share the array and the counter
  * is reset at the start of each call: calls whose work overlaps on the GPU race and must be
  * serialised by the caller (one stream, or events).  The scratch does not grow with ncells.
- * The paper has no counterpart of this entry point. */
+ * The paper has no counterpart of this entry point.
+ * The errors of chem_advance_ex. */
 int chem_advance_noalloc(chem_mech_t m, double* T, const double* p, double* Y, int64_t ld,
                          double dt, int64_t ncells, double rtol, double atol, int8_t* status,
                          int32_t* nsub, int32_t* nrej, chem_stream_t stream);
 
 /* Right-hand side f[i * ld + c] (i = 0 is dT/dt, i = 1 + k is dY_k/dt) and, if J is non-NULL,
  * the analytic Jacobian J[(i * N + j) * ld + c] = df_i/dy_j (N = ns + 1) of every cell, computed
- * by the same device code the integrator uses.  Device pointers; asynchronous. */
+ * by the same device code the integrator uses.  Device pointers; asynchronous.
+ * CHEM_EINVAL for a NULL mechanism, ncells < 0, ld < ncells, or (ncells > 0) a NULL T, p, Y or f. */
 int chem_eval_rhs_jac(chem_mech_t m, const double* T, const double* p, const double* Y,
                       int64_t ld, int64_t ncells, double* f, double* J, chem_stream_t stream);
 
@@ -203,7 +212,9 @@ typedef struct chem_surrogate_desc {
 /* Upload a surrogate for use with mechanism m on the current device.  Hidden and output weights
  * are rounded to BF16; the first layer is compensated: its weights and input features are each
  * split into a BF16 pair (hi + lo) and the product keeps the hi*hi, hi*lo and lo*hi terms, about
- * 16 significant bits, because the rates depend exponentially on the temperature feature. */
+ * 16 significant bits, because the rates depend exponentially on the temperature feature.
+ * CHEM_EINVAL for NULL arguments, weights, biases or statistics, ns different from the mechanism's
+ * or above 16, hidden other than 512, or dt <= 0; CHEM_ENOMEM / CHEM_ECUDA if the upload fails. */
 int chem_surrogate_create(const chem_surrogate_desc* desc, chem_mech_t m, chem_model_t* out);
 /* The paper's own surrogate variant (§2): one network per species, each nin -> h1 -> h2 -> h3 -> 1
  * with GELU (the paper's widths are 1600, 800, 400), on the same features, normalisation and
@@ -239,7 +250,9 @@ int chem_surrogate_create_per_species(const chem_surrogate_ps_desc* desc, chem_m
  * then W[l], b[l] (l = 0..4), x_mean, x_std, y_mean, y_std, box_lo, box_hi as little-endian
  * float32.  CHEMSUR2 (per-species networks): magic, int32 ns, int32 h1, h2, h3, double dt,
  * int32 nnet, int32 species[nnet], then for each network W1, b1, W2, b2, W3, b3, W4, b4, then
- * the statistics as in CHEMSUR1. */
+ * the statistics as in CHEMSUR1.
+ * CHEM_ENOTFOUND if the file cannot be opened; CHEM_EINVAL if it is not a CHEMSUR1 or CHEMSUR2 file
+ * of a supported shape; otherwise the errors of the matching create call. */
 int chem_surrogate_load(const char* path, chem_mech_t m, chem_model_t* out);
 /* Release a model's device memory (cudaFree, which waits for device work still using it); the
  * handle is invalid afterwards.  CHEM_EINVAL for NULL. */
@@ -257,14 +270,19 @@ int chem_surrogate_forward(chem_model_t model, const double* T, const double* p,
  * temperature from enthalpy conservation (Newton), acceptance tests; cells outside the training
  * box or failing a test are advanced by the FP64 integrator instead (indexed, same call,
  * asynchronous).  dt must equal the model's training step.  route_out[c] (nullable, int8):
- * 0 = network, 1 = FP64 fallback. */
+ * 0 = network, 1 = FP64 fallback.
+ * CHEM_EINVAL for a NULL model or mechanism, a species count that differs between them, ncells < 0,
+ * ld < ncells, rtol or atol <= 0, a dt other than the model's, or (ncells > 0) a NULL state
+ * pointer; CHEM_ENOMEM / CHEM_ECUDA from the stream-ordered allocator, a launch, or a pipeline wait
+ * that timed out. */
 int chem_surrogate_advance(chem_model_t model, chem_mech_t m, double* T, const double* p,
                            double* Y, int64_t ld, double dt, int64_t ncells, double rtol,
                            double atol, int8_t* route_out, chem_stream_t stream);
 
 /* Heat-release rate of a step (the accuracy measure of the surrogate):
  * q[c] = -rho0 sum_k h_k(T0) (Y1_k - Y0_k) / (W_k dt) with h_k molar (formation included),
- * rho0 from (T0, p, Y0).  erg / (cm^3 s).  Device pointers, asynchronous. */
+ * rho0 from (T0, p, Y0).  erg / (cm^3 s).  Device pointers, asynchronous.
+ * CHEM_EINVAL for a NULL argument, ncells < 0, ld < ncells or dt <= 0. */
 int chem_heat_release(chem_mech_t m, const double* T0, const double* p, const double* Y0,
                       const double* Y1, int64_t ld, int64_t ncells, double dt, double* q,
                       chem_stream_t stream);
@@ -272,11 +290,15 @@ int chem_heat_release(chem_mech_t m, const double* T0, const double* p, const do
 /* BF16 tensor-core GEMM used by training: C[M x N] (FP32, row pitch ldc) = A[M x K] B[N x K]^T
  * (+ bias[N], nullable); A, B device BF16 with K contiguous, row pitches lda/ldb (elements,
  * 16-byte multiples), M >= 128 and N >= 128 (ragged edges are zero-filled by TMA).  *err
- * (device int) is set to 1 if a pipeline wait times out. */
+ * (device int) is set to 1 if a pipeline wait times out.
+ * CHEM_EINVAL for M or N below 128, K <= 0, a NULL A, B, C or err, or A or B not 16-byte aligned or
+ * with a row pitch that is not a multiple of 16 bytes; CHEM_ECUDA if a tensor map cannot be
+ * encoded. */
 int chem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                    const float* bias, int M, int N, int K, int* err, chem_stream_t stream);
 /* The same product with the activation epilogue of the per-species networks: Cb[M x N] (BF16, row
- * pitch ldc) = bf16(act(A B^T + bias)) with act = exact-erf GELU if gelu != 0, else identity. */
+ * pitch ldc) = bf16(act(A B^T + bias)) with act = exact-erf GELU if gelu != 0, else identity.
+ * The errors of chem_gemm_bf16 (with Cb for C). */
 int chem_gemm_bf16_act(const void* A, int64_t lda, const void* B, int64_t ldb, void* Cb, int64_t ldc,
                        const float* bias, int gelu, int M, int N, int K, int* err, chem_stream_t stream);
 
@@ -291,12 +313,16 @@ int chem_gemm_bf16_act(const void* A, int64_t lda, const void* B, int64_t ldb, v
 typedef struct chem_trainer_s* chem_trainer_t;
 
 /* W_init / b_init: host arrays [5] of row-major [out x in] weights and [out] biases, or NULL for
- * a seeded Gaussian initialisation (std 1/sqrt(fan_in), zero biases).  batch: multiple of 128. */
+ * a seeded Gaussian initialisation (std 1/sqrt(fan_in), zero biases).  batch: multiple of 128.
+ * The errors of chem_mlp_trainer_create_layers. */
 int chem_mlp_trainer_create(int n_in, int n_out, int batch, const float* const* W_init,
                             const float* const* b_init, uint64_t seed, chem_trainer_t* out);
 /* Same with the caller's hidden widths: n_in -> hidden[0] -> ... -> hidden[n_hidden - 1] -> n_out
  * (1 <= n_hidden <= 7, widths in [1, 8192]; the per-species networks use 1600, 800, 400);
- * W_init / b_init hold n_hidden + 1 layers. */
+ * W_init / b_init hold n_hidden + 1 layers.
+ * CHEM_EINVAL for NULL out or hidden, n_in outside [1, 42], n_out outside [1, 128], n_hidden
+ * outside [1, 7], a width outside [1, 8192], or a batch that is not a positive multiple of 128;
+ * CHEM_ENOMEM / CHEM_ECUDA if the device buffers cannot be made. */
 int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden, const int* hidden, int batch,
                                    const float* const* W_init, const float* const* b_init,
                                    uint64_t seed, chem_trainer_t* out);
@@ -304,15 +330,19 @@ int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden, const int*
  * device work still using them).  CHEM_EINVAL for NULL. */
 int chem_mlp_trainer_free(chem_trainer_t t);
 /* forward pass of one batch, keeping the activations; out (nullable) receives [batch x n_out].
- * X is read again by chem_mlp_backward: it must stay valid until that call's work is done. */
+ * X is read again by chem_mlp_backward: it must stay valid until that call's work is done.
+ * CHEM_EINVAL for a NULL trainer or X. */
 int chem_mlp_forward(chem_trainer_t t, const void* X, float* out, chem_stream_t stream);
-/* mean-squared-error gradients of the last forward pass; loss (device double, nullable) */
+/* mean-squared-error gradients of the last forward pass; loss (device double, nullable).
+ * CHEM_EINVAL for a NULL trainer or target. */
 int chem_mlp_backward(chem_trainer_t t, const float* target, double* loss, chem_stream_t stream);
-/* one Adam update (bias-corrected) of all parameters with the last gradients */
+/* one Adam update (bias-corrected) of all parameters with the last gradients.
+ * CHEM_EINVAL for a NULL trainer or lr <= 0. */
 int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float beta2, float eps,
                        chem_stream_t stream);
 /* host copy of the parameters (which = 0) or of the last gradients (which = 1); W[l], b[l] are
- * host arrays of the unpadded shapes (any may be NULL); synchronises the device */
+ * host arrays of the unpadded shapes (any may be NULL); synchronises the device.
+ * CHEM_EINVAL for a NULL trainer, W or b; CHEM_ECUDA if a copy fails. */
 int chem_mlp_trainer_get(chem_trainer_t t, int which, float* const* W, float* const* b);
 
 /* Training data: raw features x [n x (ns + 2)] = [T, ln p, BC(Y0)] and targets
@@ -372,15 +402,19 @@ int chem_serve_register_state(chem_server_t s, chem_mech_t m, chem_model_t model
 int chem_serve_submit(chem_server_t s, int state_id, int route, double dt, double rtol,
                       double atol, uint64_t* req_id);
 /* Non-blocking: *state = CHEM_REQ_*, *latency_s (nullable) = seconds from submission to
- * completion once done, else -1. */
+ * completion once done, else -1.
+ * CHEM_EINVAL for a NULL server or state; CHEM_ENOTFOUND for an unknown request. For a failed
+ * request its message is left in chem_last_error. */
 int chem_serve_poll(chem_server_t s, uint64_t req_id, int* state, double* latency_s);
 /* Block until the request is done or timeout_s passes (CHEM_ETIMEOUT); never hangs. */
 int chem_serve_wait(chem_server_t s, uint64_t req_id, double timeout_s);
 /* out[8]: completed, failed, launches (jobs and surrogate launches), requests launched, max
- * concurrent launches, bytes in use, FP64 time slices issued, 0 */
+ * concurrent launches, bytes in use, FP64 time slices issued, 0.
+ * CHEM_EINVAL for NULL arguments. */
 int chem_serve_stats(chem_server_t s, int64_t* out);
 /* Stops the server after its launches finish; queued requests fail and callers blocked in
- * chem_serve_wait on them return.  No call on the server may start once this is entered. */
+ * chem_serve_wait on them return.  No call on the server may start once this is entered.
+ * CHEM_EINVAL for NULL. */
 int chem_serve_destroy(chem_server_t s);
 
 /* ---------------------------------------------------------------------------------------
@@ -389,12 +423,15 @@ int chem_serve_destroy(chem_server_t s);
  * for chem_advance; device pointers; asynchronous on stream.
  * ------------------------------------------------------------------------------------- */
 /* Mixture enthalpy h (erg/g, formation included) and cp (erg/(g K)) from the NASA-7 fits;
- * either output may be NULL. */
+ * either output may be NULL.
+ * CHEM_EINVAL for a NULL mechanism, ncells < 0, ld < ncells, or (ncells > 0) a NULL T or Y or both
+ * outputs NULL. */
 int chem_mixture_thermo(chem_mech_t m, const double* T, const double* Y, int64_t ld, int64_t ncells,
                         double* h, double* cp, chem_stream_t stream);
 /* Temperature from enthalpy: Newton T <- T - (h(T, Y) - h0) / cp(T, Y) from the initial guess in
  * T, until |dT| < 1e-9 T (at most 50 iterations, T kept in [200, 6000] K).  T is updated only
- * where it converged; status[c] (nullable, int8) = 0 converged, 1 not. */
+ * where it converged; status[c] (nullable, int8) = 0 converged, 1 not.
+ * CHEM_EINVAL for a NULL mechanism, ncells < 0, ld < ncells, or (ncells > 0) a NULL h0, Y or T. */
 int chem_temperature_from_enthalpy(chem_mech_t m, const double* h0, const double* Y, int64_t ld,
                                    int64_t ncells, double* T, int8_t* status, chem_stream_t stream);
 
@@ -417,7 +454,9 @@ int chem_transport_create(chem_mech_t m, const chem_transport_desc* desc, chem_t
 int chem_transport_free(chem_transport_t t);
 /* Mixture-averaged properties: viscosity by Wilke's rule, conductivity by the Mathur-Saxena
  * average, D_km = (1 - Y_k) / sum_{j != k} X_j / D_jk (the self-diffusion fit for a cell holding
- * species k alone).  mu [n], lambda [n], Dmix [ns][ld]: device outputs, each nullable. */
+ * species k alone).  mu [n], lambda [n], Dmix [ns][ld]: device outputs, each nullable.
+ * CHEM_EINVAL for a NULL handle, ncells < 0, ld < ncells, or (ncells > 0) a NULL T, p or Y or all
+ * three outputs NULL. */
 int chem_transport_eval(chem_transport_t t, const double* T, const double* p, const double* Y,
                         int64_t ld, int64_t ncells, double* mu, double* lambda, double* Dmix,
                         chem_stream_t stream);
@@ -426,11 +465,13 @@ int chem_transport_eval(chem_transport_t t, const double* T, const double* p, co
  * 15(2), 1989: a 64-entry table of 2^(j/64) and a degree-5 polynomial; within a few units in the
  * last place of exp; |x| >= 700 and NaN take the library exp), applied elementwise:
  * y[i] = exp(x[i]) for i < n.  x, y: device arrays of n doubles (may alias).  Asynchronous on
- * stream.  Exposed for testing and measurement. */
+ * stream.  Exposed for testing and measurement.
+ * CHEM_EINVAL for n < 0 or (n > 0) a NULL x or y. */
 int chem_fast_exp(const double* x, double* y, int64_t n, chem_stream_t stream);
 
 /* Measured FP64 FMA throughput of the current device (TFLOP/s, 2 flops per FMA) from a
- * register-resident FMA chain kernel; synchronous. */
+ * register-resident FMA chain kernel; synchronous.
+ * CHEM_EINVAL for a NULL output; CHEM_ECUDA if the probe fails. */
 int chem_fp64_fma_peak(double* tflops);
 
 /* ---------------------------------------------------------------------------------------
@@ -466,7 +507,8 @@ int chem_fvmesh_create(const chem_fvmesh_desc* desc, chem_fvmesh_t* out);
  * work still using them).  CHEM_EINVAL for NULL. */
 int chem_fvmesh_free(chem_fvmesh_t mesh);
 /* The CSR pattern (device arrays owned by the mesh): row_ptr [n_cells + 1], col_idx [nnz],
- * columns ascending within a row; the diagonal is always stored. */
+ * columns ascending within a row; the diagonal is always stored.
+ * CHEM_EINVAL for NULL arguments. */
 int chem_fvmesh_csr(chem_fvmesh_t mesh, int64_t* nnz, const int32_t** row_ptr, const int32_t** col_idx);
 
 /* Terms of one species equation over one step (device arrays; a NULL input leaves its term out):
@@ -492,16 +534,21 @@ typedef struct chem_fvm_terms {
 } chem_fvm_terms;
 /* Assemble the matrix in ldu form: upper[f] = A[owner, neighbour], lower[f] = A[neighbour,
  * owner], diag[c], and the right-hand side source[c] (nullable).  One kernel, no atomics;
- * bitwise reproducible.  Asynchronous on stream. */
+ * bitwise reproducible.  Asynchronous on stream.
+ * CHEM_EINVAL for a NULL mesh, terms or output, and for incomplete terms: the time term (dt > 0)
+ * without rho, rho_old and Y_old, boundary fluxes without boundary values, or the Laplacian on a
+ * mesh with boundary faces without gamma_b and Y_b. */
 int chem_fvm_assemble(chem_fvmesh_t mesh, const chem_fvm_terms* terms, double* lower, double* upper,
                       double* diag, double* source, chem_stream_t stream);
-/* The same matrix as CSR values vals [nnz] on the mesh's pattern (for a linear solver). */
+/* The same matrix as CSR values vals [nnz] on the mesh's pattern (for a linear solver).
+ * CHEM_EINVAL for NULL arguments. */
 int chem_fvm_to_csr(chem_fvmesh_t mesh, const double* lower, const double* upper, const double* diag,
                     double* vals, chem_stream_t stream);
 /* PaSR factor per cell: kappa = tau_c / (tau_c + tau_mix), tau_mix = c_mix sqrt(mu_eff / (rho eps)),
  * with the Smagorinsky sub-grid viscosity nu = (c_s Delta)^2 |S|, mu_eff = mu + rho nu and
  * eps = nu |S|^2; kappa = 1 where eps = 0.  tau_c (the chemical time scale), rho, mu, strain
- * (|S|) and delta (filter width): device arrays of n doubles.  Asynchronous on stream. */
+ * (|S|) and delta (filter width): device arrays of n doubles.  Asynchronous on stream.
+ * CHEM_EINVAL for n < 0, (n > 0) a NULL array, or c_s or c_mix negative or NaN. */
 int chem_pasr_kappa(int64_t n, const double* tau_c, const double* rho, const double* mu,
                     const double* strain, const double* delta, double c_s, double c_mix,
                     double* kappa, chem_stream_t stream);
