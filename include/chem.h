@@ -121,7 +121,9 @@ typedef struct chem_options {
 
 /* Advance ncells cells in place over dt.  ld = ncells.  Asynchronous on stream.
  * CHEM_EINVAL if ncells < 0, dt <= 0, rtol <= 0, atol <= 0 or a required pointer is NULL;
- * ncells == 0 is a no-op. */
+ * ncells == 0 is a no-op.  CHEM_ENOMEM / CHEM_ECUDA if the stream-ordered allocator cannot provide
+ * the 8-byte work-queue counter or the launch fails; per-cell failures go to the status codes of
+ * chem_advance_ex, not to the return value. */
 int chem_advance(chem_mech_t m, double* T, const double* p, double* Y, double dt,
                  int64_t ncells, double rtol, double atol, chem_stream_t stream);
 
