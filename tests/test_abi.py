@@ -157,3 +157,18 @@ def test_mesh_descriptions_are_validated_on_the_host():
         cg.FvMesh(m).close()
     except cg.ChemError as e:
         assert e.code != _lib.CHEM_EINVAL, str(e)
+
+
+def test_a_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """With the CUDA library unavailable, the API raises instead of falling back to anything:
+    there is no CPU path behind the binding."""
+    import pytest
+    import paper_2312_13513_gb300 as cg
+    from paper_2312_13513_gb300 import _lib
+    from synth.mechanism import h2_mechanism
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib._build, "build", lambda *a, **k: str(tmp_path / "libchem.so"))
+    with pytest.raises(ImportError):
+        _lib.load()
+    with pytest.raises(ImportError):
+        cg.Mechanism(h2_mechanism())
