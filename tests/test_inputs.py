@@ -41,3 +41,22 @@ def test_les_field_mixture_fraction_is_beta_distributed():
     assert f["Z"].var() == pytest.approx(0.05, abs=0.002)
     assert f["T"].min() >= 300.0 and f["T"].max() <= 2200.0
     assert np.allclose(f["Y"].sum(axis=0), 1.0, rtol=0, atol=1e-14) and np.all(f["Y"] >= 0.0)
+
+
+@pytest.mark.parametrize("which,ns,nr,n3,ntroe,elements", [
+    ("h2", 9, 25, 4, 1, ["H", "O", "N"]),
+    ("ch4", 53, 325, 30, 25, ["C", "H", "O", "N"])])
+def test_synthetic_mechanisms_have_the_stated_shapes(which, ns, nr, n3, ntroe, elements, request):
+    """Species, reaction, third-body and fall-off counts and elements of the H2/air- and
+    CH4/air-shaped mechanisms; log10 A in [8, 14], b in [-1, 1], Ea in [0, 40] kcal/mol,
+    collision efficiencies other than 1 in [0.5, 12]."""
+    m = request.getfixturevalue(which)
+    rt = np.asarray(m.rtype)
+    assert (m.ns, m.nr) == (ns, nr) and list(m.elements) == elements
+    assert int(np.sum(rt == 1)) == n3 and int(np.sum(rt == 2)) == ntroe
+    lA = np.log10(np.asarray(m.A))
+    assert lA.min() >= 8.0 and lA.max() <= 14.0
+    assert np.all(np.abs(m.b) <= 1.0) and np.all((np.asarray(m.Ea) >= 0.0) & (np.asarray(m.Ea) <= 40000.0))
+    e = np.asarray(m.eff)[rt != 0]
+    e = e[e != 1.0]
+    assert e.size and e.min() >= 0.5 and e.max() <= 12.0
