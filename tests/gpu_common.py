@@ -1,4 +1,6 @@
 """Helpers for the GPU parity tests (CUDA path vs the oracle on the same seeded inputs)."""
+import os
+
 import numpy as np
 import torch
 
@@ -30,11 +32,18 @@ def cell_error(T_ref, Y_ref, T_got, Y_got):
     return np.maximum(eT, eY)
 
 
-def assert_parity(om, T0, p, Y0, T_gpu, Y_gpu, dt, rtol, atol, max_outliers_frac=0.0):
+# (test, cells compared, cells outside the contract tolerance that the tight-oracle re-check
+# accepted): printed at the end of the session by tests/conftest.py
+BIFURCATIONS = []
+
+
+def assert_parity(om, T0, p, Y0, T_gpu, Y_gpu, dt, rtol, atol, max_bifurcations=None):
     """Compare GPU results with the same-tolerance oracle.  Cells outside the tolerance are
     re-checked against a tight oracle run (rtol 1e-12): they pass if the GPU's distance to the
     tight answer is no larger than the oracle's own distance plus the tolerance (an accept /
-    reject decision flipped by rounding near err = 1)."""
+    reject decision flipped by rounding near err = 1).  Such bifurcations are counted, recorded
+    for the session summary and bounded: at most max(2, 0.5 % of the cells) unless the caller
+    gives its own bound.  Returns their number."""
     T_or, Y_or, st, _ = om.advance(T0, p, Y0, dt, rtol, atol)
     assert np.all(st == 0)
     ok = within(T_or, Y_or, T_gpu, Y_gpu)
@@ -47,5 +56,8 @@ def assert_parity(om, T0, p, Y0, T_gpu, Y_gpu, dt, rtol, atol, max_outliers_frac
         assert not np.any(still), (
             f"{int(still.sum())} cells outside tolerance even against the tight oracle; "
             f"worst gpu/oracle error {e_gpu.max():.3g}/{e_or.max():.3g}")
-    assert bad.size <= max_outliers_frac * T0.size + 0.5 or max_outliers_frac == 0.0 or True
-    return bad.size
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    BIFURCATIONS.append((test, int(T0.size), int(bad.size)))
+    cap = max(2, int(0.005 * T0.size)) if max_bifurcations is None else max_bifurcations
+    assert bad.size <= cap, f"{bad.size} bifurcated cells of {T0.size} (at most {cap} expected)"
+    return int(bad.size)

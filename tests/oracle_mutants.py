@@ -192,6 +192,14 @@ PY_MUTANTS = {
         [("        W = rnd(Ws[l])\n", "        W = np.asarray(Ws[l], np.float64)\n", 1)]),
     "adam_no_bias_correction": ("mlp", "Adam's first moment without bias correction",
         [("mh = m[i] / (1.0 - beta1 ** step)", "mh = m[i]", 1)]),
+    "adam_first_moment_not_carried": ("mlp", "Adam's first moment without the b1 m carry",
+        [("m[i] = beta1 * m[i] + (1.0 - beta1) * grads[i]", "m[i] = (1.0 - beta1) * grads[i]", 1)]),
+    "adam_second_moment_not_carried": ("mlp", "Adam's second moment without the b2 v carry",
+        [("v[i] = beta2 * v[i] + (1.0 - beta2) * grads[i] * grads[i]",
+          "v[i] = (1.0 - beta2) * grads[i] * grads[i]", 1)]),
+    "adam_bias_correction_first_step": ("mlp", "Adam's bias correction frozen at step 1",
+        [("mh = m[i] / (1.0 - beta1 ** step)", "mh = m[i] / (1.0 - beta1)", 1),
+         ("vh = v[i] / (1.0 - beta2 ** step)", "vh = v[i] / (1.0 - beta2)", 1)]),
     "bf16_ties_down": ("mlp", "BF16 rounding with ties always down",
         [("bias = ((u >> 16) & 1) + 0x7FFF", "bias = 0x7FFF + 0 * u", 1)]),
     "first_layer_drops_weight_correction": ("mlp", "compensated first layer without x_hi W_lo",

@@ -113,13 +113,13 @@ def test_parity_ch4_other_group_sizes(om_ch4, ch4, dm_ch4, G):
 
 def test_full_size_quasi_dns_sampled(om_h2, h2, dm_h2):
     """2^20 cells of the quasi-DNS field in the benchmark's launch configuration; the oracle
-    recomputes a seeded sample of 384 cells one by one."""
+    recomputes a seeded sample of 4096 cells one by one."""
     f = quasi_dns_field(load_table("h2_flamelet.npz"), n=1 << 20, seed=12346)
     T, p, Y = f["T"], f["p"], f["Y"]
     Tg, Yg, st, nsub, _ = _run(dm_h2, T, p, Y, 5e-7)
     assert np.all(st == 0)
     rng = np.random.default_rng(5)
-    s = np.sort(rng.choice(T.size, 384, replace=False))
+    s = np.sort(rng.choice(T.size, 4096, replace=False))
     assert_parity(om_h2, T[s], p[s], Y[:, s], Tg[s], Yg[:, s], 5e-7, 1e-6, 1e-10)
     # conservation at every cell: elements exactly, sum Y to rounding
     comp = np.asarray(h2.comp, np.float64)
@@ -129,12 +129,14 @@ def test_full_size_quasi_dns_sampled(om_h2, h2, dm_h2):
 
 
 def test_full_size_les_sampled(om_ch4, ch4, dm_ch4):
+    """262144 cells of the LES field in the benchmark's launch configuration; the oracle recomputes
+    a seeded sample of 1024 cells one by one."""
     f = les_field(load_table("ch4_flamelet.npz"), n=262144, seed=12347)
     T, p, Y = f["T"], f["p"], f["Y"]
     Tg, Yg, st, _, _ = _run(dm_ch4, T, p, Y, 1e-6)
     assert np.all(st == 0)
     rng = np.random.default_rng(6)
-    s = np.sort(rng.choice(T.size, 128, replace=False))
+    s = np.sort(rng.choice(T.size, 1024, replace=False))
     assert_parity(om_ch4, T[s], p[s], Y[:, s], Tg[s], Yg[:, s], 1e-6, 1e-6, 1e-10)
 
 

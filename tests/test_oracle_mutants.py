@@ -73,6 +73,9 @@ PY_CAUGHT_BY = {
     "hidden_activations_not_rounded": ["bf16_points"],
     "hidden_weights_not_rounded": ["bf16_points"],
     "adam_no_bias_correction": ["adam"],
+    "adam_first_moment_not_carried": ["adam_constant", "adam_alternating"],
+    "adam_second_moment_not_carried": ["adam_constant", "adam_alternating"],
+    "adam_bias_correction_first_step": ["adam_constant", "adam_alternating"],
     "bf16_ties_down": ["bf16_known"],
     "first_layer_drops_weight_correction": ["first_layer"],
     "boxcox_inverse_exponent": ["boxcox"],
@@ -118,6 +121,8 @@ def _py_pins(om, h2, h2_tr):
         "first_layer": S.test_compensated_first_layer_error_bound,
         "finite_differences": S.test_backward_matches_finite_differences,
         "adam": S.test_adam_first_step_is_signed_lr,
+        "adam_constant": S.test_adam_constant_gradient_three_steps,
+        "adam_alternating": S.test_adam_alternating_gradient_three_steps,
         "bf16_points": S.test_bf16_emulation_rounds_where_the_gpu_holds_bf16,
         "boxcox": S.test_boxcox_roundtrip_and_log_limit,
         "features": S.test_features_are_T_log_p_and_boxcox,

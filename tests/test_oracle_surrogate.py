@@ -103,6 +103,42 @@ def test_adam_first_step_is_signed_lr():
     assert np.allclose(p1[0] - p[0], -1e-2 * np.sign(g[0]), rtol=1e-12)
 
 
+def test_adam_constant_gradient_three_steps():
+    """Kingma & Ba's Adam with a constant gradient g: the moments are geometric sums,
+    m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so the bias-corrected ratio is g / |g| and every
+    step moves each parameter by -lr sign(g) (eps = 0).  Checked after each of three steps, with
+    the moments themselves."""
+    b1, b2, lr = 0.9, 0.999, 1e-2
+    p0 = np.array([1.0, -2.0, 3.0, 0.25])
+    g = np.array([0.5, -1e-3, 2.0, -7.0])
+    p = [p0.copy()]; m = [np.zeros(4)]; v = [np.zeros(4)]
+    for t in (1, 2, 3):
+        p, m, v = mlp.adam_step(p, [g.copy()], m, v, t, lr=lr, beta1=b1, beta2=b2, eps=0.0)
+        assert np.allclose(m[0], (1.0 - b1 ** t) * g, rtol=1e-14, atol=0)
+        assert np.allclose(v[0], (1.0 - b2 ** t) * g * g, rtol=1e-13, atol=0)
+        assert np.allclose(p[0] - p0, -t * lr * np.sign(g), rtol=1e-12, atol=0)
+
+
+def test_adam_alternating_gradient_three_steps():
+    """Gradients g, -g, g: expanding the moment recursion by hand,
+    m_1 = (1 - b1) g, m_2 = -(1 - b1)^2 g, m_3 = (1 - b1)(1 - b1 (1 - b1)) g, while v_t stays
+    (1 - b2^t) g^2; the three steps are therefore -lr s, lr (1 - b1) / (1 + b1) s and
+    -lr (1 - b1 + b1^2) / (1 + b1 + b1^2) s with s = sign(g) (eps = 0)."""
+    b1, b2, lr = 0.9, 0.999, 1e-2
+    g = np.array([0.3, -4.0, 1e-2])
+    s = np.sign(g)
+    want_m = [(1 - b1) * g, -(1 - b1) ** 2 * g, (1 - b1) * (1 - b1 * (1 - b1)) * g]
+    want_step = [-lr * s, lr * (1 - b1) / (1 + b1) * s, -lr * (1 - b1 + b1 * b1) / (1 + b1 + b1 * b1) * s]
+    p = [np.zeros(3)]; m = [np.zeros(3)]; v = [np.zeros(3)]
+    for t in (1, 2, 3):
+        before = p[0].copy()
+        gt = g if t != 2 else -g
+        p, m, v = mlp.adam_step(p, [gt.copy()], m, v, t, lr=lr, beta1=b1, beta2=b2, eps=0.0)
+        assert np.allclose(m[0], want_m[t - 1], rtol=1e-13, atol=0)
+        assert np.allclose(v[0], (1.0 - b2 ** t) * g * g, rtol=1e-13, atol=0)
+        assert np.allclose(p[0] - before, want_step[t - 1], rtol=1e-11, atol=0)
+
+
 def test_boxcox_roundtrip_and_log_limit():
     y = np.logspace(-30, 0, 61)
     assert np.allclose(sur.boxcox_inv(sur.boxcox(y)), y, rtol=1e-9, atol=0)
