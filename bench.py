@@ -139,6 +139,15 @@ def parse_clock_samples(lines):
     return out
 
 
+def workload_config(world):
+    """The workload both arms report (the reference arm times a bounded sample of it, stated in
+    its cpu_baseline)."""
+    return {"workload": WORKLOAD, "cells_per_gpu": NCELLS, "dt": DT, "rtol": RTOL, "atol": ATOL,
+            "mechanism": "synthetic H2/air-shaped, 9 species, 25 reactions",
+            "l2": "flushed between steps (256 MiB write)",
+            "parallelism": f"cells sharded, {world} rank(s), no collective"}
+
+
 def make_field(rank=0, n=NCELLS):
     from synth.states import load_table, quasi_dns_field
     return quasi_dns_field(load_table("h2_flamelet.npz"), n=n, seed=FIELD_SEED + rank)
@@ -196,7 +205,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / len(t_steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_per_step": per_step},
+            "config": workload_config(world),
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
                              "kind": "oracle",
                              "sample": f"{per_step} seeded-uniform cells of the 2^20-cell field per step"},
@@ -361,8 +370,10 @@ def extra_ch4(fp64_peak, steps=2):
     return {"workload": "FP64 Rodas4, 262144 LES-shaped CH4/air cells (53 species, 325 reactions), "
                         "dt=1e-6 s, 128-thread group per cell",
             "ms": min(ms), "cell_updates_per_s": n / t,
-            "fp64_tflops": folded / t / 1e12, "fp64_frac": folded / t / 1e12 / fp64_peak,
-            "attempts_mean": att / n}
+            "fp64_frac_plain": flo / t / 1e12 / fp64_peak,
+            "fp64_frac_folded": folded / t / 1e12 / fp64_peak,
+            "fp64_tflops_plain": flo / t / 1e12, "fp64_tflops_folded": folded / t / 1e12,
+            "transcendental_weight": fl.TRANSCENDENTAL_FLOPS, "attempts_mean": att / n}
 
 
 def extra_surrogate(peaks, steps=3):
@@ -412,15 +423,17 @@ def extra_surrogate(peaks, steps=3):
     flop = 2.0 * (11 * 512 + 3 * 512 * 512 + 512 * 9) * n
     tf = flop / (ms_fwd * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    burst = peaks.get("bf16_tflops", 1900.0)
     return {"workload": "BF16 MLP 11-512x4-9 (tcgen05) with projection, Newton T and FP64 fallback, "
                         "2^22 quasi-DNS H2 cells, dt=5e-7 s",
-            "surrogate_ms": ms_sur, "surrogate_cell_updates_per_s": n / (ms_sur * 1e-3),
+            "model_trained_in_this_run": trained_here,
             "fp64_ms": ms_fp64, "fp64_cell_updates_per_s": n / (ms_fp64 * 1e-3),
-            "speedup_vs_fp64": ms_fp64 / ms_sur, "hrr_l1_rel_error_vs_fp64": err,
-            "hrr_sum_rel_error_vs_fp64": err_sum, "hrr_p99_cell_rel_error_vs_fp64": p99_rel,
-            "fallback_fraction": float((route == 1).float().mean().item()),
             "forward_kernel_ms": ms_fwd, "tensor_tflops": tf,
-            "tensor_frac_of_sustained": tf / peak, "model_trained_in_this_run": trained_here}
+            "tensor_frac_of_burst": tf / burst, "tensor_frac_of_sustained": tf / peak,
+            "fallback_fraction": float((route == 1).float().mean().item()),
+            "hrr_sum_rel_error_vs_fp64": err_sum, "hrr_p99_cell_rel_error_vs_fp64": p99_rel,
+            "surrogate_ms": ms_sur, "surrogate_cell_updates_per_s": n / (ms_sur * 1e-3),
+            "speedup_vs_fp64": ms_fp64 / ms_sur, "hrr_l1_rel_error_vs_fp64": err}
 
 
 def _score_surrogate(cg, dm, model, T0, p, Y0, Yr, stream, steps=3):
@@ -663,20 +676,34 @@ def extra_serving(duration_s=10.0, seed=12349):
     by_class = {}
     for c in sorted(set(labels.tolist())):
         lc = lat[labels == c]
-        by_class[c] = {"requests": int(lc.size), "p50_ms": float(np.percentile(lc, 50)),
-                       "p99_ms": float(np.percentile(lc, 99)),
-                       "solvers": int(sum(1 for s_ in solvers if s_["label"] == c))}
+        by_class[c] = [int(lc.size), round(float(np.percentile(lc, 50)), 1), round(float(np.percentile(lc, 99)), 1)]
     return {"workload": "64 closed-loop solvers, Exp(2 ms) gaps, 1e4-2e6 cells log-uniform, "
                         "70/30 H2/CH4, routes 50/50 (H2 only), 150 GB budget, 10 s of submissions, "
                         "FP64 jobs in 20 ms time slices",
             "requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "cell_updates_per_s": res["cells"] / res["wall_s"], "wall_s": res["wall_s"],
-            "by_class": by_class, "fp64_time_slices": st["slices"],
+            "by_class_requests_p50_p99_ms": by_class, "fp64_time_slices": st["slices"],
             "launches": st["launches"], "requests_per_launch": st["requests_launched"] / max(1, st["launches"]),
             "max_concurrent_launches": st["max_concurrent"], "failed": st["failed"],
             "cells_h2": int(sum(s["cells"] for s in solvers if s["mech"] == "h2")),
             "cells_ch4": int(sum(s["cells"] for s in solvers if s["mech"] == "ch4"))}
+
+
+def summary(line):
+    """The headline figures of every config in a few hundred bytes (the last key of the line)."""
+    ex = line.get("extras", {})
+    c2, c3, c4 = ex.get("ch4_les", {}), ex.get("surrogate", {}), ex.get("serving", {})
+    r = lambda v, d=4: None if v is None else round(float(v), d)
+    return {"cfg1_h2_cells_per_s": r(line["value"], 0), "cfg1_fp64_frac_folded": r(line["roofline"]["frac"]),
+            "cfg2_ch4_cells_per_s": r(c2.get("cell_updates_per_s"), 0),
+            "cfg2_fp64_frac_plain": r(c2.get("fp64_frac_plain")), "cfg2_fp64_frac_folded": r(c2.get("fp64_frac_folded")),
+            "cfg3_surrogate_cells_per_s": r(c3.get("surrogate_cell_updates_per_s"), 0),
+            "cfg3_speedup_vs_fp64": r(c3.get("speedup_vs_fp64"), 2),
+            "cfg3_hrr_l1_rel_error": r(c3.get("hrr_l1_rel_error_vs_fp64"), 5),
+            "cfg3_forward_frac_burst": r(c3.get("tensor_frac_of_burst")),
+            "cfg4_p50_ms": r(c4.get("p50_ms"), 1), "cfg4_p99_ms": r(c4.get("p99_ms"), 1),
+            "cfg4_cells_per_s": r(c4.get("cell_updates_per_s"), 0)}
 
 
 def main():
@@ -812,10 +839,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells_per_gpu": n, "dt": DT, "rtol": RTOL, "atol": ATOL,
-                   "mechanism": "synthetic H2/air-shaped, 9 species, 25 reactions",
-                   "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"cells sharded, {world} rank(s), no collective"},
+        "config": workload_config(world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp64_peak, "traffic": traffic,
                      "peak_source": "FP64 FMA-chain probe measured in this run (chem_fp64_fma_peak)",
@@ -832,19 +856,21 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(field, mech)
     if rank == 0 and world == 1 and not args.no_extras:
+        # configs 2 and 3 are printed last: the end of the line is what a truncated log keeps
         extras = {}
-        for name, fn in (("ch4_les", lambda: extra_ch4(fp64_peak)),
-                         ("surrogate", lambda: extra_surrogate(_peaks())),
-                         ("surrogate_per_species", lambda: extra_surrogate_per_species(_peaks())),
+        for name, fn in (("surrogate_per_species", lambda: extra_surrogate_per_species(_peaks())),
                          ("fvm_species_assembly", lambda: extra_fvm(_peaks().get("hbm_gbs", 6800.0))),
                          ("graph_small_step", extra_graph),
                          ("thermo_transport", lambda: extra_transport(fp64_peak)),
-                         ("serving", extra_serving)):
+                         ("serving", extra_serving),
+                         ("ch4_les", lambda: extra_ch4(fp64_peak)),
+                         ("surrogate", lambda: extra_surrogate(_peaks()))):
             try:
                 extras[name] = fn()
             except Exception as e:      # an extra measurement never hides the headline line
                 extras[name] = {"error": f"{type(e).__name__}: {e}"}
         line["extras"] = extras
+        line["summary"] = summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

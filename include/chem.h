@@ -172,10 +172,15 @@ int chem_advance_batch(chem_mech_t m, const chem_segment* segs, int nseg, chem_s
  * memory -- a flow solver that already owns the device memory through its own pools, code under
  * a hard allocation budget, a latency-critical loop that must not enter the allocator -- can
  * still advance their cells.  The caller passes all inputs and outputs as for chem_advance_ex.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
- * must therefore happen outside any stream capture.  All calls share the array and the counter
- * is reset at the start of each call: calls whose work overlaps on the GPU race and must be
- * serialised by the caller (one stream, or events).  The scratch does not grow with ncells.
+ * The first call on each device (and the first after a context reset, which moves the array)
+ * looks up the array's device address (cudaGetSymbolAddress) and must therefore happen outside
+ * any stream capture; the look-up is safe from several host threads.  All calls share the array
+ * and the counter is reset at the start of each call: calls whose work overlaps on the GPU race
+ * and must be serialised by the caller (one stream, or events).  What such a race does: the
+ * later call resets the counter while the earlier call's kernel is still claiming chunks, so the
+ * earlier call claims chunks again; its cells are then advanced twice (over 2 dt) or written
+ * twice and still report CHEM_CELL_OK.  Nothing detects or reports it: the results are silently
+ * wrong.  The scratch does not grow with ncells.
  * The paper has no counterpart of this entry point.
  * The errors of chem_advance_ex. */
 int chem_advance_noalloc(chem_mech_t m, double* T, const double* p, double* Y, int64_t ld,

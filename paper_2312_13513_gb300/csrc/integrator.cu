@@ -24,7 +24,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "chem_internal.h"
@@ -1371,11 +1374,20 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocSc
 
 namespace {
 constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device, looked up once per device.  In
-// host code the array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress with the device current.
+// Device address of g_noalloc_scratch per device, remembered together with the context it was
+// looked up in.  In host code the array's name is only a host-side stand-in, so the address must
+// come from cudaGetSymbolAddress with the device current.  A context reset (cudaDeviceReset, a
+// destroyed primary context) reloads the module at another address: a call made in a context
+// other than the remembered one looks the address up again.  The lock makes first calls from
+// several host threads safe.
+struct NoallocCache {
+  std::mutex mu;
+  CUcontext ctx[kMaxDevices] = {};
+  void* ptr[kMaxDevices] = {};
+};
+NoallocCache g_noalloc;
+
 int noalloc_scratch(void** out) {
   int dev = 0;
   CHEM_CUDA_TRY(cudaGetDevice(&dev));
@@ -1383,12 +1395,21 @@ int noalloc_scratch(void** out) {
     set_error("device ordinal %d out of range for the allocation-free entry point", dev);
     return CHEM_EINVAL;
   }
-  if (!g_noalloc_ptr[dev]) {
+  CUcontext ctx = nullptr;
+  if (cuCtxGetCurrent(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  std::lock_guard<std::mutex> lk(g_noalloc.mu);
+  if (!ctx || g_noalloc.ctx[dev] != ctx || !g_noalloc.ptr[dev]) {
+    // the look-up also initialises the device's primary context when nothing else has yet
     void* ptr = nullptr;
     CHEM_CUDA_TRY(cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = ptr;
+    if (cuCtxGetCurrent(&ctx) != CUDA_SUCCESS || !ctx) {
+      set_error("allocation-free entry point: no current CUDA context");
+      return CHEM_ECUDA;
+    }
+    g_noalloc.ptr[dev] = ptr;
+    g_noalloc.ctx[dev] = ctx;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = g_noalloc.ptr[dev];
   return CHEM_OK;
 }
 }  // namespace

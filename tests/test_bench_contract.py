@@ -23,7 +23,8 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert "workload" in d["config"]
+    import bench
+    assert d["config"] == bench.workload_config(1)      # the headline arm reports the same config
 
 
 def test_reference_arm_under_torchrun_prints_once_from_rank_zero():
@@ -58,3 +59,19 @@ def test_clock_samples_summary():
     hot = rows[:1] + ["0, 1200, 2070, 900.0, 0x0000000000000040, Not Active, Active, Not Active, Not Active"]
     assert bench.parse_clock_samples(hot)["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
     assert bench.parse_clock_samples([])["samples"] == 0
+
+
+def test_summary_carries_every_config_headline():
+    """The line's last key condenses configs 1-4 (a truncated log keeps the end of the line)."""
+    import bench
+    line = {"value": 4.2e6, "roofline": {"frac": 0.37},
+            "extras": {"ch4_les": {"cell_updates_per_s": 3.1e5, "fp64_frac_plain": 0.26, "fp64_frac_folded": 0.34},
+                       "surrogate": {"surrogate_cell_updates_per_s": 2.6e8, "speedup_vs_fp64": 58.0,
+                                     "hrr_l1_rel_error_vs_fp64": 0.0048, "tensor_frac_of_burst": 0.31},
+                       "serving": {"p50_ms": 12.0, "p99_ms": 40.0, "cell_updates_per_s": 4e6}}}
+    sm = bench.summary(line)
+    assert sm["cfg2_fp64_frac_plain"] == 0.26 and sm["cfg2_fp64_frac_folded"] == 0.34
+    assert sm["cfg3_speedup_vs_fp64"] == 58.0 and sm["cfg3_hrr_l1_rel_error"] == 0.0048
+    assert sm["cfg4_p99_ms"] == 40.0 and sm["cfg1_h2_cells_per_s"] == 4.2e6
+    assert len(json.dumps(sm)) < 700
+    assert bench.summary({"value": 1.0, "roofline": {"frac": 0.1}})["cfg2_ch4_cells_per_s"] is None
