@@ -352,6 +352,33 @@ int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float beta2, flo
  * CHEM_EINVAL for a NULL trainer, W or b; CHEM_ECUDA if a copy fails. */
 int chem_mlp_trainer_get(chem_trainer_t t, int which, float* const* W, float* const* b);
 
+/* Data-parallel training (each rank of a job holds a trainer with the same weights and computes
+ * the gradients of its own share of the global batch; one sum over the ranks, e.g. an NCCL
+ * all-reduce of the flat buffer, then every rank takes the same Adam step).  The flat layout of
+ * the real (unpadded) gradients is, layer by layer, dW_l [out x in] row-major then db_l [out];
+ * chem_mlp_grad_count gives its length in floats (0.80 M for the 11 -> 512 x 4 -> 9 network).
+ * pack copies the last gradients into the caller's device buffer flat; unpack writes scale * flat
+ * back as the gradients the next chem_mlp_adam_step uses (scale = 1 / ranks turns a sum of the
+ * ranks' batch means into the mean over the global batch when every rank's batch has the same
+ * size).  Asynchronous on stream.  CHEM_EINVAL for a NULL trainer, count or flat pointer, or a
+ * non-finite scale. */
+int chem_mlp_grad_count(chem_trainer_t t, int64_t* n);
+int chem_mlp_grad_pack(chem_trainer_t t, float* flat, chem_stream_t stream);
+int chem_mlp_grad_unpack(chem_trainer_t t, const float* flat, float scale, chem_stream_t stream);
+
+/* Checkpoint and resume of training (Adam, §2): save writes the FP32 master weights and biases,
+ * both Adam moments of every parameter and the Adam step counter to the file path (format
+ * CHEMTRN1: magic, int32 layers, n_in, n_out, the real input and output widths of every layer,
+ * int64 step, then per layer W, b, m_W, m_b, v_W, v_b as little-endian FP32 of the unpadded
+ * shapes); load reads such a file into a trainer of the same shape (the batch may differ),
+ * rebuilds the BF16 copies and sets the step counter, so that the next steps continue the saved
+ * run exactly.  Both synchronise the device.  chem_mlp_trainer_step returns the number of Adam
+ * steps taken.  CHEM_EINVAL for NULL arguments, a file of another shape, a truncated file (the
+ * trainer is then unchanged) or a write error; CHEM_ENOTFOUND when the file cannot be opened. */
+int chem_mlp_trainer_save(chem_trainer_t t, const char* path);
+int chem_mlp_trainer_load(chem_trainer_t t, const char* path);
+int chem_mlp_trainer_step(chem_trainer_t t, int64_t* step);
+
 /* Training data: raw features x [n x (ns + 2)] = [T, ln p, BC(Y0)] and targets
  * t [n x ns] = BC(Y1) - BC(Y0) (difference formed in FP64) from states before (T0, p, Y0) and
  * after (Y1) a step.  Device arrays; CHEM_EINVAL for a NULL array, n < 0, ld < n or ns outside

@@ -114,6 +114,12 @@ SIGNATURES = {
     "chem_mlp_adam_step": (ctypes.c_int, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                           ctypes.c_float, P]),
     "chem_mlp_trainer_get": (ctypes.c_int, [P, ctypes.c_int, P, P]),
+    "chem_mlp_grad_count": (ctypes.c_int, [P, P]),
+    "chem_mlp_grad_pack": (ctypes.c_int, [P, P, P]),
+    "chem_mlp_grad_unpack": (ctypes.c_int, [P, P, ctypes.c_float, P]),
+    "chem_mlp_trainer_save": (ctypes.c_int, [P, ctypes.c_char_p]),
+    "chem_mlp_trainer_load": (ctypes.c_int, [P, ctypes.c_char_p]),
+    "chem_mlp_trainer_step": (ctypes.c_int, [P, P]),
     "chem_train_features": (ctypes.c_int, [P, P, P, P, I64, I64, ctypes.c_int, P, P, P]),
     "chem_column_stats": (ctypes.c_int, [P, I64, ctypes.c_int, P, P]),
     "chem_train_normalize": (ctypes.c_int, [P, I64, ctypes.c_int, P, P, P, ctypes.c_int, P,

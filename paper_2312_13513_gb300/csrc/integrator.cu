@@ -1388,6 +1388,22 @@ struct NoallocCache {
 };
 NoallocCache g_noalloc;
 
+// cuCtxGetCurrent through the runtime's driver entry-point query: the library does not link the
+// driver library itself (it loads on hosts without a GPU driver)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn ctx_get_current_fn() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+  });
+  return fn;
+}
+
 int noalloc_scratch(void** out) {
   int dev = 0;
   CHEM_CUDA_TRY(cudaGetDevice(&dev));
@@ -1395,14 +1411,19 @@ int noalloc_scratch(void** out) {
     set_error("device ordinal %d out of range for the allocation-free entry point", dev);
     return CHEM_EINVAL;
   }
+  CtxGetCurrentFn get_ctx = ctx_get_current_fn();
+  if (!get_ctx) {
+    set_error("allocation-free entry point: cuCtxGetCurrent unavailable");
+    return CHEM_ECUDA;
+  }
   CUcontext ctx = nullptr;
-  if (cuCtxGetCurrent(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  if (get_ctx(&ctx) != CUDA_SUCCESS) ctx = nullptr;
   std::lock_guard<std::mutex> lk(g_noalloc.mu);
   if (!ctx || g_noalloc.ctx[dev] != ctx || !g_noalloc.ptr[dev]) {
     // the look-up also initialises the device's primary context when nothing else has yet
     void* ptr = nullptr;
     CHEM_CUDA_TRY(cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch));
-    if (cuCtxGetCurrent(&ctx) != CUDA_SUCCESS || !ctx) {
+    if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) {
       set_error("allocation-free entry point: no current CUDA context");
       return CHEM_ECUDA;
     }

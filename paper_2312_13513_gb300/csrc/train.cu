@@ -24,6 +24,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <random>
 #include <vector>
@@ -174,6 +176,16 @@ __global__ void k_to_bf16(const float* W, __nv_bfloat16* Wb, __nv_bfloat16* Wt, 
     Wb[i] = wb;
     const int r = (int)(i / cols), c = (int)(i % cols);
     Wt[(int64_t)c * rows + r] = wb;
+  }
+}
+
+// dst[r * ld + c] = scale * src[r * cols + c] for the real block of a padded gradient buffer
+// (the padding of dst keeps its zeros)
+__global__ void k_unpack_scaled(const float* src, float* dst, int rows, int cols, int ld, float scale) {
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / cols), c = (int)(i % cols);
+    dst[(int64_t)r * ld + c] = scale * src[i];
   }
 }
 
@@ -485,6 +497,145 @@ extern "C" int chem_mlp_trainer_get(chem_trainer_t t, int which, float* const* W
   int herr = 0;
   CHEM_CUDA_TRY(cudaMemcpy(&herr, t->err, sizeof(int), cudaMemcpyDeviceToHost));
   if (herr) { set_error("a GEMM pipeline wait timed out during training"); return CHEM_ECUDA; }
+  return CHEM_OK;
+}
+
+// ---- data-parallel gradient exchange ---------------------------------------------------
+// Flat layout of the real (unpadded) gradients: for each layer l in order, dW_l [real_out x
+// real_in] row-major, then db_l [real_out].
+static int64_t flat_count(const chem_trainer_s* t) {
+  int64_t n = 0;
+  for (int l = 0; l < t->nl; ++l) n += (int64_t)t->real_out[l] * t->real_in[l] + t->real_out[l];
+  return n;
+}
+
+extern "C" int chem_mlp_grad_count(chem_trainer_t t, int64_t* n) {
+  if (!t || !n) { set_error("NULL argument"); return CHEM_EINVAL; }
+  *n = flat_count(t);
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_grad_pack(chem_trainer_t t, float* flat, chem_stream_t stream) {
+  if (!t || !flat) { set_error("NULL argument"); return CHEM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t o = 0;
+  for (int l = 0; l < t->nl; ++l) {
+    const int ro = t->real_out[l], ri = t->real_in[l];
+    CHEM_CUDA_TRY(cudaMemcpy2DAsync(flat + o, (size_t)ri * 4, t->dW[l], (size_t)t->in_pad[l] * 4, (size_t)ri * 4, ro,
+                                    cudaMemcpyDeviceToDevice, st));
+    o += (int64_t)ro * ri;
+    CHEM_CUDA_TRY(cudaMemcpyAsync(flat + o, t->db[l], (size_t)ro * 4, cudaMemcpyDeviceToDevice, st));
+    o += ro;
+  }
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_grad_unpack(chem_trainer_t t, const float* flat, float scale, chem_stream_t stream) {
+  if (!t || !flat || !std::isfinite(scale)) { set_error("bad arguments"); return CHEM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t o = 0;
+  for (int l = 0; l < t->nl; ++l) {
+    const int ro = t->real_out[l], ri = t->real_in[l];
+    k_unpack_scaled<<<grid_for((int64_t)ro * ri), 256, 0, st>>>(flat + o, t->dW[l], ro, ri, t->in_pad[l], scale);
+    o += (int64_t)ro * ri;
+    k_unpack_scaled<<<grid_for(ro), 256, 0, st>>>(flat + o, t->db[l], ro, 1, 1, scale);
+    o += ro;
+  }
+  CHEM_CUDA_TRY(cudaGetLastError());
+  return CHEM_OK;
+}
+
+// ---- checkpoint / resume ---------------------------------------------------------------
+// CHEMTRN1 file: magic, int32 nl, n_in, n_out, real_in[nl], real_out[nl], int64 Adam step,
+// then per layer (real shapes, FP32): W, b, first moments of W and b, second moments of W and b.
+namespace {
+constexpr char kTrnMagic[8] = {'C', 'H', 'E', 'M', 'T', 'R', 'N', '1'};
+
+// one [rows x cols] block of a padded device buffer (leading dimension ld) to / from host
+int block_io(float* dev, int rows, int cols, int ld, std::vector<float>& host, bool to_host) {
+  host.resize((size_t)rows * cols);
+  if (to_host)
+    CHEM_CUDA_TRY(cudaMemcpy2D(host.data(), (size_t)cols * 4, dev, (size_t)ld * 4, (size_t)cols * 4, rows,
+                               cudaMemcpyDeviceToHost));
+  else
+    CHEM_CUDA_TRY(cudaMemcpy2D(dev, (size_t)ld * 4, host.data(), (size_t)cols * 4, (size_t)cols * 4, rows,
+                               cudaMemcpyHostToDevice));
+  return CHEM_OK;
+}
+}  // namespace
+
+extern "C" int chem_mlp_trainer_save(chem_trainer_t t, const char* path) {
+  if (!t || !path) { set_error("NULL argument"); return CHEM_EINVAL; }
+  CHEM_CUDA_TRY(cudaDeviceSynchronize());
+  FILE* f = fopen(path, "wb");
+  if (!f) { set_error("cannot open %s for writing", path); return CHEM_ENOTFOUND; }
+  bool ok = fwrite(kTrnMagic, 1, 8, f) == 8;
+  const int32_t hdr[3] = {t->nl, t->nin, t->nout};
+  ok = ok && fwrite(hdr, 4, 3, f) == 3;
+  ok = ok && fwrite(t->real_in, 4, t->nl, f) == (size_t)t->nl && fwrite(t->real_out, 4, t->nl, f) == (size_t)t->nl;
+  const int64_t step = t->step;
+  ok = ok && fwrite(&step, 8, 1, f) == 1;
+  std::vector<float> h;
+  for (int l = 0; l < t->nl && ok; ++l) {
+    const int ro = t->real_out[l], ri = t->real_in[l], ld = t->in_pad[l];
+    float* blocks[6] = {t->W[l], t->b[l], t->mW[l], t->mb[l], t->vW[l], t->vb[l]};
+    for (int k = 0; k < 6 && ok; ++k) {
+      const bool w = (k % 2) == 0;
+      int rc = block_io(blocks[k], w ? ro : 1, w ? ri : ro, w ? ld : ro, h, true);
+      if (rc) { fclose(f); return rc; }
+      ok = fwrite(h.data(), 4, h.size(), f) == h.size();
+    }
+  }
+  if (fclose(f) != 0) ok = false;
+  if (!ok) { set_error("write error on %s", path); return CHEM_EINVAL; }
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_trainer_load(chem_trainer_t t, const char* path) {
+  if (!t || !path) { set_error("NULL argument"); return CHEM_EINVAL; }
+  FILE* f = fopen(path, "rb");
+  if (!f) { set_error("cannot open %s", path); return CHEM_ENOTFOUND; }
+  char magic[8];
+  int32_t hdr[3];
+  std::vector<int32_t> ri(t->nl), ro(t->nl);
+  int64_t step = 0;
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kTrnMagic, 8) == 0 && fread(hdr, 4, 3, f) == 3 &&
+            hdr[0] == t->nl && hdr[1] == t->nin && hdr[2] == t->nout &&
+            fread(ri.data(), 4, t->nl, f) == (size_t)t->nl && fread(ro.data(), 4, t->nl, f) == (size_t)t->nl;
+  for (int l = 0; l < t->nl && ok; ++l) ok = ri[l] == t->real_in[l] && ro[l] == t->real_out[l];
+  ok = ok && fread(&step, 8, 1, f) == 1 && step >= 0;
+  if (!ok) { fclose(f); set_error("%s: not a trainer state of this network's shape", path); return CHEM_EINVAL; }
+  // read everything first: a truncated file leaves the trainer unchanged
+  std::vector<std::vector<float>> blocks((size_t)t->nl * 6);
+  for (int l = 0; l < t->nl && ok; ++l)
+    for (int k = 0; k < 6 && ok; ++k) {
+      std::vector<float>& h = blocks[(size_t)l * 6 + k];
+      h.resize(k % 2 == 0 ? (size_t)t->real_out[l] * t->real_in[l] : (size_t)t->real_out[l]);
+      ok = fread(h.data(), 4, h.size(), f) == h.size();
+    }
+  fclose(f);
+  if (!ok) { set_error("%s: truncated trainer state", path); return CHEM_EINVAL; }
+  CHEM_CUDA_TRY(cudaDeviceSynchronize());
+  for (int l = 0; l < t->nl; ++l) {
+    const int r = t->real_out[l], c = t->real_in[l], ld = t->in_pad[l];
+    float* dst[6] = {t->W[l], t->b[l], t->mW[l], t->mb[l], t->vW[l], t->vb[l]};
+    for (int k = 0; k < 6; ++k) {
+      const bool w = (k % 2) == 0;
+      int rc = block_io(dst[k], w ? r : 1, w ? c : r, w ? ld : r, blocks[(size_t)l * 6 + k], false);
+      if (rc) return rc;
+    }
+    const int64_t nw = (int64_t)t->out_pad[l] * t->in_pad[l];
+    if (l == 0) k_split_bf16<<<grid_for(nw), 256>>>(t->W[0], t->Wb[0], t->out_pad[0], t->in_pad[0], t->nin);
+    else k_to_bf16<<<grid_for(nw), 256>>>(t->W[l], t->Wb[l], t->Wt[l], t->out_pad[l], t->in_pad[l]);
+  }
+  t->step = (int)step;
+  CHEM_CUDA_TRY(cudaDeviceSynchronize());
+  return CHEM_OK;
+}
+
+extern "C" int chem_mlp_trainer_step(chem_trainer_t t, int64_t* step) {
+  if (!t || !step) { set_error("NULL argument"); return CHEM_EINVAL; }
+  *step = t->step;
   return CHEM_OK;
 }
 

@@ -1,9 +1,14 @@
-"""Sharding of independent cells across ranks (one process per GPU).
+"""Work across ranks (one process per GPU).
 
-Cells of the chemistry step never exchange data, so ranks need no collective on the data path:
-each rank advances its own contiguous range of cells.  For a shared field the ranges balance
-the expected work, taken as the previous step's per-cell attempt counts (accepted + rejected
-sub-steps, plus one), the load-balancing use of the integrator's counters.
+* Chemistry: cells of the chemistry step never exchange data, so ranks need no collective on the
+  data path: each rank advances its own contiguous range of cells.  For a shared field the ranges
+  balance the expected work, taken as the previous step's per-cell attempt counts (accepted +
+  rejected sub-steps, plus one), the load-balancing use of the integrator's counters.
+* Surrogate training is data-parallel: every rank holds the same network, computes the gradients
+  of its equal share of each global batch, and one all-reduce (sum) of the flat gradient buffer,
+  scaled by 1 / ranks, gives every rank the gradient of the mean loss over the global batch
+  before the identical Adam step.  The flat layout is the library's (chem_mlp_grad_pack): layer by
+  layer, dW_l [out x in] row-major, then db_l [out].
 """
 from __future__ import annotations
 
@@ -34,3 +39,44 @@ def shard(n, rank, world, weights=None):
     if weights is None:
         weights = np.ones(n)
     return partition_by_weight(weights, world)[rank]
+
+
+def batch_share(global_batch_idx, rank, world):
+    """This rank's equal, contiguous share of a global batch (its size must divide by world)."""
+    n = len(global_batch_idx)
+    if world < 1 or n % world:
+        raise ValueError(f"global batch {n} does not split into {world} equal shares")
+    b = n // world
+    return global_batch_idx[rank * b:(rank + 1) * b]
+
+
+def flatten_grads(dW, db):
+    """The flat gradient layout of chem_mlp_grad_pack, for host arrays: dW_l row-major, then db_l."""
+    parts = []
+    for w, b in zip(dW, db):
+        parts.append(np.asarray(w).reshape(-1))
+        parts.append(np.asarray(b).reshape(-1))
+    return np.concatenate(parts)
+
+
+def unflatten_grads(flat, shapes):
+    """Inverse of flatten_grads; shapes = [(out, in), ...] per layer."""
+    dW, db, o = [], [], 0
+    for (r, c) in shapes:
+        dW.append(np.asarray(flat[o:o + r * c]).reshape(r, c)); o += r * c
+        db.append(np.asarray(flat[o:o + r])); o += r
+    if o != len(flat):
+        raise ValueError("flat gradient length does not match the layer shapes")
+    return dW, db
+
+
+def allreduce_sum_(flat, group=None):
+    """Sum a flat tensor over the ranks of group in place (one collective: NCCL for CUDA
+    tensors, gloo for CPU tensors).  Returns the number of ranks, 1 without torch.distributed."""
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return 1
+    world = dist.get_world_size(group)
+    if world > 1:
+        dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    return world

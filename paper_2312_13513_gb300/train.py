@@ -8,6 +8,9 @@ chem_mlp_adam_step (tcgen05 GEMMs).  torch only holds device buffers, shuffles i
 gathers batches.
 
     python -m paper_2312_13513_gb300.train --out model.chemsur --states 4194304 --epochs 40
+    python -m torch.distributed.run --nproc-per-node N -m paper_2312_13513_gb300.train --out ...
+        (data-parallel: each rank takes 1/N of every global batch, one NCCL all-reduce of the
+        gradients per step; --checkpoint / --resume save and continue the trainer state)
 """
 from __future__ import annotations
 
@@ -59,6 +62,48 @@ class Trainer:
         check(_lib.load().chem_mlp_adam_step(self.handle, ctypes.c_float(lr), ctypes.c_float(beta1),
                                              ctypes.c_float(beta2), ctypes.c_float(eps),
                                              _stream_ptr(stream)))
+
+    @property
+    def step(self):
+        """Adam steps taken (restored by load)."""
+        v = ctypes.c_int64(0)
+        check(_lib.load().chem_mlp_trainer_step(self.handle, ctypes.byref(v)))
+        return int(v.value)
+
+    def save(self, path):
+        """Checkpoint: master weights, Adam moments and step counter (chem_mlp_trainer_save)."""
+        check(_lib.load().chem_mlp_trainer_save(self.handle, os.fsencode(path)))
+
+    def load(self, path):
+        """Resume from a checkpoint of a network of the same shape (chem_mlp_trainer_load)."""
+        check(_lib.load().chem_mlp_trainer_load(self.handle, os.fsencode(path)))
+
+    def grad_count(self):
+        v = ctypes.c_int64(0)
+        check(_lib.load().chem_mlp_grad_count(self.handle, ctypes.byref(v)))
+        return int(v.value)
+
+    def pack_grads(self, flat, stream=None):
+        """The last gradients into a flat FP32 device tensor (layout of parallel.flatten_grads)."""
+        check(_lib.load().chem_mlp_grad_pack(self.handle, _ptr(flat), _stream_ptr(stream)))
+
+    def unpack_grads(self, flat, scale=1.0, stream=None):
+        """scale * flat becomes the gradient of the next Adam step."""
+        check(_lib.load().chem_mlp_grad_unpack(self.handle, _ptr(flat), ctypes.c_float(scale),
+                                               _stream_ptr(stream)))
+
+    def allreduce_grads(self, group=None, stream=None):
+        """Data-parallel step: the mean over the ranks of their gradients, in place (pack, one
+        all-reduce of the flat buffer, unpack scaled by 1 / ranks)."""
+        import torch
+        from .parallel import allreduce_sum_
+        if getattr(self, "_flat", None) is None:
+            self._flat = torch.empty(self.grad_count(), dtype=torch.float32, device="cuda")
+        self.pack_grads(self._flat, stream)
+        world = allreduce_sum_(self._flat, group)
+        if world > 1:
+            self.unpack_grads(self._flat, 1.0 / world, stream)
+        return world
 
     def get(self, which=0):
         dims = [self.n_in] + self.hidden + [self.n_out]
@@ -136,48 +181,97 @@ def make_dataset(mech, dm, n, dt, seed, rtol=1e-6, atol=1e-10, stats=None, front
     return {"X": X, "T": Tn, "stats": stats, "state0": (T0, p, Y0), "state1": (T1, Y1)}
 
 
-def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5, dt=5e-7, seed=7,
-          log=print, time_budget_s=None, front_fraction=0.5, data=None):
+def epoch_order(n, seed, epoch):
+    """The sample order of one epoch, a function of (seed, epoch) alone: a resumed or a
+    data-parallel run visits the same batches as one uninterrupted single-rank run."""
     import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed) * 1000003 + int(epoch))
+    return torch.randperm(n, device="cuda", generator=g)
+
+
+def cosine_lr(step, total, lr, lr_final):
+    """Cosine learning-rate decay from lr to lr_final over total steps."""
+    frac = step / max(1, total - 1)
+    return lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * frac))
+
+
+def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5, dt=5e-7, seed=7,
+          log=print, time_budget_s=None, front_fraction=0.5, data=None, checkpoint=None, resume=None,
+          group=None, max_steps=None):
+    """Train the single 4 x 512 network.  checkpoint: a file rewritten at the end of every epoch
+    (and at max_steps) with the trainer state; resume: such a file to continue from (its Adam step
+    counter gives the epoch and batch to continue at).  group: a torch.distributed process group
+    for data-parallel training -- every rank builds the same data set, takes its equal share of
+    each global batch and averages the gradients with one all-reduce before Adam; the statistics
+    are rank 0's.  max_steps: stop after that many steps in total (for tests)."""
+    import torch
+    rank, world = 0, 1
+    if group is not None or (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        import torch.distributed as dist
+        rank, world = dist.get_rank(group), dist.get_world_size(group)
     dm = Mechanism(mech)
     t0 = time.time()
-    if data is None:
+    if data is None and world == 1:
         data = make_dataset(mech, dm, n_states, dt, seed, front_fraction=front_fraction)
+    elif data is None:
+        # every rank builds the same states; the normalisation statistics are rank 0's
+        import torch.distributed as dist
+        box = [None]
+        if rank == 0:
+            data = make_dataset(mech, dm, n_states, dt, seed, front_fraction=front_fraction)
+            box = [data["stats"]]
+        dist.broadcast_object_list(box, src=0, group=group)
+        if rank != 0:
+            data = make_dataset(mech, dm, n_states, dt, seed, stats=box[0], front_fraction=front_fraction)
     log(f"dataset: {data['X'].shape[0]} states in {time.time() - t0:.1f} s")
     ns = mech.ns
-    tr = Trainer(ns + 2, ns, batch, seed=seed)
+    if batch % (128 * world):
+        raise ValueError(f"global batch {batch} must split into {world} shares of a multiple of 128")
+    tr = Trainer(ns + 2, ns, batch // world, seed=seed)
+    if resume is not None:
+        tr.load(resume)
     X, Tt = data["X"], data["T"]
     n = X.shape[0]
     steps_per_epoch = n // batch
     total = epochs * steps_per_epoch
+    if max_steps is not None:
+        total_run = min(total, int(max_steps))
+    else:
+        total_run = total
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     history = []
-    step = 0
+    step = tr.step
     t1 = time.time()
-    for ep in range(epochs):
-        perm = torch.randperm(n, device="cuda")
+    from .parallel import batch_share
+    while step < total_run:
+        ep, i0 = divmod(step, steps_per_epoch)
+        perm = epoch_order(n, seed, ep)
         acc = 0.0
-        for i in range(steps_per_epoch):
-            idx = perm[i * batch:(i + 1) * batch]
+        for i in range(i0, steps_per_epoch):
+            idx = batch_share(perm[i * batch:(i + 1) * batch], rank, world)
             xb = X.index_select(0, idx)
             yb = Tt.index_select(0, idx)
-            # cosine learning-rate decay from lr to lr_final
-            frac = step / max(1, total - 1)
-            lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * frac))
             tr.forward(xb)
             tr.backward(yb, loss)
-            tr.adam(lr_t)
+            if world > 1:
+                tr.allreduce_grads(group)
+            tr.adam(cosine_lr(step, total, lr, lr_final))
             step += 1
             if i % 64 == 0:
                 acc = float(loss.item())
+            if step >= total_run:
+                break
         history.append(acc)
+        if checkpoint is not None and rank == 0:
+            tr.save(checkpoint)
         log(f"epoch {ep + 1}/{epochs}: loss {acc:.4e}  ({time.time() - t1:.1f} s)")
         if time_budget_s is not None and time.time() - t1 > time_budget_s:
             log("time budget reached")
             break
     W, b = tr.get(0)
     params = dict(data["stats"])
-    params.update({"W": W, "b": b, "dt": dt, "history": history})
+    params.update({"W": W, "b": b, "dt": dt, "history": history, "steps": step})
     return params
 
 
@@ -317,25 +411,39 @@ def main():
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--budget", type=float, default=None, help="training time budget (s)")
     ap.add_argument("--log", default=None, help="also write the training log to this file")
+    ap.add_argument("--checkpoint", default=None, help="trainer state file rewritten every epoch")
+    ap.add_argument("--resume", default=None, help="continue from this trainer state file")
     args = ap.parse_args()
     from synth.mechanism import h2_mechanism
+    import torch
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        # data-parallel training, one process per GPU (torchrun): NCCL all-reduce of the gradients
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lines = []
 
     def log(msg):
-        print(msg, flush=True)
-        lines.append(msg)
+        if rank == 0:
+            print(msg, flush=True)
+            lines.append(msg)
 
     log(f"train: states {args.states} epochs {args.epochs} batch {args.batch} lr {args.lr} -> "
         f"{args.lr_final} (cosine) front_fraction {args.front_fraction} seed {args.seed}")
     params = train(h2_mechanism(), args.states, args.epochs, args.batch, args.lr, args.lr_final,
                    seed=args.seed, log=log, time_budget_s=args.budget,
-                   front_fraction=args.front_fraction)
-    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
-    save_model(params, args.out)
-    log(f"saved {args.out}")
-    if args.log:
-        with open(args.log, "w") as f:
-            f.write("\n".join(lines) + "\n")
+                   front_fraction=args.front_fraction, checkpoint=args.checkpoint, resume=args.resume)
+    if rank == 0:
+        os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+        save_model(params, args.out)
+        log(f"saved {args.out}")
+        if args.log:
+            with open(args.log, "w") as f:
+                f.write("\n".join(lines) + "\n")
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 if __name__ == "__main__":
