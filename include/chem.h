@@ -286,6 +286,19 @@ int chem_surrogate_advance(chem_model_t model, chem_mech_t m, double* T, const d
                            double* Y, int64_t ld, double dt, int64_t ncells, double rtol,
                            double atol, int8_t* route_out, chem_stream_t stream);
 
+/* Several solvers' states advanced by the surrogate in one pass (iteration-level batching of the
+ * serving loop): the segments' cells are gathered into one contiguous state (stream-ordered
+ * temporary), advanced by one chem_surrogate_advance (one forward launch, one post-processing
+ * launch, one FP64 fallback launch) and scattered back.  Per segment: T, p, Y, ld, ncells as for
+ * chem_surrogate_advance, status (nullable) receives the route of each cell (0 network, 1 FP64),
+ * idx must be NULL, nsub and nrej are ignored; every segment's dt must be the model's and all
+ * segments share the first one's rtol and atol.  Segments beyond kMaxSegsPerLaunch (32) make
+ * consecutive passes.  Asynchronous on stream.
+ * CHEM_EINVAL for NULL arguments, nseg < 1, or a segment that breaks these rules; the errors of
+ * chem_surrogate_advance. */
+int chem_surrogate_advance_batch(chem_model_t model, chem_mech_t m, const chem_segment* segs, int nseg,
+                                 chem_stream_t stream);
+
 /* Heat-release rate of a step (the accuracy measure of the surrogate):
  * q[c] = -rho0 sum_k h_k(T0) (Y1_k - Y0_k) / (W_k dt) with h_k molar (formation included),
  * rho0 from (T0, p, Y0).  erg / (cm^3 s).  Device pointers, asynchronous.
@@ -442,8 +455,9 @@ int chem_serve_submit(chem_server_t s, int state_id, int route, double dt, doubl
 int chem_serve_poll(chem_server_t s, uint64_t req_id, int* state, double* latency_s);
 /* Block until the request is done or timeout_s passes (CHEM_ETIMEOUT); never hangs. */
 int chem_serve_wait(chem_server_t s, uint64_t req_id, double timeout_s);
-/* out[8]: completed, failed, launches (jobs and surrogate launches), requests launched, max
- * concurrent launches, bytes in use, FP64 time slices issued, 0.
+/* out[8]: completed, failed, launches (jobs and surrogate launches), requests launched (those
+ * that joined a running job included), max concurrent launches, bytes in use, FP64 time slices
+ * issued, FP64 requests that joined a running time-sliced job.
  * CHEM_EINVAL for NULL arguments. */
 int chem_serve_stats(chem_server_t s, int64_t* out);
 /* Stops the server after its launches finish; queued requests fail and callers blocked in
@@ -507,6 +521,56 @@ int chem_fast_exp(const double* x, double* y, int64_t n, chem_stream_t stream);
  * register-resident FMA chain kernel; synchronous.
  * CHEM_EINVAL for a NULL output; CHEM_ECUDA if the probe fails. */
 int chem_fp64_fma_peak(double* tflops);
+
+/* ---------------------------------------------------------------------------------------
+ * One "chemistry + thermo" step of the reactive-flow time loop (§3.1, Fig. 1: chemical source,
+ * Thermo, transport properties), optionally captured once into a CUDA graph and replayed (§3.2).
+ * Stages, on the caller's stream: (0) the start state (T, Y) is copied into buffers of the step
+ * and its mixture enthalpy h0 and cp0 are evaluated; (1) chemistry over dt: the BF16 surrogate with
+ * FP64 fallback (model given) or the FP64 integrator; (2) the heat-release rate q of the step
+ * (nullable) and T from h(T, Y1) = h0 by Newton, written into T (the adiabatic constant-pressure
+ * step conserves h, so the Thermo stage recovers T from it); (3) transport properties of the new
+ * state (transport given).  All arrays are the caller's device arrays and must stay valid while
+ * the step object lives: a captured graph replays on the same pointers.
+ * ------------------------------------------------------------------------------------- */
+typedef struct chem_step_s* chem_step_t;
+typedef struct chem_step_desc {
+  chem_mech_t mech;
+  chem_model_t model;          /* nullable: FP64 integrator when NULL */
+  chem_transport_t transport;  /* nullable: no transport stage when NULL */
+  double* T;                   /* [ncells] in/out */
+  const double* p;             /* [ncells] */
+  double* Y;                   /* [ns][ld] in/out */
+  int64_t ld, ncells;
+  double dt, rtol, atol;
+  double* h0;                  /* [ncells] out: mixture enthalpy of the start state (required) */
+  double* cp0;                 /* [ncells] out, nullable */
+  double* q;                   /* [ncells] out, nullable: heat-release rate of the step */
+  int8_t* route;               /* [ncells] out, nullable: surrogate route (0 network, 1 FP64) */
+  int8_t* status;              /* [ncells] out, nullable: FP64 integrator status */
+  int32_t* nsub;               /* [ncells] out, nullable: FP64 accepted sub-steps */
+  int8_t* thermo_status;       /* [ncells] out, nullable: 0 when the Newton on T converged */
+  double* mu;                  /* [ncells] out, nullable */
+  double* lambda;              /* [ncells] out, nullable */
+  double* Dmix;                /* [ns][ld] out, nullable */
+} chem_step_desc;
+/* Create a step over the caller's arrays (allocates the start-state copies, stage events and a
+ * private capture stream).  CHEM_EINVAL for NULL arguments, ncells < 1, ld < ncells, a NULL T, p,
+ * Y or h0, non-positive dt, rtol or atol, a model whose species count differs from the
+ * mechanism's, or a transport handle without any transport output; CHEM_ENOMEM / CHEM_ECUDA if
+ * the buffers cannot be made. */
+int chem_step_create(const chem_step_desc* desc, chem_step_t* out);
+/* Issue one step on stream.  use_graph = 0: the stages directly, with events between them
+ * (chem_step_stage_ms reads their times); use_graph != 0: the first such call captures the
+ * stage sequence into a CUDA graph (a private stream ordered after stream) and every such call
+ * launches the graph on stream.  Errors of the stage entry points, or CHEM_ECUDA from capture,
+ * instantiation or launch. */
+int chem_step_run(chem_step_t s, int use_graph, chem_stream_t stream);
+/* Device time of stages 0-3 of the last direct run, in ms (ms[4]); synchronises on its end.
+ * CHEM_EINVAL for NULL arguments or when no direct run has been issued. */
+int chem_step_stage_ms(chem_step_t s, float* ms);
+/* Release the step (the caller's arrays are untouched).  CHEM_EINVAL for NULL. */
+int chem_step_free(chem_step_t s);
 
 /* ---------------------------------------------------------------------------------------
  * Finite-volume species equation (the paper's species PDE, §3.1, with the Laplacian term of

@@ -133,6 +133,53 @@ def temperature_from_enthalpy(mech, h, Y, T, status=None, stream=None):
                                                      _ptr(status), _stream_ptr(stream)))
 
 
+class Step:
+    """chem_step_*: one "chemistry + thermo" step (start-state thermo, chemistry, heat release and
+    T from h, transport) over the caller's device arrays, direct or as a replayed CUDA graph."""
+
+    def __init__(self, mech, T, p, Y, dt, rtol=1e-6, atol=1e-10, model=None, transport=None, h0=None,
+                 cp0=None, q=None, route=None, status=None, nsub=None, thermo_status=None, mu=None,
+                 lam=None, D=None):
+        import torch
+        for a, nm in ((T, "T"), (p, "p"), (Y, "Y"), (h0, "h0"), (cp0, "cp0"), (q, "q"), (mu, "mu"),
+                      (lam, "lambda"), (D, "D")):
+            _require(a, torch.float64, nm)
+        _require(route, torch.int8, "route"); _require(status, torch.int8, "status")
+        _require(nsub, torch.int32, "nsub"); _require(thermo_status, torch.int8, "thermo_status")
+        self.mech, self.model, self.transport = mech, model, transport
+        # the graph replays on these pointers: keep the tensors alive with the step
+        self._keep = (T, p, Y, h0, cp0, q, route, status, nsub, thermo_status, mu, lam, D)
+        d = _lib.StepDesc(mech.handle, model.handle if model is not None else None,
+                          transport.handle if transport is not None else None, _ptr(T), _ptr(p), _ptr(Y),
+                          Y.shape[1], T.numel(), float(dt), float(rtol), float(atol), _ptr(h0), _ptr(cp0),
+                          _ptr(q), _ptr(route), _ptr(status), _ptr(nsub), _ptr(thermo_status), _ptr(mu),
+                          _ptr(lam), _ptr(D))
+        h = ctypes.c_void_p()
+        check(_lib.load().chem_step_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, graph=False, stream=None):
+        check(_lib.load().chem_step_run(self.handle, 1 if graph else 0, _stream_ptr(stream)))
+
+    def stage_ms(self):
+        """Device ms of (start-state thermo, chemistry, heat release + T from h, transport) of the
+        last direct run."""
+        ms = (ctypes.c_float * 4)()
+        check(_lib.load().chem_step_stage_ms(self.handle, ms))
+        return list(ms)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().chem_step_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Transport:
     """chem_transport_*: mixture-averaged transport properties from fitted pure-species data."""
 

@@ -75,6 +75,13 @@ class FvmTerms(ctypes.Structure):
                 ("gamma", P), ("gamma_b", P), ("Y_b", P), ("S", P), ("kappa", P)]
 
 
+class StepDesc(ctypes.Structure):
+    _fields_ = [("mech", P), ("model", P), ("transport", P), ("T", P), ("p", P), ("Y", P), ("ld", I64),
+                ("ncells", I64), ("dt", D), ("rtol", D), ("atol", D), ("h0", P), ("cp0", P), ("q", P),
+                ("route", P), ("status", P), ("nsub", P), ("thermo_status", P), ("mu", P), ("lam", P),
+                ("Dmix", P)]
+
+
 class SurrogatePsDesc(ctypes.Structure):
     _fields_ = [("n_species", I32), ("hidden", I32 * 3), ("dt", D), ("W", (P * 4) * 16),
                 ("b", (P * 4) * 16), ("x_mean", P), ("x_std", P), ("y_mean", P), ("y_std", P),
@@ -126,6 +133,7 @@ SIGNATURES = {
                                             ctypes.c_int, P, P, P, P]),
     "chem_heat_release": (ctypes.c_int, [P, P, P, P, P, I64, I64, D, P, P]),
     "chem_advance_batch": (ctypes.c_int, [P, P, ctypes.c_int, P]),
+    "chem_surrogate_advance_batch": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "chem_serve_create": (ctypes.c_int, [ctypes.c_size_t, P, P]),
     "chem_serve_register_state": (ctypes.c_int, [P, P, P, P, P, P, I64, I64, P]),
     "chem_serve_submit": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, D, D, D, P]),
@@ -143,6 +151,10 @@ SIGNATURES = {
     "chem_fvm_assemble": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "chem_fvm_to_csr": (ctypes.c_int, [P, P, P, P, P, P]),
     "chem_pasr_kappa": (ctypes.c_int, [I64, P, P, P, P, P, D, D, P, P]),
+    "chem_step_create": (ctypes.c_int, [P, P]),
+    "chem_step_run": (ctypes.c_int, [P, ctypes.c_int, P]),
+    "chem_step_stage_ms": (ctypes.c_int, [P, P]),
+    "chem_step_free": (ctypes.c_int, [P]),
     "chem_last_error": (ctypes.c_char_p, []),
 }
 

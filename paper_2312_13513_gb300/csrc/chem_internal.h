@@ -95,6 +95,7 @@ int launch_advance_batch(chem_mech_s* m, const chem_segment* segs, int nseg, cud
 constexpr int kMaxSegsPerLaunch = 32;
 int launch_advance_slice(chem_mech_s* m, const chem_segment* segs, int nseg, unsigned long long budget_ns,
                          unsigned long long* counter, long long* seg_end, cudaStream_t stream);
+long long advance_queue_chunks(chem_mech_s* m, int64_t ncells);
 int launch_advance(chem_mech_s* m, double* T, const double* p, double* Y, int64_t ld, double dt,
                    int64_t ncells, double rtol, double atol, const int32_t* idx, int8_t* status,
                    int32_t* nsub, int32_t* nrej, const chem_options* opt, cudaStream_t stream,

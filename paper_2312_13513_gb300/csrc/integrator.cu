@@ -1302,6 +1302,14 @@ int launch_advance_batch(chem_mech_s* m, const chem_segment* segs, int nseg, cud
   return CHEM_OK;
 }
 
+// Work-queue entries (chunks) of ncells cells in a default-shape launch for mechanism m: the
+// queue end of a segment appended to a time-sliced job
+long long advance_queue_chunks(chem_mech_s* m, int64_t ncells) {
+  LaunchShape s;
+  if (pick_shape(m, nullptr, &s) != CHEM_OK) return -1;
+  return (ncells + chunk_cells(s.G) - 1) / chunk_cells(s.G);
+}
+
 // One time slice of a batched launch whose work-queue counter the caller owns (zeroed before the
 // first slice).  Groups stop claiming chunks budget_ns after they start; the chunks claimed so far
 // form the prefix [0, counter) of the queue, so re-issuing the same slice continues the work and

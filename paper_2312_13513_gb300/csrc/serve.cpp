@@ -73,14 +73,14 @@ struct Launch {
   chem_mech_t mech = nullptr;
   std::vector<chem_segment> segs;
   std::vector<long long> seg_end;
+  long long issued_total = 0;     // queue end the running slice was issued with
   size_t ndone = 0;
 };
 
 }  // namespace
 
-extern "C" int chem_surrogate_advance(chem_model_t md, chem_mech_t mech, double* T, const double* p,
-                                      double* Y, int64_t ld, double dt, int64_t ncells, double rtol,
-                                      double atol, int8_t* route_out, chem_stream_t stream);
+extern "C" int chem_surrogate_advance_batch(chem_model_t md, chem_mech_t mech, const chem_segment* segs,
+                                            int nseg, chem_stream_t stream);
 
 struct chem_server_s {
   size_t budget = 0, resident = 0, inflight = 0;
@@ -100,19 +100,36 @@ struct chem_server_s {
   bool stop = false;
   uint64_t n_submitted = 0;                    // submissions so far: the idle server waits for a new one
   int64_t n_launches = 0, n_batched = 0, n_done = 0, n_failed = 0, max_concurrent = 0, n_slices = 0;
+  int64_t n_joined = 0;                        // FP64 requests that joined a running time-sliced job
   double idle_poll_us = 20.0;
   unsigned long long slice_ns = 20000000ull;   // 0: FP64 jobs run unsliced
   unsigned long long* d_counter = nullptr;     // one work-queue counter per stream (device)
   unsigned long long* h_counter = nullptr;     // its read-back copy (pinned host memory)
+  unsigned long long* h_reset = nullptr;       // values the counters are set back to (pinned)
 };
 
 namespace {
 
 size_t request_bytes(const StateRec& s, int route) {
-  if (route == CHEM_ROUTE_SURROGATE)    // network output, box flags, fallback list
-    return (size_t)s.ncells * ((size_t)s.mech->ns * 4 + 1 + 4) + 4096;
+  if (route == CHEM_ROUTE_SURROGATE)    // gathered state copy; network output, box flags, fallback list
+    return (size_t)s.ncells * (((size_t)s.mech->ns + 2) * 8 + 1 + (size_t)s.mech->ns * 4 + 1 + 4) + 4096;
   return 4096;                           // work-queue counter
 }
+
+// the key surrogate requests are batched by: one gathered pass needs one model, mechanism, step
+// and tolerance pair
+struct SurKey {
+  chem_model_t model;
+  chem_mech_t mech;
+  double dt, rtol, atol;
+  bool operator<(const SurKey& o) const {
+    if (model != o.model) return model < o.model;
+    if (mech != o.mech) return mech < o.mech;
+    if (dt != o.dt) return dt < o.dt;
+    if (rtol != o.rtol) return rtol < o.rtol;
+    return atol < o.atol;
+  }
+};
 
 void server_loop(chem_server_s* S) {
   cudaSetDevice(S->device);
@@ -127,8 +144,11 @@ void server_loop(chem_server_s* S) {
       if (q == cudaErrorNotReady) { ++i; continue; }
       const Clock::time_point now = Clock::now();
       if (q == cudaSuccess && L.sliced) {
+        // the slice processed every chunk it claimed below the queue end it was issued with;
+        // groups that found the queue empty still advanced the counter past that end
         const long long total = L.seg_end.back();
-        const long long done = std::min<long long>((long long)S->h_counter[L.stream], total);
+        const long long claimed = (long long)S->h_counter[L.stream];
+        const long long done = std::min<long long>(claimed, L.issued_total);
         while (L.ndone < L.reqs.size() && L.seg_end[L.ndone] <= done) {
           Req& r = S->reqs[L.reqs[L.ndone]];
           r.status = Q_DONE;
@@ -139,10 +159,20 @@ void server_loop(chem_server_s* S) {
           progressed = true;
         }
         if (done < total) {
-          // next slice of the same job, continuing the same queue
+          // next slice of the same job, continuing the same queue; requests that joined since the
+          // last slice extend it, and a counter that overshot the old end is set back to it
           cudaStream_t strm = S->streams[L.stream];
-          int rc = chem::launch_advance_slice(L.mech, L.segs.data(), (int)L.segs.size(), S->slice_ns,
-                                              S->d_counter + L.stream, nullptr, strm);
+          int rc = CHEM_OK;
+          if (claimed > L.issued_total) {
+            S->h_reset[L.stream] = (unsigned long long)L.issued_total;
+            if (cudaMemcpyAsync(S->d_counter + L.stream, S->h_reset + L.stream, sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, strm) != cudaSuccess)
+              rc = chem::cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(server counter)");
+          }
+          if (rc == CHEM_OK)
+            rc = chem::launch_advance_slice(L.mech, L.segs.data(), (int)L.segs.size(), S->slice_ns,
+                                            S->d_counter + L.stream, nullptr, strm);
+          L.issued_total = total;
           if (rc == CHEM_OK &&
               cudaMemcpyAsync(S->h_counter + L.stream, S->d_counter + L.stream, sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, strm) == cudaSuccess &&
@@ -179,23 +209,23 @@ void server_loop(chem_server_s* S) {
     for (size_t k = 0; k < S->streams.size(); ++k)
       if (!S->stream_busy[k]) { free_stream = (int)k; break; }
     if (!S->stop && free_stream >= 0 && !S->pending.empty()) {
-      const size_t n_sur_streams = S->streams.size() - (size_t)S->n_fp64;
-      // FP64 requests grouped by mechanism (one batched launch each) and surrogate requests
+      // FP64 requests grouped by mechanism (appended to a running job of that mechanism, else one
+      // batched job each) and surrogate requests grouped by model, mechanism, step and tolerances
+      // (one gathered pass each)
       std::map<chem_mech_t, std::vector<uint64_t>> fp64;
-      std::vector<uint64_t> sur;
+      std::map<SurKey, std::vector<uint64_t>> sur;
       // states registered while requests run can take resident + inflight past the budget
       size_t avail = S->resident + S->inflight < S->budget ? S->budget - S->resident - S->inflight : 0;
       std::deque<uint64_t> keep;
       for (uint64_t id : S->pending) {
         Req& r = S->reqs[id];
         StateRec& st = S->states[r.state];
-        const bool take = !st.busy && r.bytes <= avail &&
-                          (r.route == CHEM_ROUTE_FP64 || sur.size() < n_sur_streams);
+        const bool take = !st.busy && r.bytes <= avail;
         if (take) {
           avail -= r.bytes;
           st.busy = true;
           if (r.route == CHEM_ROUTE_FP64) fp64[st.mech].push_back(id);
-          else sur.push_back(id);
+          else sur[SurKey{st.model, st.mech, r.dt, r.rtol, r.atol}].push_back(id);
         } else {
           keep.push_back(id);
         }
@@ -203,15 +233,45 @@ void server_loop(chem_server_s* S) {
       S->pending.swap(keep);
       // build launches; each needs a free stream, the rest go back to the queue front
       std::vector<std::vector<uint64_t>> groups;
+      bool launched = false;             // a group was launched, joined a job or failed: look again right away
       for (auto& kv : fp64) {
-        // one job per mechanism holds at most kMaxSegsPerLaunch requests; the rest wait
+        std::vector<uint64_t>& v = kv.second;
+        // requests join a running time-sliced job of their mechanism at its next slice boundary:
+        // the job's queue grows at its end, so the claimed prefix and the retirement by queue
+        // position stay valid (the running slice keeps its own copy of the descriptors)
+        size_t used = 0;
+        for (Launch& L : S->launches) {
+          if (!L.sliced || L.mech != kv.first) continue;
+          while (used < v.size() && L.segs.size() < (size_t)chem::kMaxSegsPerLaunch) {
+            Req& r = S->reqs[v[used]];
+            const StateRec& st = S->states[r.state];
+            const long long chunks = chem::advance_queue_chunks(st.mech, st.ncells);
+            if (chunks < 0) break;
+            chem_segment g{};
+            g.T = st.T; g.p = st.p; g.Y = st.Y; g.ld = st.ld; g.ncells = st.ncells;
+            g.dt = r.dt; g.rtol = r.rtol; g.atol = r.atol;
+            L.segs.push_back(g);
+            L.seg_end.push_back(L.seg_end.back() + chunks);
+            L.reqs.push_back(r.id);
+            L.bytes += r.bytes;
+            S->inflight += r.bytes;
+            r.status = Q_RUNNING;
+            ++S->n_batched;
+            ++S->n_joined;
+            ++used;
+            launched = true;
+          }
+        }
+        // the rest: new jobs of at most kMaxSegsPerLaunch requests each
+        for (size_t b = used; b < v.size(); b += chem::kMaxSegsPerLaunch)
+          groups.push_back(std::vector<uint64_t>(v.begin() + b, v.begin() + std::min(v.size(), b + chem::kMaxSegsPerLaunch)));
+      }
+      for (auto& kv : sur) {
         std::vector<uint64_t>& v = kv.second;
         for (size_t b = 0; b < v.size(); b += chem::kMaxSegsPerLaunch)
           groups.push_back(std::vector<uint64_t>(v.begin() + b, v.begin() + std::min(v.size(), b + chem::kMaxSegsPerLaunch)));
       }
-      for (uint64_t id : sur) groups.push_back({id});
       std::vector<uint64_t> back;
-      bool launched = false;             // a group was launched or failed: look again right away
       for (auto& grp : groups) {
         // FP64 jobs on the low-priority streams, surrogate launches on the high-priority ones: when
         // a slice's blocks retire, the block scheduler starts a waiting surrogate launch first
@@ -247,15 +307,24 @@ void server_loop(chem_server_s* S) {
           } else {
             rc = chem::launch_advance_slice(L.mech, L.segs.data(), (int)L.segs.size(), S->slice_ns,
                                             S->d_counter + sidx, L.seg_end.data(), strm);
+            L.issued_total = L.seg_end.back();
           }
           if (rc == CHEM_OK &&
               cudaMemcpyAsync(S->h_counter + sidx, S->d_counter + sidx, sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, strm) != cudaSuccess)
             rc = chem::cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(server counter)");
         } else {
-          const StateRec& st = S->states[r0.state];
-          rc = chem_surrogate_advance(st.model, st.mech, st.T, st.p, st.Y, st.ld, r0.dt, st.ncells, r0.rtol,
-                                      r0.atol, nullptr, strm);
+          std::vector<chem_segment> segs;
+          for (uint64_t id : grp) {
+            const Req& r = S->reqs[id];
+            const StateRec& st = S->states[r.state];
+            chem_segment g{};
+            g.T = st.T; g.p = st.p; g.Y = st.Y; g.ld = st.ld; g.ncells = st.ncells;
+            g.dt = r.dt; g.rtol = r.rtol; g.atol = r.atol;
+            segs.push_back(g);
+          }
+          const StateRec& st0 = S->states[r0.state];
+          rc = chem_surrogate_advance_batch(st0.model, st0.mech, segs.data(), (int)segs.size(), strm);
         }
         const Clock::time_point now = Clock::now();
         if (rc != CHEM_OK) {
@@ -335,7 +404,7 @@ extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_optio
     S->slice_ns = opt->slice_ms < 0.0 ? 0ull : (unsigned long long)(opt->slice_ms * 1e6);
   if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; return cuda_fail(cudaGetLastError(), "cudaGetDevice"); }
   cudaError_t ea = cudaMalloc((void**)&S->d_counter, ns * sizeof(unsigned long long));
-  cudaError_t eh = ea == cudaSuccess ? cudaHostAlloc((void**)&S->h_counter, ns * sizeof(unsigned long long),
+  cudaError_t eh = ea == cudaSuccess ? cudaHostAlloc((void**)&S->h_counter, 2 * ns * sizeof(unsigned long long),
                                                      cudaHostAllocDefault)
                                      : ea;
   if (ea != cudaSuccess || eh != cudaSuccess) {
@@ -343,6 +412,7 @@ extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_optio
     delete S;
     return cuda_fail(ea != cudaSuccess ? ea : eh, "server counters");
   }
+  S->h_reset = S->h_counter + ns;
   for (int i = 0; i < ns; ++i) {
     cudaStream_t st;
     cudaError_t e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i < nfp ? prio_low : prio_high);
@@ -445,7 +515,7 @@ extern "C" int chem_serve_stats(chem_server_t S, int64_t* out /*[8]*/) {
   std::lock_guard<std::mutex> lk(S->mu);
   out[0] = S->n_done; out[1] = S->n_failed; out[2] = S->n_launches; out[3] = S->n_batched;
   out[4] = S->max_concurrent; out[5] = (int64_t)(S->resident + S->inflight);
-  out[6] = S->n_slices; out[7] = 0;
+  out[6] = S->n_slices; out[7] = S->n_joined;
   return CHEM_OK;
 }
 

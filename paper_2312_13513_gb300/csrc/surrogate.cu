@@ -31,6 +31,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -858,6 +859,116 @@ extern "C" int chem_surrogate_forward(chem_model_t md, const double* T, const do
   cudaFreeAsync(err, st);
   if (rc) return rc;
   if (herr) { set_error("surrogate forward kernel: a pipeline wait timed out"); return CHEM_ECUDA; }
+  return CHEM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// several solvers' states in one surrogate pass: gathered into one contiguous state, advanced by
+// one forward launch, one post-processing launch and one FP64 fallback launch, scattered back
+// ---------------------------------------------------------------------------------------
+namespace chem {
+
+struct GatherSeg {
+  double* T;
+  const double* p;
+  double* Y;
+  int64_t ld;
+  int64_t begin;        // first gathered cell of the segment
+  int8_t* route;        // nullable
+};
+
+struct GatherParams {
+  GatherSeg seg[kMaxSegsPerLaunch];
+  int nseg, ns;
+  int64_t n;            // gathered cells (also the gathered arrays' leading dimension)
+  double* T;
+  double* p;
+  double* Y;
+  const int8_t* route;
+};
+
+__device__ __forceinline__ int seg_of(const GatherParams& P, int64_t i) {
+  int s = 0;
+  while (s + 1 < P.nseg && P.seg[s + 1].begin <= i) ++s;
+  return s;
+}
+
+__global__ void gather_kernel(const __grid_constant__ GatherParams P) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const GatherSeg& g = P.seg[seg_of(P, i)];
+    const int64_t c = i - g.begin;
+    P.T[i] = g.T[c];
+    P.p[i] = g.p[c];
+    for (int k = 0; k < P.ns; ++k) P.Y[(int64_t)k * P.n + i] = g.Y[(int64_t)k * g.ld + c];
+  }
+}
+
+__global__ void scatter_kernel(const __grid_constant__ GatherParams P) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const GatherSeg& g = P.seg[seg_of(P, i)];
+    const int64_t c = i - g.begin;
+    g.T[c] = P.T[i];
+    for (int k = 0; k < P.ns; ++k) g.Y[(int64_t)k * g.ld + c] = P.Y[(int64_t)k * P.n + i];
+    if (g.route) g.route[c] = P.route[i];
+  }
+}
+
+}  // namespace chem
+
+extern "C" int chem_surrogate_advance(chem_model_t md, chem_mech_t mech, double* T, const double* p,
+                                      double* Y, int64_t ld, double dt, int64_t ncells, double rtol,
+                                      double atol, int8_t* route_out, chem_stream_t stream);
+
+extern "C" int chem_surrogate_advance_batch(chem_model_t md, chem_mech_t mech, const chem_segment* segs, int nseg,
+                                            chem_stream_t stream) {
+  if (!md || !mech || !segs || nseg < 1) { set_error("bad batch arguments"); return CHEM_EINVAL; }
+  for (int i = 0; i < nseg; ++i) {
+    const chem_segment& a = segs[i];
+    if (a.ncells < 0 || (a.ncells > 0 && (!a.T || !a.p || !a.Y)) || a.ld < a.ncells || a.idx ||
+        !(fabs(a.dt - md->dt) <= 1e-12 * md->dt) || a.rtol != segs[0].rtol || a.atol != segs[0].atol ||
+        !(a.rtol > 0.0) || !(a.atol > 0.0)) {
+      set_error("segment %d: invalid (indexed segment, bad sizes, a dt other than the model's, or "
+                "tolerances that differ from the first segment's)", i);
+      return CHEM_EINVAL;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ns = md->ns;
+  for (int first = 0; first < nseg; first += kMaxSegsPerLaunch) {
+    const int cnt = std::min(kMaxSegsPerLaunch, nseg - first);
+    GatherParams P{};
+    int64_t n = 0;
+    bool any_route = false;
+    for (int i = 0; i < cnt; ++i) {
+      const chem_segment& a = segs[first + i];
+      P.seg[i] = GatherSeg{a.T, a.p, a.Y, a.ld, n, a.status};
+      any_route = any_route || a.status;
+      n += a.ncells;
+    }
+    if (n == 0) continue;
+    P.nseg = cnt; P.ns = ns; P.n = n;
+    unsigned char* ws = nullptr;
+    const size_t bT = (size_t)n * 8, bY = (size_t)n * ns * 8, bR = ((size_t)n + 15) & ~(size_t)15;
+    CHEM_CUDA_TRY(cudaMallocAsync((void**)&ws, 2 * bT + bY + bR, st));
+    P.T = (double*)ws; P.p = (double*)(ws + bT); P.Y = (double*)(ws + 2 * bT);
+    int8_t* route = (int8_t*)(ws + 2 * bT + bY);
+    P.route = route;
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    gather_kernel<<<blocks, 256, 0, st>>>(P);
+    cudaError_t le = cudaGetLastError();
+    int rc = le == cudaSuccess ? CHEM_OK : cuda_fail(le, "gather_kernel");
+    if (!rc)
+      rc = chem_surrogate_advance(md, mech, P.T, P.p, P.Y, n, segs[first].dt, n, segs[first].rtol, segs[first].atol,
+                                  any_route ? route : nullptr, stream);
+    if (!rc) {
+      scatter_kernel<<<blocks, 256, 0, st>>>(P);
+      le = cudaGetLastError();
+      if (le != cudaSuccess) rc = cuda_fail(le, "scatter_kernel");
+    }
+    cudaError_t fe = cudaFreeAsync(ws, st);
+    if (rc) return rc;
+    CHEM_CUDA_TRY(fe);
+  }
   return CHEM_OK;
 }
 

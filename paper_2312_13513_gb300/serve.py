@@ -25,6 +25,24 @@ def advance_batch(mech, segments, stream=None):
     check(_lib.load().chem_advance_batch(mech.handle, arr, len(segments), _stream_ptr(stream)))
 
 
+def surrogate_advance_batch(model, segments, stream=None):
+    """segments: list of dicts(T, p, Y, dt[, rtol, atol, route]) of device tensors, all on the
+    model's dt and the same tolerances; one gathered surrogate pass (chem_surrogate_advance_batch)."""
+    arr = (_lib.Segment * len(segments))()
+    for i, s in enumerate(segments):
+        a = arr[i]
+        a.T, a.p, a.Y = s["T"].data_ptr(), s["p"].data_ptr(), s["Y"].data_ptr()
+        a.ld = s["Y"].shape[1]
+        a.ncells = s["T"].numel()
+        a.idx = None
+        a.status = s["route"].data_ptr() if s.get("route") is not None else None
+        a.nsub = None
+        a.nrej = None
+        a.dt, a.rtol, a.atol = float(s["dt"]), float(s.get("rtol", 1e-6)), float(s.get("atol", 1e-10))
+    check(_lib.load().chem_surrogate_advance_batch(model.handle, model.mech.handle, arr, len(segments),
+                                                   _stream_ptr(stream)))
+
+
 class Server:
     def __init__(self, budget_bytes, n_streams=4, idle_poll_us=20.0, slice_ms=0.0):
         """slice_ms: FP64 time slice (0: library default, negative: unsliced jobs)."""
@@ -61,7 +79,7 @@ class Server:
         out = (ctypes.c_int64 * 8)()
         check(_lib.load().chem_serve_stats(self.handle, out))
         keys = ("completed", "failed", "launches", "requests_launched", "max_concurrent", "bytes_in_use",
-                "slices")
+                "slices", "joined")
         return dict(zip(keys, list(out)))
 
     def close(self):
@@ -77,19 +95,24 @@ class Server:
 
 
 def run_closed_loop(server, solvers, duration_s=10.0, mean_gap_s=2e-3, seed=0, max_requests=4000):
-    """Closed-loop load: each solver submits its next sub-step an Exp(mean_gap_s) gap after its
-    previous result completes, for duration_s seconds or max_requests requests; requests still
-    in flight at the end are waited for.
+    """Closed-loop load: each solver submits its next sub-step an Exp(gap) gap after its previous
+    result completes, for duration_s seconds or max_requests requests; requests still in flight at
+    the end are waited for.  gap = the solver's own "think_s" when it has one (its flow solve
+    between chemistry steps; its first submission then comes at a uniform time in [0, think_s)),
+    else mean_gap_s.
 
-    solvers: list of dicts(state_id, route, dt, cells[, label]).  Returns dict with per-request
-    latencies (s) and the label of each request's solver, cells advanced and the wall time.
+    solvers: list of dicts(state_id, route, dt, cells[, label, think_s]).  Returns dict with
+    per-request latencies (s) and the label of each request's solver, cells advanced and the wall
+    time.
     """
     import heapq
     import random
     import time as _time
     rng = random.Random(seed)
     t0 = _time.perf_counter()
-    due = [(t0 + rng.expovariate(1.0 / mean_gap_s), i) for i in range(len(solvers))]
+    gap = [s.get("think_s", mean_gap_s) for s in solvers]
+    due = [(t0 + (rng.uniform(0.0, gap[i]) if "think_s" in solvers[i] else rng.expovariate(1.0 / gap[i])), i)
+           for i in range(len(solvers))]
     heapq.heapify(due)
     inflight = {}
     lat, labels, cells, submitted = [], [], 0, 0
@@ -110,7 +133,7 @@ def run_closed_loop(server, solvers, duration_s=10.0, mean_gap_s=2e-3, seed=0, m
                     lat.append(l)
                     labels.append(solvers[i].get("label", ""))
                     cells += solvers[i]["cells"]
-                heapq.heappush(due, (_time.perf_counter() + rng.expovariate(1.0 / mean_gap_s), i))
+                heapq.heappush(due, (_time.perf_counter() + rng.expovariate(1.0 / gap[i]), i))
         if (now >= end or submitted >= max_requests) and not inflight:
             break
         _time.sleep(1e-4)

@@ -94,7 +94,8 @@ def test_small_budget_forces_queueing(h2):
     states = [to_dev(*_h2_state(20000, 300 + i)) for i in range(4)]
     model = _identity_model(dm, h2, *[s.cpu().numpy() for s in states[0]])
     resident = sum(s[0].numel() * (h2.ns + 2) * 8 for s in states)
-    one_request = 20000 * (h2.ns * 4 + 5) + 4096
+    # a surrogate request's workspace: gathered state copy, route, network output, box flag, fallback index
+    one_request = 20000 * ((h2.ns + 2) * 8 + 1 + h2.ns * 4 + 1 + 4) + 4096
     srv = serve.Server(resident + one_request + 1000, n_streams=4)
     ids = [srv.register(dm, *s, model=model) for s in states]
     reqs = [srv.submit(i, serve.ROUTE_SURROGATE, 5e-7) for i in ids]
@@ -198,3 +199,62 @@ def test_small_request_is_not_stuck_behind_a_long_fp64_job(h2, ch4):
     srv.close()
     assert state_big in (serve.QUEUED, serve.RUNNING), "the long job finished before the small request"
     assert lat_small < 0.5 * lat_big, (lat_small, lat_big)
+
+
+def test_surrogate_batch_equals_individual_passes(h2):
+    """Several states in one gathered surrogate pass give bitwise the results and routes of one
+    chem_surrogate_advance per state (out-of-box cells take the FP64 fallback in both)."""
+    dm = cg.Mechanism(h2)
+    base = [_h2_state(n, 700 + i) for i, n in enumerate((5000, 129, 20000, 1))]
+    model = _identity_model(dm, h2, *base[2])
+    segs, ref = [], []
+    for i, (T, p, Y) in enumerate(base):
+        T = T.copy()
+        T[::11] = 2600.0                          # outside the training box: FP64 fallback
+        a = to_dev(T, p, Y)
+        b = to_dev(T, p, Y)
+        ra = torch.full((T.size,), -1, dtype=torch.int8, device="cuda")
+        rb = torch.full((T.size,), -1, dtype=torch.int8, device="cuda")
+        cg.surrogate_advance(model, b[0], b[1], b[2], 5e-7, route=rb)
+        segs.append({"T": a[0], "p": a[1], "Y": a[2], "dt": 5e-7, "route": ra})
+        ref.append((b, rb))
+    serve.surrogate_advance_batch(model, segs)
+    torch.cuda.synchronize()
+    for s_, (b, rb) in zip(segs, ref):
+        assert torch.equal(s_["T"], b[0]) and torch.equal(s_["Y"], b[2])
+        assert torch.equal(s_["route"], rb) and int(rb.sum()) >= 1
+
+
+def test_fp64_requests_join_a_running_sliced_job(ch4):
+    """FP64 requests of a mechanism whose time-sliced job is running join that job at its next
+    slice boundary (no new launch) and give bitwise the result of their own launch."""
+    dm = cg.Mechanism(ch4)
+    f = les_field(load_table("ch4_flamelet.npz"), n=30000, seed=41)
+    big = to_dev(f["T"], f["p"], f["Y"])
+    smalls = []
+    for i in range(3):
+        g = les_field(load_table("ch4_flamelet.npz"), n=300 + 57 * i, seed=42 + i)
+        smalls.append((g["T"], g["p"], g["Y"]))
+    srv = serve.Server(8 << 30, n_streams=2, slice_ms=2.0)
+    sid_big = srv.register(dm, *big)
+    dev_small = [to_dev(*x) for x in smalls]
+    sids = [srv.register(dm, *x) for x in dev_small]
+    r_big = srv.submit(sid_big, serve.ROUTE_FP64, 1e-6)
+    time.sleep(0.05)
+    assert srv.poll(r_big)[0] == serve.RUNNING
+    reqs = [srv.submit(s_, serve.ROUTE_FP64, 1e-6) for s_ in sids]
+    for r in reqs + [r_big]:
+        srv.wait(r, 120.0)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 4 and st["failed"] == 0
+    assert st["joined"] >= 1 and st["launches"] <= 3
+    for (T, p, Y), d in zip(smalls, dev_small):
+        r = to_dev(T, p, Y)
+        cg.advance(dm, r[0], r[1], r[2], 1e-6)
+        torch.cuda.synchronize()
+        assert torch.equal(d[0], r[0]) and torch.equal(d[2], r[2])
+    rb = to_dev(f["T"], f["p"], f["Y"])
+    cg.advance(dm, rb[0], rb[1], rb[2], 1e-6)
+    torch.cuda.synchronize()
+    assert torch.equal(big[0], rb[0]) and torch.equal(big[2], rb[2])

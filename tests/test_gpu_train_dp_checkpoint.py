@@ -55,7 +55,9 @@ def test_pack_layout_is_the_flat_layout():
     assert all(np.array_equal(a, np.float32(0.25) * c) for a, c in zip(dW2 + db2, dW + db))
 
 
-def test_two_ranks_on_half_batches_take_the_single_rank_step():
+def test_two_ranks_on_half_batches_take_the_single_rank_step(tmp_path):
+    """Each step starts the single trainer from the ranks' state (a checkpoint of rank a), so each
+    step's comparison sees the same weights and moments on both sides."""
     from paper_2312_13513_gb300.train import Trainer
     W, b, X, T = _problem(2, 512)
     ra = Trainer(11, 9, 256, W=W, b=b)
@@ -85,8 +87,11 @@ def test_two_ranks_on_half_batches_take_the_single_rank_step():
         # Adam divides by |g|: where g sits at rounding level its update can differ by up to lr;
         # elsewhere the two steps agree to FP32 rounding
         big = np.abs(g1) > 1e-3 * np.max(np.abs(g1))
-        assert np.max(np.abs(wA.astype(np.float64) - w1)[big]) <= 1e-6 * (step + 1), step
-        assert np.max(np.abs(wA.astype(np.float64) - w1)) <= 2.0 * lr * (step + 1), step
+        assert np.max(np.abs(wA.astype(np.float64) - w1)[big]) <= 1e-6, step
+        assert np.max(np.abs(wA.astype(np.float64) - w1)) <= 2.0 * lr, step
+        ck = str(tmp_path / f"ranks_after_{step}.chemtrn")
+        ra.save(ck)
+        one.load(ck)
 
 
 def test_checkpoint_resume_is_bitwise_the_uninterrupted_run(tmp_path):
