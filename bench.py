@@ -145,7 +145,18 @@ def workload_config(world):
     return {"workload": WORKLOAD, "cells_per_gpu": NCELLS, "dt": DT, "rtol": RTOL, "atol": ATOL,
             "mechanism": "synthetic H2/air-shaped, 9 species, 25 reactions",
             "l2": "flushed between steps (256 MiB write)",
-            "parallelism": f"cells sharded, {world} rank(s), no collective"}
+            "parallelism": f"one field of {world} x 2^20 cells in contiguous ranges per rank, balanced "
+                           f"by the warm-up's attempt counts; no collective in the timed steps"}
+
+
+def shared_field(world):
+    """The field a job of world ranks advances: world seeded 2^20-cell quasi-DNS fields end to end
+    (one field for a single GPU)."""
+    parts = [make_field(r) for r in range(world)]
+    if world == 1:
+        return parts[0]
+    return {"T": np.concatenate([f["T"] for f in parts]), "p": np.concatenate([f["p"] for f in parts]),
+            "Y": np.concatenate([f["Y"] for f in parts], axis=1)}
 
 
 def make_field(rank=0, n=NCELLS):
@@ -755,9 +766,9 @@ def _service_s_per_cell(dm_h2, dm_ch4, model):
     return out
 
 
-def _serving_run(dm_h2, dm_ch4, model, solvers, think, duration_s, seed):
+def _serving_run(dm_h2, dm_ch4, model, solvers, think, duration_s, seed, slice_ms=0.0):
     from paper_2312_13513_gb300 import serve
-    srv = serve.Server(150 << 30, n_streams=4)
+    srv = serve.Server(150 << 30, n_streams=4, slice_ms=slice_ms)
     run_solvers = []
     for s_ in solvers:
         sid = srv.register(dm_h2 if s_["mech"] == "h2" else dm_ch4, s_["T"], s_["p"], s_["Y"],
@@ -784,7 +795,7 @@ def _serving_run(dm_h2, dm_ch4, model, solvers, think, duration_s, seed):
             "failed": st["failed"]}
 
 
-def extra_serving(duration_s=10.0, seed=12349, duty=1.0 / 128.0):
+def extra_serving(duration_s=10.0, seed=12349, duty=1.0 / 128.0, slice_ms=0.0):
     """Config 4 at two loads: (a) sustainable -- each solver spends 1/duty - 1 times its idle-GPU
     chemistry time on its own flow solve between requests, so the 64 solvers together offer about
     64 duty = 50 % of the GPU; (b) overload -- Exp(2 ms) gaps between a solver's result and its next
@@ -793,10 +804,10 @@ def extra_serving(duration_s=10.0, seed=12349, duty=1.0 / 128.0):
     per_cell = _service_s_per_cell(dm_h2, dm_ch4, model)
     offered = sum(s_["cells"] * per_cell[s_["label"]] for s_ in solvers)
     think = lambda s_: s_["cells"] * per_cell[s_["label"]] * (1.0 / duty - 1.0)
-    sustainable = _serving_run(dm_h2, dm_ch4, model, solvers, think, duration_s, seed)
+    sustainable = _serving_run(dm_h2, dm_ch4, model, solvers, think, duration_s, seed, slice_ms)
     sustainable["load"] = (f"each solver thinks {1.0 / duty - 1.0:.0f}x its idle-GPU service time "
                            f"(offered ~{64 * duty:.0%} of the GPU)")
-    overload = _serving_run(dm_h2, dm_ch4, model, solvers, None, duration_s, seed)
+    overload = _serving_run(dm_h2, dm_ch4, model, solvers, None, duration_s, seed, slice_ms)
     overload["load"] = "Exp(2 ms) think time (offered work far above capacity)"
     return {"workload": "64 closed-loop solvers, 1e4-2e6 cells log-uniform, 70/30 H2/CH4, routes 50/50 "
                         "(H2 only), 150 GB budget, 10 s of submissions per load, FP64 jobs in 20 ms time "
@@ -869,31 +880,55 @@ def main():
 
     mech = h2_mechanism()
     dm = cg.Mechanism(mech)
-    field = make_field(rank)
     dev = torch.device("cuda", local)
-    T0 = torch.tensor(field["T"], device=dev)
-    p = torch.tensor(field["p"], device=dev)
-    Y0 = torch.tensor(np.ascontiguousarray(field["Y"]), device=dev)
-    T = T0.clone(); Y = Y0.clone()
-    n = T.numel()
-    nsub = torch.zeros(n, dtype=torch.int32, device=dev)
-    nrej = torch.zeros(n, dtype=torch.int32, device=dev)
-    status = torch.zeros(n, dtype=torch.int8, device=dev)
+    # one shared field of world x 2^20 cells; each rank advances a contiguous range of it, first
+    # equal, then balanced by the attempt counts measured in the warm-up (weak scaling: 2^20 cells
+    # per GPU on average, no collective inside the timed steps)
+    from paper_2312_13513_gb300 import parallel
+    field_all = shared_field(world)
+    n_total = field_all["T"].size
+    S = {}
+
+    def take(a, b):
+        S["range"] = (a, b)
+        S["T0"] = torch.tensor(field_all["T"][a:b], device=dev)
+        S["p"] = torch.tensor(field_all["p"][a:b], device=dev)
+        S["Y0"] = torch.tensor(np.ascontiguousarray(field_all["Y"][:, a:b]), device=dev)
+        S["T"], S["Y"] = S["T0"].clone(), S["Y0"].clone()
+        m = b - a
+        S["nsub"] = torch.zeros(m, dtype=torch.int32, device=dev)
+        S["nrej"] = torch.zeros(m, dtype=torch.int32, device=dev)
+        S["status"] = torch.zeros(m, dtype=torch.int8, device=dev)
+
+    take(*parallel.shard(n_total, rank, world))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
+        T, Y, T0, Y0, p = S["T"], S["Y"], S["T0"], S["Y0"], S["p"]
         T.copy_(T0); Y.copy_(Y0)
         flush.fill_(1)
         if ev is not None:
             ev[0].record(stream)
-        cg.advance(dm, T, p, Y, DT, RTOL, ATOL, status=status, nsub=nsub, nrej=nrej, stream=stream)
+        cg.advance(dm, T, p, Y, DT, RTOL, ATOL, status=S["status"], nsub=S["nsub"], nrej=S["nrej"], stream=stream)
         if ev is not None:
             ev[1].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    if world > 1:
+        # the next steps' ranges from this step's per-cell attempts (parallel.rebalance), then one
+        # more untimed step on the new range
+        w = (S["nsub"] + S["nrej"] + 1).to(torch.float64)
+        take(*parallel.rebalance(w, S["range"][0], n_total))
+        step()
+        torch.cuda.synchronize()
+    T, Y, T0, Y0, p = S["T"], S["Y"], S["T0"], S["Y0"], S["p"]
+    nsub, nrej, status = S["nsub"], S["nrej"], S["status"]
+    n = T.numel()
+    a0, b0 = S["range"]
+    field = {"T": field_all["T"][a0:b0], "p": field_all["p"][a0:b0], "Y": field_all["Y"][:, a0:b0]}
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -917,7 +952,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value = n_total * args.steps / (total_ms * 1e-3)
     bad = int((status != 0).sum().item())
     acc = int(nsub.sum().item())
     att = acc + int(nrej.sum().item())
@@ -968,7 +1003,7 @@ def main():
                      "kernel_ms": kernel_ms, "flops_per_launch": flops,
                      "transcendentals_per_launch": trans,
                      "transcendental_weight": fl.TRANSCENDENTAL_FLOPS},
-        "e2e": {"value": world * n * args.steps / (e2e_ms * 1e-3), "unit": "cell-updates/s",
+        "e2e": {"value": n_total * args.steps / (e2e_ms * 1e-3), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clk,

@@ -428,6 +428,9 @@ typedef struct chem_serve_options {
                                 concurrent surrogate launches (0 -> 4 each) */
   double idle_poll_us;       /* polling interval while launches are in flight (0 -> 20 us) */
   double slice_ms;           /* FP64 time slice (0 -> 20 ms; negative: no slicing) */
+  double max_pause_ms;       /* a time-sliced FP64 job whose slice ends while surrogate passes run
+                                waits up to this long before its next slice, so that the passes'
+                                kernels find the SMs free (0 -> 20 ms; negative: never waits) */
 } chem_serve_options;
 
 /* Start a server on the current device: its streams (half low-priority FP64, half high-priority

@@ -55,7 +55,7 @@ class TransportDesc(ctypes.Structure):
 
 
 class ServeOptions(ctypes.Structure):
-    _fields_ = [("n_streams", I32), ("idle_poll_us", D), ("slice_ms", D)]
+    _fields_ = [("n_streams", I32), ("idle_poll_us", D), ("slice_ms", D), ("max_pause_ms", D)]
 
 
 class SurrogateDesc(ctypes.Structure):

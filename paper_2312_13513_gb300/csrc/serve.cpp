@@ -75,6 +75,10 @@ struct Launch {
   std::vector<long long> seg_end;
   long long issued_total = 0;     // queue end the running slice was issued with
   size_t ndone = 0;
+  // a job whose slice ended while surrogate passes run waits (at most max_pause) before its next
+  // slice, so that the passes' kernels find the SMs free
+  bool paused = false;
+  Clock::time_point paused_since;
 };
 
 }  // namespace
@@ -103,6 +107,7 @@ struct chem_server_s {
   int64_t n_joined = 0;                        // FP64 requests that joined a running time-sliced job
   double idle_poll_us = 20.0;
   unsigned long long slice_ns = 20000000ull;   // 0: FP64 jobs run unsliced
+  unsigned long long max_pause_ns = 20000000ull;  // longest wait of an FP64 job for surrogate passes
   unsigned long long* d_counter = nullptr;     // one work-queue counter per stream (device)
   unsigned long long* h_counter = nullptr;     // its read-back copy (pinned host memory)
   unsigned long long* h_reset = nullptr;       // values the counters are set back to (pinned)
@@ -138,6 +143,9 @@ void server_loop(chem_server_s* S) {
     const uint64_t submitted = S->n_submitted;
     // ---- retire finished launches ----
     bool progressed = false;
+    bool sur_running = false;
+    for (const Launch& L : S->launches)
+      if (!L.sliced && cudaEventQuery(L.ev) == cudaErrorNotReady) sur_running = true;
     for (size_t i = 0; i < S->launches.size();) {
       Launch& L = S->launches[i];
       cudaError_t q = cudaEventQuery(L.ev);
@@ -158,6 +166,16 @@ void server_loop(chem_server_s* S) {
           ++L.ndone;
           progressed = true;
         }
+        if (done < total && sur_running && S->max_pause_ns > 0 &&
+            (!L.paused || (unsigned long long)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                              now - L.paused_since).count() < S->max_pause_ns)) {
+          // surrogate passes are running: their kernels get the whole GPU before this job's next
+          // slice (requests wait for a pass, not for FP64 slices between its kernels)
+          if (!L.paused) { L.paused = true; L.paused_since = now; }
+          ++i;
+          continue;
+        }
+        L.paused = false;
         if (done < total) {
           // next slice of the same job, continuing the same queue; requests that joined since the
           // last slice extend it, and a counter that overshot the old end is set back to it
@@ -402,6 +420,8 @@ extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_optio
   if (opt && opt->idle_poll_us > 0) S->idle_poll_us = opt->idle_poll_us;
   if (opt && opt->slice_ms != 0.0)
     S->slice_ns = opt->slice_ms < 0.0 ? 0ull : (unsigned long long)(opt->slice_ms * 1e6);
+  if (opt && opt->max_pause_ms != 0.0)
+    S->max_pause_ns = opt->max_pause_ms < 0.0 ? 0ull : (unsigned long long)(opt->max_pause_ms * 1e6);
   if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; return cuda_fail(cudaGetLastError(), "cudaGetDevice"); }
   cudaError_t ea = cudaMalloc((void**)&S->d_counter, ns * sizeof(unsigned long long));
   cudaError_t eh = ea == cudaSuccess ? cudaHostAlloc((void**)&S->h_counter, 2 * ns * sizeof(unsigned long long),

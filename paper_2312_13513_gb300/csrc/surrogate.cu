@@ -336,7 +336,223 @@ struct PostParams {
 };
 
 
-__global__ void surrogate_post_kernel(const PostParams P) {
+// The mixture's NASA-7 polynomials of one temperature range for a register-resident
+// composition (the sums of mixture_nasa, with the species loop unrolled to the array extent).
+template <int AS>
+__device__ __forceinline__ void mixture_poly(const double (&Y)[AS], int ns, int rg, const double* hcoef,
+                                             const double* ccoef, const double* invW, double (&Ah)[6],
+                                             double (&Ac)[5]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Ah[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) Ac[i] = 0.0;
+#pragma unroll
+  for (int k = 0; k < AS; ++k) {
+    if (k < ns) {
+      const double yw = Y[k] * __ldg(invW + k);
+      const double* a = hcoef + (rg * ns + k) * 6;
+      const double* c = ccoef + (rg * ns + k) * 5;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) Ah[i] = fma(yw, a[i], Ah[i]);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) Ac[i] = fma(yw, c[i], Ac[i]);
+    }
+  }
+}
+
+// One cell's post-processing for a mechanism of NS_ species and NE_ elements known at compile
+// time: every per-cell array lives in registers (no local-memory frame).
+template <int NS_, int NE_>
+__global__ void __launch_bounds__(256) surrogate_post_kernel(const PostParams P) {
+  constexpr int AS = NS_ > 0 ? NS_ : MAXNS;          // array extents
+  constexpr int AE = NE_ > 0 ? NE_ : NEMAX;
+  const int ns = NS_ > 0 ? NS_ : P.lay.ns;
+  const int ne = NE_ > 0 ? NE_ : P.ne;
+  const double* hcoef = (const double*)(P.blob + P.lay.o_hc);
+  const double* ccoef = (const double*)(P.blob + P.lay.o_cpc);
+  const double* invW = (const double*)(P.blob + P.lay.o_invW);
+  for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < P.ncells;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    bool pass = P.outbox[cell] == 0;
+    double Y0[AS], Y1[AS];
+    const double T0 = P.T[cell];
+#pragma unroll
+    for (int k = 0; k < AS; ++k) {
+      if (k < ns) {
+        Y0[k] = P.Y[(int64_t)k * P.ld + cell];
+        Y1[k] = (double)P.ynet[(int64_t)k * P.ncells + cell];
+        if (!isfinite(Y1[k])) pass = false;
+      }
+    }
+    double Tn = T0;
+    if (pass) {
+      // element-conservation projection: Y'' = Y' - D A^T (A D A^T)^-1 (A Y' - b), D = diag(Y' + 1e-12)
+      double b[AE], lam[AE], G[AE][AE];
+#pragma unroll
+      for (int e = 0; e < AE; ++e) {
+        if (e < ne) {
+          double sb = 0.0, sr = 0.0;
+#pragma unroll
+          for (int k = 0; k < AS; ++k) {
+            if (k < ns) {
+              const double a = P.Aem[e * ns + k];
+              sb += a * Y0[k];
+              sr += a * Y1[k];
+            }
+          }
+          b[e] = sb;
+          lam[e] = sr - sb;
+        }
+      }
+      const double* AA = P.Aem + ne * ns;
+#pragma unroll
+      for (int e = 0; e < AE; ++e)
+#pragma unroll
+        for (int f = 0; f <= e; ++f) {
+          if (e < ne) {
+            double sg = 0.0;
+#pragma unroll
+            for (int k = 0; k < AS; ++k)
+              if (k < ns) sg = fma(AA[k], Y1[k] + 1e-12, sg);
+            AA += ns;
+            G[e][f] = sg;
+            G[f][e] = sg;
+          }
+        }
+      // Gaussian elimination with partial pivoting on the small SPD system
+#pragma unroll
+      for (int k = 0; k < AE; ++k) {
+        if (k < ne && pass) {
+          // pivot search on values (no runtime index into the register array)
+          int pr = k;
+          double gmax = fabs(G[k][k]);
+#pragma unroll
+          for (int i = k + 1; i < AE; ++i)
+            if (i < ne && fabs(G[i][k]) > gmax) { pr = i; gmax = fabs(G[i][k]); }
+          if (gmax == 0.0) {
+            pass = false;
+          } else {
+            if (pr != k) {
+#pragma unroll
+              for (int j = 0; j < AE; ++j) {
+                if (j < ne) {
+                  double gk = G[k][j], gp = 0.0;
+#pragma unroll
+                  for (int i = k + 1; i < AE; ++i) if (i == pr) gp = G[i][j];
+                  G[k][j] = gp;
+#pragma unroll
+                  for (int i = k + 1; i < AE; ++i) if (i == pr) G[i][j] = gk;
+                }
+              }
+              double lk = lam[k], lp = 0.0;
+#pragma unroll
+              for (int i = k + 1; i < AE; ++i) if (i == pr) lp = lam[i];
+              lam[k] = lp;
+#pragma unroll
+              for (int i = k + 1; i < AE; ++i) if (i == pr) lam[i] = lk;
+            }
+#pragma unroll
+            for (int i = k + 1; i < AE; ++i) {
+              if (i < ne) {
+                const double l = G[i][k] / G[k][k];
+#pragma unroll
+                for (int j = k; j < AE; ++j)
+                  if (j < ne) G[i][j] -= l * G[k][j];
+                lam[i] -= l * lam[k];
+              }
+            }
+          }
+        }
+      }
+      if (pass) {
+#pragma unroll
+        for (int i = AE - 1; i >= 0; --i) {
+          if (i < ne) {
+            double sl = lam[i];
+#pragma unroll
+            for (int j = i + 1; j < AE; ++j)
+              if (j < ne) sl -= G[i][j] * lam[j];
+            lam[i] = sl / G[i][i];
+          }
+        }
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < AS; ++k) {
+          if (k < ns) {
+            double c = 0.0;
+#pragma unroll
+            for (int e = 0; e < AE; ++e)
+              if (e < ne) c += P.Aem[e * ns + k] * lam[e];
+            Y1[k] = fmax(Y1[k] - (Y1[k] + 1e-12) * c, 0.0);
+            s0 += Y0[k];
+            s1 += Y1[k];
+          }
+        }
+        double res = 0.0;
+#pragma unroll
+        for (int e = 0; e < AE; ++e) {
+          if (e < ne) {
+            double sr = 0.0;
+#pragma unroll
+            for (int k = 0; k < AS; ++k)
+              if (k < ns) sr += P.Aem[e * ns + k] * Y1[k];
+            res = fmax(res, fabs(sr - b[e]));
+          }
+        }
+        if (!(res <= 1e-9) || !(fabs(s1 - s0) <= 1e-9)) pass = false;
+      }
+      if (pass) {
+        // temperature from enthalpy conservation: h(T, Y'') = h(T0, Y0); the new composition is
+        // fixed during the iteration, so its mixture NASA-7 polynomial is formed once per
+        // temperature range visited
+        double h0;
+        {
+          const int rg0 = T0 < TMID ? 0 : 1;
+          const double invT0 = 1.0 / T0;
+          double hs = 0.0;
+#pragma unroll
+          for (int k = 0; k < AS; ++k) {
+            if (k < ns) {
+              const double* a = hcoef + (rg0 * ns + k) * 6;
+              const double hRT = a[0] + T0 * (a[1] + T0 * (a[2] + T0 * (a[3] + T0 * a[4]))) + a[5] * invT0;
+              hs += Y0[k] * hRT * __ldg(invW + k);
+            }
+          }
+          h0 = RU * T0 * hs;
+        }
+        double Ah[6], Ac[5];
+        int rg = Tn < TMID ? 0 : 1;
+        mixture_poly<AS>(Y1, ns, rg, hcoef, ccoef, invW, Ah, Ac);
+        bool conv = false;
+        for (int it = 0; it < 50; ++it) {
+          const int r = Tn < TMID ? 0 : 1;
+          if (r != rg) { rg = r; mixture_poly<AS>(Y1, ns, rg, hcoef, ccoef, invW, Ah, Ac); }
+          double hh, cp;
+          h_cp_from_mixture(Ah, Ac, Tn, &hh, &cp);
+          const double dT = (hh - h0) / cp;
+          Tn -= dT;
+          if (!(Tn >= 200.0 && Tn <= 6000.0)) break;
+          if (fabs(dT) < 1e-9 * Tn) { conv = true; break; }
+        }
+        if (!conv) pass = false;
+      }
+    }
+    if (pass) {
+      P.T[cell] = Tn;
+#pragma unroll
+      for (int k = 0; k < AS; ++k)
+        if (k < ns) P.Y[(int64_t)k * P.ld + cell] = Y1[k];
+    } else {
+      const unsigned slot = atomicAdd(P.fb_count, 1u);
+      P.fb_idx[slot] = (int32_t)cell;
+    }
+    if (P.route) P.route[cell] = pass ? 0 : 1;
+  }
+}
+
+// The same post-processing for any species and element counts (runtime loops; per-cell arrays
+// sized for the maxima, in local memory).
+__global__ void surrogate_post_general(const PostParams P) {
   const int ns = P.lay.ns;
   for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < P.ncells;
        cell += (int64_t)gridDim.x * blockDim.x) {
@@ -1006,7 +1222,8 @@ extern "C" int chem_surrogate_advance(chem_model_t md, chem_mech_t mech, double*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long blocks = std::min<long long>((ncells + 255) / 256, (long long)sms * 16);
-    surrogate_post_kernel<<<(unsigned)blocks, 256, 0, st>>>(Q);
+    if (md->ns == 9 && md->ne == 3) surrogate_post_kernel<9, 3><<<(unsigned)blocks, 256, 0, st>>>(Q);
+    else surrogate_post_general<<<(unsigned)blocks, 256, 0, st>>>(Q);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) rc = cuda_fail(le, "surrogate_post_kernel");
   }

@@ -80,3 +80,22 @@ def allreduce_sum_(flat, group=None):
     if world > 1:
         dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
     return world
+
+
+def rebalance(local_weights, start, n_total, group=None):
+    """Balanced contiguous ranges for the next step of a shared field of n_total cells, from the
+    per-cell weights (attempt counts + 1) each rank measured on its current range [start, start +
+    len(local_weights)): one all-reduce (sum) assembles the field's weights on every rank (the
+    ranges tile the field, so every cell has exactly one contributor), then every rank takes its
+    quantile range.  local_weights is a torch tensor on the process group's device (CUDA for NCCL,
+    CPU for gloo).  Returns (start, end) of this rank; without torch.distributed, (0, n_total)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return 0, n_total
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    full = torch.zeros(n_total, dtype=torch.float64, device=local_weights.device)
+    full[start:start + local_weights.numel()] = local_weights.to(torch.float64)
+    if world > 1:
+        dist.all_reduce(full, op=dist.ReduceOp.SUM, group=group)
+    return shard(n_total, rank, world, full.cpu().numpy())

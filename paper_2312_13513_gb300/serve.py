@@ -44,10 +44,11 @@ def surrogate_advance_batch(model, segments, stream=None):
 
 
 class Server:
-    def __init__(self, budget_bytes, n_streams=4, idle_poll_us=20.0, slice_ms=0.0):
-        """slice_ms: FP64 time slice (0: library default, negative: unsliced jobs)."""
+    def __init__(self, budget_bytes, n_streams=4, idle_poll_us=20.0, slice_ms=0.0, max_pause_ms=0.0):
+        """slice_ms: FP64 time slice (0: library default, negative: unsliced jobs); max_pause_ms:
+        longest wait of an FP64 job for running surrogate passes (0: default, negative: none)."""
         h = ctypes.c_void_p()
-        opt = _lib.ServeOptions(n_streams, idle_poll_us, slice_ms)
+        opt = _lib.ServeOptions(n_streams, idle_poll_us, slice_ms, max_pause_ms)
         check(_lib.load().chem_serve_create(int(budget_bytes), ctypes.byref(opt), ctypes.byref(h)))
         self.handle = h
         self._keep = []

@@ -142,3 +142,43 @@ def test_two_gloo_ranks_data_parallel_step_equals_single_rank_step():
         assert gerr <= 1e-12, gerr           # mean of the two shares' means = the global mean
         assert werr <= 1e-12, werr
         assert same
+
+
+def _rebalance_worker(rank, world, port, out):
+    """Each rank advanced an equal shard; with the attempt counts it measured, the next step's
+    ranges are rebuilt from the whole field's counts."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2312_13513_gb300.parallel import rebalance
+    n = 10001
+    rng = np.random.default_rng(7)            # the field's per-cell attempt counts (same on all ranks)
+    counts = rng.integers(1, 40, n).astype(float)
+    counts[: n // 3] *= 5.0                   # a costly flame region at the start of the field
+    s, e = shard(n, rank, world)              # first step: equal cell counts
+    mine = torch.tensor(counts[s:e] + 1.0)
+    ns, ne = rebalance(mine, s, n)
+    out.put((rank, s, e, ns, ne))
+    dist.destroy_process_group()
+
+
+def test_rebalance_by_measured_attempts_on_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rebalance_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, s0, e0, a0, b0), (_, s1, e1, a1, b1) = res
+    assert s0 == 0 and e0 == s1 and e1 == 10001                     # equal first split
+    assert a0 == 0 and b0 == a1 and b1 == 10001                     # new ranges tile the field
+    rng = np.random.default_rng(7)
+    counts = rng.integers(1, 40, 10001).astype(float)
+    counts[: 10001 // 3] *= 5.0
+    w = counts + 1.0
+    assert b0 < e0                         # the costly first part gets fewer cells
+    assert abs(w[:b0].sum() - w[b0:].sum()) <= 2 * w.max()
