@@ -727,9 +727,11 @@ def _serving_setup(seed):
         label = ("h2" if is_h2 else "ch4") + ("_surrogate" if route == serve.ROUTE_SURROGATE else "_fp64")
         solvers.append({"route": route, "dt": DT if is_h2 else 1e-6, "cells": n, "mech": "h2" if is_h2 else "ch4",
                         "label": label, "off": off,
-                        "T": torch.tensor(f["T"][off:off + n], device="cuda"),
+                        "T0": torch.tensor(f["T"][off:off + n], device="cuda"),
                         "p": torch.tensor(f["p"][off:off + n], device="cuda"),
-                        "Y": torch.tensor(np.ascontiguousarray(f["Y"][:, off:off + n]), device="cuda")})
+                        "Y0": torch.tensor(np.ascontiguousarray(f["Y"][:, off:off + n]), device="cuda")})
+        solvers[-1]["T"] = solvers[-1]["T0"].clone()
+        solvers[-1]["Y"] = solvers[-1]["Y0"].clone()
     return dm_h2, dm_ch4, model, solvers
 
 
@@ -768,12 +770,25 @@ def _service_s_per_cell(dm_h2, dm_ch4, model):
 
 def _serving_run(dm_h2, dm_ch4, model, solvers, think, duration_s, seed, slice_ms=0.0):
     from paper_2312_13513_gb300 import serve
+    import torch
     srv = serve.Server(150 << 30, n_streams=4, slice_ms=slice_ms)
     run_solvers = []
+
+    def flow_step(s_):
+        # the solver's own step between two chemistry sub-steps: here it brings the state back to
+        # the field's (a chemistry-only loop would drift towards equilibrium, out of the surrogate's
+        # training distribution, which a real flow step keeps it in)
+        def run():
+            s_["T"].copy_(s_["T0"]); s_["Y"].copy_(s_["Y0"])
+            torch.cuda.current_stream().synchronize()
+        return run
+
     for s_ in solvers:
+        s_["T"].copy_(s_["T0"]); s_["Y"].copy_(s_["Y0"])
         sid = srv.register(dm_h2 if s_["mech"] == "h2" else dm_ch4, s_["T"], s_["p"], s_["Y"],
                            model=model if s_["mech"] == "h2" else None)
-        d = {"state_id": sid, "route": s_["route"], "dt": s_["dt"], "cells": s_["cells"], "label": s_["label"]}
+        d = {"state_id": sid, "route": s_["route"], "dt": s_["dt"], "cells": s_["cells"], "label": s_["label"],
+             "flow": flow_step(s_)}
         if think is not None:
             d["think_s"] = think(s_)
         run_solvers.append(d)
@@ -811,7 +826,8 @@ def extra_serving(duration_s=10.0, seed=12349, duty=1.0 / 128.0, slice_ms=0.0):
     overload["load"] = "Exp(2 ms) think time (offered work far above capacity)"
     return {"workload": "64 closed-loop solvers, 1e4-2e6 cells log-uniform, 70/30 H2/CH4, routes 50/50 "
                         "(H2 only), 150 GB budget, 10 s of submissions per load, FP64 jobs in 20 ms time "
-                        "slices that requests join, surrogate requests gathered into one pass per model",
+                        "slices that requests join, surrogate requests gathered into one pass per model; "
+                        "each solver's flow step restores its state to the field's before it submits",
             "idle_service_us_per_kcell": {k: round(v * 1e9, 3) for k, v in per_cell.items()},
             "all_solvers_once_idle_s": offered,
             "cells_h2": int(sum(s_["cells"] for s_ in solvers if s_["mech"] == "h2")),

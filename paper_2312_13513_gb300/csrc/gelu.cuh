@@ -33,4 +33,51 @@ __device__ __forceinline__ float gelu_f(float v) {
   return fmaf(-0.5f * x, rcp_approx(q), fmaxf(v, 0.0f));
 }
 
+// Two GELUs at once with the packed FP32 instructions (fma/mul .f32x2: each half rounds exactly
+// like the scalar instruction, so gelu2 gives bitwise the values of two gelu_f calls) at half the
+// instruction count of the polynomial and the squarings; v0, v1 are updated in place.
+__device__ __forceinline__ unsigned long long f32x2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+__device__ __forceinline__ void f32x2_split(unsigned long long r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+
+__device__ __forceinline__ unsigned long long fma_x2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+__device__ __forceinline__ unsigned long long mul_x2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+__device__ __forceinline__ void gelu2(float& v0, float& v1) {
+  const float x0 = fabsf(v0), x1 = fabsf(v1);
+  const unsigned long long x = f32x2(x0, x1);
+  unsigned long long q = fma_x2(x, f32x2(5.3829750000e-06f, 5.3829750000e-06f),
+                                f32x2(4.8890635643e-05f, 4.8890635643e-05f));
+  q = fma_x2(q, x, f32x2(3.8003575000e-05f, 3.8003575000e-05f));
+  q = fma_x2(q, x, f32x2(3.2776263241e-03f, 3.2776263241e-03f));
+  q = fma_x2(q, x, f32x2(2.1141006150e-02f, 2.1141006150e-02f));
+  q = fma_x2(q, x, f32x2(4.9867346967e-02f, 4.9867346967e-02f));
+  q = fma_x2(q, x, f32x2(1.0f, 1.0f));
+  q = mul_x2(q, q);
+  q = mul_x2(q, q);
+  q = mul_x2(q, q);
+  q = mul_x2(q, q);                                  // (...)^16
+  float q0, q1;
+  f32x2_split(q, q0, q1);
+  const unsigned long long r = f32x2(rcp_approx(q0), rcp_approx(q1));
+  const unsigned long long hx = mul_x2(x, f32x2(-0.5f, -0.5f));
+  const unsigned long long out = fma_x2(hx, r, f32x2(fmaxf(v0, 0.0f), fmaxf(v1, 0.0f)));
+  f32x2_split(out, v0, v1);
+}
+
 }  // namespace chem

@@ -83,6 +83,28 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// Bias, GELU and BF16 rounding of 32 accumulator columns (c0 .. c0 + 31) of one row, written as
+// half of a 128-byte K chunk of the next layer's input (128-byte swizzled K-major layout).  The
+// 32 biases are warp-uniform reads of the kernel's parameter bank.
+__device__ __forceinline__ void epilogue_block(const uint32_t (&a)[32], const float* bias, int c0,
+                                               unsigned char* arow, int r) {
+  unsigned char* chunk = arow + (c0 >> 6) * ACT_CHUNK;
+  const int part = (c0 >> 5) & 1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float* bq = bias + c0 + 8 * q;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(a[8 * q + e]) + bq[e];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) gelu2(v[e], v[e + 1]);
+    uint4 pk;
+    pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
+    pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4*>(chunk + (((part * 4 + q) ^ (r & 7)) << 4)) = pk;
+  }
+}
+
 // the per-tile chunk schedule shared by the producer and the MMA issuer
 // layer 0: 2 chunks (rows 0-255, 256-511 of W1, K = 64); layers 1-3: 8 K-chunks x 2 halves;
 // layer 4: 8 K-chunks of W5 (16 rows)
@@ -102,9 +124,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   unsigned char* wst = smem + ACT_BYTES;
   uint64_t* full = (uint64_t*)(wst + WSTAGES * WSTAGE_BYTES);
   uint64_t* empty = full + WSTAGES;
-  uint64_t* acc_done = empty + WSTAGES;
-  uint64_t* act_ready = acc_done + 1;
-  uint32_t* tmem_slot = (uint32_t*)(act_ready + 1);
+  // acc_full[h]: the MMAs into accumulator half h (TMEM columns 256 h .. + 255) of a layer are
+  // done; lo_free: the layer's second-half MMAs have read activation chunks 0-3, which the first
+  // half's epilogue then overwrites; act_ready[h]: the epilogue of half h has drained its
+  // accumulator and written activation chunks 4 h .. 4 h + 3
+  uint64_t* acc_full = empty + WSTAGES;
+  uint64_t* lo_free = acc_full + 2;
+  uint64_t* act_ready = lo_free + 1;
+  uint64_t* feat_ready = act_ready + 2;       // the tile's features are in chunk 0
+  uint32_t* tmem_slot = (uint32_t*)(feat_ready + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ntiles = (P.ncells + TM - 1) / TM;
@@ -113,8 +141,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < WSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(acc_done, 1);
-    mbar_init(act_ready, 32 * kEpiWarps);
+    mbar_init(&acc_full[0], 1);
+    mbar_init(&acc_full[1], 1);
+    mbar_init(lo_free, 1);
+    mbar_init(&act_ready[0], 32 * kEpiWarps / 2);
+    mbar_init(&act_ready[1], 32 * kEpiWarps / 2);
+    mbar_init(feat_ready, 32 * kEpiWarps / 2);
     fence_barrier_init();
   }
   if (warp == kTmaWarp) tmem_alloc(tmem_slot, 512);
@@ -126,6 +158,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   if (warp == kTmaWarp) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
+      // weight stages in the order the MMA issuer consumes them: layer 0 (rows 0-255, then
+      // 256-511 of W1), layers 1-3 (first output half: K chunks 0-7, then the second half), layer 4
       prefetch_tmap(&tW1); prefetch_tmap(&tW2); prefetch_tmap(&tW3); prefetch_tmap(&tW4); prefetch_tmap(&tW5);
       long long it = 0;
       bool ok = true;
@@ -138,7 +172,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             mbar_arrive_expect_tx(&full[s], WSTAGE_BYTES);
             tma_load_2d(dst, &tW1, &full[s], 0, c * 256);
           } else if (c < 2 + 48) {
-            const int l = (c - 2) / 16, r = (c - 2) % 16, kc = r / 2, nh = r % 2;
+            const int l = (c - 2) / 16, r = (c - 2) % 16, nh = r / 8, kc = r % 8;
             const CUtensorMap* tm = l == 0 ? &tW2 : (l == 1 ? &tW3 : &tW4);
             mbar_arrive_expect_tx(&full[s], WSTAGE_BYTES);
             tma_load_2d(dst, tm, &full[s], kc * 64, nh * 256);
@@ -158,45 +192,74 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       // ---------------- MMA issuer ----------------
       constexpr uint32_t id256 = idesc_bf16_f32(128, 256);
       constexpr uint32_t id16 = idesc_bf16_f32(128, NOUT);
-      long long it = 0, nready = 0;
+      long long it = 0;
+      long long n_ready[2] = {0, 0};
       bool ok = true;
       const uint32_t abase = smem_addr(act);
-      for (long long rd = 0; rd < rounds && ok; ++rd) {
-        int c = 0;
-        for (int l = 0; l < 5 && ok; ++l) {
-          if (!mbar_wait(act_ready, (uint32_t)(nready & 1), P.err)) { ok = false; break; }
-          ++nready;
-          tc_fence_after();
-          const int nchunks = l == 0 ? 2 : (l < 4 ? 16 : 8);
-          for (int i = 0; i < nchunks; ++i, ++c, ++it) {
-            const int s = (int)(it % WSTAGES);
-            if (!mbar_wait(&full[s], (uint32_t)((it / WSTAGES) & 1), P.err)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t bbase = smem_addr(wst + s * WSTAGE_BYTES);
-            int kc, nh;
-            if (l == 0) { kc = 0; nh = i; }
-            else if (l < 4) { kc = i / 2; nh = i % 2; }
-            else { kc = i; nh = 0; }
-            const uint32_t d = tmem + (l < 4 ? nh * 256 : 0);
-            const uint32_t idesc = l < 4 ? id256 : id16;
+      // one weight stage: A chunk kc (128 x 64) times the stage's B (N x 64) into d
+      auto stage = [&](int kc, uint32_t d, uint32_t idesc, bool accumulate) -> bool {
+        const int s = (int)(it % WSTAGES);
+        if (!mbar_wait(&full[s], (uint32_t)((it / WSTAGES) & 1), P.err)) return false;
+        tc_fence_after();
+        const uint32_t bbase = smem_addr(wst + s * WSTAGE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_bf16(d, sdesc_k128(abase + kc * ACT_CHUNK + kk * 32), sdesc_k128(bbase + kk * 32), idesc,
-                       (kc > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(&empty[s]);                             // frees the stage
-          }
-          if (ok) mma_commit(acc_done);
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(d, sdesc_k128(abase + kc * ACT_CHUNK + kk * 32), sdesc_k128(bbase + kk * 32), idesc,
+                   (accumulate || kk > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);                               // frees the stage
+        ++it;
+        return true;
+      };
+      auto wait_ready = [&](int h) -> bool {
+        if (!mbar_wait(&act_ready[h], (uint32_t)(n_ready[h] & 1), P.err)) return false;
+        ++n_ready[h];
+        tc_fence_after();
+        return true;
+      };
+      long long n_feat = 0;
+      for (long long rd = 0; rd < rounds && ok; ++rd) {
+        // layer 0: the features (chunk 0) into both halves
+        ok = mbar_wait(feat_ready, (uint32_t)(n_feat & 1), P.err);
+        ++n_feat;
+        tc_fence_after();
+        if (ok) ok = stage(0, tmem, id256, false);
+        if (ok) { mma_commit(&acc_full[0]); ok = stage(0, tmem + 256, id256, false); }
+        if (ok) { mma_commit(lo_free); mma_commit(&acc_full[1]); }
+        // hidden layers: the first half starts on chunks 0-3 while the second half's epilogue of
+        // the previous layer still runs
+        for (int l = 1; l < 4 && ok; ++l) {
+          ok = wait_ready(0);
+          for (int kc = 0; kc < 4 && ok; ++kc) ok = stage(kc, tmem, id256, kc > 0);
+          if (ok) ok = wait_ready(1);
+          for (int kc = 4; kc < 8 && ok; ++kc) ok = stage(kc, tmem, id256, true);
+          if (!ok) break;
+          mma_commit(&acc_full[0]);
+          for (int kc = 0; kc < 4 && ok; ++kc) ok = stage(kc, tmem + 256, id256, kc > 0);
+          if (!ok) break;
+          mma_commit(lo_free);
+          for (int kc = 4; kc < 8 && ok; ++kc) ok = stage(kc, tmem + 256, id256, true);
+          if (ok) mma_commit(&acc_full[1]);
         }
+        // output layer into columns 0-15
+        if (ok) ok = wait_ready(0);
+        if (ok) ok = wait_ready(1);
+        for (int kc = 0; kc < 8 && ok; ++kc) ok = stage(kc, tmem, id16, kc > 0);
+        if (ok) mma_commit(&acc_full[0]);
       }
     }
   } else {
-    // ---------------- epilogue warps 0-7; warps 0-3 also do features and output ----------------
+    // ---------------- epilogue warps ----------------
+    // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its cells) of accumulator half w / 4 (columns
+    // 256 (w / 4) .. + 255, four 64-column K chunks of the next layer's input): warps 0-3 drain the
+    // first half while the second half's MMAs still run, warps 4-7 the second half while the next
+    // layer's first-half MMAs start.  Warps 0-3 also build the input tile and apply the output
+    // transform.
     const int quarter = warp & 3, half = warp >> 2;
     const int r = quarter * 32 + lane;                 // cell row of the tile = TMEM lane
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
     unsigned char* arow = act + r * 128;               // row r inside each 16 KB chunk
     const bool io = half == 0;
-    long long nacc = 0;
+    long long n_full[2] = {0, 0}, n_lo = 0;
     bool ok = true;
     float bc0[MAXNS];
     for (long long rd = 0; rd < rounds && ok; ++rd) {
@@ -246,51 +309,44 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           v.w = pack_bf16(x[8 * u + 6], x[8 * u + 7]);
           *reinterpret_cast<uint4*>(arow + ((u ^ (r & 7)) << 4)) = v;
         }
+        fence_async_smem();
+        mbar_arrive(feat_ready);
       }
-      fence_async_smem();
-      mbar_arrive(act_ready);
-      // ---- hidden layers: this warp's half of the 512 columns ----
-      for (int l = 0; l < 4; ++l) {
-        // tcgen05.ld is warp-collective: the warp agrees on the wait's outcome
-        if (!__all_sync(0xffffffffu, mbar_wait(acc_done, (uint32_t)(nacc & 1), P.err))) { ok = false; break; }
-        ++nacc;
-        tc_fence_after();
+      // ---- hidden layers: this warp's half of the layer's columns ----
+      for (int l = 0; l < 4 && ok; ++l) {
         const float* bias = P.hb[l];
-        // 64 columns per step: two TMEM loads in flight behind one wait; every lane needs the same
-        // 64 biases, warp-uniform reads of the kernel's parameter bank (constant cache)
-        for (int cc = half * (HID / 64); cc < (half + 1) * (HID / 64); cc += 2) {
-          uint32_t a[2][32];
-          tmem_ld32(trow + cc * 32, a[0]);
-          tmem_ld32(trow + (cc + 1) * 32, a[1]);
-          tmem_ld_wait();
-          // columns cc*32 .. cc*32+63 form one 128-byte K chunk of the next layer's input
-          unsigned char* chunk = arow + (cc >> 1) * ACT_CHUNK;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              // the eight biases of these columns, warp-uniform reads of the parameter bank
-              const float* bq = bias + (cc + h) * 32 + 8 * q;
-              const float bv[8] = {bq[0], bq[1], bq[2], bq[3], bq[4], bq[5], bq[6], bq[7]};
-              float v[8];
-#pragma unroll
-              for (int e = 0; e < 8; ++e) v[e] = gelu_f(__uint_as_float(a[h][8 * q + e]) + bv[e]);
-              uint4 pk;
-              pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
-              pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
-              *reinterpret_cast<uint4*>(chunk + (((h * 4 + q) ^ (r & 7)) << 4)) = pk;
-            }
-          }
+        // tcgen05.ld is warp-collective: the warp agrees on the wait's outcome.  The first half's
+        // columns overwrite activation chunks 0-3, which the second half's MMAs must have read.
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[half], (uint32_t)(n_full[half] & 1), P.err))) { ok = false; break; }
+        ++n_full[half];
+        if (io) {
+          if (!__all_sync(0xffffffffu, mbar_wait(lo_free, (uint32_t)(n_lo & 1), P.err))) { ok = false; break; }
+          ++n_lo;
+        }
+        tc_fence_after();
+        // eight blocks of 32 columns; the TMEM load of the next block is in flight while the
+        // current one is computed
+        const int col0 = half * 256;
+        uint32_t a[2][32];
+        tmem_ld32(trow + col0, a[0]);
+#pragma unroll 1
+        for (int blk = 0; blk < 8; blk += 2) {
+          tmem_ld_wait(a[0]);
+          tmem_ld32(trow + col0 + (blk + 1) * 32, a[1]);
+          epilogue_block(a[0], bias, col0 + blk * 32, arow, r);
+          tmem_ld_wait(a[1]);
+          if (blk + 2 < 8) tmem_ld32(trow + col0 + (blk + 2) * 32, a[0]);
+          epilogue_block(a[1], bias, col0 + (blk + 1) * 32, arow, r);
         }
         tc_fence_before();
         fence_async_smem();
-        mbar_arrive(act_ready);
+        mbar_arrive(&act_ready[half]);
       }
       if (!ok) break;
-      // ---- output layer and inverse transform (every epilogue warp consumes the phase) ----
-      if (!__all_sync(0xffffffffu, mbar_wait(acc_done, (uint32_t)(nacc & 1), P.err))) { ok = false; break; }
-      ++nacc;
+      // ---- output layer (columns 0-15 of the first half) and inverse transform ----
       if (io) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[0], (uint32_t)(n_full[0] & 1), P.err))) { ok = false; break; }
+        ++n_full[0];
         tc_fence_after();
         uint32_t o[16];
         tmem_ld16(trow, o);

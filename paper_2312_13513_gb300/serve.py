@@ -102,9 +102,10 @@ def run_closed_loop(server, solvers, duration_s=10.0, mean_gap_s=2e-3, seed=0, m
     between chemistry steps; its first submission then comes at a uniform time in [0, think_s)),
     else mean_gap_s.
 
-    solvers: list of dicts(state_id, route, dt, cells[, label, think_s]).  Returns dict with
-    per-request latencies (s) and the label of each request's solver, cells advanced and the wall
-    time.
+    solvers: list of dicts(state_id, route, dt, cells[, label, think_s, flow]).  flow (optional) is
+    called before each submission of the solver: the solver's own step between two chemistry
+    sub-steps (it must leave the state ready on the device).  Returns dict with per-request
+    latencies (s) and the label of each request's solver, cells advanced and the wall time.
     """
     import heapq
     import random
@@ -123,6 +124,8 @@ def run_closed_loop(server, solvers, duration_s=10.0, mean_gap_s=2e-3, seed=0, m
         while due and due[0][0] <= now and now < end and submitted < max_requests:
             _, i = heapq.heappop(due)
             s = solvers[i]
+            if s.get("flow") is not None:
+                s["flow"]()
             rid = server.submit(s["state_id"], s["route"], s["dt"])
             inflight[rid] = i
             submitted += 1
