@@ -11,8 +11,13 @@ HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
                    "csrc", "gelu.cuh")
 
 
+def _body(signature):
+    text = open(HDR).read().split(signature)[1]
+    return text.split("__device__ __forceinline__")[0]
+
+
 def _coefficients():
-    body = open(HDR).read().split("float gelu_f(float v)")[1]
+    body = _body("float gelu_f(float v)")
     c = [float(x) for x in re.findall(r"([0-9]\.[0-9]+e[-+][0-9]+)f", body)]
     assert len(c) == 6
     # Horner from the highest power: fmaf(x, c6, c5), then c4 .. c1
@@ -35,3 +40,12 @@ def test_gelu_within_5e7_of_the_erf_form():
         g = max(v, 0.0) - 0.5 * x * q ** -16
         worst = max(worst, abs(g - 0.5 * v * (1.0 + math.erf(v / math.sqrt(2.0)))))
     assert worst <= 5e-7, worst
+
+
+def test_packed_gelu_uses_the_same_coefficients():
+    """gelu2 (two lanes of fma.rn.f32x2) carries each coefficient twice, the same as gelu_f's."""
+    c = [float(x) for x in re.findall(r"([0-9]\.[0-9]+e[-+][0-9]+)f", _body("void gelu2(float& v0, float& v1)"))]
+    assert len(c) == 12
+    assert all(c[2 * i] == c[2 * i + 1] for i in range(6))
+    single = [float(x) for x in re.findall(r"([0-9]\.[0-9]+e[-+][0-9]+)f", _body("float gelu_f(float v)"))]
+    assert c[0::2] == single
