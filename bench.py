@@ -36,11 +36,10 @@ METRIC = "chem cell-updates/s, FP64 Rosenbrock vs BF16 MLP at stated error; p50/
 WORKLOAD = ("FP64 Rodas4 chemistry advance, 2^20 cells of a 128^3 quasi-DNS H2/air field "
             "(9 species, 25 reactions), dt=5e-7 s, rtol=1e-6, atol=1e-10")
 
-# DRAM traffic of one integrator launch from an ncu capture (profiles/integrator_h2_quasi_dns.md:
-# 6.01 MB read, 0 B written for 65536 cells of the same field and launch shape -- the written
-# state stays in L2 at that size -- scaled by cells to 2^20), valid only for the kernel source it
-# was measured on.
-TRAFFIC = {"bytes_per_launch": 16 * (6013952 + 0), "source_sha1": "d641dd08253098b82348cc5a0efac85caa814942"}
+# DRAM traffic of one integrator launch from an ncu capture of the full bench launch
+# (profiles/integrator_h2_quasi_dns.md: 2^20 cells of the same field and launch shape, 93.47 MB
+# read + 40.27 MB written, one pass), valid only for the kernel source it was measured on.
+TRAFFIC = {"bytes_per_launch": 93470000 + 40270000, "source_sha1": "3c3f7d03493773597f58f53f26bdec752c062083"}
 
 # The paper's chemistry time per step for its H2-air case (Table 1, Section 3.2), in seconds:
 # CVODE on one CPU core and DNN inference on one GPU card, on uniform meshes of 32^3, 64^3 and
