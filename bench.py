@@ -351,7 +351,22 @@ def _time_ms(fn, stream, reps=1):
     return out
 
 
-def extra_ch4(fp64_peak, steps=2):
+def oracle_rate(mech, f, dt, sample, seed=0):
+    """The oracle (plain FP64 CPU) on a seeded uniform sample of a field's cells, all host cores:
+    its cell-updates/s, which extrapolates per cell to the whole field."""
+    import oracle
+    om = oracle.OracleMech(mech)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    s = np.sort(rng.choice(f["T"].size, min(sample, f["T"].size), replace=False))
+    t0 = time.perf_counter()
+    om.advance(f["T"][s], f["p"][s], f["Y"][:, s], dt, RTOL, ATOL, nthreads=cores)
+    el = time.perf_counter() - t0
+    return {"value": s.size / el, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{s.size} seeded-uniform cells of the field, {el:.1f} s, extrapolated per cell"}
+
+
+def extra_ch4(fp64_peak, steps=2, oracle_sample=4096):
     """Config 2: CH4/air-shaped mechanism (53 species, 325 reactions), 262144 LES cells."""
     import torch
     import paper_2312_13513_gb300 as cg
@@ -377,13 +392,17 @@ def extra_ch4(fp64_peak, steps=2):
     acc = int(ns_.sum()); att = acc + int(nr_.sum())
     flo, tr, folded = fl.launch_flops(mech, acc, att)
     t = min(ms) * 1e-3
-    return {"workload": "FP64 Rodas4, 262144 LES-shaped CH4/air cells (53 species, 325 reactions), "
-                        "dt=1e-6 s, 128-thread group per cell",
-            "ms": min(ms), "cell_updates_per_s": n / t,
+    out = {"workload": "FP64 Rodas4, 262144 LES-shaped CH4/air cells (53 species, 325 reactions), "
+                       "dt=1e-6 s, 128-thread group per cell",
+           "ms": min(ms), "cell_updates_per_s": n / t}
+    if oracle_sample:
+        out["cpu_oracle"] = oracle_rate(mech, f, 1e-6, oracle_sample, seed=2)
+    out.update({
             "fp64_frac_plain": flo / t / 1e12 / fp64_peak,
             "fp64_frac_folded": folded / t / 1e12 / fp64_peak,
             "fp64_tflops_plain": flo / t / 1e12, "fp64_tflops_folded": folded / t / 1e12,
-            "transcendental_weight": fl.TRANSCENDENTAL_FLOPS, "attempts_mean": att / n}
+            "transcendental_weight": fl.TRANSCENDENTAL_FLOPS, "attempts_mean": att / n})
+    return out
 
 
 def extra_surrogate(peaks, steps=3):
@@ -413,6 +432,7 @@ def extra_surrogate(peaks, steps=3):
         cg.advance(dm, Tr, p, Yr, DT, RTOL, ATOL, stream=stream)
 
     ms_fp64 = min(_time_ms(fp64, stream, 1))
+    cpu = oracle_rate(mech, f, DT, 16384, seed=3)
     Ts, Ys = T0.clone(), Y0.clone()
     route = torch.empty(n, dtype=torch.int8, device="cuda")
 
@@ -436,7 +456,7 @@ def extra_surrogate(peaks, steps=3):
     burst = peaks.get("bf16_tflops", 1900.0)
     return {"workload": "BF16 MLP 11-512x4-9 (tcgen05) with projection, Newton T and FP64 fallback, "
                         "2^22 quasi-DNS H2 cells, dt=5e-7 s",
-            "model_trained_in_this_run": trained_here,
+            "model_trained_in_this_run": trained_here, "cpu_oracle_fp64": cpu,
             "fp64_ms": ms_fp64, "fp64_cell_updates_per_s": n / (ms_fp64 * 1e-3),
             "forward_kernel_ms": ms_fwd, "tensor_tflops": tf,
             "tensor_frac_of_burst": tf / burst, "tensor_frac_of_sustained": tf / peak,
