@@ -5,7 +5,10 @@
 // networks.
 //
 // Used by the surrogate's training (forward and backward products of §2's MLP, trained with
-// Adam); inference uses the fused kernel in surrogate.cu built from the same primitives.
+// Adam) and by the per-species networks' inference; the single network's inference uses the
+// fused kernel in surrogate.cu built from the same primitives.  Launches go to the persistent
+// form below (gemm_bf16_persistent); the one-tile-per-CTA kernel that follows is its predecessor,
+// kept as the simplest statement of the tile computation.
 // One CTA computes a 128 x 128 tile: warp 0 (one lane) streams 128 x 64 tiles of A and B with TMA
 // (128-byte swizzle) through a 3-stage mbarrier ring, warp 1 (one lane) issues
 // tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16) into a TMEM accumulator, and the
@@ -18,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "chem_internal.h"
@@ -234,6 +238,183 @@ __global__ void __launch_bounds__(128, 2)
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
+// ---------------------------------------------------------------------------------------
+// Persistent form: one CTA per SM walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... (N-fastest
+// within a row block, so consecutive tiles share their A rows in L2) with a 128 x BN_ tile and
+// two TMEM accumulators: the epilogue of one tile runs while the MMAs of the next fill the other
+// accumulator.  Warp 0 (one lane): TMA producer over a STAGES_P-stage ring; warp 1 (one lane):
+// MMA issuer; warps 2-5: epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31), storing each
+// row's 32-column pieces straight to global memory.
+// ---------------------------------------------------------------------------------------
+constexpr int kPersistThreads = 192;
+
+template <int BN_>
+struct PersistCfg {
+  static constexpr int STAGES_P = BN_ == 256 ? 4 : 6;
+  static constexpr int TA = BM * BK * 2;                   // 16 KB
+  static constexpr int TB = BN_ * BK * 2;                  // 16 or 32 KB
+  static constexpr int SMEM = STAGES_P * (TA + TB) + 1024 + 256;
+};
+
+template <int BN_>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    gemm_bf16_persistent(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                         const GemmArgs a) {
+  using Cfg = PersistCfg<BN_>;
+  constexpr int NS = Cfg::STAGES_P;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + NS * Cfg::TA;
+  uint64_t* full = (uint64_t*)(sB + NS * Cfg::TB);
+  uint64_t* empty = full + NS;
+  uint64_t* acc_full = empty + NS;        // [2]: the MMAs of a tile into accumulator b are done
+  uint64_t* acc_empty = acc_full + 2;     // [2]: the epilogue has read accumulator b
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntm = (a.M + BM - 1) / BM, ntn = (a.N + BN_ - 1) / BN_;
+  const long long ntiles = (long long)ntm * ntn;
+  const int nk = (a.K + BK - 1) / BK;
+  const long long rounds = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
+    fence_barrier_init();
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * BN_);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer
+      long long it = 0;
+      bool ok = true;
+      for (long long rd = 0; rd < rounds && ok; ++rd) {
+        const long long t = blockIdx.x + rd * gridDim.x;
+        const int m0 = (int)(t / ntn) * BM, n0 = (int)(t % ntn) * BN_;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = (int)(it % NS);
+          if (!mbar_wait(&empty[s], (uint32_t)((it / NS) & 1) ^ 1u, a.err)) { ok = false; break; }
+          mbar_arrive_expect_tx(&full[s], Cfg::TA + Cfg::TB);
+          tma_load_2d(sA + s * Cfg::TA, &tmA, &full[s], kb * BK, m0);
+          tma_load_2d(sB + s * Cfg::TB, &tmB, &full[s], kb * BK, n0);
+        }
+      }
+      // drain: every issued stage has been consumed by the MMAs
+      const long long first = it > NS ? it - NS : 0;
+      for (long long k = first; k < it; ++k) mbar_wait(&empty[k % NS], (uint32_t)((k / NS) & 1), a.err);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = idesc_bf16_f32(BM, BN_);
+      long long it = 0;
+      bool ok = true;
+      for (long long rd = 0; rd < rounds && ok; ++rd) {
+        const int b = (int)(rd & 1);
+        // the epilogue has drained this accumulator (its use two tiles ago)
+        if (rd >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)(((rd - 2) >> 1) & 1), a.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * BN_);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = (int)(it % NS);
+          if (!mbar_wait(&full[s], (uint32_t)((it / NS) & 1), a.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t abase = smem_addr(sA + s * Cfg::TA), bbase = smem_addr(sB + s * Cfg::TB);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16(d, sdesc_k128(abase + kk * 32), sdesc_k128(bbase + kk * 32), idesc,
+                     (kb > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&acc_full[b]);
+      }
+    }
+  } else {
+    // epilogue warps 2-5
+    const int quarter = warp & 3;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+    bool ok = true;
+    for (long long rd = 0; rd < rounds && ok; ++rd) {
+      const long long t = blockIdx.x + rd * gridDim.x;
+      const int m0 = (int)(t / ntn) * BM, n0 = (int)(t % ntn) * BN_;
+      const int b = (int)(rd & 1);
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((rd >> 1) & 1), a.err))) { ok = false; break; }
+      tc_fence_after();
+      const int row = m0 + quarter * 32 + lane;
+      const bool rv = row < a.M;
+      const uint32_t tb = trow + (uint32_t)(b * BN_);
+      uint32_t r[2][32];
+      tmem_ld32(tb, r[0]);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN_; c0 += 64) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int cc = c0 + 32 * h;
+          tmem_ld_wait(r[h]);
+          if (cc + 32 < BN_) tmem_ld32(tb + cc + 32, r[h ^ 1]);
+          const int col = n0 + cc;
+          if (a.Cb) {
+            uint32_t pk[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int cj = col + 2 * j;
+              float v0 = __uint_as_float(r[h][2 * j]) + (a.bias && cj < a.N ? a.bias[cj] : 0.0f);
+              float v1 = __uint_as_float(r[h][2 * j + 1]) + (a.bias && cj + 1 < a.N ? a.bias[cj + 1] : 0.0f);
+              if (a.gelu) gelu2(v0, v1);
+              __nv_bfloat162 hv = __floats2bfloat162_rn(v0, v1);
+              pk[j] = *reinterpret_cast<uint32_t*>(&hv);
+            }
+            if (rv) {
+              __nv_bfloat16* out = a.Cb + (int64_t)row * a.ldc + col;
+              if (a.vec && col + 32 <= a.N) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  reinterpret_cast<uint4*>(out)[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  if (col + j < a.N) {
+                    const uint32_t w = pk[j >> 1];
+                    reinterpret_cast<uint16_t*>(out)[j] = (uint16_t)((j & 1) ? (w >> 16) : (w & 0xffffu));
+                  }
+                }
+              }
+            }
+          } else if (rv) {
+            float* out = a.C + (int64_t)row * a.ldc + col;
+            float v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              v[j] = __uint_as_float(r[h][j]) + (a.bias && col + j < a.N ? a.bias[col + j] : 0.0f);
+            if (a.vec && col + 32 <= a.N) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                reinterpret_cast<float4*>(out)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (col + j < a.N) out[j] = v[j];
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[b]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 2 * BN_);
+}
+
 }  // namespace
 
 static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, void* Cb, int gelu,
@@ -256,8 +437,37 @@ static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, f
   const int64_t opitch = ldc * (C ? 4 : 2);
   const int vec = (obase % 16 == 0 && opitch % 16 == 0) ? 1 : 0;
   GemmArgs g{C, (__nv_bfloat16*)Cb, gelu, vec, bias, M, N, K, ldc, err};
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-  gemm_bf16_kernel<<<grid, 128, GEMM_SMEM, stream>>>(ta, tb, g);
+  // persistent kernel, 256-column tiles unless 128-column tiles pad N less
+  const int pad128 = (N + 127) / 128 * 128 - N, pad256 = (N + 255) / 256 * 256 - N;
+  const int bn = (N >= 256 && pad256 <= pad128) ? 256 : 128;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    CHEM_CUDA_TRY(cudaGetDevice(&dev));
+    CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const long long ntiles = (long long)((M + BM - 1) / BM) * ((N + bn - 1) / bn);
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, sms);
+  if (bn == 256) {
+    CUtensorMap tb2;
+    rc = make_tmap_bf16(&tb2, B, N, K, ldb, 256, BK);
+    if (rc) return rc;
+    static bool attr256 = false;
+    if (!attr256) {
+      CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_persistent<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         PersistCfg<256>::SMEM));
+      attr256 = true;
+    }
+    gemm_bf16_persistent<256><<<grid, kPersistThreads, PersistCfg<256>::SMEM, stream>>>(ta, tb2, g);
+  } else {
+    static bool attr128 = false;
+    if (!attr128) {
+      CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_persistent<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         PersistCfg<128>::SMEM));
+      attr128 = true;
+    }
+    gemm_bf16_persistent<128><<<grid, kPersistThreads, PersistCfg<128>::SMEM, stream>>>(ta, tb, g);
+  }
   CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
 }

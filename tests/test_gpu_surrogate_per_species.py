@@ -17,7 +17,8 @@ from helpers import random_states  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("M,N,K,gelu", [(300, 200, 192, True), (128, 1600, 64, True), (1000, 400, 800, False)])
+@pytest.mark.parametrize("M,N,K,gelu", [(300, 200, 192, True), (128, 1600, 64, True), (1000, 400, 800, False),
+                                        (16384, 800, 1600, True), (777, 12800, 64, True), (4096, 300, 400, True)])
 def test_gemm_activation_epilogue_matches_torch(M, N, K, gelu):
     g = torch.Generator(device="cuda").manual_seed(M + N + K)
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
