@@ -243,10 +243,10 @@ __global__ void __launch_bounds__(128, 2)
 // within a row block, so consecutive tiles share their A rows in L2) with a 128 x BN_ tile and
 // two TMEM accumulators: the epilogue of one tile runs while the MMAs of the next fill the other
 // accumulator.  Warp 0 (one lane): TMA producer over a STAGES_P-stage ring; warp 1 (one lane):
-// MMA issuer; warps 2-5: epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31), storing each
-// row's 32-column pieces straight to global memory.
+// MMA issuer; warps 2-9: epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31 and the columns of
+// half (w - 2) / 4 of the tile), storing each row's 32-column pieces straight to global memory.
 // ---------------------------------------------------------------------------------------
-constexpr int kPersistThreads = 192;
+constexpr int kPersistThreads = 320;     // TMA warp, MMA warp, eight epilogue warps
 
 template <int BN_>
 struct PersistCfg {
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], kPersistThreads - 64); }
     fence_barrier_init();
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
@@ -338,9 +338,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       }
     }
   } else {
-    // epilogue warps 2-5
-    const int quarter = warp & 3;
+    // epilogue warps 2-9
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+    constexpr int HW = BN_ / 2;                              // columns per epilogue warp
     bool ok = true;
     for (long long rd = 0; rd < rounds && ok; ++rd) {
       const long long t = blockIdx.x + rd * gridDim.x;
@@ -350,17 +351,17 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       tc_fence_after();
       const int row = m0 + quarter * 32 + lane;
       const bool rv = row < a.M;
-      const uint32_t tb = trow + (uint32_t)(b * BN_);
+      const uint32_t tb = trow + (uint32_t)(b * BN_ + half * HW);
       uint32_t r[2][32];
       tmem_ld32(tb, r[0]);
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN_; c0 += 64) {
+      for (int c0 = 0; c0 < HW; c0 += 64) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int cc = c0 + 32 * h;
           tmem_ld_wait(r[h]);
-          if (cc + 32 < BN_) tmem_ld32(tb + cc + 32, r[h ^ 1]);
-          const int col = n0 + cc;
+          if (cc + 32 < HW) tmem_ld32(tb + cc + 32, r[h ^ 1]);
+          const int col = n0 + half * HW + cc;
           if (a.Cb) {
             uint32_t pk[16];
 #pragma unroll
