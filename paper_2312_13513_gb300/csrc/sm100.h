@@ -10,9 +10,9 @@
 namespace chem {
 namespace sm100 {
 
-// bounded spin: an mbarrier wait gives up after this many polls and raises the kernel's error
-// flag instead of hanging the GPU
-constexpr long long kSpinLimit = 1ll << 22;
+// bounded wait: an mbarrier wait gives up after this long and raises the kernel's error flag
+// instead of hanging the GPU
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;     // 2 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -47,14 +47,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity; on timeout set *err (global) and return false.
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with the given parity; after kWaitLimitNs set *err (global) and return
+// false.  The error flag (a global load) and the clock are read once every 256 polls only, so
+// that a completed phase is seen within one poll rather than after a memory round trip.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_timer_ns();
+  for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*(volatile int*)err) return false;      // another thread already gave up
+    if ((i & 255u) == 0u) {
+      if (*(volatile int*)err) return false;    // another thread already gave up
+      if (global_timer_ns() - t0 > kWaitLimitNs) {
+        atomicExch(err, 1);
+        return false;
+      }
+    }
   }
-  atomicExch(err, 1);
-  return false;
 }
 
 // 2D tiled TMA load of box (x = inner, y = outer) into shared memory, completing on bar.
