@@ -225,6 +225,28 @@ def test_surrogate_batch_equals_individual_passes(h2):
         assert torch.equal(s_["route"], rb) and int(rb.sum()) >= 1
 
 
+def test_surrogate_batch_of_more_segments_than_one_pass_takes(h2):
+    """40 states (more than the 32 segments of one pass): consecutive passes, same results as one
+    call per state, an empty segment included."""
+    dm = cg.Mechanism(h2)
+    base = _h2_state(40 * 301, 800)
+    model = _identity_model(dm, h2, *base)
+    segs, ref = [], []
+    for i in range(40):
+        n = 0 if i == 7 else 301
+        T, p, Y = (a[..., i * 301:i * 301 + n] for a in base)
+        a = to_dev(T, p, Y)
+        b = to_dev(T, p, Y)
+        if n:
+            cg.surrogate_advance(model, b[0], b[1], b[2], 5e-7)
+        segs.append({"T": a[0], "p": a[1], "Y": a[2], "dt": 5e-7})
+        ref.append(b)
+    serve.surrogate_advance_batch(model, segs)
+    torch.cuda.synchronize()
+    for s_, b in zip(segs, ref):
+        assert torch.equal(s_["T"], b[0]) and torch.equal(s_["Y"], b[2])
+
+
 def test_fp64_requests_join_a_running_sliced_job(ch4):
     """FP64 requests of a mechanism whose time-sliced job is running join that job at its next
     slice boundary (no new launch) and give bitwise the result of their own launch."""
