@@ -262,6 +262,20 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     long long n_full[2] = {0, 0}, n_lo = 0;
     bool ok = true;
     float bc0[MAXNS];
+    // the state of the warp's next cell, loaded one tile ahead (the loads' latency hides behind
+    // the current tile's layers)
+    double nT = 0.0, np = 1.0, nY[MAXNS] = {};
+    auto load_state = [&](long long rd) {
+      const long long c = (blockIdx.x + rd * gridDim.x) * TM + r;
+      if (io && rd < rounds && c < P.ncells) {
+        nT = P.T[c];
+        np = P.p[c];
+#pragma unroll
+        for (int k = 0; k < MAXNS; ++k)
+          if (k < P.ns) nY[k] = P.Y[(int64_t)k * P.ld + c];
+      }
+    };
+    load_state(0);
     for (long long rd = 0; rd < rounds && ok; ++rd) {
       const long long tile = blockIdx.x + rd * gridDim.x;
       const long long cell = tile * TM + r;
@@ -271,15 +285,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         float x[KIN];
 #pragma unroll
         for (int i = 0; i < KIN; ++i) x[i] = 0.0f;
+        double yv[MAXNS];
+        const double tv = nT, pv = np;
+#pragma unroll
+        for (int k = 0; k < MAXNS; ++k) yv[k] = nY[k];
+        load_state(rd + 1);
         if (valid) {
           bool outside = false;
           float f[2 + MAXNS];
-          // all loads of the cell's state first, so their latencies overlap
-          double yv[MAXNS];
-          const double tv = P.T[cell], pv = P.p[cell];
-#pragma unroll
-          for (int k = 0; k < MAXNS; ++k)
-            if (k < P.ns) yv[k] = P.Y[(int64_t)k * P.ld + cell];
           f[0] = (float)tv;
           f[1] = logf((float)pv);
 #pragma unroll
