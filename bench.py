@@ -625,47 +625,49 @@ def extra_transport(fp64_peak, reps=3):
     return out
 
 
-def extra_graph(n=4096, reps=20):
-    """A small chemistry step (n quasi-DNS H2 cells) issued directly and as a captured CUDA-graph
-    replay: per-step time of each (the launch and allocation overhead the graph removes)."""
+def extra_graph(sizes=(4096, 65536), reps=50):
+    """The chemistry + thermo step (surrogate route) on small fields, issued back to back: directly
+    (about a dozen API calls and launches per step) and as replays of the captured CUDA graph.  At
+    these sizes the host's issue rate, not the GPU, sets the direct rate: per-step time of each."""
     import torch
     import paper_2312_13513_gb300 as cg
     from synth.mechanism import h2_mechanism
-    dm = cg.Mechanism(h2_mechanism())
-    f = make_field(0, n)
-    T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
-    Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
-    T, Y = T0.clone(), Y0.clone()
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        cg.advance(dm, T, p, Y, DT, RTOL, ATOL, stream=s)
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=s):
-        cg.advance(dm, T, p, Y, DT, RTOL, ATOL, stream=s)
-    torch.cuda.synchronize()
-
-    def timed(fn):
-        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
-        out = []
-        for _ in range(reps):
-            T.copy_(T0); Y.copy_(Y0)
+    from synth.transport import generate_transport
+    mech = h2_mechanism()
+    dm = cg.Mechanism(mech)
+    if not os.path.exists(MODEL_PATH):
+        return {"skipped": "no trained model"}
+    model = cg.Surrogate(dm, path=MODEL_PATH)
+    tr = cg.Transport(dm, generate_transport(mech))
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"chemistry + thermo step (surrogate route) from the field's state, {reps} steps back to "
+                       f"back, per step"}
+    for n in sizes:
+        f = make_field(0, n)
+        T0 = torch.tensor(f["T"], device="cuda"); p = torch.tensor(f["p"], device="cuda")
+        Y0 = torch.tensor(np.ascontiguousarray(f["Y"]), device="cuda")
+        T, Y = T0.clone(), Y0.clone()
+        f64 = lambda *sh: torch.empty(*sh, dtype=torch.float64, device="cuda")
+        st = cg.Step(dm, T, p, Y, DT, RTOL, ATOL, model=model, transport=tr, h0=f64(n), cp0=f64(n), q=f64(n),
+                     thermo_status=torch.empty(n, dtype=torch.int8, device="cuda"), mu=f64(n), lam=f64(n),
+                     D=f64(mech.ns, n))
+        st.run(graph=False, stream=stream)
+        st.run(graph=True, stream=stream)            # capture
+        torch.cuda.synchronize()
+        res = {}
+        for name, use_graph in (("direct_ms", False), ("graph_ms", True)):
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
-            a.record(s); fn(); b.record(s)
+            a.record(stream)
+            for _ in range(reps):
+                T.copy_(T0); Y.copy_(Y0)        # every step from the field's state (two copies in both)
+                st.run(graph=use_graph, stream=stream)
+            b.record(stream)
             torch.cuda.synchronize()
-            out.append(a.elapsed_time(b))
-        return float(np.median(out))
-
-    def replay():
-        with torch.cuda.stream(s):        # a graph replays on the current stream
-            g.replay()
-
-    ms_direct = timed(lambda: cg.advance(dm, T, p, Y, DT, RTOL, ATOL, stream=s))
-    ms_graph = timed(replay)
-    return {"workload": f"FP64 integrator step on {n} quasi-DNS H2 cells: direct call vs captured "
-                        f"CUDA-graph replay, median of {reps}",
-            "direct_ms": ms_direct, "graph_ms": ms_graph}
+            res[name] = a.elapsed_time(b) / reps
+        st.close()
+        out[f"{n}_cells"] = res
+    return out
 
 
 def extra_step(n=1 << 20, reps=3):
