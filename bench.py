@@ -534,6 +534,61 @@ def extra_surrogate_per_species(peaks, n_states=1 << 20, epochs=12):
     return out
 
 
+def extra_train_step(peaks, batch=4096, n_states=1 << 20, steps=256):
+    """Training steps of the single 11-512x4-9 network (batch gather, forward, backward, Adam) on
+    2^20 states, issued directly and replayed from one captured CUDA graph; both runs start from
+    the same weights and visit the same batches, and end with bitwise the same weights."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from paper_2312_13513_gb300 import parallel
+    from paper_2312_13513_gb300 import train as trn
+    from synth.mechanism import h2_mechanism
+    mech = h2_mechanism()
+    dm = cg.Mechanism(mech)
+    data = trn.make_dataset(mech, dm, n_states, DT, 7)
+    X, Tt = data["X"], data["T"]
+    perm = trn.epoch_order(n_states, 7, 0)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    lrs = [trn.cosine_lr(k, steps, 3e-4, 1e-5) for k in range(steps)]
+    out = {"workload": f"11-512x4-9 GELU network, batch {batch}, {steps} Adam steps over {n_states} "
+                       f"H2 states (one epoch's first batches)"}
+    weights = {}
+    for mode in ("direct", "graph"):
+        tr = trn.Trainer(mech.ns + 2, mech.ns, batch, seed=7)
+        replay = trn._captured_step(tr, X, Tt, batch, loss) if mode == "graph" else None
+
+        def run():
+            for k in range(steps):
+                idx = perm[k * batch:(k + 1) * batch]
+                if replay is not None:
+                    replay(idx, lrs[k])
+                else:
+                    tr.forward(X.index_select(0, idx))
+                    tr.backward(Tt.index_select(0, idx), loss)
+                    tr.adam(lrs[k])
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ms = _time_ms(run, stream, 1)[0]
+        wall = time.perf_counter() - t0
+        weights[mode] = parallel.flatten_grads(*tr.get(0))
+        tr.close()
+        out[mode + "_ms_per_step"] = ms / steps
+        out[mode + "_host_ms_per_step"] = wall * 1e3 / steps
+    p = 11 * 512 + 3 * 512 * 512 + 512 * 9
+    # forward 2 flop per weight and sample, backward 4 (input and weight gradients)
+    flop = 6.0 * p * batch
+    tf = flop / (out["graph_ms_per_step"] * 1e-3) / 1e12
+    out.update({"samples_per_s_graph": batch / (out["graph_ms_per_step"] * 1e-3),
+                "samples_per_s_direct": batch / (out["direct_ms_per_step"] * 1e-3),
+                "graph_speedup": out["direct_ms_per_step"] / out["graph_ms_per_step"],
+                "tensor_tflops_graph": tf,
+                "tensor_frac_of_sustained": tf / peaks.get("bf16_tflops_sustained", 1700.0),
+                "graph_weights_equal_direct": bool(np.array_equal(weights["direct"], weights["graph"]))})
+    return out
+
+
 def _fvm_inputs(n_side, seed=21):
     """A 128^3-style box in face-addressed form (natural numbering, mildly stretched) and seeded
     species-equation inputs of realistic magnitude (cgs), all terms on."""
@@ -1053,6 +1108,7 @@ def main():
         # configs 2 and 3 are printed last: the end of the line is what a truncated log keeps
         extras = {}
         for name, fn in (("surrogate_per_species", lambda: extra_surrogate_per_species(_peaks())),
+                         ("train_step", lambda: extra_train_step(_peaks())),
                          ("fvm_species_assembly", lambda: extra_fvm(_peaks().get("hbm_gbs", 6800.0))),
                          ("graph_small_step", extra_graph),
                          ("chemistry_thermo_step", extra_step),

@@ -356,10 +356,18 @@ int chem_mlp_forward(chem_trainer_t t, const void* X, float* out, chem_stream_t 
 /* mean-squared-error gradients of the last forward pass; loss (device double, nullable).
  * CHEM_EINVAL for a NULL trainer or target. */
 int chem_mlp_backward(chem_trainer_t t, const float* target, double* loss, chem_stream_t stream);
-/* one Adam update (bias-corrected) of all parameters with the last gradients.
+/* one Adam update (bias-corrected) of all parameters with the last gradients.  The step counter
+ * and the bias corrections 1 - beta^step live in device memory and are advanced by the first
+ * kernel of the update, so the whole update can be captured in a CUDA graph and replayed.
  * CHEM_EINVAL for a NULL trainer or lr <= 0. */
 int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float beta2, float eps,
                        chem_stream_t stream);
+/* the same update with the learning rate read from device memory (*lr, FP32) when the update
+ * runs: a training step captured once in a CUDA graph takes each step's scheduled rate from a
+ * buffer the host rewrites between replays.  The result is bitwise that of chem_mlp_adam_step
+ * with the same rate.  CHEM_EINVAL for a NULL trainer or lr. */
+int chem_mlp_adam_step_dev(chem_trainer_t t, const float* lr, float beta1, float beta2, float eps,
+                           chem_stream_t stream);
 /* host copy of the parameters (which = 0) or of the last gradients (which = 1); W[l], b[l] are
  * host arrays of the unpadded shapes (any may be NULL); synchronises the device.
  * CHEM_EINVAL for a NULL trainer, W or b; CHEM_ECUDA if a copy fails. */

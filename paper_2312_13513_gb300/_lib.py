@@ -120,6 +120,7 @@ SIGNATURES = {
     "chem_mlp_backward": (ctypes.c_int, [P, P, P, P]),
     "chem_mlp_adam_step": (ctypes.c_int, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                           ctypes.c_float, P]),
+    "chem_mlp_adam_step_dev": (ctypes.c_int, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, P]),
     "chem_mlp_trainer_get": (ctypes.c_int, [P, ctypes.c_int, P, P]),
     "chem_mlp_grad_count": (ctypes.c_int, [P, P]),
     "chem_mlp_grad_pack": (ctypes.c_int, [P, P, P]),

@@ -130,7 +130,8 @@ __global__ void k_colsum_finish(const double* part, float* s, int nparts, int C)
 // Adam on a [rows x cols] parameter block (cols = 1 for biases); writes the BF16 copy of W if given
 // (its transpose follows by the tiled k_transpose)
 __global__ void k_adam(float* W, const float* G, float* m, float* v, __nv_bfloat16* Wb, __nv_bfloat16* Wt,
-                       int rows, int cols, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       int rows, int cols, const float* coef, float b1, float b2, float eps) {
+  const float lr = coef[0], c1 = coef[1], c2 = coef[2];
   const int64_t n = (int64_t)rows * cols;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float g = G[i];
@@ -142,6 +143,16 @@ __global__ void k_adam(float* W, const float* G, float* m, float* v, __nv_bfloat
     W[i] = w;
     if (Wb) Wb[i] = __float2bfloat16_rn(w);
   }
+}
+
+// One Adam step's scalars on the device: step += 1, coef = {lr, 1 - b1^step, 1 - b2^step}, with lr
+// from lr_dev when given (a captured training step reads its learning rate from device memory)
+__global__ void k_adam_prep(int64_t* step, float* coef, const float* lr_dev, float lr, float b1, float b2) {
+  const int64_t s = *step + 1;
+  *step = s;
+  coef[0] = lr_dev ? *lr_dev : lr;
+  coef[1] = (float)(1.0 - pow((double)b1, (double)s));
+  coef[2] = (float)(1.0 - pow((double)b2, (double)s));
 }
 
 // compensated BF16 copy of the first layer: Wb row = [W_hi | W_hi | W_lo | 0] from master W[:, :nin]
@@ -298,7 +309,8 @@ struct chem_trainer_s {
   __nv_bfloat16 *dZb, *dZt, *At;
   int* err;
   double* loss;
-  int step;
+  int64_t* d_step;                 // Adam steps taken (device: a captured step advances it)
+  float* d_coef;                   // the current step's lr, 1 - b1^step, 1 - b2^step
   std::vector<void*> allocs;
 };
 
@@ -336,7 +348,7 @@ extern "C" int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden,
     if (hidden[h] < 1 || hidden[h] > 8192) { set_error("trainer: hidden width %d out of range", hidden[h]); return CHEM_EINVAL; }
   *out = nullptr;
   chem_trainer_s* t = new chem_trainer_s();
-  t->nin = n_in; t->nout = n_out; t->B = batch; t->step = 0; t->nl = n_hidden + 1;
+  t->nin = n_in; t->nout = n_out; t->B = batch; t->nl = n_hidden + 1;
   const int NL = t->nl;
   auto pad = [](int w) { return std::max(128, (w + 7) / 8 * 8); };
   int ins[MAXL], outs[MAXL];
@@ -398,6 +410,8 @@ extern "C" int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden,
   if (!rc) rc = tr_alloc(t, &p, (size_t)((batch + kColRows - 1) / kColRows) * maxw * 8), t->colpart = (double*)p;
   if (!rc) rc = tr_alloc(t, &p, 16), t->err = (int*)p;
   if (!rc) rc = tr_alloc(t, &p, 16), t->loss = (double*)p;
+  if (!rc) rc = tr_alloc(t, &p, 16), t->d_step = (int64_t*)p;
+  if (!rc) rc = tr_alloc(t, &p, 16), t->d_coef = (float*)p;
   if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "trainer init");
   if (rc) { chem_mlp_trainer_free(t); return rc; }
   *out = t;
@@ -460,24 +474,33 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
   return CHEM_OK;
 }
 
-extern "C" int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float beta2, float eps,
-                                  chem_stream_t stream) {
-  if (!t || !(lr > 0.0f)) { set_error("bad Adam arguments"); return CHEM_EINVAL; }
-  cudaStream_t st = (cudaStream_t)stream;
-  t->step += 1;
-  const float c1 = 1.0f - powf(beta1, (float)t->step), c2 = 1.0f - powf(beta2, (float)t->step);
+static int adam_step(chem_trainer_t t, const float* lr_dev, float lr, float beta1, float beta2, float eps,
+                     cudaStream_t st) {
+  k_adam_prep<<<1, 1, 0, st>>>(t->d_step, t->d_coef, lr_dev, lr, beta1, beta2);
   for (int l = 0; l < t->nl; ++l) {
     const int r = t->out_pad[l], c = t->in_pad[l];
     k_adam<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[l], t->dW[l], t->mW[l], t->vW[l],
-                                                      l == 0 ? nullptr : t->Wb[l], nullptr, r, c, lr, beta1,
-                                                      beta2, eps, c1, c2);
+                                                      l == 0 ? nullptr : t->Wb[l], nullptr, r, c, t->d_coef, beta1,
+                                                      beta2, eps);
     if (l > 0) k_transpose<<<dim3((c + 31) / 32, (r + 31) / 32), dim3(32, 8), 0, st>>>(t->Wb[l], t->Wt[l], r, c);
     if (l == 0) k_split_bf16<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[0], t->Wb[0], r, c, t->nin);
-    k_adam<<<grid_for(r), 256, 0, st>>>(t->b[l], t->db[l], t->mb[l], t->vb[l], nullptr, nullptr, r, 1, lr, beta1,
-                                        beta2, eps, c1, c2);
+    k_adam<<<grid_for(r), 256, 0, st>>>(t->b[l], t->db[l], t->mb[l], t->vb[l], nullptr, nullptr, r, 1, t->d_coef,
+                                        beta1, beta2, eps);
   }
   CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
+}
+
+extern "C" int chem_mlp_adam_step(chem_trainer_t t, float lr, float beta1, float beta2, float eps,
+                                  chem_stream_t stream) {
+  if (!t || !(lr > 0.0f)) { set_error("bad Adam arguments"); return CHEM_EINVAL; }
+  return adam_step(t, nullptr, lr, beta1, beta2, eps, (cudaStream_t)stream);
+}
+
+extern "C" int chem_mlp_adam_step_dev(chem_trainer_t t, const float* lr, float beta1, float beta2, float eps,
+                                      chem_stream_t stream) {
+  if (!t || !lr) { set_error("NULL argument"); return CHEM_EINVAL; }
+  return adam_step(t, lr, 0.0f, beta1, beta2, eps, (cudaStream_t)stream);
 }
 
 // copy parameters (which = 0) or gradients (which = 1) of the real (unpadded) layers to host
@@ -573,7 +596,11 @@ extern "C" int chem_mlp_trainer_save(chem_trainer_t t, const char* path) {
   const int32_t hdr[3] = {t->nl, t->nin, t->nout};
   ok = ok && fwrite(hdr, 4, 3, f) == 3;
   ok = ok && fwrite(t->real_in, 4, t->nl, f) == (size_t)t->nl && fwrite(t->real_out, 4, t->nl, f) == (size_t)t->nl;
-  const int64_t step = t->step;
+  int64_t step = 0;
+  if (cudaMemcpy(&step, t->d_step, 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    fclose(f);
+    return cuda_fail(cudaGetLastError(), "cudaMemcpy(trainer step)");
+  }
   ok = ok && fwrite(&step, 8, 1, f) == 1;
   std::vector<float> h;
   for (int l = 0; l < t->nl && ok; ++l) {
@@ -628,14 +655,14 @@ extern "C" int chem_mlp_trainer_load(chem_trainer_t t, const char* path) {
     if (l == 0) k_split_bf16<<<grid_for(nw), 256>>>(t->W[0], t->Wb[0], t->out_pad[0], t->in_pad[0], t->nin);
     else k_to_bf16<<<grid_for(nw), 256>>>(t->W[l], t->Wb[l], t->Wt[l], t->out_pad[l], t->in_pad[l]);
   }
-  t->step = (int)step;
+  CHEM_CUDA_TRY(cudaMemcpy(t->d_step, &step, 8, cudaMemcpyHostToDevice));
   CHEM_CUDA_TRY(cudaDeviceSynchronize());
   return CHEM_OK;
 }
 
 extern "C" int chem_mlp_trainer_step(chem_trainer_t t, int64_t* step) {
   if (!t || !step) { set_error("NULL argument"); return CHEM_EINVAL; }
-  *step = t->step;
+  CHEM_CUDA_TRY(cudaMemcpy(step, t->d_step, 8, cudaMemcpyDeviceToHost));
   return CHEM_OK;
 }
 

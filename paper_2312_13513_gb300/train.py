@@ -63,6 +63,13 @@ class Trainer:
                                              ctypes.c_float(beta2), ctypes.c_float(eps),
                                              _stream_ptr(stream)))
 
+    def adam_dev(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        """Adam with the learning rate read from the one-element FP32 device tensor lr when the
+        update runs (chem_mlp_adam_step_dev: capturable in a CUDA graph)."""
+        check(_lib.load().chem_mlp_adam_step_dev(self.handle, _ptr(lr), ctypes.c_float(beta1),
+                                                 ctypes.c_float(beta2), ctypes.c_float(eps),
+                                                 _stream_ptr(stream)))
+
     @property
     def step(self):
         """Adam steps taken (restored by load)."""
@@ -198,13 +205,16 @@ def cosine_lr(step, total, lr, lr_final):
 
 def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5, dt=5e-7, seed=7,
           log=print, time_budget_s=None, front_fraction=0.5, data=None, checkpoint=None, resume=None,
-          group=None, max_steps=None):
+          group=None, max_steps=None, graph=False):
     """Train the single 4 x 512 network.  checkpoint: a file rewritten at the end of every epoch
     (and at max_steps) with the trainer state; resume: such a file to continue from (its Adam step
     counter gives the epoch and batch to continue at).  group: a torch.distributed process group
     for data-parallel training -- every rank builds the same data set, takes its equal share of
     each global batch and averages the gradients with one all-reduce before Adam; the statistics
-    are rank 0's.  max_steps: stop after that many steps in total (for tests)."""
+    are rank 0's.  max_steps: stop after that many steps in total (for tests).  graph: on one rank,
+    capture the step (batch gather, forward, backward, Adam with the rate from a device buffer)
+    once in a CUDA graph and replay it per batch; the results are bitwise those of the direct
+    calls, without the per-kernel launch cost."""
     import torch
     rank, world = 0, 1
     if group is not None or (torch.distributed.is_available() and torch.distributed.is_initialized()):
@@ -244,19 +254,25 @@ def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5,
     step = tr.step
     t1 = time.time()
     from .parallel import batch_share
+    replay = None
+    if graph and world == 1 and step < total_run:
+        replay = _captured_step(tr, X, Tt, batch, loss)
     while step < total_run:
         ep, i0 = divmod(step, steps_per_epoch)
         perm = epoch_order(n, seed, ep)
         acc = 0.0
         for i in range(i0, steps_per_epoch):
             idx = batch_share(perm[i * batch:(i + 1) * batch], rank, world)
-            xb = X.index_select(0, idx)
-            yb = Tt.index_select(0, idx)
-            tr.forward(xb)
-            tr.backward(yb, loss)
-            if world > 1:
-                tr.allreduce_grads(group)
-            tr.adam(cosine_lr(step, total, lr, lr_final))
+            if replay is not None:
+                replay(idx, cosine_lr(step, total, lr, lr_final))
+            else:
+                xb = X.index_select(0, idx)
+                yb = Tt.index_select(0, idx)
+                tr.forward(xb)
+                tr.backward(yb, loss)
+                if world > 1:
+                    tr.allreduce_grads(group)
+                tr.adam(cosine_lr(step, total, lr, lr_final))
             step += 1
             if i % 64 == 0:
                 acc = float(loss.item())
@@ -273,6 +289,41 @@ def train(mech, n_states=1 << 22, epochs=40, batch=4096, lr=3e-4, lr_final=1e-5,
     params = dict(data["stats"])
     params.update({"W": W, "b": b, "dt": dt, "history": history, "steps": step})
     return params
+
+
+def _captured_step(tr, X, Tt, batch, loss):
+    """One training step captured in a CUDA graph: gather the batch rows named by a static index
+    buffer, forward, backward, Adam with the rate from a static device buffer.  Returns
+    replay(idx, lr), which writes idx and lr into the buffers and replays the graph on the current
+    stream.  The capture runs nothing: the trainer's state is untouched until the first replay."""
+    import torch
+    idx_buf = torch.zeros(batch, dtype=torch.int64, device="cuda")
+    lr_buf = torch.zeros(1, dtype=torch.float32, device="cuda")
+    xb = torch.empty((batch, X.shape[1]), dtype=X.dtype, device="cuda")
+    yb = torch.empty((batch, Tt.shape[1]), dtype=Tt.dtype, device="cuda")
+    # one direct forward + backward first (it writes activations and gradients only, which the
+    # first replay overwrites): the kernels' one-time host set-up then happens outside the capture
+    torch.index_select(X, 0, idx_buf, out=xb)
+    torch.index_select(Tt, 0, idx_buf, out=yb)
+    tr.forward(xb)
+    tr.backward(yb, loss)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        s = torch.cuda.current_stream()
+        torch.index_select(X, 0, idx_buf, out=xb)
+        torch.index_select(Tt, 0, idx_buf, out=yb)
+        tr.forward(xb, stream=s)
+        tr.backward(yb, loss, stream=s)
+        tr.adam_dev(lr_buf, stream=s)
+
+    def replay(idx, lr):
+        idx_buf.copy_(idx, non_blocking=True)
+        lr_buf.fill_(float(lr))
+        g.replay()
+
+    replay.graph = g
+    return replay
 
 
 PER_SPECIES_HIDDEN = (1600, 800, 400)

@@ -143,3 +143,25 @@ def test_train_resume_continues_the_epoch_schedule(tmp_path, h2):
     assert rest["steps"] == 12 == ref["steps"]
     for x, y in zip(rest["W"] + rest["b"], ref["W"] + ref["b"]):
         assert np.array_equal(x, y)
+
+
+def test_captured_training_step_is_bitwise_the_direct_step(tmp_path, h2):
+    """train(graph=True) replays one captured step (gather, forward, backward, Adam with the rate
+    and the step counter in device memory): the same weights as the direct calls, bitwise, also
+    when it resumes a run that the direct path checkpointed."""
+    from paper_2312_13513_gb300 import Mechanism
+    from paper_2312_13513_gb300 import train as trn
+    dm = Mechanism(h2)
+    data = trn.make_dataset(h2, dm, 4096, 5e-7, seed=4)
+    quiet = lambda *a: None
+    ref = trn.train(h2, epochs=3, batch=512, data=data, seed=4, log=quiet, max_steps=20)
+    cap = trn.train(h2, epochs=3, batch=512, data=data, seed=4, log=quiet, max_steps=20, graph=True)
+    assert cap["steps"] == ref["steps"] == 20
+    for x, y in zip(cap["W"] + cap["b"], ref["W"] + ref["b"]):
+        assert np.array_equal(x, y)
+    ck = str(tmp_path / "ck.chemtrn")
+    trn.train(h2, epochs=3, batch=512, data=data, seed=4, log=quiet, max_steps=7, checkpoint=ck)
+    rest = trn.train(h2, epochs=3, batch=512, data=data, seed=4, log=quiet, max_steps=20, resume=ck, graph=True)
+    assert rest["steps"] == 20
+    for x, y in zip(rest["W"] + rest["b"], ref["W"] + ref["b"]):
+        assert np.array_equal(x, y)
