@@ -63,10 +63,12 @@ constexpr int ACT_BYTES = 8 * ACT_CHUNK;             // 128 KB
 constexpr int FWD_SMEM = ACT_BYTES + WSTAGES * WSTAGE_BYTES + 1024 + 256;
 constexpr float BC_LAMBDA = SUR_BC_LAMBDA;
 
+// rows of SurParams::st: feature statistics and box, target statistics, output bias
+enum { ST_XMU, ST_XSD, ST_LO, ST_HI, ST_YMU, ST_YSD, ST_B5, ST_ROWS };
+
 struct SurParams {
-  const float* bias[5];
   float hb[4][HID];     // hidden-layer biases by value: read from the parameter (constant) bank
-  const float *xmu, *xsd, *ymu, *ysd, *lo, *hi;
+  float st[ST_ROWS][MAXNS + 2];   // statistics, box and output bias, also from the parameter bank
   int ns, nin;
   const double* T;
   const double* p;
@@ -114,6 +116,81 @@ constexpr int kEpiWarps = 8;
 constexpr int kFwdThreads = 32 * (kEpiWarps + 2);
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 
+// Input features of one cell (x = [T, ln p, BC(Y)], z-scored, split into BF16 hi and lo parts:
+// [x_hi | x_lo | x_hi | 0], packed two per word) and its Box-Cox values bc (the output transform
+// adds the network's increments to them); outside = the features leave the training box.
+template <int NS_>
+struct CellFeatures {
+  static constexpr int AS = NS_ > 0 ? NS_ : MAXNS;
+  static constexpr int KP = NS_ > 0 ? (3 * (NS_ + 2) + 1) / 2 : KIN / 2;   // packed words in use
+  uint32_t xp[KP];
+  float bc[AS];
+};
+
+template <int NS_>
+__device__ __forceinline__ void cell_features(const SurParams& P, double tv, double pv,
+                                              const double (&yv)[CellFeatures<NS_>::AS], CellFeatures<NS_>& F,
+                                              bool& outside) {
+  constexpr int AS = CellFeatures<NS_>::AS;
+  const int ns = NS_ > 0 ? NS_ : P.ns, nin = ns + 2;
+  float x[2 * CellFeatures<NS_>::KP];
+#pragma unroll
+  for (int i = 0; i < 2 * CellFeatures<NS_>::KP; ++i) x[i] = 0.0f;
+  float f[2 + AS];
+  f[0] = (float)tv;
+  f[1] = logf((float)pv);
+#pragma unroll
+  for (int k = 0; k < AS; ++k) {
+    if (k < ns) {
+      const float yf = fmaxf((float)yv[k], 0.0f);
+      F.bc[k] = (powf(yf, BC_LAMBDA) - 1.0f) / BC_LAMBDA;
+      f[2 + k] = F.bc[k];
+    }
+  }
+  outside = false;
+#pragma unroll
+  for (int i = 0; i < 2 + AS; ++i) {
+    if (i < nin) {
+      if (!(f[i] >= P.st[ST_LO][i] && f[i] <= P.st[ST_HI][i])) outside = true;
+      const float v = (f[i] - P.st[ST_XMU][i]) / P.st[ST_XSD][i];
+      const float vh = __bfloat162float(__float2bfloat16_rn(v));
+      if (NS_ > 0) {
+        x[i] = vh;
+        x[nin + i] = v - vh;
+        x[2 * nin + i] = vh;
+      } else {
+        // runtime widths: place the three parts with compile-time indices
+#pragma unroll
+        for (int j = 0; j < KIN; ++j) {
+          if (j == i) x[j] = vh;
+          if (j == nin + i) x[j] = v - vh;
+          if (j == 2 * nin + i) x[j] = vh;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int w = 0; w < CellFeatures<NS_>::KP; ++w) F.xp[w] = pack_bf16(x[2 * w], x[2 * w + 1]);
+}
+
+// the packed features of row r into activation chunk 0 (128-byte swizzled K-major row)
+template <int NS_>
+__device__ __forceinline__ void put_features(const CellFeatures<NS_>& F, unsigned char* arow, int r) {
+  constexpr int KP = CellFeatures<NS_>::KP;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    uint4 v;
+    v.x = 4 * u + 0 < KP ? F.xp[4 * u + 0] : 0u;
+    v.y = 4 * u + 1 < KP ? F.xp[4 * u + 1] : 0u;
+    v.z = 4 * u + 2 < KP ? F.xp[4 * u + 2] : 0u;
+    v.w = 4 * u + 3 < KP ? F.xp[4 * u + 3] : 0u;
+    *reinterpret_cast<uint4*>(arow + ((u ^ (r & 7)) << 4)) = v;
+  }
+}
+
+// NS_ = the number of species when it is fixed at compile time (every per-cell array in
+// registers), 0 for any count up to MAXNS.
+template <int NS_>
 __global__ void __launch_bounds__(kFwdThreads, 1)
     surrogate_forward_kernel(const __grid_constant__ CUtensorMap tW1, const __grid_constant__ CUtensorMap tW2,
                              const __grid_constant__ CUtensorMap tW3, const __grid_constant__ CUtensorMap tW4,
@@ -131,7 +208,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   uint64_t* acc_full = empty + WSTAGES;
   uint64_t* lo_free = acc_full + 2;
   uint64_t* act_ready = lo_free + 1;
-  uint64_t* feat_ready = act_ready + 2;       // the tile's features are in chunk 0
+  // feat_ready: the tile's features are in chunk 0 and the previous tile's output (TMEM columns
+  // 256 .. 271) has been read
+  uint64_t* feat_ready = act_ready + 2;
   uint32_t* tmem_slot = (uint32_t*)(feat_ready + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -240,11 +319,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           for (int kc = 4; kc < 8 && ok; ++kc) ok = stage(kc, tmem + 256, id256, true);
           if (ok) mma_commit(&acc_full[1]);
         }
-        // output layer into columns 0-15
+        // output layer into columns 256-271 (the second half): the next tile's first-half MMAs
+        // need not wait for the output transform
         if (ok) ok = wait_ready(0);
         if (ok) ok = wait_ready(1);
-        for (int kc = 0; kc < 8 && ok; ++kc) ok = stage(kc, tmem, id16, kc > 0);
-        if (ok) mma_commit(&acc_full[0]);
+        for (int kc = 0; kc < 8 && ok; ++kc) ok = stage(kc, tmem + 256, id16, kc > 0);
+        if (ok) mma_commit(&acc_full[1]);
       }
     }
   } else {
@@ -252,87 +332,67 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its cells) of accumulator half w / 4 (columns
     // 256 (w / 4) .. + 255, four 64-column K chunks of the next layer's input): warps 0-3 drain the
     // first half while the second half's MMAs still run, warps 4-7 the second half while the next
-    // layer's first-half MMAs start.  Warps 0-3 also build the input tile and apply the output
-    // transform.
+    // layer's first-half MMAs start.  Warps 4-7, which wait longer between their blocks, also
+    // build the input tiles (the next tile's features right after the current tile's first
+    // layer, written once the output layer has read chunk 0) and apply the output transform.
+    constexpr int AS = CellFeatures<NS_>::AS;
     const int quarter = warp & 3, half = warp >> 2;
     const int r = quarter * 32 + lane;                 // cell row of the tile = TMEM lane
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
     unsigned char* arow = act + r * 128;               // row r inside each 16 KB chunk
-    const bool io = half == 0;
-    long long n_full[2] = {0, 0}, n_lo = 0;
+    const bool io = half == 1;
+    const int ns = NS_ > 0 ? NS_ : P.ns;
+    long long n_full = 0, n_lo = 0;
     bool ok = true;
-    float bc0[MAXNS];
-    // the state of the warp's next cell, loaded one tile ahead (the loads' latency hides behind
-    // the current tile's layers)
-    double nT = 0.0, np = 1.0, nY[MAXNS] = {};
-    auto load_state = [&](long long rd) {
-      const long long c = (blockIdx.x + rd * gridDim.x) * TM + r;
-      if (io && rd < rounds && c < P.ncells) {
-        nT = P.T[c];
-        np = P.p[c];
+    CellFeatures<NS_> F;          // the next tile's features
+    float bc[AS];                 // the current tile's Box-Cox values
+    double sT = 0.0, sp = 1.0, sY[AS];
 #pragma unroll
-        for (int k = 0; k < MAXNS; ++k)
-          if (k < P.ns) nY[k] = P.Y[(int64_t)k * P.ld + c];
+    for (int k = 0; k < AS; ++k) sY[k] = 0.0;
+    auto tile_cell = [&](long long rd) { return (blockIdx.x + rd * gridDim.x) * TM + r; };
+    auto load_state = [&](long long rd) {
+      const long long c = tile_cell(rd);
+      if (rd < rounds && c < P.ncells) {
+        sT = P.T[c];
+        sp = P.p[c];
+#pragma unroll
+        for (int k = 0; k < AS; ++k)
+          if (k < ns) sY[k] = P.Y[(int64_t)k * P.ld + c];
       }
     };
-    load_state(0);
-    for (long long rd = 0; rd < rounds && ok; ++rd) {
-      const long long tile = blockIdx.x + rd * gridDim.x;
-      const long long cell = tile * TM + r;
-      const bool valid = cell < P.ncells;
-      if (io) {
-        // ---- input features ----
-        float x[KIN];
+    // features of tile rd from the loaded state; the box flag is stored at once
+    auto make_features = [&](long long rd) {
+      const long long c = tile_cell(rd);
+      if (c < P.ncells) {
+        bool outside;
+        cell_features<NS_>(P, sT, sp, sY, F, outside);
+        P.outbox[c] = outside ? 1 : 0;
+      } else {
 #pragma unroll
-        for (int i = 0; i < KIN; ++i) x[i] = 0.0f;
-        double yv[MAXNS];
-        const double tv = nT, pv = np;
-#pragma unroll
-        for (int k = 0; k < MAXNS; ++k) yv[k] = nY[k];
-        load_state(rd + 1);
-        if (valid) {
-          bool outside = false;
-          float f[2 + MAXNS];
-          f[0] = (float)tv;
-          f[1] = logf((float)pv);
-#pragma unroll
-          for (int k = 0; k < MAXNS; ++k) {
-            if (k < P.ns) {
-              const float yf = fmaxf((float)yv[k], 0.0f);
-              bc0[k] = (powf(yf, BC_LAMBDA) - 1.0f) / BC_LAMBDA;
-              f[2 + k] = bc0[k];
-            }
-          }
-          for (int i = 0; i < P.nin; ++i) {
-            if (!(f[i] >= P.lo[i] && f[i] <= P.hi[i])) outside = true;
-            const float v = (f[i] - P.xmu[i]) / P.xsd[i];
-            const float vh = __bfloat162float(__float2bfloat16_rn(v));
-            x[i] = vh;                      // [x_hi | x_lo | x_hi]
-            x[P.nin + i] = v - vh;
-            x[2 * P.nin + i] = vh;
-          }
-          P.outbox[cell] = outside ? 1 : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          uint4 v;
-          v.x = pack_bf16(x[8 * u + 0], x[8 * u + 1]);
-          v.y = pack_bf16(x[8 * u + 2], x[8 * u + 3]);
-          v.z = pack_bf16(x[8 * u + 4], x[8 * u + 5]);
-          v.w = pack_bf16(x[8 * u + 6], x[8 * u + 7]);
-          *reinterpret_cast<uint4*>(arow + ((u ^ (r & 7)) << 4)) = v;
-        }
-        fence_async_smem();
-        mbar_arrive(feat_ready);
+        for (int w = 0; w < CellFeatures<NS_>::KP; ++w) F.xp[w] = 0u;
       }
+    };
+    if (io && rounds > 0) {
+      load_state(0);
+      make_features(0);
+      put_features<NS_>(F, arow, r);
+      fence_async_smem();
+      mbar_arrive(feat_ready);
+#pragma unroll
+      for (int k = 0; k < AS; ++k) bc[k] = F.bc[k];
+    }
+    for (long long rd = 0; rd < rounds && ok; ++rd) {
+      const long long cell = tile_cell(rd);
+      const bool valid = cell < P.ncells;
       // ---- hidden layers: this warp's half of the layer's columns ----
       for (int l = 0; l < 4 && ok; ++l) {
+        if (io && l == 0) load_state(rd + 1);         // consumed after this layer's epilogue
         const float* bias = P.hb[l];
         // tcgen05.ld is warp-collective: the warp agrees on the wait's outcome.  The first half's
         // columns overwrite activation chunks 0-3, which the second half's MMAs must have read.
-        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[half], (uint32_t)(n_full[half] & 1), P.err))) { ok = false; break; }
-        ++n_full[half];
-        if (io) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[half], (uint32_t)(n_full & 1), P.err))) { ok = false; break; }
+        ++n_full;
+        if (!io) {
           if (!__all_sync(0xffffffffu, mbar_wait(lo_free, (uint32_t)(n_lo & 1), P.err))) { ok = false; break; }
           ++n_lo;
         }
@@ -354,26 +414,37 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         tc_fence_before();
         fence_async_smem();
         mbar_arrive(&act_ready[half]);
+        if (io && l == 0 && rd + 1 < rounds) make_features(rd + 1);
       }
       if (!ok) break;
-      // ---- output layer (columns 0-15 of the first half) and inverse transform ----
+      // ---- output layer (columns 256-271), the next tile's input, the output transform ----
       if (io) {
-        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[0], (uint32_t)(n_full[0] & 1), P.err))) { ok = false; break; }
-        ++n_full[0];
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[1], (uint32_t)(n_full & 1), P.err))) { ok = false; break; }
+        ++n_full;
         tc_fence_after();
         uint32_t o[16];
-        tmem_ld16(trow, o);
+        tmem_ld16(trow + 256, o);
         tmem_ld_wait();
         tc_fence_before();
+        if (rd + 1 < rounds) {
+          put_features<NS_>(F, arow, r);
+          fence_async_smem();
+          mbar_arrive(feat_ready);
+        }
         if (valid) {
-          for (int k = 0; k < P.ns; ++k) {
-            const float z = __uint_as_float(o[k]) + __ldg(P.bias[4] + k);
-            if (P.zout) P.zout[(int64_t)k * P.ncells + cell] = z;
-            const float d = z * P.ysd[k] + P.ymu[k];
-            const float b1 = bc0[k] + d;
-            P.ynet[(int64_t)k * P.ncells + cell] = powf(fmaxf(1.0f + BC_LAMBDA * b1, 0.0f), 1.0f / BC_LAMBDA);
+#pragma unroll
+          for (int k = 0; k < AS; ++k) {
+            if (k < ns) {
+              const float z = __uint_as_float(o[k]) + P.st[ST_B5][k];
+              if (P.zout) P.zout[(int64_t)k * P.ncells + cell] = z;
+              const float d = z * P.st[ST_YSD][k] + P.st[ST_YMU][k];
+              const float b1 = bc[k] + d;
+              P.ynet[(int64_t)k * P.ncells + cell] = powf(fmaxf(1.0f + BC_LAMBDA * b1, 0.0f), 1.0f / BC_LAMBDA);
+            }
           }
         }
+#pragma unroll
+        for (int k = 0; k < AS; ++k) bc[k] = F.bc[k];
       }
     }
   }
@@ -793,14 +864,15 @@ int surrogate_forward(chem_model_s* md, const double* T, const double* p, const 
   if (md->kind == 1) return surrogate_forward_ps(md, T, p, Y, ld, ncells, ynet, zout, outbox, err, stream);
   static bool attr = false;
   if (!attr) {
-    CHEM_CUDA_TRY(cudaFuncSetAttribute(surrogate_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CHEM_CUDA_TRY(cudaFuncSetAttribute(surrogate_forward_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       FWD_SMEM));
+    CHEM_CUDA_TRY(cudaFuncSetAttribute(surrogate_forward_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FWD_SMEM));
     attr = true;
   }
   SurParams P;
-  for (int l = 0; l < 5; ++l) P.bias[l] = md->bias[l];
   memcpy(P.hb, md->hbias, sizeof(P.hb));
-  P.xmu = md->xmu; P.xsd = md->xsd; P.ymu = md->ymu; P.ysd = md->ysd; P.lo = md->lo; P.hi = md->hi;
+  memcpy(P.st, md->hstat, sizeof(P.st));
   P.ns = md->ns; P.nin = md->nin; P.T = T; P.p = p; P.Y = Y; P.ld = ld; P.ncells = ncells;
   P.ynet = ynet; P.zout = zout; P.outbox = outbox; P.err = err;
   // persistent grid: as many CTAs as can be resident at once (one per SM), no more than the tiles
@@ -809,15 +881,20 @@ int surrogate_forward(chem_model_s* md, const double* T, const double* p, const 
     int dev = 0, sms = 0, per_sm = 0;
     CHEM_CUDA_TRY(cudaGetDevice(&dev));
     CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CHEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, surrogate_forward_kernel, kFwdThreads,
+    CHEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, surrogate_forward_kernel<0>, kFwdThreads,
                                                                 FWD_SMEM));
     if (per_sm < 1) { set_error("surrogate kernel does not fit on an SM"); return CHEM_ECUDA; }
     max_ctas = sms * per_sm;
   }
+  if (ncells < 1) return CHEM_OK;
   const long long ntiles = (ncells + TM - 1) / TM;
   const long long grid = std::min<long long>(ntiles, max_ctas);
-  surrogate_forward_kernel<<<(unsigned)grid, kFwdThreads, FWD_SMEM, stream>>>(md->tw[0], md->tw[1], md->tw[2],
-                                                                              md->tw[3], md->tw[4], P);
+  if (md->ns == 9)
+    surrogate_forward_kernel<9><<<(unsigned)grid, kFwdThreads, FWD_SMEM, stream>>>(md->tw[0], md->tw[1], md->tw[2],
+                                                                                  md->tw[3], md->tw[4], P);
+  else
+    surrogate_forward_kernel<0><<<(unsigned)grid, kFwdThreads, FWD_SMEM, stream>>>(md->tw[0], md->tw[1], md->tw[2],
+                                                                                  md->tw[3], md->tw[4], P);
   CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
 }
@@ -898,6 +975,17 @@ extern "C" int chem_surrogate_create(const chem_surrogate_desc* d, chem_mech_t m
   for (int k = 0; k < ns; ++k) {
     st[2 * KIN + k] = d->y_mean[k];
     st[3 * KIN + k] = d->y_std[k];
+  }
+  for (int i = 0; i < nin; ++i) {
+    md->hstat[ST_XMU][i] = st[i];
+    md->hstat[ST_XSD][i] = st[KIN + i];
+    md->hstat[ST_LO][i] = st[4 * KIN + i];
+    md->hstat[ST_HI][i] = st[5 * KIN + i];
+  }
+  for (int k = 0; k < ns; ++k) {
+    md->hstat[ST_YMU][k] = st[2 * KIN + k];
+    md->hstat[ST_YSD][k] = st[3 * KIN + k];
+    md->hstat[ST_B5][k] = d->b[4][k];
   }
   std::vector<double> A = element_matrices(mech, ns);
   auto fail = [&](int rc) { chem_surrogate_free(md); return rc; };

@@ -41,6 +41,7 @@ struct chem_model_s {
   const float *xmu = nullptr, *xsd = nullptr, *ymu = nullptr, *ysd = nullptr, *lo = nullptr, *hi = nullptr;
   CUtensorMap tw[5];
   float hbias[4][512];       // host copy of the hidden-layer biases (single network)
+  float hstat[7][chem::SUR_MAXNS + 2] = {};   // host copy of the statistics, box and output bias (single network)
   // per-species networks (kind 1)
   int h[3] = {0, 0, 0};
   int nnet = 0;
