@@ -112,25 +112,27 @@ __device__ __forceinline__ void epilogue_block(const uint32_t (&a)[32], const fl
 // layer 4: 8 K-chunks of W5 (16 rows)
 constexpr int CHUNKS_PER_TILE = 2 + 3 * 16 + 8;
 
-constexpr int kEpiWarps = 8;
+// Epilogue warps: two per TMEM lane quarter and accumulator half, each draining 128 of the
+// half's 256 columns (four 32-column blocks)
+constexpr int kEpiParts = 2;
+constexpr int kEpiWarps = 8 * kEpiParts;
 constexpr int kFwdThreads = 32 * (kEpiWarps + 2);
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 
 // Input features of one cell (x = [T, ln p, BC(Y)], z-scored, split into BF16 hi and lo parts:
-// [x_hi | x_lo | x_hi | 0], packed two per word) and its Box-Cox values bc (the output transform
+// [x_hi | x_lo | x_hi | 0], packed two per word), with its Box-Cox values bc (the output transform
 // adds the network's increments to them); outside = the features leave the training box.
 template <int NS_>
 struct CellFeatures {
   static constexpr int AS = NS_ > 0 ? NS_ : MAXNS;
   static constexpr int KP = NS_ > 0 ? (3 * (NS_ + 2) + 1) / 2 : KIN / 2;   // packed words in use
   uint32_t xp[KP];
-  float bc[AS];
 };
 
 template <int NS_>
 __device__ __forceinline__ void cell_features(const SurParams& P, double tv, double pv,
                                               const double (&yv)[CellFeatures<NS_>::AS], CellFeatures<NS_>& F,
-                                              bool& outside) {
+                                              float (&bc)[CellFeatures<NS_>::AS], bool& outside) {
   constexpr int AS = CellFeatures<NS_>::AS;
   const int ns = NS_ > 0 ? NS_ : P.ns, nin = ns + 2;
   float x[2 * CellFeatures<NS_>::KP];
@@ -143,8 +145,8 @@ __device__ __forceinline__ void cell_features(const SurParams& P, double tv, dou
   for (int k = 0; k < AS; ++k) {
     if (k < ns) {
       const float yf = fmaxf((float)yv[k], 0.0f);
-      F.bc[k] = (powf(yf, BC_LAMBDA) - 1.0f) / BC_LAMBDA;
-      f[2 + k] = F.bc[k];
+      bc[k] = (powf(yf, BC_LAMBDA) - 1.0f) / BC_LAMBDA;
+      f[2 + k] = bc[k];
     }
   }
   outside = false;
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     mbar_init(lo_free, 1);
     mbar_init(&act_ready[0], 32 * kEpiWarps / 2);
     mbar_init(&act_ready[1], 32 * kEpiWarps / 2);
-    mbar_init(feat_ready, 32 * kEpiWarps / 2);
+    mbar_init(feat_ready, 32 * 4);
     fence_barrier_init();
   }
   if (warp == kTmaWarp) tmem_alloc(tmem_slot, 512);
@@ -329,87 +331,75 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     }
   } else {
     // ---------------- epilogue warps ----------------
-    // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its cells) of accumulator half w / 4 (columns
-    // 256 (w / 4) .. + 255, four 64-column K chunks of the next layer's input): warps 0-3 drain the
-    // first half while the second half's MMAs still run, warps 4-7 the second half while the next
-    // layer's first-half MMAs start.  Warps 4-7, which wait longer between their blocks, also
-    // build the input tiles (the next tile's features right after the current tile's first
-    // layer, written once the output layer has read chunk 0) and apply the output transform.
+    // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its cells) of accumulator half w / 8, columns
+    // 256 (w / 8) + 128 ((w / 4) % 2) .. + 127 (two 64-column K chunks of the next layer's input):
+    // warps 0-7 drain the first half while the second half's MMAs still run, warps 8-15 the second
+    // half while the next layer's first-half MMAs start.  Warps 8-11, which wait longer between
+    // their blocks, also build the input tiles (the next tile's features right after the current
+    // tile's first layer, written once the output layer has read chunk 0) and apply the output
+    // transform.
     constexpr int AS = CellFeatures<NS_>::AS;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, half = warp / (kEpiWarps / 2), part = (warp >> 2) % kEpiParts;
     const int r = quarter * 32 + lane;                 // cell row of the tile = TMEM lane
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
     unsigned char* arow = act + r * 128;               // row r inside each 16 KB chunk
-    const bool io = half == 1;
+    const bool io = half == 1 && part == 0;
     const int ns = NS_ > 0 ? NS_ : P.ns;
     long long n_full = 0, n_lo = 0;
     bool ok = true;
     CellFeatures<NS_> F;          // the next tile's features
-    float bc[AS];                 // the current tile's Box-Cox values
-    double sT = 0.0, sp = 1.0, sY[AS];
-#pragma unroll
-    for (int k = 0; k < AS; ++k) sY[k] = 0.0;
     auto tile_cell = [&](long long rd) { return (blockIdx.x + rd * gridDim.x) * TM + r; };
-    auto load_state = [&](long long rd) {
-      const long long c = tile_cell(rd);
-      if (rd < rounds && c < P.ncells) {
-        sT = P.T[c];
-        sp = P.p[c];
-#pragma unroll
-        for (int k = 0; k < AS; ++k)
-          if (k < ns) sY[k] = P.Y[(int64_t)k * P.ld + c];
-      }
-    };
-    // features of tile rd from the loaded state; the box flag is stored at once
+    // features of tile rd from the cell's state; the box flag is stored at once, and the Box-Cox
+    // values wait in the cell's output slots ynet[k][cell], which the output transform reads and
+    // overwrites (this keeps them out of registers for the whole tile)
     auto make_features = [&](long long rd) {
       const long long c = tile_cell(rd);
       if (c < P.ncells) {
+        double yv[AS];
+#pragma unroll
+        for (int k = 0; k < AS; ++k) yv[k] = k < ns ? P.Y[(int64_t)k * P.ld + c] : 0.0;
         bool outside;
-        cell_features<NS_>(P, sT, sp, sY, F, outside);
+        float bc[AS];
+        cell_features<NS_>(P, P.T[c], P.p[c], yv, F, bc, outside);
         P.outbox[c] = outside ? 1 : 0;
+#pragma unroll
+        for (int k = 0; k < AS; ++k)
+          if (k < ns) P.ynet[(int64_t)k * P.ncells + c] = bc[k];
       } else {
 #pragma unroll
         for (int w = 0; w < CellFeatures<NS_>::KP; ++w) F.xp[w] = 0u;
       }
     };
     if (io && rounds > 0) {
-      load_state(0);
       make_features(0);
       put_features<NS_>(F, arow, r);
       fence_async_smem();
       mbar_arrive(feat_ready);
-#pragma unroll
-      for (int k = 0; k < AS; ++k) bc[k] = F.bc[k];
     }
     for (long long rd = 0; rd < rounds && ok; ++rd) {
       const long long cell = tile_cell(rd);
       const bool valid = cell < P.ncells;
       // ---- hidden layers: this warp's half of the layer's columns ----
       for (int l = 0; l < 4 && ok; ++l) {
-        if (io && l == 0) load_state(rd + 1);         // consumed after this layer's epilogue
         const float* bias = P.hb[l];
         // tcgen05.ld is warp-collective: the warp agrees on the wait's outcome.  The first half's
         // columns overwrite activation chunks 0-3, which the second half's MMAs must have read.
         if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[half], (uint32_t)(n_full & 1), P.err))) { ok = false; break; }
         ++n_full;
-        if (!io) {
+        if (half == 0) {
           if (!__all_sync(0xffffffffu, mbar_wait(lo_free, (uint32_t)(n_lo & 1), P.err))) { ok = false; break; }
           ++n_lo;
         }
         tc_fence_after();
-        // eight blocks of 32 columns; the TMEM load of the next block is in flight while the
-        // current one is computed
-        const int col0 = half * 256;
-        uint32_t a[2][32];
-        tmem_ld32(trow + col0, a[0]);
+        // blocks of 32 columns, one TMEM load at a time (four warps per scheduler hide its latency)
+        constexpr int NBLK = 8 / kEpiParts;
+        const int col0 = half * 256 + part * (256 / kEpiParts);
 #pragma unroll 1
-        for (int blk = 0; blk < 8; blk += 2) {
-          tmem_ld_wait(a[0]);
-          tmem_ld32(trow + col0 + (blk + 1) * 32, a[1]);
-          epilogue_block(a[0], bias, col0 + blk * 32, arow, r);
-          tmem_ld_wait(a[1]);
-          if (blk + 2 < 8) tmem_ld32(trow + col0 + (blk + 2) * 32, a[0]);
-          epilogue_block(a[1], bias, col0 + (blk + 1) * 32, arow, r);
+        for (int blk = 0; blk < NBLK; ++blk) {
+          uint32_t a[32];
+          tmem_ld32(trow + col0 + blk * 32, a);
+          tmem_ld_wait(a);
+          epilogue_block(a, bias, col0 + blk * 32, arow, r);
         }
         tc_fence_before();
         fence_async_smem();
@@ -418,6 +408,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       }
       if (!ok) break;
       // ---- output layer (columns 256-271), the next tile's input, the output transform ----
+      // Every second-half warp follows each phase of acc_full[1] (its parity must not run ahead):
+      // the others only wait for the output layer's phase.
+      if (half == 1 && !io) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[1], (uint32_t)(n_full & 1), P.err))) { ok = false; break; }
+        ++n_full;
+      }
       if (io) {
         if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[1], (uint32_t)(n_full & 1), P.err))) { ok = false; break; }
         ++n_full;
@@ -438,13 +434,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
               const float z = __uint_as_float(o[k]) + P.st[ST_B5][k];
               if (P.zout) P.zout[(int64_t)k * P.ncells + cell] = z;
               const float d = z * P.st[ST_YSD][k] + P.st[ST_YMU][k];
-              const float b1 = bc[k] + d;
-              P.ynet[(int64_t)k * P.ncells + cell] = powf(fmaxf(1.0f + BC_LAMBDA * b1, 0.0f), 1.0f / BC_LAMBDA);
+              float* yk = P.ynet + (int64_t)k * P.ncells + cell;
+              const float b1 = *yk + d;                // the cell's Box-Cox value, left by make_features
+              *yk = powf(fmaxf(1.0f + BC_LAMBDA * b1, 0.0f), 1.0f / BC_LAMBDA);
             }
           }
         }
-#pragma unroll
-        for (int k = 0; k < AS; ++k) bc[k] = F.bc[k];
       }
     }
   }

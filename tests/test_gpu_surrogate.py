@@ -84,9 +84,13 @@ def _inverse_boxcox_fp32_bound(Y0, z, ysd, ymu, lam=0.1):
     return 2.0 * (rel * yr) + 1e-30
 
 
-def test_forward_matches_oracle_mlp(h2):
+@pytest.mark.parametrize("n", [1000, 2 * 152 * 128 + 77])
+def test_forward_matches_oracle_mlp(h2, n):
+    """n = 1000: eight tiles, one per CTA; 2 * 152 * 128 + 77: every CTA of the persistent grid
+    takes two or three tiles in turn (the barriers' phases carry from tile to tile), the last
+    one ragged."""
     dm = cg.Mechanism(h2)
-    T, p, Y = random_states(h2, 1000, 9, "H2", Tlo=300.0, Thi=2500.0)
+    T, p, Y = random_states(h2, n, 9, "H2", Tlo=300.0, Thi=2500.0)
     x = osur.features(T, p, Y)
     prm = _random_params(h2.ns, 3)
     prm["x_mean"] = x.mean(axis=0)
