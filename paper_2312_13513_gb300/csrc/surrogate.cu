@@ -204,12 +204,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   uint64_t* full = (uint64_t*)(wst + WSTAGES * WSTAGE_BYTES);
   uint64_t* empty = full + WSTAGES;
   // acc_full[h]: the MMAs into accumulator half h (TMEM columns 256 h .. + 255) of a layer are
-  // done; lo_free: the layer's second-half MMAs have read activation chunks 0-3, which the first
-  // half's epilogue then overwrites; act_ready[h]: the epilogue of half h has drained its
+  // done; chunk_free[c] (c < 4): the layer's second-half MMAs have read activation chunk c, which
+  // the first half's epilogue then overwrites (it starts on its accumulator at once and waits
+  // only before writing each chunk); act_ready[h]: the epilogue of half h has drained its
   // accumulator and written activation chunks 4 h .. 4 h + 3
   uint64_t* acc_full = empty + WSTAGES;
-  uint64_t* lo_free = acc_full + 2;
-  uint64_t* act_ready = lo_free + 1;
+  uint64_t* chunk_free = acc_full + 2;
+  uint64_t* act_ready = chunk_free + 4;
   // feat_ready: the tile's features are in chunk 0 and the previous tile's output (TMEM columns
   // 256 .. 271) has been read
   uint64_t* feat_ready = act_ready + 2;
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     for (int s = 0; s < WSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     mbar_init(&acc_full[0], 1);
     mbar_init(&acc_full[1], 1);
-    mbar_init(lo_free, 1);
+    for (int c = 0; c < 4; ++c) mbar_init(&chunk_free[c], 1);
     mbar_init(&act_ready[0], 32 * kEpiWarps / 2);
     mbar_init(&act_ready[1], 32 * kEpiWarps / 2);
     mbar_init(feat_ready, 32 * 4);
@@ -305,7 +306,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         tc_fence_after();
         if (ok) ok = stage(0, tmem, id256, false);
         if (ok) { mma_commit(&acc_full[0]); ok = stage(0, tmem + 256, id256, false); }
-        if (ok) { mma_commit(lo_free); mma_commit(&acc_full[1]); }
+        if (ok) {
+          for (int c = 0; c < 4; ++c) mma_commit(&chunk_free[c]);
+          mma_commit(&acc_full[1]);
+        }
         // hidden layers: the first half starts on chunks 0-3 while the second half's epilogue of
         // the previous layer still runs
         for (int l = 1; l < 4 && ok; ++l) {
@@ -315,9 +319,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           for (int kc = 4; kc < 8 && ok; ++kc) ok = stage(kc, tmem, id256, true);
           if (!ok) break;
           mma_commit(&acc_full[0]);
-          for (int kc = 0; kc < 4 && ok; ++kc) ok = stage(kc, tmem + 256, id256, kc > 0);
+          for (int kc = 0; kc < 4 && ok; ++kc) {
+            ok = stage(kc, tmem + 256, id256, kc > 0);
+            if (ok) mma_commit(&chunk_free[kc]);
+          }
           if (!ok) break;
-          mma_commit(lo_free);
           for (int kc = 4; kc < 8 && ok; ++kc) ok = stage(kc, tmem + 256, id256, true);
           if (ok) mma_commit(&acc_full[1]);
         }
@@ -386,21 +392,26 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         // columns overwrite activation chunks 0-3, which the second half's MMAs must have read.
         if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[half], (uint32_t)(n_full & 1), P.err))) { ok = false; break; }
         ++n_full;
-        if (half == 0) {
-          if (!__all_sync(0xffffffffu, mbar_wait(lo_free, (uint32_t)(n_lo & 1), P.err))) { ok = false; break; }
-          ++n_lo;
-        }
+
         tc_fence_after();
         // blocks of 32 columns, one TMEM load at a time (four warps per scheduler hide its latency)
         constexpr int NBLK = 8 / kEpiParts;
         const int col0 = half * 256 + part * (256 / kEpiParts);
 #pragma unroll 1
+        bool fine = true;
         for (int blk = 0; blk < NBLK; ++blk) {
+          if (half == 0 && (blk & 1) == 0 &&
+              !__all_sync(0xffffffffu, mbar_wait(&chunk_free[(col0 + blk * 32) >> 6], (uint32_t)(n_lo & 1), P.err))) {
+            fine = false;
+            break;
+          }
           uint32_t a[32];
           tmem_ld32(trow + col0 + blk * 32, a);
           tmem_ld_wait(a);
           epilogue_block(a, bias, col0 + blk * 32, arow, r);
         }
+        if (!fine) { ok = false; break; }
+        ++n_lo;
         tc_fence_before();
         fence_async_smem();
         mbar_arrive(&act_ready[half]);
