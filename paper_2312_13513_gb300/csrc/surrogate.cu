@@ -388,16 +388,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       // ---- hidden layers: this warp's half of the layer's columns ----
       for (int l = 0; l < 4 && ok; ++l) {
         const float* bias = P.hb[l];
-        // tcgen05.ld is warp-collective: the warp agrees on the wait's outcome.  The first half's
-        // columns overwrite activation chunks 0-3, which the second half's MMAs must have read.
+        // tcgen05.ld is warp-collective: the warp agrees on the wait's outcome
         if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[half], (uint32_t)(n_full & 1), P.err))) { ok = false; break; }
         ++n_full;
-
         tc_fence_after();
-        // blocks of 32 columns, one TMEM load at a time (four warps per scheduler hide its latency)
+        // blocks of 32 columns, one TMEM load at a time (four warps per scheduler hide its latency);
+        // the first half's columns overwrite activation chunks 0-3, each once the second half's
+        // MMAs have read it
         constexpr int NBLK = 8 / kEpiParts;
         const int col0 = half * 256 + part * (256 / kEpiParts);
-#pragma unroll 1
         bool fine = true;
         for (int blk = 0; blk < NBLK; ++blk) {
           if (half == 0 && (blk & 1) == 0 &&
