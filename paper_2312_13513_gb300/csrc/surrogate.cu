@@ -564,7 +564,9 @@ __global__ void __launch_bounds__(256) surrogate_post_kernel(const PostParams P)
             G[f][e] = sg;
           }
         }
-      // Gaussian elimination with partial pivoting on the small SPD system
+      // Gaussian elimination with partial pivoting on the small SPD system; one reciprocal per
+      // pivot serves the elimination below it and the back substitution
+      double inv_piv[AE];
 #pragma unroll
       for (int k = 0; k < AE; ++k) {
         if (k < ne && pass) {
@@ -596,10 +598,11 @@ __global__ void __launch_bounds__(256) surrogate_post_kernel(const PostParams P)
 #pragma unroll
               for (int i = k + 1; i < AE; ++i) if (i == pr) lam[i] = lk;
             }
+            inv_piv[k] = 1.0 / G[k][k];
 #pragma unroll
             for (int i = k + 1; i < AE; ++i) {
               if (i < ne) {
-                const double l = G[i][k] / G[k][k];
+                const double l = G[i][k] * inv_piv[k];
 #pragma unroll
                 for (int j = k; j < AE; ++j)
                   if (j < ne) G[i][j] -= l * G[k][j];
@@ -617,7 +620,7 @@ __global__ void __launch_bounds__(256) surrogate_post_kernel(const PostParams P)
 #pragma unroll
             for (int j = i + 1; j < AE; ++j)
               if (j < ne) sl -= G[i][j] * lam[j];
-            lam[i] = sl / G[i][i];
+            lam[i] = sl * inv_piv[i];
           }
         }
         double s0 = 0.0, s1 = 0.0;
@@ -652,18 +655,18 @@ __global__ void __launch_bounds__(256) surrogate_post_kernel(const PostParams P)
         // temperature range visited
         double h0;
         {
+          // h / R = a5 + a0 T + ... + a4 T^5 per species (no division by T)
           const int rg0 = T0 < TMID ? 0 : 1;
-          const double invT0 = 1.0 / T0;
           double hs = 0.0;
 #pragma unroll
           for (int k = 0; k < AS; ++k) {
             if (k < ns) {
               const double* a = hcoef + (rg0 * ns + k) * 6;
-              const double hRT = a[0] + T0 * (a[1] + T0 * (a[2] + T0 * (a[3] + T0 * a[4]))) + a[5] * invT0;
-              hs += Y0[k] * hRT * __ldg(invW + k);
+              const double hR = a[5] + T0 * (a[0] + T0 * (a[1] + T0 * (a[2] + T0 * (a[3] + T0 * a[4]))));
+              hs += Y0[k] * hR * __ldg(invW + k);
             }
           }
-          h0 = RU * T0 * hs;
+          h0 = RU * hs;
         }
         double Ah[6], Ac[5];
         int rg = Tn < TMID ? 0 : 1;
@@ -734,7 +737,9 @@ __global__ void surrogate_post_general(const PostParams P) {
           G[e][f] = s;
           G[f][e] = s;
         }
-      // Gaussian elimination with partial pivoting on the small SPD system
+      // Gaussian elimination with partial pivoting on the small SPD system; one reciprocal per
+      // pivot serves the elimination below it and the back substitution
+      double inv_piv[NEMAX];
       for (int e = 0; e < ne; ++e) lam[e] = rr[e];
       for (int k = 0; k < ne; ++k) {
         int pr = k;
@@ -745,8 +750,9 @@ __global__ void surrogate_post_general(const PostParams P) {
           for (int j = 0; j < ne; ++j) { const double t = G[k][j]; G[k][j] = G[pr][j]; G[pr][j] = t; }
           const double t = lam[k]; lam[k] = lam[pr]; lam[pr] = t;
         }
+        inv_piv[k] = 1.0 / G[k][k];
         for (int i = k + 1; i < ne; ++i) {
-          const double l = G[i][k] / G[k][k];
+          const double l = G[i][k] * inv_piv[k];
           for (int j = k; j < ne; ++j) G[i][j] -= l * G[k][j];
           lam[i] -= l * lam[k];
         }
@@ -755,7 +761,7 @@ __global__ void surrogate_post_general(const PostParams P) {
         for (int i = ne - 1; i >= 0; --i) {
           double s = lam[i];
           for (int j = i + 1; j < ne; ++j) s -= G[i][j] * lam[j];
-          lam[i] = s / G[i][i];
+          lam[i] = s * inv_piv[i];
         }
         double s0 = 0.0, s1 = 0.0;
         for (int k = 0; k < ns; ++k) {

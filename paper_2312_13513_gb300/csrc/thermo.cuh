@@ -34,21 +34,21 @@ __device__ __forceinline__ void h_cp_mass(const unsigned char* blob, const MechL
   *cp = RU * cs;
 }
 
-// Mass-specific enthalpy alone (erg/g, formation included) of the composition Yloc at T.
+// Mass-specific enthalpy alone (erg/g, formation included) of the composition Yloc at T, as the
+// polynomial h / R = a5 + a0 T + a1 T^2 + ... + a4 T^5 per species (no division by T).
 __device__ __forceinline__ double h_mass(const unsigned char* blob, const MechLayout& L, double T,
                                          const double* Yloc) {
   const int ns = L.ns;
   const int rg = T < TMID ? 0 : 1;
   const double* hc = (const double*)(blob + L.o_hc);
   const double* invW = (const double*)(blob + L.o_invW);
-  const double invT = 1.0 / T;
   double hs = 0.0;
   for (int k = 0; k < ns; ++k) {
     const double* a = hc + (rg * ns + k) * 6;
-    const double hRT = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4]))) + a[5] * invT;
-    hs += Yloc[k] * hRT * __ldg(invW + k);
+    const double hR = a[5] + T * (a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4]))));
+    hs += Yloc[k] * hR * __ldg(invW + k);
   }
-  return RU * T * hs;
+  return RU * hs;
 }
 
 // The mixture's NASA-7 polynomials for one temperature range: for mass fractions Yloc,
@@ -73,10 +73,10 @@ __device__ __forceinline__ void mixture_nasa(const unsigned char* blob, const Me
   }
 }
 
+// h and cp of a mixture polynomial at T; h = R (Ah5 + Ah0 T + ... + Ah4 T^5), no division by T
 __device__ __forceinline__ void h_cp_from_mixture(const double Ah[6], const double Ac[5], double T, double* h,
                                                   double* cp) {
-  const double hRT = Ah[0] + T * (Ah[1] + T * (Ah[2] + T * (Ah[3] + T * Ah[4]))) + Ah[5] / T;
-  *h = RU * T * hRT;
+  *h = RU * (Ah[5] + T * (Ah[0] + T * (Ah[1] + T * (Ah[2] + T * (Ah[3] + T * Ah[4])))));
   *cp = RU * (Ac[0] + T * (Ac[1] + T * (Ac[2] + T * (Ac[3] + T * Ac[4]))));
 }
 
