@@ -58,6 +58,12 @@ __device__ __forceinline__ unsigned long long mul_x2(unsigned long long a, unsig
   return d;
 }
 
+__device__ __forceinline__ unsigned long long add_x2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 __device__ __forceinline__ void gelu2(float& v0, float& v1) {
   const float x0 = fabsf(v0), x1 = fabsf(v1);
   const unsigned long long x = f32x2(x0, x1);

@@ -97,9 +97,13 @@ __device__ __forceinline__ void epilogue_block(const uint32_t (&a)[32], const fl
     const float* bq = bias + c0 + 8 * q;
     float v[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(a[8 * q + e]) + bq[e];
-#pragma unroll
-    for (int e = 0; e < 8; e += 2) gelu2(v[e], v[e + 1]);
+    for (int e = 0; e < 8; e += 2) {
+      // the bias of a pair of columns in one packed add (each half rounds like the scalar add)
+      const unsigned long long s2 = add_x2(f32x2(__uint_as_float(a[8 * q + e]), __uint_as_float(a[8 * q + e + 1])),
+                                           f32x2(bq[e], bq[e + 1]));
+      f32x2_split(s2, v[e], v[e + 1]);
+      gelu2(v[e], v[e + 1]);
+    }
     uint4 pk;
     pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
     pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
