@@ -243,10 +243,11 @@ __global__ void __launch_bounds__(128, 2)
 // within a row block, so consecutive tiles share their A rows in L2) with a 128 x BN_ tile and
 // two TMEM accumulators: the epilogue of one tile runs while the MMAs of the next fill the other
 // accumulator.  Warp 0 (one lane): TMA producer over a STAGES_P-stage ring; warp 1 (one lane):
-// MMA issuer; warps 2-9: epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31 and the columns of
-// half (w - 2) / 4 of the tile), storing each row's 32-column pieces straight to global memory.
+// MMA issuer; warps 2-17: epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31 and the columns of
+// quarter (w - 2) / 4 of the tile: four warps per scheduler hide the latency of the bias, GELU and
+// store chain), storing each row's 32-column pieces straight to global memory.
 // ---------------------------------------------------------------------------------------
-constexpr int kPersistThreads = 320;     // TMA warp, MMA warp, eight epilogue warps
+constexpr int kPersistThreads = 576;     // TMA warp, MMA warp, sixteen epilogue warps
 
 template <int BN_>
 struct PersistCfg {
@@ -338,10 +339,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       }
     }
   } else {
-    // epilogue warps 2-9
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    // epilogue warps 2-17
+    const int quarter = warp & 3, part = (warp - 2) >> 2;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-    constexpr int HW = BN_ / 2;                              // columns per epilogue warp
+    constexpr int HW = BN_ / 4;                              // columns per epilogue warp
     bool ok = true;
     for (long long rd = 0; rd < rounds && ok; ++rd) {
       const long long t = blockIdx.x + rd * gridDim.x;
@@ -351,59 +352,54 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       tc_fence_after();
       const int row = m0 + quarter * 32 + lane;
       const bool rv = row < a.M;
-      const uint32_t tb = trow + (uint32_t)(b * BN_ + half * HW);
-      uint32_t r[2][32];
-      tmem_ld32(tb, r[0]);
+      const uint32_t tb = trow + (uint32_t)(b * BN_ + part * HW);
 #pragma unroll 1
-      for (int c0 = 0; c0 < HW; c0 += 64) {
+      for (int cc = 0; cc < HW; cc += 32) {
+        uint32_t r[32];
+        tmem_ld32(tb + cc, r);
+        tmem_ld_wait(r);
+        const int col = n0 + part * HW + cc;
+        if (a.Cb) {
+          uint32_t pk[16];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int cc = c0 + 32 * h;
-          tmem_ld_wait(r[h]);
-          if (cc + 32 < HW) tmem_ld32(tb + cc + 32, r[h ^ 1]);
-          const int col = n0 + half * HW + cc;
-          if (a.Cb) {
-            uint32_t pk[16];
+          for (int j = 0; j < 16; ++j) {
+            const int cj = col + 2 * j;
+            float v0 = __uint_as_float(r[2 * j]) + (a.bias && cj < a.N ? a.bias[cj] : 0.0f);
+            float v1 = __uint_as_float(r[2 * j + 1]) + (a.bias && cj + 1 < a.N ? a.bias[cj + 1] : 0.0f);
+            if (a.gelu) gelu2(v0, v1);
+            __nv_bfloat162 hv = __floats2bfloat162_rn(v0, v1);
+            pk[j] = *reinterpret_cast<uint32_t*>(&hv);
+          }
+          if (rv) {
+            __nv_bfloat16* out = a.Cb + (int64_t)row * a.ldc + col;
+            if (a.vec && col + 32 <= a.N) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int cj = col + 2 * j;
-              float v0 = __uint_as_float(r[h][2 * j]) + (a.bias && cj < a.N ? a.bias[cj] : 0.0f);
-              float v1 = __uint_as_float(r[h][2 * j + 1]) + (a.bias && cj + 1 < a.N ? a.bias[cj + 1] : 0.0f);
-              if (a.gelu) gelu2(v0, v1);
-              __nv_bfloat162 hv = __floats2bfloat162_rn(v0, v1);
-              pk[j] = *reinterpret_cast<uint32_t*>(&hv);
-            }
-            if (rv) {
-              __nv_bfloat16* out = a.Cb + (int64_t)row * a.ldc + col;
-              if (a.vec && col + 32 <= a.N) {
+              for (int q = 0; q < 4; ++q)
+                reinterpret_cast<uint4*>(out)[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                  reinterpret_cast<uint4*>(out)[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-              } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  if (col + j < a.N) {
-                    const uint32_t w = pk[j >> 1];
-                    reinterpret_cast<uint16_t*>(out)[j] = (uint16_t)((j & 1) ? (w >> 16) : (w & 0xffffu));
-                  }
+              for (int j = 0; j < 32; ++j) {
+                if (col + j < a.N) {
+                  const uint32_t w = pk[j >> 1];
+                  reinterpret_cast<uint16_t*>(out)[j] = (uint16_t)((j & 1) ? (w >> 16) : (w & 0xffffu));
                 }
               }
             }
-          } else if (rv) {
-            float* out = a.C + (int64_t)row * a.ldc + col;
-            float v[32];
+          }
+        } else if (rv) {
+          float* out = a.C + (int64_t)row * a.ldc + col;
+          float v[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            v[j] = __uint_as_float(r[j]) + (a.bias && col + j < a.N ? a.bias[col + j] : 0.0f);
+          if (a.vec && col + 32 <= a.N) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              reinterpret_cast<float4*>(out)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              v[j] = __uint_as_float(r[h][j]) + (a.bias && col + j < a.N ? a.bias[col + j] : 0.0f);
-            if (a.vec && col + 32 <= a.N) {
-#pragma unroll
-              for (int q = 0; q < 8; ++q)
-                reinterpret_cast<float4*>(out)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (col + j < a.N) out[j] = v[j];
-            }
+              if (col + j < a.N) out[j] = v[j];
           }
         }
       }
