@@ -4,18 +4,17 @@
 // GELU to 5e-7, gelu.cuh; round to nearest even): the layer-by-layer inference of the per-species
 // networks.
 //
+// A training forward layer can take both outputs at once: the FP32 pre-activation and the BF16
+// GELU of it (gemm_bf16_gelu2).
+//
 // Used by the surrogate's training (forward and backward products of §2's MLP, trained with
 // Adam) and by the per-species networks' inference; the single network's inference uses the
-// fused kernel in surrogate.cu built from the same primitives.  Launches go to the persistent
-// form below (gemm_bf16_persistent); the one-tile-per-CTA kernel that follows is its predecessor,
-// kept as the simplest statement of the tile computation.
-// One CTA computes a 128 x 128 tile: warp 0 (one lane) streams 128 x 64 tiles of A and B with TMA
-// (128-byte swizzle) through a 3-stage mbarrier ring, warp 1 (one lane) issues
-// tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16) into a TMEM accumulator, and the
-// four warps read their 32 TMEM lanes back with tcgen05.ld for the epilogue, which stages the tile
-// in the (then idle) stage buffers and writes whole rows with 16-byte stores.  Two CTAs share an
-// SM, so one's epilogue overlaps the other's main loop.  Every wait is
-// bounded: a timeout sets a device error flag and the kernel drains and exits.
+// fused kernel in surrogate.cu built from the same primitives.  One persistent kernel
+// (gemm_bf16_persistent): warp 0 (one lane) streams 128 x 64 tiles of A and B with TMA (128-byte
+// swizzle) through an mbarrier ring, warp 1 (one lane) issues tcgen05.mma.cta_group::1.kind::f16
+// (M = 128, N = BN, K = 16) into one of two TMEM accumulators, and sixteen warps read the other
+// accumulator back with tcgen05.ld for the epilogue.  Every wait is bounded: a timeout sets a
+// device error flag and the kernel drains and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -77,14 +76,12 @@ int make_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t col
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;   // 97 KB: two CTAs per SM
-constexpr int TILE_A = BM * BK * 2;              // 16 KB
-constexpr int TILE_B = BN * BK * 2;              // 16 KB
-constexpr int GEMM_SMEM = STAGES * (TILE_A + TILE_B) + 1024 + 256;
+constexpr int BM = 128, BN = 128, BK = 64;      // tile rows, the narrower tile width, K step
 
 struct GemmArgs {
   float* C;
   __nv_bfloat16* Cb;       // non-null: BF16 output of the activation epilogue instead of C
+  float* Cz;               // with Cb (persistent kernel): also the FP32 pre-activation, same pitch
   int gelu;                // activation epilogue: apply GELU before rounding
   int vec;                 // output base and row pitch allow 16-byte stores
   const float* bias;
@@ -93,150 +90,6 @@ struct GemmArgs {
   int* err;
 };
 
-
-
-__global__ void __launch_bounds__(128, 2)
-    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const GemmArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + STAGES * TILE_A;
-  uint64_t* full = (uint64_t*)(sB + STAGES * TILE_B);
-  uint64_t* empty = full + STAGES;
-  uint64_t* acc_done = empty + STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(acc_done + 1);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int nk = (a.K + BK - 1) / BK;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(acc_done, 1);
-    fence_barrier_init();
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
-  }
-  if (warp == 0) tmem_alloc(tmem_slot, BN);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  if (warp == 0 && lane == 0) {
-    // producer
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(&empty[s], ph ^ 1, a.err)) break;
-      mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
-      tma_load_2d(sA + s * TILE_A, &tmA, &full[s], kb * BK, m0);
-      tma_load_2d(sB + s * TILE_B, &tmB, &full[s], kb * BK, n0);
-      ++issued;
-    }
-    // drain: wait for the loads still in flight before the CTA may exit
-    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-      mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, a.err);
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1, a.err)) break;
-      tc_fence_after();
-      const uint32_t abase = smem_addr(sA + s * TILE_A), bbase = smem_addr(sB + s * TILE_B);
-#pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        mma_bf16(tmem, sdesc_k128(abase + kk * 32), sdesc_k128(bbase + kk * 32), idesc,
-                 (kb > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
-    }
-    mma_commit(acc_done);
-  }
-  __syncwarp();
-  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31.  TMEM -> registers (bias, activation)
-  // -> shared memory (the stage buffers: every MMA, hence every read of them, has completed once
-  // acc_done fires) -> coalesced row stores, 16 bytes per lane.  The wait's outcome is agreed
-  // block-wide first (tcgen05.ld is warp-collective and the staging needs block barriers).
-  const bool ok = __syncthreads_and(mbar_wait(acc_done, 0, a.err)) != 0;
-  tc_fence_after();
-  const int rl = warp * 32 + lane;                       // tile row of this thread
-  if (ok) {
-    if (a.Cb) {
-      constexpr int SP = BN + 8;                           // BF16 row pitch: 272 B
-      __nv_bfloat16* st = (__nv_bfloat16*)sA;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
-        tmem_ld_wait();
-        uint32_t pk[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + 2 * j;
-          float v0 = __uint_as_float(r[2 * j]) + (a.bias && col < a.N ? a.bias[col] : 0.0f);
-          float v1 = __uint_as_float(r[2 * j + 1]) + (a.bias && col + 1 < a.N ? a.bias[col + 1] : 0.0f);
-          if (a.gelu) { v0 = gelu_f(v0); v1 = gelu_f(v1); }
-          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-          pk[j] = *reinterpret_cast<uint32_t*>(&h);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(st + rl * SP + c0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-      }
-      __syncthreads();
-      // 16 lanes per 256-byte row: a warp stores two rows per instruction
-      const int cg = threadIdx.x & 15;
-      for (int rr = threadIdx.x >> 4; rr < BM; rr += 8) {
-        const int row = m0 + rr, col = n0 + 8 * cg;
-        if (row >= a.M || col >= a.N) continue;
-        const __nv_bfloat16* src = st + rr * SP + 8 * cg;
-        __nv_bfloat16* out = a.Cb + (int64_t)row * a.ldc + col;
-        if (a.vec && col + 8 <= a.N) {
-          *reinterpret_cast<uint4*>(out) = *reinterpret_cast<const uint4*>(src);
-        } else {
-          for (int j = 0; j < 8 && col + j < a.N; ++j) out[j] = src[j];
-        }
-      }
-    } else {
-      constexpr int SP = BN + 4;                           // FP32 row pitch: 528 B
-      float* st = (float*)sA;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
-        tmem_ld_wait();
-        float4* dst = reinterpret_cast<float4*>(st + rl * SP + c0);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          float v[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int col = n0 + c0 + 4 * q + j;
-            v[j] = __uint_as_float(r[4 * q + j]) + (a.bias && col < a.N ? a.bias[col] : 0.0f);
-          }
-          dst[q] = make_float4(v[0], v[1], v[2], v[3]);
-        }
-      }
-      __syncthreads();
-      // 32 lanes per 512-byte row: a warp stores one row per instruction
-      for (int rr = warp; rr < BM; rr += 4) {
-        const int row = m0 + rr, col = n0 + 4 * lane;
-        if (row >= a.M || col >= a.N) continue;
-        const float* src = st + rr * SP + 4 * lane;
-        float* out = a.C + (int64_t)row * a.ldc + col;
-        if (a.vec && col + 4 <= a.N) {
-          *reinterpret_cast<float4*>(out) = *reinterpret_cast<const float4*>(src);
-        } else {
-          for (int j = 0; j < 4 && col + j < a.N; ++j) out[j] = src[j];
-        }
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, BN);
-}
 
 // ---------------------------------------------------------------------------------------
 // Persistent form: one CTA per SM walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... (N-fastest
@@ -360,12 +213,33 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         tmem_ld_wait(r);
         const int col = n0 + part * HW + cc;
         if (a.Cb) {
+          if (a.Cz) {
+            // the pre-activation z = acc + bias, kept in r for the activation below
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              r[j] = __float_as_uint(__uint_as_float(r[j]) + (a.bias && col + j < a.N ? a.bias[col + j] : 0.0f));
+            if (rv) {
+              float* outz = a.Cz + (int64_t)row * a.ldc + col;
+              if (a.vec && col + 32 <= a.N) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                  reinterpret_cast<float4*>(outz)[q] =
+                      make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                  __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                  if (col + j < a.N) outz[j] = __uint_as_float(r[j]);
+              }
+            }
+          }
+          const bool add_bias = a.bias && !a.Cz;
           uint32_t pk[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int cj = col + 2 * j;
-            float v0 = __uint_as_float(r[2 * j]) + (a.bias && cj < a.N ? a.bias[cj] : 0.0f);
-            float v1 = __uint_as_float(r[2 * j + 1]) + (a.bias && cj + 1 < a.N ? a.bias[cj + 1] : 0.0f);
+            float v0 = __uint_as_float(r[2 * j]) + (add_bias && cj < a.N ? a.bias[cj] : 0.0f);
+            float v1 = __uint_as_float(r[2 * j + 1]) + (add_bias && cj + 1 < a.N ? a.bias[cj + 1] : 0.0f);
             if (a.gelu) gelu2(v0, v1);
             __nv_bfloat162 hv = __floats2bfloat162_rn(v0, v1);
             pk[j] = *reinterpret_cast<uint32_t*>(&hv);
@@ -415,7 +289,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 }  // namespace
 
 static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, void* Cb, int gelu,
-                       int64_t ldc, const float* bias, int M, int N, int K, int* err, cudaStream_t stream) {
+                       int64_t ldc, const float* bias, int M, int N, int K, int* err, cudaStream_t stream,
+                       float* Cz = nullptr) {
   if (M < BM || N < BN || K <= 0 || !A || !B || (!C && !Cb) || !err) {
     set_error("gemm_bf16: bad arguments (M=%d N=%d K=%d; M and N must be >= 128)", M, N, K);
     return CHEM_EINVAL;
@@ -425,15 +300,11 @@ static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, f
   if (rc) return rc;
   rc = make_tmap_bf16(&tb, B, N, K, ldb, BN, BK);
   if (rc) return rc;
-  static bool attr_set = false;
-  if (!attr_set) {
-    CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
-    attr_set = true;
-  }
   const uintptr_t obase = C ? (uintptr_t)C : (uintptr_t)Cb;
   const int64_t opitch = ldc * (C ? 4 : 2);
-  const int vec = (obase % 16 == 0 && opitch % 16 == 0) ? 1 : 0;
-  GemmArgs g{C, (__nv_bfloat16*)Cb, gelu, vec, bias, M, N, K, ldc, err};
+  int vec = (obase % 16 == 0 && opitch % 16 == 0) ? 1 : 0;
+  if (Cz && ((uintptr_t)Cz % 16 != 0 || (ldc * 4) % 16 != 0)) vec = 0;
+  GemmArgs g{C, (__nv_bfloat16*)Cb, Cz, gelu, vec, bias, M, N, K, ldc, err};
   // persistent kernel, 256-column tiles unless 128-column tiles pad N less
   const int pad128 = (N + 127) / 128 * 128 - N, pad256 = (N + 255) / 256 * 256 - N;
   const int bn = (N >= 256 && pad256 <= pad128) ? 256 : 128;
@@ -477,6 +348,14 @@ int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, 
 int gemm_bf16_act(const void* A, int64_t lda, const void* B, int64_t ldb, void* Cb, int64_t ldc,
                   const float* bias, int gelu, int M, int N, int K, int* err, cudaStream_t stream) {
   return gemm_launch(A, lda, B, ldb, nullptr, Cb, gelu, ldc, bias, M, N, K, err, stream);
+}
+
+// C = A B^T + bias twice: the FP32 pre-activation into Cz and GELU of it, rounded to BF16, into Cb
+// (both [M x N] with row pitch ldc elements): a training forward layer in one launch
+int gemm_bf16_gelu2(const void* A, int64_t lda, const void* B, int64_t ldb, float* Cz, void* Cb, int64_t ldc,
+                    const float* bias, int M, int N, int K, int* err, cudaStream_t stream) {
+  if (!Cz || !Cb) { set_error("gemm_bf16_gelu2: both outputs are required"); return CHEM_EINVAL; }
+  return gemm_launch(A, lda, B, ldb, nullptr, Cb, 1, ldc, bias, M, N, K, err, stream, Cz);
 }
 
 }  // namespace chem

@@ -35,6 +35,8 @@
 namespace chem {
 int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
               const float* bias, int M, int N, int K, int* err, cudaStream_t stream);
+int gemm_bf16_gelu2(const void* A, int64_t lda, const void* B, int64_t ldb, float* Cz, void* Cb, int64_t ldc,
+                    const float* bias, int M, int N, int K, int* err, cudaStream_t stream);
 }
 
 using namespace chem;
@@ -45,14 +47,8 @@ constexpr int HID = 512;
 constexpr int PADIO = 128;
 constexpr int MAXL = 8;          // layers at most (hidden layers + output)
 
-__device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float v) {
   return 0.5f * (1.0f + erff(v * 0.70710678118654752f)) + v * 0.3989422804014327f * expf(-0.5f * v * v);
-}
-
-__global__ void k_gelu_fwd(const float* Z, __nv_bfloat16* A, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    A[i] = __float2bfloat16_rn(gelu(Z[i]));
 }
 
 __global__ void k_gelu_bwd(const float* dA, const float* Z, float* dZf, __nv_bfloat16* dZb, int64_t n) {
@@ -80,8 +76,17 @@ __global__ void k_mse_grad(const float* out, const float* target, float* dZf, __
     dZf[i] = g;
     dZb[i] = __float2bfloat16_rn(g);
   }
+  // one atomic per block: the warps' sums through shared memory
+  __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, part / ((double)B * nout));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  if (warp == 0) {
+    part = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0 && loss) atomicAdd(loss, part / ((double)B * nout));
+  }
 }
 
 // out[c * R + r] = in[r * C + c] (BF16), 32 x 32 tiles through shared memory
@@ -119,12 +124,14 @@ __global__ void k_colsum_part(const float* A, double* part, int R, int C) {
   }
 }
 
+// one warp per column: the lanes sum strided partials, then a shuffle reduction
 __global__ void k_colsum_finish(const double* part, float* s, int nparts, int C) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (c >= C) return;                                // whole warps leave together
   double t = 0.0;
-  for (int i = 0; i < nparts; ++i) t += part[(int64_t)i * C + c];
-  s[c] = (float)t;
+  for (int i = lane; i < nparts; i += 32) t += part[(int64_t)i * C + c];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) s[c] = (float)t;
 }
 
 // Adam on a [rows x cols] parameter block (cols = 1 for biases); writes the BF16 copy of W if given
@@ -424,13 +431,14 @@ extern "C" int chem_mlp_forward(chem_trainer_t t, const void* X, float* out, che
   t->A[0] = (__nv_bfloat16*)X;
   const int B = t->B, NL = t->nl;
   for (int l = 0; l < NL; ++l) {
-    int rc = gemm_bf16(t->A[l], t->in_pad[l], t->Wb[l], t->in_pad[l], t->Z[l], t->out_pad[l], t->b[l], B,
-                       t->out_pad[l], t->in_pad[l], t->err, st);
+    // hidden layers keep the pre-activation Z (for the backward pass) and write the next
+    // layer's BF16 input GELU(Z) from the same epilogue
+    const int rc = l < NL - 1
+                       ? gemm_bf16_gelu2(t->A[l], t->in_pad[l], t->Wb[l], t->in_pad[l], t->Z[l], t->A[l + 1],
+                                         t->out_pad[l], t->b[l], B, t->out_pad[l], t->in_pad[l], t->err, st)
+                       : gemm_bf16(t->A[l], t->in_pad[l], t->Wb[l], t->in_pad[l], t->Z[l], t->out_pad[l], t->b[l],
+                                   B, t->out_pad[l], t->in_pad[l], t->err, st);
     if (rc) return rc;
-    if (l < NL - 1) {
-      const int64_t n = (int64_t)B * t->out_pad[l];
-      k_gelu_fwd<<<grid_for(n), 256, 0, st>>>(t->Z[l], t->A[l + 1], n);
-    }
   }
   if (out) {
     CHEM_CUDA_TRY(cudaMemcpy2DAsync(out, t->nout * 4, t->Z[NL - 1], PADIO * 4, t->nout * 4, B,
@@ -446,8 +454,8 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
   cudaStream_t st = (cudaStream_t)stream;
   const int B = t->B, NL = t->nl;
   CHEM_CUDA_TRY(cudaMemsetAsync(t->loss, 0, sizeof(double), st));
-  k_mse_grad<<<grid_for((int64_t)B * PADIO), 256, 0, st>>>(t->Z[NL - 1], target, t->dZf, t->dZb, t->loss, B,
-                                                          t->nout, PADIO);
+  k_mse_grad<<<std::min(grid_for((int64_t)B * PADIO), 1024u), 256, 0, st>>>(t->Z[NL - 1], target, t->dZf, t->dZb,
+                                                                         t->loss, B, t->nout, PADIO);
   dim3 tb(32, 8);
   for (int l = NL - 1; l >= 0; --l) {
     const int nout = t->out_pad[l], nin = t->in_pad[l];
@@ -460,7 +468,7 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
     {
       const int nparts = (B + kColRows - 1) / kColRows;
       k_colsum_part<<<dim3((nout + 31) / 32, nparts), dim3(32, 8), 0, st>>>(t->dZf, t->colpart, B, nout);
-      k_colsum_finish<<<(nout + 127) / 128, 128, 0, st>>>(t->colpart, t->db[l], nparts, nout);
+      k_colsum_finish<<<(nout + 7) / 8, 256, 0, st>>>(t->colpart, t->db[l], nparts, nout);
     }
     if (l > 0) {
       rc = gemm_bf16(t->dZb, nout, t->Wt[l], nout, t->dA, nin, nullptr, B, nin, nout, t->err, st);
