@@ -25,3 +25,30 @@ def prereacted_mixing_states(om, mech, n, seed):
     T[idx] = T1
     Y[:, idx] = Y1
     return T, p, Y
+
+
+def with_inert_argon(mech):
+    """The mechanism with an inert argon appended (one more species and one more element): a
+    species and element count the fixed-size kernel instances do not cover, so the runtime-width
+    paths run.  Argon's NASA-7 polynomial is the monatomic ideal gas: cp/R = 5/2 in both ranges,
+    h(298.15 K) = 0 (a6 = -5/2 * 298.15) and a7 = 4.366 (its standard entropy); third-body
+    efficiency 1."""
+    m = mech.copy()
+    m.name = mech.name + "+AR"
+    m.elements = list(mech.elements) + ["AR"]
+    m.elem_mass = np.append(mech.elem_mass, 39.948)
+    comp = np.zeros((mech.ns + 1, mech.ne + 1), mech.comp.dtype)
+    comp[:mech.ns, :mech.ne] = mech.comp
+    comp[mech.ns, mech.ne] = 1
+    m.comp = comp
+    m.species = list(mech.species) + ["AR"]
+    m.W = np.append(mech.W, 39.948)
+    ar = np.array([2.5, 0.0, 0.0, 0.0, 0.0, -2.5 * 298.15, 4.366])
+    m.nasa_lo = np.vstack([mech.nasa_lo, ar])
+    m.nasa_hi = np.vstack([mech.nasa_hi, ar])
+    m.eff = np.hstack([mech.eff, np.ones((mech.nr, 1))])
+    if mech.hf_R is not None:
+        m.hf_R = np.append(mech.hf_R, 0.0)
+    if mech.s0_R is not None:
+        m.s0_R = np.append(mech.s0_R, 2.5 * np.log(298.15) + 4.366)
+    return m

@@ -89,14 +89,20 @@ def test_forward_matches_oracle_mlp(h2, n):
     """n = 1000: eight tiles, one per CTA; 2 * 152 * 128 + 77: every CTA of the persistent grid
     takes two or three tiles in turn (the barriers' phases carry from tile to tile), the last
     one ragged."""
-    dm = cg.Mechanism(h2)
-    T, p, Y = random_states(h2, n, 9, "H2", Tlo=300.0, Thi=2500.0)
+    check_forward_against_oracle(h2, n)
+
+
+def check_forward_against_oracle(mech, n):
+    """The forward pass on n random states of mech against the oracle's BF16 emulation: z to
+    1e-2, the trust-box flags exactly, the inverse Box-Cox on the device's own z to FP32 rounding."""
+    dm = cg.Mechanism(mech)
+    T, p, Y = random_states(mech, n, 9, "H2", Tlo=300.0, Thi=2500.0)
     x = osur.features(T, p, Y)
-    prm = _random_params(h2.ns, 3)
+    prm = _random_params(mech.ns, 3)
     prm["x_mean"] = x.mean(axis=0)
     prm["x_std"] = _std(x)
-    prm["y_mean"] = 0.01 * np.arange(h2.ns)
-    prm["y_std"] = 0.05 + 0.01 * np.arange(h2.ns)
+    prm["y_mean"] = 0.01 * np.arange(mech.ns)
+    prm["y_std"] = 0.05 + 0.01 * np.arange(mech.ns)
     prm["box_lo"] = x.min(axis=0) - 1.0
     prm["box_hi"] = x.max(axis=0) + 1.0
     prm["box_hi"][0] = 2000.0           # cells hotter than 2000 K leave the box
