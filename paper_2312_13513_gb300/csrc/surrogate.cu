@@ -9,18 +9,19 @@
 // W_lo x_hi (the W_lo x_lo term is below FP32 accumulation noise).  Reaction rates depend
 // exponentially on T, and a plain BF16 T feature (8-bit mantissa) is off by several kelvin.
 //
-// surrogate_forward_kernel (persistent, one CTA per SM, 10 warps):
-//   warps 0-7  epilogue: after every hidden layer read the FP32 accumulator from TMEM
+// surrogate_forward_kernel (persistent, one CTA per SM, 18 warps; a layer's 512 outputs are two
+// accumulator halves of 256 TMEM columns):
+//   warps 0-15 epilogue: after every hidden layer read the FP32 accumulator from TMEM
 //              (tcgen05.ld), add the bias, apply GELU, round to BF16 and write the next layer's
 //              input tile in place (128-byte swizzled K-major layout).  Warp w reads TMEM lanes
-//              32 (w % 4) .. + 31 (its cells) and columns 256 (w / 4) .. + 255, so two warps per
-//              SM sub-partition share a layer's 512 columns.
-//              Warps 0-3 also build the input tile (FP64 state -> features -> BF16) and, after
-//              the last layer, apply the inverse transform (de-normalise, add to BC(Y0), invert
-//              Box-Cox) and write Y' (FP32).  The trust-region test (training box) is done on
-//              the features.
-//   warp 8     one lane streams weight tiles (256 x 64 BF16, 32 KB) with TMA into a 3-stage ring.
-//   warp 9     one lane issues tcgen05.mma (M = 128, N = 256 or 16, K = 16) into 512 TMEM columns.
+//              32 (w % 4) .. + 31 (its cells) and 128 columns of half w / 8, so four warps per SM
+//              sub-partition share a layer's 512 columns.
+//              Warps 8-11 also build the next tile's input (FP64 state -> features -> BF16) right
+//              after its first layer and, after the last layer, apply the inverse transform
+//              (de-normalise, add to BC(Y0), invert Box-Cox) and write Y' (FP32).  The
+//              trust-region test (training box) is done on the features.
+//   warp 16    one lane streams weight tiles (256 x 64 BF16, 32 KB) with TMA into a 3-stage ring.
+//   warp 17    one lane issues tcgen05.mma (M = 128, N = 256 or 16, K = 16) into 512 TMEM columns.
 // surrogate_post_kernel (FP64, one thread per cell): element-conservation projection, clip,
 //   temperature from enthalpy by Newton (the paper's Thermo class, §3.1), acceptance tests, and
 //   compaction of rejected cells into a fallback list that the FP64 integrator then advances
