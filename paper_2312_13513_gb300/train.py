@@ -10,7 +10,8 @@ gathers batches.
     python -m paper_2312_13513_gb300.train --out model.chemsur --states 4194304 --epochs 40
     python -m torch.distributed.run --nproc-per-node N -m paper_2312_13513_gb300.train --out ...
         (data-parallel: each rank takes 1/N of every global batch, one NCCL all-reduce of the
-        gradients per step; --checkpoint / --resume save and continue the trainer state)
+        gradients per step; --checkpoint / --resume save and continue the trainer state; --graph
+        replays one captured step per batch on a single GPU)
 """
 from __future__ import annotations
 
@@ -464,6 +465,8 @@ def main():
     ap.add_argument("--log", default=None, help="also write the training log to this file")
     ap.add_argument("--checkpoint", default=None, help="trainer state file rewritten every epoch")
     ap.add_argument("--resume", default=None, help="continue from this trainer state file")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay one captured CUDA graph per batch (one GPU; bitwise the direct steps)")
     args = ap.parse_args()
     from synth.mechanism import h2_mechanism
     import torch
@@ -485,7 +488,8 @@ def main():
         f"{args.lr_final} (cosine) front_fraction {args.front_fraction} seed {args.seed}")
     params = train(h2_mechanism(), args.states, args.epochs, args.batch, args.lr, args.lr_final,
                    seed=args.seed, log=log, time_budget_s=args.budget,
-                   front_fraction=args.front_fraction, checkpoint=args.checkpoint, resume=args.resume)
+                   front_fraction=args.front_fraction, checkpoint=args.checkpoint, resume=args.resume,
+                   graph=args.graph)
     if rank == 0:
         os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
         save_model(params, args.out)
