@@ -690,8 +690,12 @@ __device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* perm, 
     const int pk = perm[k];
     best = 0ull;
     bi = k + 1;
+    // e / n by a multiply-high with ceil(2^32 / n) (formed in 32 bits; it wraps to 0 for n = 1,
+    // where e = 0), exact while e * n < 2^32 (here e < n^2 < 2^12)
+    const unsigned magic = 0xFFFFFFFFu / (unsigned)n + 1u;
     for (int e = g.tid; e < n * n; e += G) {
-      const int i = k + 1 + e / n, j = k + 1 + e % n;
+      const int q = (int)__umulhi((unsigned)e, magic);
+      const int i = k + 1 + q, j = k + 1 + (e - q * n);
       const int ph = perm[i];
       const double v = M[ph * LD + j] - M[ph * LD + k] * M[pk * LD + j];
       M[ph * LD + j] = v;
