@@ -275,6 +275,12 @@ __device__ __forceinline__ void gsum_lead(const Grp<G>& g, double (&v)[K], doubl
   }
 }
 
+// Division of a flat index by a run-time row length d without the integer divide: q = e / d is
+// the high word of e * ceil(2^32 / d) (div_magic, formed in 32 bits; it wraps to 0 for d = 1,
+// where only e = 0 occurs), exact while e * d < 2^32 (the loops below: e < d^2 < 2^12).
+__device__ __forceinline__ unsigned div_magic(unsigned d) { return 0xFFFFFFFFu / d + 1u; }
+__device__ __forceinline__ int div_by(int e, unsigned magic) { return (int)__umulhi((unsigned)e, magic); }
+
 // Pivot key of a matrix entry: the bit pattern of |a| read as an unsigned integer.  For
 // non-negative doubles the integer order is the numeric order, so the pivot search runs on the
 // integer pipes instead of FP64 compares (the FP64 pipe is the scarce one).  NaN maps to 0.
@@ -570,7 +576,11 @@ __device__ __forceinline__ void eval_fj(const Grp<G>& g, const MechView& m, cons
 
   // analytic Jacobian (A5): d(wdot)/dC by the precomputed assembly program ...
   double* Jm = Jneg;
-  for (int e = g.tid; e < ns * ns; e += G) Jm[(1 + e / ns) * LD + 1 + e % ns] = 0.0;
+  const unsigned mns = div_magic((unsigned)ns);
+  for (int e = g.tid; e < ns * ns; e += G) {
+    const int k = div_by(e, mns);
+    Jm[(1 + k) * LD + 1 + (e - k * ns)] = 0.0;
+  }
   g.sync();
   for (int e = g.tid; e < jp.nent; e += G) {
     double s = 0.0;
@@ -630,7 +640,7 @@ __device__ __forceinline__ void eval_fj(const Grp<G>& g, const MechView& m, cons
     g.sync();
   }
   for (int e = g.tid; e < ns * ns; e += G) {
-    const int k = e / ns, mm = e % ns;
+    const int k = div_by(e, mns), mm = e - k * ns;
     double* Jkm = Jm + (1 + k) * LD + 1 + mm;
     *Jkm = m.W[k] * m.invW[mm] * (w.rk[k] - *Jkm);
   }
@@ -690,11 +700,9 @@ __device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* perm, 
     const int pk = perm[k];
     best = 0ull;
     bi = k + 1;
-    // e / n by a multiply-high with ceil(2^32 / n) (formed in 32 bits; it wraps to 0 for n = 1,
-    // where e = 0), exact while e * n < 2^32 (here e < n^2 < 2^12)
-    const unsigned magic = 0xFFFFFFFFu / (unsigned)n + 1u;
+    const unsigned magic = div_magic((unsigned)n);
     for (int e = g.tid; e < n * n; e += G) {
-      const int q = (int)__umulhi((unsigned)e, magic);
+      const int q = div_by(e, magic);
       const int i = k + 1 + q, j = k + 1 + (e - q * n);
       const int ph = perm[i];
       const double v = M[ph * LD + j] - M[ph * LD + k] * M[pk * LD + j];
