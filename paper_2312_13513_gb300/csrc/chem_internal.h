@@ -94,7 +94,8 @@ namespace chem {
 int launch_advance_batch(chem_mech_s* m, const chem_segment* segs, int nseg, cudaStream_t stream);
 constexpr int kMaxSegsPerLaunch = 32;
 int launch_advance_slice(chem_mech_s* m, const chem_segment* segs, int nseg, unsigned long long budget_ns,
-                         unsigned long long* counter, long long* seg_end, cudaStream_t stream);
+                         unsigned long long* counter, long long* seg_end, cudaStream_t stream,
+                         const unsigned int* stop = nullptr, unsigned long long min_ns = 0);
 long long advance_queue_chunks(chem_mech_s* m, int64_t ncells);
 int launch_advance(chem_mech_s* m, double* T, const double* p, double* Y, int64_t ld, double dt,
                    int64_t ncells, double rtol, double atol, const int32_t* idx, int8_t* status,

@@ -776,6 +776,10 @@ struct AdvanceParams {
   unsigned long long* counter;
   const unsigned int* ncells_dev;  // single segment: cell count read from device memory
   unsigned long long budget_ns = 0;  // > 0: stop claiming chunks this long after the group started
+  // time-sliced launches: a nonzero *stop (device memory, set by the caller while the slice runs)
+  // also stops the claiming, once the group has run min_ns
+  const unsigned int* stop = nullptr;
+  unsigned long long min_ns = 0;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -910,10 +914,17 @@ __device__ bool next_cell(const Grp<G>& g, const MechView& m, const WsPtr& w,
       g.sync();
     }
     if (q.exhausted) return false;
-    // a time-sliced launch stops claiming once its budget is spent: the chunks claimed so far
-    // are exactly the prefix [0, counter) of the queue, and the next slice continues from there
-    if (g.tid == 0)
-      w.ctl[0] = (P.budget_ns > 0 && global_ns() - q.t0 > P.budget_ns) ? ~0ull : atomicAdd(P.counter, 1ull);
+    // a time-sliced launch stops claiming once its budget is spent or its caller asks it to stop:
+    // the chunks claimed so far are exactly the prefix [0, counter) of the queue, and the next
+    // slice continues from there
+    if (g.tid == 0) {
+      bool stop = false;
+      if (P.budget_ns > 0) {
+        const unsigned long long el = global_ns() - q.t0;
+        stop = el > P.budget_ns || (P.stop && el > P.min_ns && *(const volatile unsigned int*)P.stop != 0u);
+      }
+      w.ctl[0] = stop ? ~0ull : atomicAdd(P.counter, 1ull);
+    }
     g.sync();
     const unsigned long long claimed = w.ctl[0];      // ~0 when the time budget is spent
     g.sync();
@@ -1326,9 +1337,11 @@ long long advance_queue_chunks(chem_mech_s* m, int64_t ncells) {
 // first slice).  Groups stop claiming chunks budget_ns after they start; the chunks claimed so far
 // form the prefix [0, counter) of the queue, so re-issuing the same slice continues the work and
 // a segment is complete once the counter reaches seg_end[i] (its last chunk + 1, written here).
-// A slice issued after the counter reached the total returns at once.
+// A slice issued after the counter reached the total returns at once.  stop (nullable, device
+// memory): a nonzero value ends the slice early the same way, for groups that have run min_ns.
 int launch_advance_slice(chem_mech_s* m, const chem_segment* segs, int nseg, unsigned long long budget_ns,
-                         unsigned long long* counter, long long* seg_end, cudaStream_t stream) {
+                         unsigned long long* counter, long long* seg_end, cudaStream_t stream,
+                         const unsigned int* stop, unsigned long long min_ns) {
   if (!m || !segs || nseg < 1 || nseg > kMaxSegs || !counter) { set_error("bad slice arguments"); return CHEM_EINVAL; }
   LaunchShape s;
   int rc = pick_shape(m, nullptr, &s);
@@ -1354,6 +1367,8 @@ int launch_advance_slice(chem_mech_s* m, const chem_segment* segs, int nseg, uns
   P.counter = counter;
   P.ncells_dev = nullptr;
   P.budget_ns = budget_ns;
+  P.stop = stop;
+  P.min_ns = min_ns;
   return dispatch_adv(s, P, nullptr, stream);
 }
 

@@ -111,7 +111,14 @@ struct chem_server_s {
   unsigned long long* d_counter = nullptr;     // one work-queue counter per stream (device)
   unsigned long long* h_counter = nullptr;     // its read-back copy (pinned host memory)
   unsigned long long* h_reset = nullptr;       // values the counters are set back to (pinned)
+  // per stream: a nonzero word ends the stream's running FP64 slice early (device; set when a
+  // surrogate pass is issued, so that its kernels need not wait for the slice's time budget)
+  unsigned int* d_stop = nullptr;
+  unsigned int* h_flags = nullptr;             // {0, 1}: the values copied into d_stop (pinned)
 };
+
+// a slice ends early on request only after this long (every slice makes progress)
+constexpr unsigned long long kMinSliceNs = 2000000ull;
 
 namespace {
 
@@ -181,7 +188,10 @@ void server_loop(chem_server_s* S) {
           // last slice extend it, and a counter that overshot the old end is set back to it
           cudaStream_t strm = S->streams[L.stream];
           int rc = CHEM_OK;
-          if (claimed > L.issued_total) {
+          if (cudaMemcpyAsync(S->d_stop + L.stream, S->h_flags, sizeof(unsigned int), cudaMemcpyHostToDevice,
+                              strm) != cudaSuccess)
+            rc = chem::cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(server stop flag)");
+          if (rc == CHEM_OK && claimed > L.issued_total) {
             S->h_reset[L.stream] = (unsigned long long)L.issued_total;
             if (cudaMemcpyAsync(S->d_counter + L.stream, S->h_reset + L.stream, sizeof(unsigned long long),
                                 cudaMemcpyHostToDevice, strm) != cudaSuccess)
@@ -189,7 +199,8 @@ void server_loop(chem_server_s* S) {
           }
           if (rc == CHEM_OK)
             rc = chem::launch_advance_slice(L.mech, L.segs.data(), (int)L.segs.size(), S->slice_ns,
-                                            S->d_counter + L.stream, nullptr, strm);
+                                            S->d_counter + L.stream, nullptr, strm, S->d_stop + L.stream,
+                                            kMinSliceNs);
           L.issued_total = total;
           if (rc == CHEM_OK &&
               cudaMemcpyAsync(S->h_counter + L.stream, S->d_counter + L.stream, sizeof(unsigned long long),
@@ -320,11 +331,14 @@ void server_loop(chem_server_s* S) {
           L.sliced = true;
           L.mech = S->states[r0.state].mech;
           L.seg_end.assign(L.segs.size(), 0);
-          if (cudaMemsetAsync(S->d_counter + sidx, 0, sizeof(unsigned long long), strm) != cudaSuccess) {
-            rc = chem::cuda_fail(cudaGetLastError(), "cudaMemsetAsync(server counter)");
+          if (cudaMemsetAsync(S->d_counter + sidx, 0, sizeof(unsigned long long), strm) != cudaSuccess ||
+              cudaMemcpyAsync(S->d_stop + sidx, S->h_flags, sizeof(unsigned int), cudaMemcpyHostToDevice,
+                              strm) != cudaSuccess) {
+            rc = chem::cuda_fail(cudaGetLastError(), "server counter / stop flag");
           } else {
             rc = chem::launch_advance_slice(L.mech, L.segs.data(), (int)L.segs.size(), S->slice_ns,
-                                            S->d_counter + sidx, L.seg_end.data(), strm);
+                                            S->d_counter + sidx, L.seg_end.data(), strm, S->d_stop + sidx,
+                                            kMinSliceNs);
             L.issued_total = L.seg_end.back();
           }
           if (rc == CHEM_OK &&
@@ -342,7 +356,16 @@ void server_loop(chem_server_s* S) {
             segs.push_back(g);
           }
           const StateRec& st0 = S->states[r0.state];
-          rc = chem_surrogate_advance_batch(st0.model, st0.mech, segs.data(), (int)segs.size(), strm);
+          // running FP64 slices stop claiming cells (after their minimum time), so that this
+          // pass's kernels get the SMs as the slices' cells in flight finish; the copies run on
+          // this pass's stream, ahead of its kernels
+          for (const Launch& F : S->launches)
+            if (F.sliced && cudaEventQuery(F.ev) == cudaErrorNotReady &&
+                cudaMemcpyAsync(S->d_stop + F.stream, S->h_flags + 1, sizeof(unsigned int), cudaMemcpyHostToDevice,
+                                strm) != cudaSuccess)
+              rc = chem::cuda_fail(cudaGetLastError(), "cudaMemcpyAsync(server stop flag)");
+          if (rc == CHEM_OK)
+            rc = chem_surrogate_advance_batch(st0.model, st0.mech, segs.data(), (int)segs.size(), strm);
         }
         const Clock::time_point now = Clock::now();
         if (rc != CHEM_OK) {
@@ -423,8 +446,12 @@ extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_optio
   if (opt && opt->max_pause_ms != 0.0)
     S->max_pause_ns = opt->max_pause_ms < 0.0 ? 0ull : (unsigned long long)(opt->max_pause_ms * 1e6);
   if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; return cuda_fail(cudaGetLastError(), "cudaGetDevice"); }
-  cudaError_t ea = cudaMalloc((void**)&S->d_counter, ns * sizeof(unsigned long long));
-  cudaError_t eh = ea == cudaSuccess ? cudaHostAlloc((void**)&S->h_counter, 2 * ns * sizeof(unsigned long long),
+  // device: the counters, then the stop words; pinned host: counter copies, reset values, {0, 1}.
+  // Both device words of a stream are set on that stream before each slice it runs (nothing here
+  // writes them: a synchronous memset would run on the legacy default stream, unordered with the
+  // server's non-blocking streams, and could land in the middle of a job)
+  cudaError_t ea = cudaMalloc((void**)&S->d_counter, ns * (sizeof(unsigned long long) + sizeof(unsigned int)));
+  cudaError_t eh = ea == cudaSuccess ? cudaHostAlloc((void**)&S->h_counter, (2 * ns + 1) * sizeof(unsigned long long),
                                                      cudaHostAllocDefault)
                                      : ea;
   if (ea != cudaSuccess || eh != cudaSuccess) {
@@ -433,6 +460,10 @@ extern "C" int chem_serve_create(size_t hbm_budget_bytes, const chem_serve_optio
     return cuda_fail(ea != cudaSuccess ? ea : eh, "server counters");
   }
   S->h_reset = S->h_counter + ns;
+  S->d_stop = (unsigned int*)(S->d_counter + ns);
+  S->h_flags = (unsigned int*)(S->h_counter + 2 * ns);
+  S->h_flags[0] = 0u;
+  S->h_flags[1] = 1u;
   for (int i = 0; i < ns; ++i) {
     cudaStream_t st;
     cudaError_t e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i < nfp ? prio_low : prio_high);
