@@ -424,7 +424,9 @@ int chem_train_normalize(const float* x, int64_t n, int c, const float* mean, co
  * admitted FP64 requests of a mechanism into one job of the persistent integrator and overlaps
  * launches on a small stream pool (continuous batching).  An FP64 job runs as time slices of
  * slice_ms: each slice stops claiming cells after that time and the next continues the same work
- * queue, so launches on other streams get the SMs in between.  A request completes when the
+ * queue, so launches on other streams get the SMs in between; issuing a surrogate pass also ends
+ * the running slices early (once they have run 2 ms), so that the pass does not wait for the
+ * rest of a slice.  Results do not depend on where slices end.  A request completes when the
  * queue passes its last cell.  Latency = submission to completion.  No counterpart in the paper,
  * whose solver owns the GPU alone (§3.1). 
  * ------------------------------------------------------------------------------------- */
