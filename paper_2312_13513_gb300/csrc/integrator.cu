@@ -277,7 +277,8 @@ __device__ __forceinline__ void gsum_lead(const Grp<G>& g, double (&v)[K], doubl
 
 // Division of a flat index by a run-time row length d without the integer divide: q = e / d is
 // the high word of e * ceil(2^32 / d) (div_magic, formed in 32 bits; it wraps to 0 for d = 1,
-// where only e = 0 occurs), exact while e * d < 2^32 (the loops below: e < d^2 < 2^12).
+// where only e = 0 occurs), exact while e * d < 2^32: the loops below have e < d^2, so any row
+// length up to 1625, far beyond a matrix that fits in shared memory.
 __device__ __forceinline__ unsigned div_magic(unsigned d) { return 0xFFFFFFFFu / d + 1u; }
 __device__ __forceinline__ int div_by(int e, unsigned magic) { return (int)__umulhi((unsigned)e, magic); }
 
