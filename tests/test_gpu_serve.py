@@ -280,3 +280,34 @@ def test_fp64_requests_join_a_running_sliced_job(ch4):
     cg.advance(dm, rb[0], rb[1], rb[2], 1e-6)
     torch.cuda.synchronize()
     assert torch.equal(big[0], rb[0]) and torch.equal(big[2], rb[2])
+
+
+def test_surrogate_pass_ends_a_long_fp64_slice_early(h2, ch4):
+    """With 500 ms FP64 slices, a surrogate request submitted while a long CH4 job runs completes
+    in far less than a slice: issuing its pass ends the running slice (after its 2 ms minimum),
+    and the job continues in later slices with bitwise the result of one launch."""
+    dm_h2, dm_ch4 = cg.Mechanism(h2), cg.Mechanism(ch4)
+    f = les_field(load_table("ch4_flamelet.npz"), n=262144, seed=35)
+    big = to_dev(f["T"], f["p"], f["Y"])
+    small = to_dev(*_h2_state(20000, 36))
+    model = _identity_model(dm_h2, h2, *[x.cpu().numpy() for x in small])
+    srv = serve.Server(8 << 30, slice_ms=500.0)
+    s_big = srv.register(dm_ch4, *big)
+    s_small = srv.register(dm_h2, *small, model=model)
+    r_big = srv.submit(s_big, serve.ROUTE_FP64, 1e-6)
+    time.sleep(0.05)
+    assert srv.poll(r_big)[0] == serve.RUNNING
+    r_small = srv.submit(s_small, serve.ROUTE_SURROGATE, 5e-7)
+    srv.wait(r_small, 60.0)
+    lat_small = srv.poll(r_small)[1]
+    state_big = srv.poll(r_big)[0]
+    srv.wait(r_big, 120.0)
+    st = srv.stats()
+    srv.close()
+    assert state_big == serve.RUNNING, "the long job finished before the small request"
+    assert lat_small < 0.15, lat_small          # a whole 500 ms slice would be waited out otherwise
+    assert st["slices"] >= 2 and st["failed"] == 0
+    ref = to_dev(f["T"], f["p"], f["Y"])
+    cg.advance(dm_ch4, ref[0], ref[1], ref[2], 1e-6)
+    torch.cuda.synchronize()
+    assert torch.equal(big[0], ref[0]) and torch.equal(big[2], ref[2])
