@@ -88,6 +88,10 @@ struct GemmArgs {
   int M, N, K;
   int64_t ldc;
   int* err;
+  // split-K (FP32 output C only, no bias): the K steps of every output tile are dealt to `splits`
+  // tiles of the queue, split s writing its partial sum to C + s * split_stride
+  int splits = 1;
+  int64_t split_stride = 0;
 };
 
 
@@ -110,7 +114,9 @@ struct PersistCfg {
   static constexpr int SMEM = STAGES_P * (TA + TB) + 1024 + 256;
 };
 
-template <int BN_>
+// SPLITK_: the split-K decode is compiled in (training's weight gradients); without it every tile
+// takes all K steps, as the inference products do
+template <int BN_, bool SPLITK_>
 __global__ void __launch_bounds__(kPersistThreads, 1)
     gemm_bf16_persistent(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const GemmArgs a) {
@@ -128,8 +134,18 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntm = (a.M + BM - 1) / BM, ntn = (a.N + BN_ - 1) / BN_;
-  const long long ntiles = (long long)ntm * ntn;
-  const int nk = (a.K + BK - 1) / BK;
+  const int splits = SPLITK_ ? a.splits : 1;
+  const long long ntiles = (long long)ntm * ntn * splits;
+  // K steps of one split (the host makes splits divide the step count)
+  const int nk = (a.K + BK - 1) / BK / splits;
+  // queue entry t: output tile t / splits (N-fastest within a row block), split t % splits
+  auto decode = [&](long long t, int& m0, int& n0, int& kb0, int& split) {
+    const long long mn = SPLITK_ ? t / splits : t;
+    split = SPLITK_ ? (int)(t % splits) : 0;
+    m0 = (int)(mn / ntn) * BM;
+    n0 = (int)(mn % ntn) * BN_;
+    kb0 = split * nk;
+  };
   const long long rounds = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
   if (threadIdx.x == 0) {
@@ -151,9 +167,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       long long it = 0;
       bool ok = true;
       for (long long rd = 0; rd < rounds && ok; ++rd) {
-        const long long t = blockIdx.x + rd * gridDim.x;
-        const int m0 = (int)(t / ntn) * BM, n0 = (int)(t % ntn) * BN_;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        int m0, n0, kb0, split;
+        decode(blockIdx.x + rd * gridDim.x, m0, n0, kb0, split);
+        for (int kb = kb0; kb < kb0 + nk; ++kb, ++it) {
           const int s = (int)(it % NS);
           if (!mbar_wait(&empty[s], (uint32_t)((it / NS) & 1) ^ 1u, a.err)) { ok = false; break; }
           mbar_arrive_expect_tx(&full[s], Cfg::TA + Cfg::TB);
@@ -198,8 +214,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     constexpr int HW = BN_ / 4;                              // columns per epilogue warp
     bool ok = true;
     for (long long rd = 0; rd < rounds && ok; ++rd) {
-      const long long t = blockIdx.x + rd * gridDim.x;
-      const int m0 = (int)(t / ntn) * BM, n0 = (int)(t % ntn) * BN_;
+      int m0, n0, kb0, split;
+      decode(blockIdx.x + rd * gridDim.x, m0, n0, kb0, split);
       const int b = (int)(rd & 1);
       if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (uint32_t)((rd >> 1) & 1), a.err))) { ok = false; break; }
       tc_fence_after();
@@ -261,7 +277,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             }
           }
         } else if (rv) {
-          float* out = a.C + (int64_t)row * a.ldc + col;
+          float* out = a.C + (SPLITK_ ? split * a.split_stride : 0) + (int64_t)row * a.ldc + col;
           float v[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j)
@@ -288,9 +304,22 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 
 }  // namespace
 
+template <int BN_, bool SPLITK_>
+static int launch_persistent(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, unsigned grid,
+                             cudaStream_t stream) {
+  static bool attr = false;
+  if (!attr) {
+    CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_persistent<BN_, SPLITK_>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, PersistCfg<BN_>::SMEM));
+    attr = true;
+  }
+  gemm_bf16_persistent<BN_, SPLITK_><<<grid, kPersistThreads, PersistCfg<BN_>::SMEM, stream>>>(ta, tb, g);
+  return CHEM_OK;
+}
+
 static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, void* Cb, int gelu,
                        int64_t ldc, const float* bias, int M, int N, int K, int* err, cudaStream_t stream,
-                       float* Cz = nullptr) {
+                       float* Cz = nullptr, int splits = 1, int64_t split_stride = 0) {
   if (M < BM || N < BN || K <= 0 || !A || !B || (!C && !Cb) || !err) {
     set_error("gemm_bf16: bad arguments (M=%d N=%d K=%d; M and N must be >= 128)", M, N, K);
     return CHEM_EINVAL;
@@ -305,37 +334,32 @@ static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, f
   int vec = (obase % 16 == 0 && opitch % 16 == 0) ? 1 : 0;
   if (Cz && ((uintptr_t)Cz % 16 != 0 || (ldc * 4) % 16 != 0)) vec = 0;
   GemmArgs g{C, (__nv_bfloat16*)Cb, Cz, gelu, vec, bias, M, N, K, ldc, err};
-  // persistent kernel, 256-column tiles unless 128-column tiles pad N less
-  const int pad128 = (N + 127) / 128 * 128 - N, pad256 = (N + 255) / 256 * 256 - N;
-  const int bn = (N >= 256 && pad256 <= pad128) ? 256 : 128;
+  g.splits = splits;
+  g.split_stride = split_stride;
   static int sms = 0;
   if (!sms) {
     int dev = 0;
     CHEM_CUDA_TRY(cudaGetDevice(&dev));
     CHEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  const long long ntiles = (long long)((M + BM - 1) / BM) * ((N + bn - 1) / bn);
+  // persistent kernel, 256-column tiles unless 128-column tiles pad N less, or unless 256-column
+  // tiles would leave SMs without a tile (small products: more, smaller tiles finish sooner)
+  const int pad128 = (N + 127) / 128 * 128 - N, pad256 = (N + 255) / 256 * 256 - N;
+  int bn = (N >= 256 && pad256 <= pad128) ? 256 : 128;
+  if (bn == 256 && (long long)((M + BM - 1) / BM) * ((N + 255) / 256) * splits < sms) bn = 128;
+  const long long ntiles = (long long)((M + BM - 1) / BM) * ((N + bn - 1) / bn) * splits;
   const unsigned grid = (unsigned)std::min<long long>(ntiles, sms);
   if (bn == 256) {
     CUtensorMap tb2;
     rc = make_tmap_bf16(&tb2, B, N, K, ldb, 256, BK);
     if (rc) return rc;
-    static bool attr256 = false;
-    if (!attr256) {
-      CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_persistent<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         PersistCfg<256>::SMEM));
-      attr256 = true;
-    }
-    gemm_bf16_persistent<256><<<grid, kPersistThreads, PersistCfg<256>::SMEM, stream>>>(ta, tb2, g);
+    rc = splits > 1 ? launch_persistent<256, true>(ta, tb2, g, grid, stream)
+                    : launch_persistent<256, false>(ta, tb2, g, grid, stream);
   } else {
-    static bool attr128 = false;
-    if (!attr128) {
-      CHEM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_persistent<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         PersistCfg<128>::SMEM));
-      attr128 = true;
-    }
-    gemm_bf16_persistent<128><<<grid, kPersistThreads, PersistCfg<128>::SMEM, stream>>>(ta, tb, g);
+    rc = splits > 1 ? launch_persistent<128, true>(ta, tb, g, grid, stream)
+                    : launch_persistent<128, false>(ta, tb, g, grid, stream);
   }
+  if (rc) return rc;
   CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
 }
@@ -343,6 +367,20 @@ static int gemm_launch(const void* A, int64_t lda, const void* B, int64_t ldb, f
 int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
               const float* bias, int M, int N, int K, int* err, cudaStream_t stream) {
   return gemm_launch(A, lda, B, ldb, C, nullptr, 0, ldc, bias, M, N, K, err, stream);
+}
+
+// Split-K product for short, deep shapes (training's weight gradients: a few output tiles, K =
+// the batch): split s of `splits` multiplies over K steps [s, s + 1) * K / splits and writes its
+// FP32 partial [M x N] (pitch ldc) to Cparts + s * split_stride; the caller adds the partials.
+// The number of 64-wide K steps must be a multiple of splits.
+int gemm_bf16_splitk(const void* A, int64_t lda, const void* B, int64_t ldb, float* Cparts, int64_t ldc,
+                     int64_t split_stride, int splits, int M, int N, int K, int* err, cudaStream_t stream) {
+  if (splits < 1 || ((K + BK - 1) / BK) % splits != 0 || split_stride < (int64_t)M * ldc) {
+    set_error("gemm_bf16_splitk: splits must divide the K steps (%d) and the stride hold M x ldc", (K + BK - 1) / BK);
+    return CHEM_EINVAL;
+  }
+  return gemm_launch(A, lda, B, ldb, Cparts, nullptr, 0, ldc, nullptr, M, N, K, err, stream, nullptr, splits,
+                     split_stride);
 }
 
 int gemm_bf16_act(const void* A, int64_t lda, const void* B, int64_t ldb, void* Cb, int64_t ldc,

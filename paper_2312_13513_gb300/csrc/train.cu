@@ -37,6 +37,8 @@ int gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, 
               const float* bias, int M, int N, int K, int* err, cudaStream_t stream);
 int gemm_bf16_gelu2(const void* A, int64_t lda, const void* B, int64_t ldb, float* Cz, void* Cb, int64_t ldc,
                     const float* bias, int M, int N, int K, int* err, cudaStream_t stream);
+int gemm_bf16_splitk(const void* A, int64_t lda, const void* B, int64_t ldb, float* Cparts, int64_t ldc,
+                     int64_t split_stride, int splits, int M, int N, int K, int* err, cudaStream_t stream);
 }
 
 using namespace chem;
@@ -121,6 +123,16 @@ __global__ void k_colsum_part(const float* A, double* part, int R, int C) {
     double t = 0.0;
     for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
     part[(int64_t)blockIdx.y * C + c] = t;
+  }
+}
+
+// out[i] = sum over s of parts[s * stride + i], in the order s = 0, 1, ...: the split-K partial
+// products of a weight gradient added deterministically
+__global__ void k_sum_parts(const float* parts, float* out, int64_t n, int splits, int64_t stride) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float v = parts[i];
+    for (int s = 1; s < splits; ++s) v += parts[s * stride + i];
+    out[i] = v;
   }
 }
 
@@ -312,6 +324,8 @@ struct chem_trainer_s {
   float* Z[MAXL];                  // pre-activations [B x out_pad]
   __nv_bfloat16* A[MAXL];          // A[0] = caller's input, A[l] = bf16(GELU(Z[l-1]))
   float *dA, *dZf;
+  float* dWparts;                  // split-K partials of the weight gradients (null: no layer splits)
+  int splitsW[MAXL];               // K splits of each layer's weight-gradient product
   double* colpart;                 // row-block partial column sums [B / 64 x max width]
   __nv_bfloat16 *dZb, *dZt, *At;
   int* err;
@@ -410,6 +424,25 @@ extern "C" int chem_mlp_trainer_create_layers(int n_in, int n_out, int n_hidden,
   }
   void* p;
   if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 4), t->dA = (float*)p;
+  // weight gradients dW = dZ^T A have few output tiles and K = batch: split K over the SMs (a
+  // power of two dividing the 64-wide K steps, splits x tiles at most the SM count) and add the
+  // partials in a fixed order
+  if (!rc) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nk = (batch + 63) / 64;
+    size_t parts = 0;
+    for (int l = 0; l < NL; ++l) {
+      const long long tiles = (long long)((t->out_pad[l] + 127) / 128) * ((t->in_pad[l] + 127) / 128);
+      int sp = 1;
+      while (nk % (2 * sp) == 0 && tiles * 2 * sp <= sms) sp *= 2;
+      t->splitsW[l] = sp;
+      if (sp > 1) parts = std::max(parts, (size_t)sp * t->out_pad[l] * t->in_pad[l]);
+    }
+    t->dWparts = nullptr;
+    if (parts) rc = tr_alloc(t, &p, parts * 4), t->dWparts = (float*)p;
+  }
   if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 4), t->dZf = (float*)p;
   if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 2), t->dZb = (__nv_bfloat16*)p;
   if (!rc) rc = tr_alloc(t, &p, (size_t)batch * maxw * 2), t->dZt = (__nv_bfloat16*)p;
@@ -462,8 +495,16 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
     // dZ^T and A^T (batch contiguous) for the weight gradient
     k_transpose<<<dim3((nout + 31) / 32, (B + 31) / 32), tb, 0, st>>>(t->dZb, t->dZt, B, nout);
     k_transpose<<<dim3((nin + 31) / 32, (B + 31) / 32), tb, 0, st>>>(t->A[l], t->At, B, nin);
-    int rc = gemm_bf16(t->dZt, B, t->At, B, t->dW[l], nin, nullptr, nout, nin, B, t->err, st);
-    if (rc) return rc;
+    int rc;
+    if (t->splitsW[l] > 1) {
+      const int64_t n = (int64_t)nout * nin;
+      rc = gemm_bf16_splitk(t->dZt, B, t->At, B, t->dWparts, nin, n, t->splitsW[l], nout, nin, B, t->err, st);
+      if (rc) return rc;
+      k_sum_parts<<<grid_for(n), 256, 0, st>>>(t->dWparts, t->dW[l], n, t->splitsW[l], n);
+    } else {
+      rc = gemm_bf16(t->dZt, B, t->At, B, t->dW[l], nin, nullptr, nout, nin, B, t->err, st);
+      if (rc) return rc;
+    }
     if (l == 0) k_fold_split_grad<<<(nout + 127) / 128, 128, 0, st>>>(t->dW[0], nout, nin, t->nin);
     {
       const int nparts = (B + kColRows - 1) / kColRows;
