@@ -91,19 +91,41 @@ __global__ void k_mse_grad(const float* out, const float* target, float* dZf, __
   }
 }
 
-// out[c * R + r] = in[r * C + c] (BF16), 32 x 32 tiles through shared memory
-__global__ void k_transpose(const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C) {
-  __shared__ __nv_bfloat16 t[32][33];
+// several BF16 transposes in one launch: blockIdx.z selects the job (out[c * R + r] = in[r * C + c])
+struct TransposeJob {
+  const __nv_bfloat16* in;
+  __nv_bfloat16* out;
+  int R, C;
+};
+struct TransposeSet {
+  TransposeJob j[MAXL];
+  int n;
+};
+
+__global__ void k_transpose_set(const __grid_constant__ TransposeSet S) {
+  if ((int)blockIdx.z >= S.n) return;
+  const TransposeJob& J = S.j[blockIdx.z];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  if (r0 >= J.R || c0 >= J.C) return;                // the whole block: before the barrier
+  __shared__ __nv_bfloat16 t[32][33];
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int r = r0 + i, c = c0 + threadIdx.x;
-    if (r < R && c < C) t[i][threadIdx.x] = in[(int64_t)r * C + c];
+    if (r < J.R && c < J.C) t[i][threadIdx.x] = J.in[(int64_t)r * J.C + c];
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int c = c0 + i, r = r0 + threadIdx.x;
-    if (r < R && c < C) out[(int64_t)c * R + r] = t[threadIdx.x][i];
+    if (r < J.R && c < J.C) J.out[(int64_t)c * J.R + r] = t[threadIdx.x][i];
   }
+}
+
+void launch_transposes(const TransposeSet& S, cudaStream_t st) {
+  int gx = 1, gy = 1;
+  for (int k = 0; k < S.n; ++k) {
+    gx = std::max(gx, (S.j[k].C + 31) / 32);
+    gy = std::max(gy, (S.j[k].R + 31) / 32);
+  }
+  k_transpose_set<<<dim3(gx, gy, S.n), dim3(32, 8), 0, st>>>(S);
 }
 
 // column sums of a [R x C] FP32 matrix, in two deterministic passes spread over the whole GPU:
@@ -148,19 +170,39 @@ __global__ void k_colsum_finish(const double* part, float* s, int nparts, int C)
 
 // Adam on a [rows x cols] parameter block (cols = 1 for biases); writes the BF16 copy of W if given
 // (its transpose follows by the tiled k_transpose)
-__global__ void k_adam(float* W, const float* G, float* m, float* v, __nv_bfloat16* Wb, __nv_bfloat16* Wt,
-                       int rows, int cols, const float* coef, float b1, float b2, float eps) {
+// Adam over every parameter block of the network in one launch: block b of the grid serves the
+// segment whose first block is the last one <= b; each segment is one weight matrix or bias
+// vector (W, its gradient G, moments m and v; Wb: the BF16 copy of W to write, or null).
+struct AdamSeg {
+  float* W;
+  const float* G;
+  float* m;
+  float* v;
+  __nv_bfloat16* Wb;
+  int64_t n;
+  int block0;
+};
+struct AdamSet {
+  AdamSeg s[2 * MAXL];
+  int n;
+};
+
+__global__ void k_adam_set(const __grid_constant__ AdamSet S, const float* coef, float b1, float b2, float eps) {
+  int k = 0;
+  while (k + 1 < S.n && S.s[k + 1].block0 <= (int)blockIdx.x) ++k;
+  const AdamSeg& q = S.s[k];
+  const int nb = (k + 1 < S.n ? S.s[k + 1].block0 : (int)gridDim.x) - q.block0;
   const float lr = coef[0], c1 = coef[1], c2 = coef[2];
-  const int64_t n = (int64_t)rows * cols;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float g = G[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * g;
-    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
-    m[i] = mi;
-    v[i] = vi;
-    const float w = W[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    W[i] = w;
-    if (Wb) Wb[i] = __float2bfloat16_rn(w);
+  for (int64_t i = (int64_t)(blockIdx.x - q.block0) * blockDim.x + threadIdx.x; i < q.n;
+       i += (int64_t)nb * blockDim.x) {
+    const float g = q.G[i];
+    const float mi = b1 * q.m[i] + (1.0f - b1) * g;
+    const float vi = b2 * q.v[i] + (1.0f - b2) * g * g;
+    q.m[i] = mi;
+    q.v[i] = vi;
+    const float w = q.W[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    q.W[i] = w;
+    if (q.Wb) q.Wb[i] = __float2bfloat16_rn(w);
   }
 }
 
@@ -489,12 +531,16 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
   CHEM_CUDA_TRY(cudaMemsetAsync(t->loss, 0, sizeof(double), st));
   k_mse_grad<<<std::min(grid_for((int64_t)B * PADIO), 1024u), 256, 0, st>>>(t->Z[NL - 1], target, t->dZf, t->dZb,
                                                                          t->loss, B, t->nout, PADIO);
-  dim3 tb(32, 8);
   for (int l = NL - 1; l >= 0; --l) {
     const int nout = t->out_pad[l], nin = t->in_pad[l];
     // dZ^T and A^T (batch contiguous) for the weight gradient
-    k_transpose<<<dim3((nout + 31) / 32, (B + 31) / 32), tb, 0, st>>>(t->dZb, t->dZt, B, nout);
-    k_transpose<<<dim3((nin + 31) / 32, (B + 31) / 32), tb, 0, st>>>(t->A[l], t->At, B, nin);
+    {
+      TransposeSet T{};
+      T.j[0] = TransposeJob{t->dZb, t->dZt, B, nout};
+      T.j[1] = TransposeJob{t->A[l], t->At, B, nin};
+      T.n = 2;
+      launch_transposes(T, st);
+    }
     int rc;
     if (t->splitsW[l] > 1) {
       const int64_t n = (int64_t)nout * nin;
@@ -526,16 +572,27 @@ extern "C" int chem_mlp_backward(chem_trainer_t t, const float* target, double* 
 static int adam_step(chem_trainer_t t, const float* lr_dev, float lr, float beta1, float beta2, float eps,
                      cudaStream_t st) {
   k_adam_prep<<<1, 1, 0, st>>>(t->d_step, t->d_coef, lr_dev, lr, beta1, beta2);
+  // every weight matrix and bias vector in one launch (BF16 copies of the hidden weights written
+  // on the way), then the transposed copies the backward pass multiplies with and the first
+  // layer's split copy
+  AdamSet A{};
+  int blocks = 0;
+  auto add = [&](float* W, const float* G, float* m, float* v, __nv_bfloat16* Wb, int64_t n) {
+    A.s[A.n] = AdamSeg{W, G, m, v, Wb, n, blocks};
+    blocks += (int)std::min<int64_t>((n + 255) / 256, 1024);
+    ++A.n;
+  };
   for (int l = 0; l < t->nl; ++l) {
     const int r = t->out_pad[l], c = t->in_pad[l];
-    k_adam<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[l], t->dW[l], t->mW[l], t->vW[l],
-                                                      l == 0 ? nullptr : t->Wb[l], nullptr, r, c, t->d_coef, beta1,
-                                                      beta2, eps);
-    if (l > 0) k_transpose<<<dim3((c + 31) / 32, (r + 31) / 32), dim3(32, 8), 0, st>>>(t->Wb[l], t->Wt[l], r, c);
-    if (l == 0) k_split_bf16<<<grid_for((int64_t)r * c), 256, 0, st>>>(t->W[0], t->Wb[0], r, c, t->nin);
-    k_adam<<<grid_for(r), 256, 0, st>>>(t->b[l], t->db[l], t->mb[l], t->vb[l], nullptr, nullptr, r, 1, t->d_coef,
-                                        beta1, beta2, eps);
+    add(t->W[l], t->dW[l], t->mW[l], t->vW[l], l == 0 ? nullptr : t->Wb[l], (int64_t)r * c);
+    add(t->b[l], t->db[l], t->mb[l], t->vb[l], nullptr, r);
   }
+  k_adam_set<<<blocks, 256, 0, st>>>(A, t->d_coef, beta1, beta2, eps);
+  TransposeSet T{};
+  for (int l = 1; l < t->nl; ++l) T.j[T.n++] = TransposeJob{t->Wb[l], t->Wt[l], t->out_pad[l], t->in_pad[l]};
+  if (T.n) launch_transposes(T, st);
+  k_split_bf16<<<grid_for((int64_t)t->out_pad[0] * t->in_pad[0]), 256, 0, st>>>(t->W[0], t->Wb[0], t->out_pad[0],
+                                                                                 t->in_pad[0], t->nin);
   CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
 }
