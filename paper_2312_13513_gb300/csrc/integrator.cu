@@ -717,17 +717,106 @@ __device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* perm, 
   return true;
 }
 
+// The two triangular sweeps of lu_solve for a group of one or more whole warps and at most 64
+// unknowns: the group's first warp alone runs them with the rows in registers, two per lane, and
+// hands each finished unknown to the other lanes by a shuffle, so no row ends in a group barrier;
+// the other warps wait at one barrier at the end.  The forward sweep keeps the last min(N, 32)
+// rows in one register (lane l: row N - 32 + l) and the backward sweep the first 32 (lane l: row
+// l), so that while at most 32 rows are open each step is one FMA instruction.  Every row sees
+// the same operations in the same order as in the shared-memory sweeps below (both write the
+// updates as explicit FMAs), so the two sweeps give bitwise the same solution.
+template <int G>
+__device__ void lu_solve_regs(const Grp<G>& g, const double* M, int N, int LD, const int* perm,
+                              const double* invd, double* b, double* t) {
+  if (g.tid < 32) {
+    constexpr unsigned F = 0xffffffffu;
+    const int l = g.tid;
+    // forward sweep, L y = P b (unit diagonal): set B rows [0, nb), set A rows [nb, N)
+    const int nb = N > 32 ? N - 32 : 0, na = N - nb;
+    const bool hb = l < nb, ha = l < na;
+    const int rb = hb ? perm[l] : 0, ra = ha ? perm[nb + l] : 0;
+    const double* Lb = M + rb * LD;
+    const double* La = M + ra * LD;
+    double tb = hb ? b[rb] : 0.0;
+    double ta = ha ? b[ra] : 0.0;
+    for (int k = 0; k < nb - 1; ++k) {             // rows of both sets still open
+      const double xk = __shfl_sync(F, tb, k);
+      if (hb && l > k) tb = fma(-Lb[k], xk, tb);
+      if (ha) ta = fma(-La[k], xk, ta);
+    }
+    if (nb > 0) {                                  // the last row of set B
+      const double xk = __shfl_sync(F, tb, nb - 1);
+      if (ha) ta = fma(-La[nb - 1], xk, ta);
+    }
+#pragma unroll 4
+    for (int k = nb; k < N - 1; ++k) {
+      const double xk = __shfl_sync(F, ta, k - nb);
+      if (ha && nb + l > k) ta = fma(-La[k], xk, ta);
+    }
+    // the backward sweep's layout: set 1 rows [0, min(N, 32)), set 2 rows [32, N)
+    if (hb) t[l] = tb;
+    if (ha) t[nb + l] = ta;
+    __syncwarp();
+    const int n1 = N < 32 ? N : 32;
+    const bool h1 = l < n1, h2 = 32 + l < N;
+    double u1 = h1 ? t[l] : 0.0;
+    double u2 = h2 ? t[32 + l] : 0.0;
+    const double* U1 = M + (h1 ? perm[l] : 0) * LD;
+    const double* U2 = M + (h2 ? perm[32 + l] : 0) * LD;
+    const double d1 = h1 ? invd[l] : 0.0, d2 = h2 ? invd[32 + l] : 0.0;
+    // U x = y, column by column; a row is final once scaled by the reciprocal of its pivot
+    if (N > 32) {
+      if (32 + l == N - 1) u2 *= d2;
+    } else {
+      if (l == N - 1) u1 *= d1;
+    }
+    for (int k = N - 1; k > 32; --k) {             // rows of both sets still open
+      const double xk = __shfl_sync(F, u2, k - 32);
+      if (32 + l < k) {
+        double v = fma(-U2[k], xk, u2);
+        if (32 + l == k - 1) v *= d2;
+        u2 = v;
+      }
+      u1 = fma(-U1[k], xk, u1);
+    }
+    if (N > 32) {                                  // the first row of set 2
+      const double xk = __shfl_sync(F, u2, 0);
+      double v = fma(-U1[32], xk, u1);
+      if (l == 31) v *= d1;
+      u1 = v;
+    }
+#pragma unroll 4
+    for (int k = n1 - 1; k > 0; --k) {
+      const double xk = __shfl_sync(F, u1, k);
+      if (l < k) {
+        double v = fma(-U1[k], xk, u1);
+        if (l == k - 1) v *= d1;
+        u1 = v;
+      }
+    }
+    if (h1) b[l] = u1;
+    if (h2) b[32 + l] = u2;
+  }
+  g.sync();
+}
+
 // Solves A x = b with the factors of lu_factor; b (length N) is overwritten with x.  t: N-double
 // scratch holding the permuted right-hand side during the two triangular sweeps.  The division
 // by the diagonal of U happens once per row, in the thread that finishes that row.
 template <int G>
 __device__ void lu_solve(const Grp<G>& g, const double* M, int N, int LD, const int* perm,
                          const double* invd, double* b, double* t) {
+  if constexpr (G >= 32) {
+    if (N <= 64) {
+      lu_solve_regs<G>(g, M, N, LD, perm, invd, b, t);
+      return;
+    }
+  }
   for (int i = g.tid; i < N; i += G) t[i] = b[perm[i]];
   g.sync();
   for (int k = 0; k < N - 1; ++k) {          // L y = P b (unit diagonal)
     const double xk = t[k];
-    for (int i = k + 1 + g.tid; i < N; i += G) t[i] -= M[perm[i] * LD + k] * xk;
+    for (int i = k + 1 + g.tid; i < N; i += G) t[i] = fma(-M[perm[i] * LD + k], xk, t[i]);
     g.sync();
   }
   if (g.tid == 0) t[N - 1] *= invd[N - 1];
@@ -736,7 +825,7 @@ __device__ void lu_solve(const Grp<G>& g, const double* M, int N, int LD, const 
     const double xk = t[k];
     if (g.tid == 0) b[k] = xk;
     for (int i = g.tid; i < k; i += G) {
-      double v = t[i] - M[perm[i] * LD + k] * xk;
+      double v = fma(-M[perm[i] * LD + k], xk, t[i]);
       if (i == k - 1) v *= invd[i];
       t[i] = v;
     }
