@@ -706,13 +706,96 @@ __device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* perm, 
       const int q = div_by(e, magic);
       const int i = k + 1 + q, j = k + 1 + (e - q * n);
       const int ph = perm[i];
-      const double v = M[ph * LD + j] - M[ph * LD + k] * M[pk * LD + j];
+      const double v = fma(-M[ph * LD + k], M[pk * LD + j], M[ph * LD + j]);
       M[ph * LD + j] = v;
       if (j == k + 1) argmax_merge(best, bi, pivot_key(v), i);
     }
     warp_argmax<G>(g, best, bi);
     if (G > 32 && (g.tid & 31) == 0) { rkey[g.tid >> 5] = best; ridx[g.tid >> 5] = bi; }
     g.sync();
+  }
+  return true;
+}
+
+// LU factorisation for a group of several warps and at most 64 unknowns, one group barrier per
+// step: in step k the first warp (the panel warp) finishes column k + 1 of the trailing update,
+// chooses the pivot of step k + 1 among those values, forms its reciprocal and the multipliers
+// of column k + 1, while the other warps update columns k + 2 .. N - 1.  The logical-to-physical
+// row map is double-buffered (pbuf[0 .. N) for even steps, pbuf[N .. 2N) for odd ones), so the
+// panel warp writes the next step's row swap while the other warps still read this step's map;
+// the singular flag is double-buffered the same way.  Each element sees the same operations as
+// in lu_factor (explicit FMAs in both) and the pivot choice is the same (largest magnitude, the
+// lowest logical row on ties), so the factors, perm and invd are bitwise lu_factor's.
+template <int G>
+__device__ bool lu_factor_panel(const Grp<G>& g, double* M, int N, int LD, int* perm,
+                                double* invd, int* pbuf, int* sing) {
+  static_assert(G > 32, "groups of several warps");
+  constexpr unsigned F = 0xffffffffu;
+  const bool panel = g.tid < 32;
+  const int l = g.tid;
+  if (panel) {                                      // the pivot of step 0
+    unsigned long long best = 0ull;
+    int bi = 0;
+    for (int i = l; i < N; i += 32) argmax_merge(best, bi, pivot_key(M[i * LD]), i);
+    warp_argmax<G>(g, best, bi);
+    for (int i = l; i < N; i += 32) pbuf[i] = i == 0 ? bi : (i == bi ? 0 : i);
+    if (best != 0ull) {
+      const double ip = 1.0 / M[bi * LD];
+      for (int i = 1 + l; i < N; i += 32) {
+        const int ph = i == bi ? 0 : i;
+        M[ph * LD] *= ip;
+      }
+      if (l == 0) { invd[0] = ip; perm[0] = bi; }
+    }
+    if (l == 0) sing[1] = best == 0ull;
+  }
+  g.sync();
+  if (sing[1]) return false;
+  for (int k = 0; k < N - 1; ++k) {
+    const int* Pk = pbuf + (k & 1) * N;
+    const int pk = Pk[k];
+    const int n = N - k - 1;
+    if (panel) {
+      int* Pn = pbuf + ((k + 1) & 1) * N;
+      const int i0 = k + 1 + l, i1 = k + 33 + l;
+      const double ukj = M[pk * LD + k + 1];
+      unsigned long long best = 0ull;
+      int bi = k + 1;
+      double v0 = 0.0, v1 = 0.0;
+      int ph0 = -1, ph1 = -1;
+      if (i0 < N) {
+        ph0 = Pk[i0];
+        v0 = fma(-M[ph0 * LD + k], ukj, M[ph0 * LD + k + 1]);
+        argmax_merge(best, bi, pivot_key(v0), i0);
+      }
+      if (i1 < N) {
+        ph1 = Pk[i1];
+        v1 = fma(-M[ph1 * LD + k], ukj, M[ph1 * LD + k + 1]);
+        argmax_merge(best, bi, pivot_key(v1), i1);
+      }
+      warp_argmax<G>(g, best, bi);
+      const int pnew = Pk[bi], pold = Pk[k + 1];
+      for (int i = k + 1 + l; i < N; i += 32) Pn[i] = i == k + 1 ? pnew : (i == bi ? pold : Pk[i]);
+      if (best != 0ull) {
+        const int src = bi - (k + 1);
+        const double piv = __shfl_sync(F, src < 32 ? v0 : v1, src & 31);
+        const double ip = 1.0 / piv;
+        if (ph0 >= 0) M[ph0 * LD + k + 1] = ph0 == pnew ? v0 : v0 * ip;
+        if (ph1 >= 0) M[ph1 * LD + k + 1] = ph1 == pnew ? v1 : v1 * ip;
+        if (l == 0) { invd[k + 1] = ip; perm[k + 1] = pnew; }
+      }
+      if (l == 0) sing[k & 1] = best == 0ull;
+    } else if (n > 1) {                             // columns k + 2 .. N - 1
+      const int m = n - 1;
+      const unsigned magic = div_magic((unsigned)m);
+      for (int e = g.tid - 32; e < n * m; e += G - 32) {
+        const int q = div_by(e, magic);
+        const int ph = Pk[k + 1 + q], j = k + 2 + (e - q * m);
+        M[ph * LD + j] = fma(-M[ph * LD + k], M[pk * LD + j], M[ph * LD + j]);
+      }
+    }
+    g.sync();
+    if (sing[k & 1]) return false;
   }
   return true;
 }
@@ -901,7 +984,14 @@ __device__ bool rodas4_attempt(const Grp<G>& g, const MechView& m, const WsPtr& 
   if (kMulti) { ig = w.sc[S_IG]; invh = w.sc[S_INVH]; }
   for (int i = g.tid; i < N; i += G) w.M[i * LD + i] += ig;   // M = I / (gamma h) - J
   g.sync();
-  if (!lu_factor<G>(g, w.M, N, LD, w.perm, w.invd, w.red)) return false;
+  bool regular;
+  if constexpr (G > 32) {
+    regular = N <= 64 ? lu_factor_panel<G>(g, w.M, N, LD, w.perm, w.invd, (int*)w.ys, (int*)w.red)
+                      : lu_factor<G>(g, w.M, N, LD, w.perm, w.invd, w.red);
+  } else {
+    regular = lu_factor<G>(g, w.M, N, LD, w.perm, w.invd, w.red);
+  }
+  if (!regular) return false;
   for (int s = 0; s < 6; ++s) {
     const double* src = w.f0;
     if (s > 0) {
