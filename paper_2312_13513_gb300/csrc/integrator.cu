@@ -720,12 +720,21 @@ __device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* perm, 
 // LU factorisation for a group of several warps and at most 64 unknowns, one group barrier per
 // step: in step k the first warp (the panel warp) finishes column k + 1 of the trailing update,
 // chooses the pivot of step k + 1 among those values, forms its reciprocal and the multipliers
-// of column k + 1, while the other warps update columns k + 2 .. N - 1.  The logical-to-physical
+// of column k + 1, while the other warps update columns k + 2 .. N - 1 (the panel warp takes the
+// last part of those elements once its pivot work is done).  The logical-to-physical
 // row map is double-buffered (pbuf[0 .. N) for even steps, pbuf[N .. 2N) for odd ones), so the
 // panel warp writes the next step's row swap while the other warps still read this step's map;
 // the singular flag is double-buffered the same way.  Each element sees the same operations as
 // in lu_factor (explicit FMAs in both) and the pivot choice is the same (largest magnitude, the
 // lowest logical row on ties), so the factors, perm and invd are bitwise lu_factor's.
+// Elements [0, E1) of a step's update of columns k + 2 .. go to the warps other than the panel
+// warp, [E1, E) to the panel warp after its pivot work: its per-lane share of a balanced split
+// less 8 elements, the pivot work's measured worth (shares of 3, 12 and 16 elements measured
+// slower on the CH4 LES field).
+__device__ __forceinline__ int panel_split(int E, int G) {
+  return max(E - max((E * 32) / G - 32 * 8, 0), 0);
+}
+
 template <int G>
 __device__ bool lu_factor_panel(const Grp<G>& g, double* M, int N, int LD, int* perm,
                                 double* invd, int* pbuf, int* sing) {
@@ -785,10 +794,21 @@ __device__ bool lu_factor_panel(const Grp<G>& g, double* M, int N, int LD, int* 
         if (l == 0) { invd[k + 1] = ip; perm[k + 1] = pnew; }
       }
       if (l == 0) sing[k & 1] = best == 0ull;
+      if (n > 1) {                                  // then its share of the other columns
+        const int m = n - 1, E = n * m;
+        const int E1 = panel_split(E, G);
+        const unsigned magic = div_magic((unsigned)m);
+        for (int e = E1 + l; e < E; e += 32) {
+          const int q = div_by(e, magic);
+          const int ph = Pk[k + 1 + q], j = k + 2 + (e - q * m);
+          M[ph * LD + j] = fma(-M[ph * LD + k], M[pk * LD + j], M[ph * LD + j]);
+        }
+      }
     } else if (n > 1) {                             // columns k + 2 .. N - 1
-      const int m = n - 1;
+      const int m = n - 1, E = n * m;
+      const int E1 = panel_split(E, G);
       const unsigned magic = div_magic((unsigned)m);
-      for (int e = g.tid - 32; e < n * m; e += G - 32) {
+      for (int e = g.tid - 32; e < E1; e += G - 32) {
         const int q = div_by(e, magic);
         const int ph = Pk[k + 1 + q], j = k + 2 + (e - q * m);
         M[ph * LD + j] = fma(-M[ph * LD + k], M[pk * LD + j], M[ph * LD + j]);
