@@ -231,6 +231,10 @@ def run_case(args):
     import paper_2312_13513_gb300 as cg
     from synth.mechanism import ch4_mechanism, h2_mechanism
     from synth.states import les_field, load_table
+    if args.case == "h2small":
+        print(json.dumps(dict(case=args.case, **extra_h2_small(cg.fp64_fma_peak(), n=args.cells, reps=args.steps))),
+              flush=True)
+        return
     if args.case == "fvm":
         side = max(2, int(round(args.cells ** (1.0 / 3.0))))
         m, kw = _fvm_inputs(side)
@@ -403,6 +407,66 @@ def extra_ch4(fp64_peak, steps=2, oracle_sample=4096):
             "fp64_tflops_plain": flo / t / 1e12, "fp64_tflops_folded": folded / t / 1e12,
             "transcendental_weight": fl.TRANSCENDENTAL_FLOPS, "attempts_mean": att / n})
     return out
+
+
+def small_h2_states(n=4096, seed=12345):
+    """The small H2 case: n H2/air mixing states (Z ~ U[0, 1], T ~ U[900, 2200] K, 1 atm), half of
+    them first reacted by this integrator for log-uniform times in [1e-7, 1e-3] s (eight bins of
+    the drawn time, each advanced by its bin's geometric centre).  Returns device tensors."""
+    import torch
+    import paper_2312_13513_gb300 as cg
+    from synth.mechanism import h2_mechanism
+    from synth.states import mixing_states
+    mech = h2_mechanism()
+    dm = cg.Mechanism(mech)
+    st = mixing_states(mech, n, seed)
+    T = torch.tensor(st["T"], device="cuda"); p = torch.tensor(st["p"], device="cuda")
+    Y = torch.tensor(np.ascontiguousarray(st["Y"]), device="cuda")
+    react = np.nonzero(st["react"])[0]
+    lt = np.log10(st["t_react"][react])
+    edges = np.linspace(-7.0, -3.0, 9)
+    bins = np.clip(np.searchsorted(edges, lt, side="right") - 1, 0, 7)
+    failed = 0
+    for b in range(8):
+        sel = react[bins == b]
+        if sel.size == 0:
+            continue
+        idx = torch.tensor(sel.astype(np.int32), device="cuda")
+        status = torch.zeros(n, dtype=torch.int8, device="cuda")
+        cg.advance(dm, T, p, Y, 10.0 ** (0.5 * (edges[b] + edges[b + 1])), RTOL, ATOL, idx=idx, status=status)
+        failed += int((status != 0).sum())
+    torch.cuda.synchronize()
+    return mech, dm, T, p, Y, failed
+
+
+def extra_h2_small(fp64_peak, n=4096, reps=10):
+    """Config 0: the small H2 case (4096 cells, dt = 1e-6 s).  Too few cells to fill the GPU (the
+    bench launch holds 80 two-thread groups = 80 cells per SM), so it is latency-bound: reported
+    with the share of the GPU's cell slots the launch can fill."""
+    import torch
+    from paper_2312_13513_gb300 import flops as fl
+    import paper_2312_13513_gb300 as cg
+    mech, dm, T0, p, Y0, failed = small_h2_states(n)
+    T, Y = T0.clone(), Y0.clone()
+    ns_ = torch.zeros(n, dtype=torch.int32, device="cuda"); nr_ = torch.zeros_like(ns_)
+    stream = torch.cuda.current_stream()
+
+    def run():
+        T.copy_(T0); Y.copy_(Y0)
+        cg.advance(dm, T, p, Y, 1e-6, RTOL, ATOL, nsub=ns_, nrej=nr_, stream=stream)
+
+    for _ in range(3):
+        run()
+    ms = sorted(_time_ms(run, stream, reps))
+    t = ms[len(ms) // 2] * 1e-3
+    acc = int(ns_.sum()); att = acc + int(nr_.sum())
+    _, _, folded = fl.launch_flops(mech, acc, att)
+    slots = torch.cuda.get_device_properties(0).multi_processor_count * 80
+    return {"workload": f"FP64 Rodas4, {n} H2/air mixing states (half pre-reacted by this integrator), "
+                        "dt=1e-6 s, two-thread group per cell",
+            "ms": t * 1e3, "cell_updates_per_s": n / t, "attempts_mean": att / n,
+            "fp64_frac_folded": folded / t / 1e12 / fp64_peak,
+            "cell_slot_occupancy": min(n, slots) / slots, "prereact_failed": failed}
 
 
 def extra_surrogate(peaks, steps=3):
@@ -917,9 +981,10 @@ def extra_serving(duration_s=10.0, seed=12349, duty=1.0 / 128.0, slice_ms=0.0):
 def summary(line):
     """The headline figures of every config in a few hundred bytes (the last key of the line)."""
     ex = line.get("extras", {})
-    c2, c3, c4 = ex.get("ch4_les", {}), ex.get("surrogate", {}), ex.get("serving", {})
+    c0, c2, c3, c4 = ex.get("h2_small", {}), ex.get("ch4_les", {}), ex.get("surrogate", {}), ex.get("serving", {})
     r = lambda v, d=4: None if v is None else round(float(v), d)
-    return {"cfg1_h2_cells_per_s": r(line["value"], 0), "cfg1_fp64_frac_folded": r(line["roofline"]["frac"]),
+    return {"cfg0_h2_small_ms": r(c0.get("ms"), 3), "cfg0_fp64_frac_folded": r(c0.get("fp64_frac_folded")),
+            "cfg1_h2_cells_per_s": r(line["value"], 0), "cfg1_fp64_frac_folded": r(line["roofline"]["frac"]),
             "cfg2_ch4_cells_per_s": r(c2.get("cell_updates_per_s"), 0),
             "cfg2_fp64_frac_plain": r(c2.get("fp64_frac_plain")), "cfg2_fp64_frac_folded": r(c2.get("fp64_frac_folded")),
             "cfg3_surrogate_cells_per_s": r(c3.get("surrogate_cell_updates_per_s"), 0),
@@ -939,7 +1004,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", choices=["h2", "ch4", "surrogate", "surrogate_ps", "transport", "fvm"], default=None,
+    ap.add_argument("--case", choices=["h2", "h2small", "ch4", "surrogate", "surrogate_ps", "transport", "fvm"],
+                    default=None,
                     help="time one kernel family on a small case (profiling)")
     ap.add_argument("--cells", type=int, default=65536)
     ap.add_argument("--group", type=int, default=0, help="threads per cell (profiling mode; 0 = auto)")
@@ -1114,6 +1180,7 @@ def main():
                          ("chemistry_thermo_step", extra_step),
                          ("thermo_transport", lambda: extra_transport(fp64_peak)),
                          ("serving", extra_serving),
+                         ("h2_small", lambda: extra_h2_small(fp64_peak)),
                          ("ch4_les", lambda: extra_ch4(fp64_peak)),
                          ("surrogate", lambda: extra_surrogate(_peaks()))):
             try:

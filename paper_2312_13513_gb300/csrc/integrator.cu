@@ -1370,10 +1370,25 @@ int launch_adv_t(const LaunchShape& s, const AdvanceParams& P, const chem_option
   if (per_sm < 1) { set_error("kernel does not fit on an SM"); return CHEM_EINVAL; }
   int64_t chunks = P.total_chunks;     // an upper bound when the count is read on the device
   int64_t grid = (int64_t)sms * per_sm;
-  if (opt && opt->max_ctas > 0) grid = std::min<int64_t>(grid, opt->max_ctas);
-  grid = std::min<int64_t>(grid, (chunks + s.groups - 1) / s.groups);
+  int threads = s.threads;
+  size_t smem = s.smem;
+  const bool shaped = opt && (opt->groups_per_cta > 0 || opt->max_ctas > 0);
+  if (!shaped && chunks < grid * s.groups) {
+    // fewer chunks than group slots: spread the groups over every SM (fewer groups per CTA)
+    // rather than filling a few SMs, so that a cell shares its SM's FP64 pipe with fewer others
+    const int unit = G < 32 ? 32 / G : 1;
+    int64_t gpc = (chunks + grid - 1) / grid;
+    gpc = std::max<int64_t>(unit, (gpc + unit - 1) / unit * unit);
+    gpc = std::min<int64_t>(gpc, s.groups);
+    threads = G * (int)gpc;
+    smem = s.smem - (size_t)s.ws.total * 8 * (size_t)(s.groups - gpc);
+    grid = (chunks + gpc - 1) / gpc;
+  } else {
+    if (opt && opt->max_ctas > 0) grid = std::min<int64_t>(grid, opt->max_ctas);
+    grid = std::min<int64_t>(grid, (chunks + s.groups - 1) / s.groups);
+  }
   if (grid < 1) grid = 1;
-  advance_kernel<G><<<(unsigned)grid, s.threads, s.smem, stream>>>(P);
+  advance_kernel<G><<<(unsigned)grid, threads, smem, stream>>>(P);
   CHEM_CUDA_TRY(cudaGetLastError());
   return CHEM_OK;
 }
