@@ -8,10 +8,11 @@ namespace chem {
 // Abramowitz & Stegun, Handbook of Mathematical Functions, 7.1.28:
 //   erf(x) = 1 - (1 + a1 x + a2 x^2 + ... + a6 x^6)^-16 for x >= 0 (|error| <= 3e-7), odd in x.
 // With r = (1 + a1 x + ...)^-16 at x = |v| / sqrt 2, GELU(v) = max(v, 0) - |v| r / 2 for either
-// sign; the coefficients below are a_i / sqrt(2)^i, so the polynomial takes |v| directly.  One
-// polynomial, four squarings and one approximate reciprocal (rcp.approx, relative error below
-// 2^-22): GELU is within 5e-7 of the exact value, and the activation is rounded to BF16
-// (relative step 2^-8) right after.
+// sign.  The coefficients below are c a_i / sqrt(2)^i with the constant term c = 2^(1/16): the
+// polynomial takes |v| directly, and its 16th power is 2 (1 + a1 x + ...)^16, so its reciprocal
+// is already r / 2 and the last step is one FMA.  One polynomial, four squarings and one
+// approximate reciprocal (rcp.approx, relative error below 2^-22): GELU is within 5e-7 of the
+// exact value, and the activation is rounded to BF16 (relative step 2^-8) right after.
 __device__ __forceinline__ float rcp_approx(float q) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
@@ -20,17 +21,17 @@ __device__ __forceinline__ float rcp_approx(float q) {
 
 __device__ __forceinline__ float gelu_f(float v) {
   const float x = fabsf(v);
-  float q = fmaf(x, 5.3829750000e-06f, 4.8890635643e-05f);
-  q = fmaf(q, x, 3.8003575000e-05f);
-  q = fmaf(q, x, 3.2776263241e-03f);
-  q = fmaf(q, x, 2.1141006150e-02f);
-  q = fmaf(q, x, 4.9867346967e-02f);
-  q = fmaf(q, x, 1.0f);
+  float q = fmaf(x, 5.6212998061e-06f, 5.1055209042e-05f);
+  q = fmaf(q, x, 3.9686136006e-05f);
+  q = fmaf(q, x, 3.4227392171e-03f);
+  q = fmaf(q, x, 2.2076997906e-02f);
+  q = fmaf(q, x, 5.2075162530e-02f);
+  q = fmaf(q, x, 1.0442737341e+00f);
   q = q * q;
   q = q * q;
   q = q * q;
   q = q * q;                                         // (...)^16; overflow to inf gives r = 0
-  return fmaf(-0.5f * x, rcp_approx(q), fmaxf(v, 0.0f));
+  return fmaf(x, rcp_approx(-q), fmaxf(v, 0.0f));
 }
 
 // Two GELUs at once with the packed FP32 instructions (fma/mul .f32x2: each half rounds exactly
@@ -67,22 +68,21 @@ __device__ __forceinline__ unsigned long long add_x2(unsigned long long a, unsig
 __device__ __forceinline__ void gelu2(float& v0, float& v1) {
   const float x0 = fabsf(v0), x1 = fabsf(v1);
   const unsigned long long x = f32x2(x0, x1);
-  unsigned long long q = fma_x2(x, f32x2(5.3829750000e-06f, 5.3829750000e-06f),
-                                f32x2(4.8890635643e-05f, 4.8890635643e-05f));
-  q = fma_x2(q, x, f32x2(3.8003575000e-05f, 3.8003575000e-05f));
-  q = fma_x2(q, x, f32x2(3.2776263241e-03f, 3.2776263241e-03f));
-  q = fma_x2(q, x, f32x2(2.1141006150e-02f, 2.1141006150e-02f));
-  q = fma_x2(q, x, f32x2(4.9867346967e-02f, 4.9867346967e-02f));
-  q = fma_x2(q, x, f32x2(1.0f, 1.0f));
+  unsigned long long q = fma_x2(x, f32x2(5.6212998061e-06f, 5.6212998061e-06f),
+                                f32x2(5.1055209042e-05f, 5.1055209042e-05f));
+  q = fma_x2(q, x, f32x2(3.9686136006e-05f, 3.9686136006e-05f));
+  q = fma_x2(q, x, f32x2(3.4227392171e-03f, 3.4227392171e-03f));
+  q = fma_x2(q, x, f32x2(2.2076997906e-02f, 2.2076997906e-02f));
+  q = fma_x2(q, x, f32x2(5.2075162530e-02f, 5.2075162530e-02f));
+  q = fma_x2(q, x, f32x2(1.0442737341e+00f, 1.0442737341e+00f));
   q = mul_x2(q, q);
   q = mul_x2(q, q);
   q = mul_x2(q, q);
   q = mul_x2(q, q);                                  // (...)^16
   float q0, q1;
   f32x2_split(q, q0, q1);
-  const unsigned long long r = f32x2(rcp_approx(q0), rcp_approx(q1));
-  const unsigned long long hx = mul_x2(x, f32x2(-0.5f, -0.5f));
-  const unsigned long long out = fma_x2(hx, r, f32x2(fmaxf(v0, 0.0f), fmaxf(v1, 0.0f)));
+  const unsigned long long r = f32x2(rcp_approx(-q0), rcp_approx(-q1));
+  const unsigned long long out = fma_x2(x, r, f32x2(fmaxf(v0, 0.0f), fmaxf(v1, 0.0f)));
   f32x2_split(out, v0, v1);
 }
 
