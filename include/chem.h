@@ -115,9 +115,12 @@ int chem_mechanism_info(chem_mech_t m, int* n_species, int* n_reactions, int* n_
 typedef struct chem_options {
   int32_t max_steps;      /* step attempts per cell before CHEM_CELL_MAX_STEPS; 0 -> 100000 */
   int32_t group_threads;  /* threads per cell: 0 auto (2 if ns+1 <= 16 else 128); 2, 4, 8, 16, 32, 64, 128, 256 */
-  int32_t groups_per_cta; /* 0 auto */
+  int32_t groups_per_cta; /* 0 auto (as many as shared memory holds) */
   int32_t max_ctas;       /* 0 auto (SM count x resident CTAs per SM) */
 } chem_options;
+/* With groups_per_cta and max_ctas both 0, a launch whose cells fill fewer groups than the grid
+ * holds is spread over every SM with fewer groups per CTA.  A cell's result does not depend on
+ * the launch shape (bitwise); it does depend on group_threads (the order of the group's sums). */
 
 /* Advance ncells cells in place over dt.  ld = ncells.  Asynchronous on stream.
  * CHEM_EINVAL if ncells < 0, dt <= 0, rtol <= 0, atol <= 0 or a required pointer is NULL;
