@@ -232,7 +232,8 @@ def run_case(args):
     from synth.mechanism import ch4_mechanism, h2_mechanism
     from synth.states import les_field, load_table
     if args.case == "h2small":
-        print(json.dumps(dict(case=args.case, **extra_h2_small(cg.fp64_fma_peak(), n=args.cells, reps=args.steps))),
+        print(json.dumps(dict(case=args.case, **extra_h2_small(cg.fp64_fma_peak(), n=args.cells, reps=args.steps,
+                                                               group=args.group))),
               flush=True)
         return
     if args.case == "fvm":
@@ -439,10 +440,13 @@ def small_h2_states(n=4096, seed=12345):
     return mech, dm, T, p, Y, failed
 
 
-def extra_h2_small(fp64_peak, n=4096, reps=10):
+def extra_h2_small(fp64_peak, n=4096, reps=10, group=0):
     """Config 0: the small H2 case (4096 cells, dt = 1e-6 s).  Too few cells to fill the GPU (the
-    bench launch holds 80 two-thread groups = 80 cells per SM), so it is latency-bound: reported
-    with the share of the GPU's cell slots the launch can fill."""
+    bench launch holds 80 two-thread groups = 80 cells per SM): the time is the sequential
+    attempts of the stiffest cells, each attempt's FP64 instructions issued by one warp.  Reported
+    with the library's default group (two threads per cell) and, with the default, also with one
+    warp per cell (group_threads = 32, a caller's option: fewer instructions per attempt for each
+    cell, fewer cells per warp)."""
     import torch
     from paper_2312_13513_gb300 import flops as fl
     import paper_2312_13513_gb300 as cg
@@ -451,22 +455,33 @@ def extra_h2_small(fp64_peak, n=4096, reps=10):
     ns_ = torch.zeros(n, dtype=torch.int32, device="cuda"); nr_ = torch.zeros_like(ns_)
     stream = torch.cuda.current_stream()
 
-    def run():
-        T.copy_(T0); Y.copy_(Y0)
-        cg.advance(dm, T, p, Y, 1e-6, RTOL, ATOL, nsub=ns_, nrej=nr_, stream=stream)
+    def timed(g):
+        opts = cg.options(group_threads=g) if g else None
 
-    for _ in range(3):
-        run()
-    ms = sorted(_time_ms(run, stream, reps))
-    t = ms[len(ms) // 2] * 1e-3
+        def run():
+            T.copy_(T0); Y.copy_(Y0)
+            cg.advance(dm, T, p, Y, 1e-6, RTOL, ATOL, nsub=ns_, nrej=nr_, stream=stream, opts=opts)
+
+        for _ in range(3):
+            run()
+        ms = sorted(_time_ms(run, stream, reps))
+        return ms[len(ms) // 2] * 1e-3
+
+    t = timed(group)
     acc = int(ns_.sum()); att = acc + int(nr_.sum())
     _, _, folded = fl.launch_flops(mech, acc, att)
     slots = torch.cuda.get_device_properties(0).multi_processor_count * 80
-    return {"workload": f"FP64 Rodas4, {n} H2/air mixing states (half pre-reacted by this integrator), "
-                        "dt=1e-6 s, two-thread group per cell",
-            "ms": t * 1e3, "cell_updates_per_s": n / t, "attempts_mean": att / n,
-            "fp64_frac_folded": folded / t / 1e12 / fp64_peak,
-            "cell_slot_occupancy": min(n, slots) / slots, "prereact_failed": failed}
+    out = {"workload": f"FP64 Rodas4, {n} H2/air mixing states (half pre-reacted by this integrator), "
+                       "dt=1e-6 s",
+           "group_threads": group or 2, "ms": t * 1e3, "cell_updates_per_s": n / t,
+           "attempts_mean": att / n, "max_attempts": int((ns_ + nr_).max()),
+           "fp64_frac_folded": folded / t / 1e12 / fp64_peak,
+           "cell_slot_occupancy": min(n, slots) / slots, "prereact_failed": failed}
+    if not group:
+        t32 = timed(32)
+        out["warp_per_cell"] = {"group_threads": 32, "ms": t32 * 1e3, "cell_updates_per_s": n / t32,
+                                "fp64_frac_folded": folded / t32 / 1e12 / fp64_peak}
+    return out
 
 
 def extra_surrogate(peaks, steps=3):
