@@ -52,3 +52,30 @@ def with_inert_argon(mech):
     if mech.s0_R is not None:
         m.s0_R = np.append(mech.s0_R, 2.5 * np.log(298.15) + 4.366)
     return m
+
+
+def with_inert_species(mech, k):
+    """The mechanism with k inert species appended, AR_1 .. AR_k made of 1 .. k argon atoms (one
+    more element; molar masses 39.948 i, so no two columns of the Jacobian coincide), each with
+    argon's monatomic NASA-7 polynomial and third-body efficiency 1.  CH4 with 11 of them has
+    N = 65 unknowns, beyond the 64 rows of the register-held triangular solves and the panel LU,
+    so the shared-memory LU and sweeps run."""
+    m = mech.copy()
+    m.name = f"{mech.name}+{k}inert"
+    m.elements = list(mech.elements) + ["AR"]
+    m.elem_mass = np.append(mech.elem_mass, 39.948)
+    comp = np.zeros((mech.ns + k, mech.ne + 1), mech.comp.dtype)
+    comp[:mech.ns, :mech.ne] = mech.comp
+    comp[mech.ns:, mech.ne] = np.arange(1, k + 1)
+    m.comp = comp
+    m.species = list(mech.species) + [f"AR_{i}" for i in range(1, k + 1)]
+    m.W = np.append(mech.W, 39.948 * np.arange(1, k + 1))
+    ar = np.array([2.5, 0.0, 0.0, 0.0, 0.0, -2.5 * 298.15, 4.366])
+    m.nasa_lo = np.vstack([mech.nasa_lo] + [ar] * k)
+    m.nasa_hi = np.vstack([mech.nasa_hi] + [ar] * k)
+    m.eff = np.hstack([mech.eff, np.ones((mech.nr, k))])
+    if mech.hf_R is not None:
+        m.hf_R = np.append(mech.hf_R, np.zeros(k))
+    if mech.s0_R is not None:
+        m.s0_R = np.append(mech.s0_R, np.full(k, 2.5 * np.log(298.15) + 4.366))
+    return m
