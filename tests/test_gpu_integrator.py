@@ -94,8 +94,10 @@ def test_parity_ch4_les_subset(om_ch4, ch4, dm_ch4):
     assert out <= 3
 
 
-@pytest.mark.parametrize("G", [4, 8, 16, 32])
+@pytest.mark.parametrize("G", [4, 8, 16, 32, 64, 128])
 def test_parity_h2_other_group_sizes(om_h2, h2, dm_h2, G):
+    """Sub-warp, warp and multi-warp groups on the H2 mechanism (N = 10): the multi-warp groups
+    run the panel LU and the register-held sweeps with fewer than 32 rows."""
     T, p, Y = prereacted_mixing_states(om_h2, h2, 301, 17)
     Tg, Yg, st, _, _ = _run(dm_h2, T, p, Y, 1e-6, opts=cg.options(group_threads=G))
     assert np.all(st == 0)
