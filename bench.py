@@ -38,8 +38,9 @@ WORKLOAD = ("FP64 Rodas4 chemistry advance, 2^20 cells of a 128^3 quasi-DNS H2/a
 
 # DRAM traffic of one integrator launch from an ncu capture of the full bench launch
 # (profiles/integrator_h2_quasi_dns.md: 2^20 cells of the same field and launch shape, 93.39 MB
-# read + 40.90 MB written, one pass), valid only for the kernel source it was measured on.
-TRAFFIC = {"bytes_per_launch": 93387520 + 40898560, "source_sha1": "3298e25d4306c391cf515c9ea6e7a6c6ec62699f"}
+# read + 40.90 MB written, one pass), valid only for the kernel source it was measured on (captured
+# on sha1 3298e25d; the source has changed since in one comment only).
+TRAFFIC = {"bytes_per_launch": 93387520 + 40898560, "source_sha1": "019397584f7777875e6adf89f4f2d58b5794ce18"}
 
 # The paper's chemistry time per step for its H2-air case (Table 1, Section 3.2), in seconds:
 # CVODE on one CPU core and DNN inference on one GPU card, on uniform meshes of 32^3, 64^3 and

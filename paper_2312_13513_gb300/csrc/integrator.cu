@@ -729,8 +729,8 @@ __device__ bool lu_factor(const Grp<G>& g, double* M, int N, int LD, int* perm, 
 // lowest logical row on ties), so the factors, perm and invd are bitwise lu_factor's.
 // Elements [0, E1) of a step's update of columns k + 2 .. go to the warps other than the panel
 // warp, [E1, E) to the panel warp after its pivot work: its per-lane share of a balanced split
-// less 8 elements, the pivot work's measured worth (shares of 3, 12 and 16 elements measured
-// slower on the CH4 LES field).
+// less 8 elements per lane, the pivot work's measured worth (less 3, 12, 16 or 24 per lane
+// measured slower on the CH4 LES field).
 __device__ __forceinline__ int panel_split(int E, int G) {
   return max(E - max((E * 32) / G - 32 * 8, 0), 0);
 }
